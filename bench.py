@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark of the region-adaptive DP pixelization hot path on B300.
+
+Workload (one step): a clip of 64 frames of 1920x1080 RGB u8 (moving-rectangle generator), four
+local-variance classes on 32x32 tiles with grids {32, 16, 8, 4} and budgets {2, 1, 0.5, 0.25}, m = 16:
+classify + exact cell sums + Laplace noise + clip + compact record (dp_pix_release), then the
+pixelized frames rebuilt from the records (dp_pix_reconstruct).  Inputs (398 MB per step) are larger than
+the 126 MB L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is whole-job Mpx/s (frames * M * N over all ranks / max-over-ranks time) with
+inputs resident in HBM; `e2e` is the same metric through the C ABI with host buffers (pinned host -> device
+copy of the frames, release, reconstruct, device -> host copy of the records, every step).  The reference
+arm is the CPU oracle (a deliberately plain program) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "megapixels/sec released (1 B300) and % HBM roofline; p50/p99 frame latency"
+F, M, N, C = 64, 1080, 1920, 3
+GRIDS, EPS, MVAR, SEED = [32, 16, 8, 4], [2.0, 1.0, 0.5, 0.25], 16.0, 2
+WORKLOAD = "clip64_1920x1080_rgb_u8_var4"
+
+
+def set_frames(n):
+    global F, WORKLOAD
+    F = n
+    WORKLOAD = "clip%d_1920x1080_rgb_u8_var4" % n
+
+
+def config(extra=None):
+    c = {"workload": WORKLOAD, "frames": F, "M": M, "N": N, "C": C, "grids": GRIDS, "eps": EPS, "m": MVAR,
+         "region_source": "variance quantiles on 32x32 tiles", "record": "f32 means + u8 tile map",
+         "step": "dp_pix_release + dp_pix_reconstruct of all frames",
+         "l2": "inputs larger than L2 (%.0f MB of frames read and written per step)" % (F * M * N * C / 1e6),
+         "generator_seed": 1002,
+         "philox_seed": SEED}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------------
+# clocks during the timed region (NVML, sampled from a thread)
+# ------------------------------------------------------------------------------------------------------
+REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+           0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+           0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    def __init__(self, device_index=0, period=0.002):
+        self.samples, self.reasons, self.ok, self.period = [], set(), False, period
+        self.max_mhz = None
+        try:
+            import pynvml as nv
+            import torch
+            nv.nvmlInit()
+            h = None
+            try:
+                uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+                h = nv.nvmlDeviceGetHandleByUUID(("GPU-" + uuid) if not uuid.startswith("GPU-") else uuid)
+            except Exception:
+                vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+                idx = int(vis.split(",")[device_index]) if vis and vis.split(",")[0].isdigit() else device_index
+                h = nv.nvmlDeviceGetHandleByIndex(idx)
+            self.nv, self.h = nv, h
+            self.max_mhz = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+            self.ok = True
+        except Exception as e:  # no NVML: report what is known
+            self.err = repr(e)
+
+    def _reasons(self):
+        nv = self.nv
+        fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        return fn(self.h)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                self.samples.append(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM))
+                r = self._reasons()
+                for bit, name in REASONS.items():
+                    if r & bit:
+                        self.reasons.add(name)
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def start(self):
+        if not self.ok:
+            return
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+
+    def stop(self):
+        if not self.ok:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "NVML unavailable"}
+        self._stop.set()
+        self._t.join()
+        s = self.samples
+        return {"sm_mhz": statistics.median(s) if s else None, "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons - {"gpu_idle"}), "samples": len(s)}
+
+
+# ------------------------------------------------------------------------------------------------------
+# distributed helpers (one process per GPU; the frames of different ranks are independent clips)
+# ------------------------------------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------------------
+# algorithmic bytes per launch of each kernel on this workload
+# ------------------------------------------------------------------------------------------------------
+def algorithmic_bytes(plan, payload_bytes):
+    frame_bytes = F * M * N * C
+    ntiles = plan.GR * plan.GC
+    g = 4
+    gsum_tile = ((plan.T // g) ** 2 * C + 7) // 8 * 8 * 2
+    return {
+        # frames read once; g-cell sums and rank keys written
+        "k_tile_stats_gsum": frame_bytes + F * ntiles * (gsum_tile + 8),
+        # g-cell sums and offsets read; record payload written
+        "k_emit": F * ntiles * (gsum_tile + 4 + 1) + payload_bytes,
+        # frames written; record payload and maps read
+        "k_reconstruct_u8": frame_bytes + payload_bytes + F * ntiles,
+        # keys read; map, offsets, index and header written
+        "k_rank": F * ntiles * (8 + 1 + 4) + F * (512 + plan.GR * 16),
+    }
+
+
+def traffic_from_profile(kernel):
+    """dram bytes per launch from the committed ncu summary of this kernel on this workload, if the kernel
+    source has not changed since the capture (the summary records the source's sha256)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, WORKLOAD))
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    src = vals.get("source_file")
+    sha = vals.get("source_sha256")
+    tr = vals.get("dram_bytes_per_launch_full_workload")
+    if not (src and sha and tr):
+        return None
+    try:
+        cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return int(float(tr)) if cur == sha else None
+
+
+# ------------------------------------------------------------------------------------------------------
+# the CPU oracle on a bounded sample (reference arm and cpu_baseline)
+# ------------------------------------------------------------------------------------------------------
+def oracle_time(clip, n_frames, budget_s=None):
+    import oracle as O
+    kw = dict(M=M, N=N, C=C, grids=GRIDS, eps=EPS, source=O.SRC_VARIANCE, dtype=O.DT_F32, seed=SEED, m=MVAR)
+    t0 = time.perf_counter()
+    done = 0
+    for i in range(n_frames):
+        rec, *_ = O.release(clip[i % len(clip)], None, frame_idx=i, **kw)
+        O.reconstruct(rec, 0)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt
+
+
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    from paper_2511_04261_b300 import synth
+    per_step = 2
+    clip = synth.moving_rect_clip(seed=1002, frames=per_step, M=M, N=N)
+    for _ in range(args.warmup):
+        oracle_time(clip, per_step)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_time(clip, per_step)
+        times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = per_step * M * N / 1e6 / (ms / 1e3)
+    sample = "%d of the %d frames per step (oracle release + reconstruct, 1 thread)" % (per_step, F)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": config({"reference": "CPU oracle (plain C, fp64), not a GPU program"}),
+            "cpu_baseline": {"value": value, "unit": "Mpx/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Mpx/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_2511_04261_b300 as P
+    from paper_2511_04261_b300 import build, synth
+    build.build()
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    clip = synth.moving_rect_clip(seed=1002 + rank, frames=F, M=M, N=N)
+    plan = P.Plan(M=M, N=N, C=C, grids=GRIDS, eps=EPS, m=MVAR, source=P.SRC_VARIANCE, dtype=P.REC_F32, seed=SEED)
+    frames = torch.from_numpy(clip).to(dev)
+    records = plan.alloc_records(F, device=dev)
+    ws = plan.alloc_workspace(F, device=dev)
+    out = torch.empty((F, M, N, C), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(fr, frame_idx0):
+        plan.release(fr, None, stream_id=rank, frame_idx0=frame_idx0, records=records, ws=ws)
+        P.dp_pix_reconstruct(records, M, N, C, P.OUT_U8, out=out)
+
+    for w in range(args.warmup):
+        step(frames, w * F)
+    torch.cuda.synchronize()
+    P.dp_pix_status()
+
+    # ---- device-resident timed region ----
+    sampler = ClockSampler(torch.cuda.current_device())
+    barrier(world)
+    torch.cuda.synchronize()
+    P.prof_reset()
+    P.prof_enable(True)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(frames, (args.warmup + k) * F)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    prof = P.prof_read()
+    P.prof_enable(False)
+    P.dp_pix_status()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms, world)
+    value = world * F * M * N / 1e6 / (ms_max / 1e3)
+    launches = sum(v[0] for v in prof.values())
+
+    # ---- roofline of the dominant kernel (its own launch durations, from events on its stream) ----
+    hbm, peak_kind = measured_peaks()
+    hdrs = [P.record_header(P.dp_pix_store(records[i])) for i in range(F)]
+    payload = sum(h["total_bytes"] - h["payload_offset"] for h in hdrs)
+    algo = algorithmic_bytes(plan, payload)
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_launches, dom_ms) = dom[0], dom[1]
+    per_launch_ms = dom_ms / max(1, dom_launches)
+    ab = algo.get(dom_name)
+    achieved = ab / (per_launch_ms / 1e3) / 1e9 if ab else None
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "traffic": traffic_from_profile(dom_name),
+                "algorithmic_bytes_per_launch": ab, "avg_launch_ms": per_launch_ms,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else
+                "fallback 6.4 TB/s",
+                "kernels": {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / max(1e-9, sum(x[1] for x in prof.values())),
+                                "algorithmic_GBps": (algo[k] / (v[1] / max(1, v[0]) / 1e3) / 1e9) if k in algo and v[1] > 0 else None}
+                            for k, v in prof.items()}}
+
+    # ---- single-frame latency (release + reconstruct of one device-resident frame) ----
+    lat = []
+    rec1 = plan.alloc_records(1, device=dev)
+    ws1 = plan.alloc_workspace(1, device=dev)
+    out1 = out[:1]
+    for i in range(60):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.release(frames[i % F], None, stream_id=rank, frame_idx0=10**6 + i, records=rec1, ws=ws1)
+        P.dp_pix_reconstruct(rec1, M, N, C, P.OUT_U8, out=out1)
+        b.record(stream)
+        b.synchronize()
+        if i >= 10:
+            lat.append(a.elapsed_time(b))
+    latency = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "what": "one 1920x1080 frame, release + reconstruct, device-resident, 50 reps"}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, P, torch, plan, clip, frames, records, step, world)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        done, dt = oracle_time(clip, F, budget_s=args.cpu_budget)
+        cpu = {"value": done * M * N / 1e6 / dt, "unit": "Mpx/s", "cores": 1, "kind": "oracle",
+               "sample": "%d frames of the clip (oracle release + reconstruct, 1 thread, %.1f s)" % (done, dt)}
+    return finish(args, rank, world, value, ms_max, roofline, cpu, e2e, clocks, launches, latency)
+
+
+def run_e2e(args, P, torch, plan, clip, frames, records, step, world):
+    host_frames = torch.from_numpy(clip).pin_memory()
+    host_recs = torch.empty((F, plan.record_stride()), dtype=torch.uint8).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step(k):
+        frames.copy_(host_frames, non_blocking=True)
+        step(frames, 10**7 + k * F)
+        return P.dp_pix_store_batch(records, host_recs)
+
+    e2e_step(0)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    written = []
+    for k in range(e2e_steps):
+        written = e2e_step(k + 1)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / e2e_steps, world)
+    return {"value": world * F * M * N / 1e6 / (e2e_ms / 1e3), "unit": "Mpx/s", "ms_per_step": e2e_ms,
+            "h2d_bytes_per_step": F * M * N * C, "d2h_bytes_per_step": int(sum(written)) + F * 512,
+            "path": "pinned host frames -> device copy, dp_pix_release, dp_pix_reconstruct, dp_pix_store_batch"}
+
+
+def finish(args, rank, world, value, ms_max, roofline, cpu, e2e, clocks, launches, latency):
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+                "config": config({"parallelism": "replicas: one clip per GPU, no collective" if world > 1 else "1 GPU",
+                                  "arith": "u8 samples, exact u32 cell sums, f32 noise/mean"}),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+                "latency": latency}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--frames", type=int, default=64, help="frames per step (64 = the benchmark workload)")
+    args = ap.parse_args()
+    set_frames(args.frames)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

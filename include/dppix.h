@@ -1,0 +1,240 @@
+/*
+ * dppix.h -- C ABI of libdppix: region-adaptive differentially private pixelization on NVIDIA B300.
+ *
+ * The calls follow the paper's statement of the problem (Alg. 3 inputs: image I, grid sizes, privacy
+ * budget eps, max variation m, region mask; outputs: the compact noisy-statistics record of Table 3 and
+ * the restored image I').  A frame is M x N pixels of C interleaved uint8 samples (C = 1..4).  The frame
+ * is split into K <= 8 regions; region r gets grid side b_r and budget eps_r, and every b_r x b_r cell of
+ * it is released as clip(mean + Laplace(0, sigma_r), 0, R) with sigma_r = R*m / (b_r^2 eps_r) (Eq. 12,
+ * Eq. 8).  Regions live on square tiles of side T = lcm{b_r}; each tile belongs to one region (the
+ * paper's b x b grid with its subgrids, Eq. 14).
+ *
+ * Conventions shared by every call:
+ *  - Every pointer named d_* is a device pointer owned by the caller; the library never allocates device
+ *    memory on these paths.  Host pointers are named h_* or documented as host.
+ *  - Calls are asynchronous on `cuda_stream` (a cudaStream_t, NULL = legacy default stream) unless the
+ *    comment says they synchronize.
+ *  - Every call returns DP_PIX_OK (0) or a negative DP_PIX_E_* code and never throws or aborts.  The
+ *    thread-local message of the last failure is returned by dp_pix_last_error().
+ *  - A plan is immutable after dp_pix_plan(); it may be used from several host threads and streams at
+ *    once.  Calls that share a workspace or output buffer must be ordered by the caller.
+ *  - No CPU fallback exists: without a usable CUDA device the compute calls return DP_PIX_E_CUDA.
+ */
+#ifndef DPPIX_H
+#define DPPIX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DPPIX_API __attribute__((visibility("default")))
+#else
+#define DPPIX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DP_PIX_MAX_REGIONS 8
+#define DP_PIX_RECORD_HEADER_BYTES 512
+
+/* ---- return codes ---------------------------------------------------------------------------------- */
+#define DP_PIX_OK 0
+#define DP_PIX_E_INVALID_ARG (-1)      /* a null pointer, a size or a field out of its documented range */
+#define DP_PIX_E_UNSUPPORTED (-2)      /* valid but beyond this library's limits (e.g. T > 128) */
+#define DP_PIX_E_PAD_TOO_LARGE (-3)    /* mirror padding would reach past the opposite edge */
+#define DP_PIX_E_BUFFER_TOO_SMALL (-4) /* record, workspace or destination capacity too small */
+#define DP_PIX_E_BAD_RECORD (-5)       /* record header malformed */
+#define DP_PIX_E_CUDA (-6)             /* a CUDA runtime call failed (message has the CUDA error) */
+#define DP_PIX_E_TIMEOUT (-7)          /* a bounded device-side wait gave up */
+#define DP_PIX_E_DEVICE (-8)           /* a device-side check failed (see dp_pix_status) */
+
+/* ---- enumerations ------------------------------------------------------------------------------------ */
+/* Mirror padding of the last tile row/column (Alg. 2 step 4, Alg. 3 step 3).  reflect: the edge sample is
+ * not repeated (numpy "reflect"); symmetric: it is (numpy "symmetric"). */
+#define DP_PIX_PAD_REFLECT 0
+#define DP_PIX_PAD_SYMMETRIC 1
+
+/* Where the tile -> region map comes from (Alg. 3 steps 5-6 and their generalisations).
+ *  TILE_LABELS: caller passes u8 labels [G_R][G_C] (values < K), copied into the record.
+ *  MASK_U8:     K = 2.  Caller passes the paper's simple-region mask (u8, nonzero = simple) of M x N.
+ *               A tile is simple (region 0) iff more than half of its T*T mirror-padded mask samples are
+ *               simple (mask mean > 1/2), else complex (region 1); a tie goes to complex.
+ *  MATTE_F32:   K = 2.  Caller passes an f32 alpha matte of M x N; a pixel is complex iff
+ *               alpha >= matte_threshold; then as MASK_U8.
+ *  VARIANCE:    K classes by local variance: per tile S = sum x and Q = sum x^2 over the C*T*T padded
+ *               samples, key = n*Q - S^2 (n = C*T*T), tiles ranked ascending by (key, tile index) within the
+ *               frame, class q = floor(K * rank / #tiles) -> region q (region 0 = lowest variance). */
+#define DP_PIX_SRC_TILE_LABELS 0
+#define DP_PIX_SRC_MASK_U8 1
+#define DP_PIX_SRC_MATTE_F32 2
+#define DP_PIX_SRC_VARIANCE 3
+
+/* Record payload element type: clipped noisy means as f32 or as u8 (round half to even of the f32
+ * value), or the exact u32 cell sums (diagnostic: no noise, for integer parity checks). */
+#define DP_PIX_REC_F32 0
+#define DP_PIX_REC_U8 1
+#define DP_PIX_REC_SUM_U32 2
+
+/* Reconstructed image element type: u8 (round half to even) or f32, C interleaved samples per pixel. */
+#define DP_PIX_OUT_U8 0
+#define DP_PIX_OUT_F32 1
+
+/* ---- problem description ------------------------------------------------------------------------------ */
+typedef struct dp_pix_desc {
+    int32_t M, N, C;              /* frame rows, columns, interleaved channels (1..4) */
+    int32_t K;                    /* number of regions, 1..8 */
+    int64_t row_pitch;            /* bytes between consecutive frame rows, >= N*C */
+    int32_t grid[DP_PIX_MAX_REGIONS]; /* b_r, 1..64; T = lcm{b_r} <= 128 and T*T*C <= 49152 */
+    double eps[DP_PIX_MAX_REGIONS];   /* eps_r > 0 (ignored when noise_free) */
+    double value_range;           /* R: samples lie in [0, R]; 255 for u8 frames */
+    double m;                     /* max number of samples two neighbouring frames differ in (> 0) */
+    int32_t pad_mode;             /* DP_PIX_PAD_* */
+    int32_t region_source;        /* DP_PIX_SRC_* */
+    float matte_threshold;        /* MATTE_F32 only */
+    int32_t record_dtype;         /* DP_PIX_REC_* */
+    int32_t noise_free;           /* 1: eta = 0 (the eps -> infinity limit; testing only) */
+    int32_t reserved0;
+    uint64_t seed;                /* Philox key: (seed mod 2^32, seed >> 32) */
+} dp_pix_desc;
+
+typedef struct dp_pix_sizes {
+    uint64_t record_bytes;        /* capacity one frame's record buffer must have (worst case) */
+    uint64_t workspace_per_frame; /* workspace bytes needed per frame of a dp_pix_release call */
+    uint64_t workspace_fixed;     /* plus this many bytes per call */
+    uint32_t T, GR, GC, PR, PC;   /* tile side, tile rows/cols, padded rows/cols (Alg. 3 steps 1-2) */
+    uint32_t num_tiles;           /* GR * GC */
+    uint64_t max_values;          /* max payload elements of one record */
+    double sigma[DP_PIX_MAX_REGIONS]; /* Laplace scale of each region */
+} dp_pix_sizes;
+
+/* The 512-byte record header, little-endian, at the start of every record (Table 3 generalised).
+ * The tile-row index, map and payload follow at the offsets it gives. */
+typedef struct dp_pix_record_header {
+    char magic[4];                /* "DPPX" */
+    uint32_t version;             /* 1 */
+    uint32_t header_bytes;        /* 512 */
+    uint32_t flags;               /* bit 0: noise-free release */
+    uint32_t M, N, C, T, K, GR, GC;
+    uint32_t pad_mode, record_dtype, region_source, stream_id, reserved0;
+    uint64_t seed, frame_idx;
+    double value_range, m;
+    uint64_t total_bytes;         /* bytes in use (multiple of 16): what dp_pix_store copies */
+    uint64_t map_offset;          /* u8 map [GR][GC] */
+    uint32_t grid[DP_PIX_MAX_REGIONS];
+    double eps[DP_PIX_MAX_REGIONS];
+    double sigma[DP_PIX_MAX_REGIONS];
+    uint32_t count[DP_PIX_MAX_REGIONS];          /* tiles of region r */
+    uint64_t region_offset[DP_PIX_MAX_REGIONS];  /* byte offset of region r's payload */
+    uint64_t rowidx_offset;       /* u32 [GR][K]: region-r tiles in tile rows above */
+    uint64_t payload_offset;      /* start of region 0's payload */
+    uint8_t reserved[128];
+} dp_pix_record_header;
+
+typedef struct dp_pix_plan_s *dp_pix_plan_t;
+
+/* Validates `d`, derives the geometry and sizes (Alg. 2 steps 1-3, Alg. 3 steps 1-2) and returns an
+ * immutable plan.  Host only: no CUDA call.  `sz` may be NULL.  Errors: INVALID_ARG, UNSUPPORTED (b_r > 64,
+ * T > 128, T*T*C > 49152, more than 200000 tiles per frame; VARIANCE: more than 16384 tiles or T*C not a
+ * multiple of 4), PAD_TOO_LARGE (reflect needs P_R <= M-1 and P_C <= N-1; symmetric P_R <= M, P_C <= N). */
+DPPIX_API int dp_pix_plan(const dp_pix_desc *d, dp_pix_plan_t *out, dp_pix_sizes *sz);
+
+/* Frees a plan (host only).  NULL is allowed. */
+DPPIX_API int dp_pix_plan_destroy(dp_pix_plan_t plan);
+
+/*
+ * Releases n_frames frames (Alg. 3, generalised to K regions): classifies tiles, reduces every cell of
+ * its tile's grid to an exact integer sum, adds Laplace noise drawn from Philox4x32-10 with
+ * key (seed mod 2^32, seed >> 32) and counter (cell index in the frame's padded b_r-grid,
+ * r | stream_id << 8, frame mod 2^32, frame >> 32) -- word ch for channel ch, inverse-CDF sampler
+ * eta = +-sigma_r * ln((k + 1/2) / 2^31) -- clips to [0, R] and writes one self-describing record per
+ * frame (Table 3 generalised).
+ *   d_frames:         frame i starts at d_frames + i*frame_stride (bytes); rows are row_pitch apart.
+ *   d_region_src:     per the plan's region_source: u8 labels [G_R][G_C] (src_pitch ignored, frames
+ *                     src_frame_stride apart), u8 mask / f32 matte rows src_pitch bytes apart, or NULL
+ *                     for VARIANCE.
+ *   stream_id:        < 2^24; frame i uses frame index frame_idx0 + i.
+ *   d_records:        record i at d_records + i*record_stride; record_stride >= sizes.record_bytes and a
+ *                     multiple of 16; d_records 16-byte aligned.
+ *   d_ws / ws_bytes:  workspace of >= workspace_fixed + n_frames * workspace_per_frame bytes, 256-byte
+ *                     aligned; its contents need not be initialised and are scratch after the call.
+ * Record layout (little-endian): 512-byte header, then u32 tile-row index [G_R][K] (number of region-r
+ * tiles above each tile row), then the u8 region map [G_R][G_C], then region-major payload: region r's
+ * tiles in row-major tile order, each tile's (T/b_r)^2 cells row-major, C channel values per cell; each
+ * section starts on a 16-byte boundary.  Header fields are those of dp_pix_record_header above.
+ */
+DPPIX_API int dp_pix_release(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride, const void *d_region_src,
+                   int64_t src_pitch, int64_t src_frame_stride, uint32_t n_frames, uint32_t stream_id,
+                   uint64_t frame_idx0, void *d_records, int64_t record_stride, void *d_ws, uint64_t ws_bytes,
+                   void *cuda_stream);
+
+/*
+ * Copies one record's used bytes (header total_bytes, <= capacity) from device memory to `dst` (host if
+ * dst_is_host, else device) and writes that count to *written.  Synchronizes on cuda_stream to read the
+ * header.  Errors: BAD_RECORD, BUFFER_TOO_SMALL (cap < total_bytes), CUDA.
+ */
+DPPIX_API int dp_pix_store(const void *d_record, void *dst, uint64_t cap, uint64_t *written, int dst_is_host,
+                 void *cuda_stream);
+
+/*
+ * Batched dp_pix_store for n records d_records + i*record_stride (device) into host memory
+ * h_dst + i*dst_stride (pinned memory makes the copies asynchronous to the host until the final sync):
+ * one strided device->host read of the n headers, then one copy of each record's used bytes.  written[i]
+ * (host array, may be NULL) receives record i's size.  Synchronizes on cuda_stream.  Errors: BAD_RECORD,
+ * BUFFER_TOO_SMALL (a record larger than dst_stride), CUDA.
+ */
+DPPIX_API int dp_pix_store_batch(const void *d_records, int64_t record_stride, uint32_t n, void *h_dst,
+                                 int64_t dst_stride, uint64_t *written, void *cuda_stream);
+
+/*
+ * Rebuilds the pixelized frames from their records alone (Sec. V-E: the stored metadata suffice;
+ * Alg. 2 steps 10-11): every pixel of a cell takes the cell's stored value; the padding is cropped.
+ * Geometry is read from each record's header on the device, so no plan and no host sync are needed.
+ *   d_records:   n_records records, record_stride bytes apart (>= 512, multiple of 16); record_stride is
+ *                also each record's capacity: a header whose sections reach past it is rejected.
+ *   d_out:       image i at d_out + i*out_frame_stride; rows out_pitch bytes apart; out_type DP_PIX_OUT_*.
+ *   max_M, max_N, max_C: caller's bound on the records' geometry (checked on the device; a record beyond
+ *                it, or a malformed one, is skipped and flags DP_PIX_E_DEVICE in the status word).
+ */
+DPPIX_API int dp_pix_reconstruct(const void *d_records, int64_t record_stride, uint32_t n_records, void *d_out,
+                       int64_t out_frame_stride, int64_t out_pitch, int out_type, int32_t max_M, int32_t max_N,
+                       int32_t max_C, void *cuda_stream);
+
+/*
+ * Diagnostic: for i < n, runs Philox4x32-10 on counter h_ctr-style d_ctr[4i..4i+3] and key (seed mod 2^32,
+ * seed >> 32), writes the four words to d_words[4i..] (may be NULL) and the Laplace(0, sigma) draws of
+ * the four words to d_eta[4i..] (may be NULL) with the release path's sampler.
+ */
+DPPIX_API int dp_pix_debug_noise(uint64_t seed, const uint32_t *d_ctr, uint64_t n, uint32_t *d_words, float *d_eta,
+                       float sigma, void *cuda_stream);
+
+/* Synchronizes cuda_stream and returns DP_PIX_OK, or the first device-side error code recorded since the
+ * last call (then clears it).  *detail (may be NULL) receives a kernel-specific detail word. */
+DPPIX_API int dp_pix_status(void *cuda_stream, uint32_t *detail);
+
+/* Thread-local, NUL-terminated message of the last failed call on this thread ("" if none). */
+DPPIX_API const char *dp_pix_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+DPPIX_API int dp_pix_version(void);
+
+/* ---- launch accounting ------------------------------------------------------------------------------- */
+/* Every kernel launch the library makes is counted per kernel name.  With timing enabled (1) each
+ * launch is bracketed by CUDA events on its stream and the elapsed times are summed when
+ * dp_pix_prof_read() is called (which synchronizes those events).  Host-side bookkeeping only. */
+typedef struct dp_pix_prof_entry {
+    char name[48];
+    uint64_t launches;
+    double total_ms;              /* only while timing was enabled */
+} dp_pix_prof_entry;
+
+DPPIX_API int dp_pix_prof_enable(int timing);
+/* Fills up to `cap` entries, returns the number of distinct kernels (>= 0) or a negative error. */
+DPPIX_API int dp_pix_prof_read(dp_pix_prof_entry *out, int cap);
+DPPIX_API int dp_pix_prof_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPPIX_H */

@@ -1,0 +1,13 @@
+"""B300-native region-adaptive differentially private pixelization (arxiv 2511.04261).
+
+The compute path is libdppix.so (hand-written CUDA for sm_103a behind the C ABI of include/dppix.h);
+this package is its Python binding.  The library is loaded on first use and there is no fallback: a
+missing or unloadable library raises.
+"""
+from . import _lib
+from ._lib import (DppixError, OUT_F32, OUT_U8, PAD_REFLECT, PAD_SYMMETRIC, REC_F32, REC_SUM_U32, REC_U8,
+                   SRC_MASK_U8, SRC_MATTE_F32, SRC_TILE_LABELS, SRC_VARIANCE)
+from .api import (Plan, dp_pix_debug_noise, dp_pix_plan, dp_pix_reconstruct, dp_pix_release, dp_pix_status,
+                  dp_pix_store, dp_pix_store_batch, prof_enable, prof_read, prof_reset, record_header)
+
+__version__ = "0.1.0"

@@ -1,0 +1,531 @@
+// api.cu -- the C ABI of libdppix (see include/dppix.h): plans, release orchestration, store,
+// reconstruction, status, and launch accounting.
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+static_assert(sizeof(dp_pix_record_header) == DP_PIX_RECORD_HEADER_BYTES, "record header must be 512 bytes");
+static_assert(offsetof(dp_pix_record_header, total_bytes) == 96, "record header layout");
+static_assert(offsetof(dp_pix_record_header, grid) == 112, "record header layout");
+static_assert(offsetof(dp_pix_record_header, eps) == 144, "record header layout");
+static_assert(offsetof(dp_pix_record_header, sigma) == 208, "record header layout");
+static_assert(offsetof(dp_pix_record_header, count) == 272, "record header layout");
+static_assert(offsetof(dp_pix_record_header, region_offset) == 304, "record header layout");
+static_assert(offsetof(dp_pix_record_header, payload_offset) == 376, "record header layout");
+
+struct dp_pix_plan_s {
+    dppix::Geom g;
+};
+
+// Device status word of the library: [0] first error code, [1] detail.
+__device__ int32_t g_dppix_status[2];
+
+namespace dppix {
+namespace {
+
+thread_local char t_err[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(DP_PIX_E_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+uint64_t a16(uint64_t x) { return (x + 15ull) & ~15ull; }
+uint64_t a256(uint64_t x) { return (x + 255ull) & ~255ull; }
+int64_t gcd64(int64_t a, int64_t b) {
+    while (b) {
+        const int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+int bits_for(unsigned __int128 v) {
+    int b = 0;
+    while (v) {
+        ++b;
+        v >>= 1;
+    }
+    return b;
+}
+
+// ---- launch accounting -------------------------------------------------------------------------------
+struct ProfEntry {
+    uint64_t launches = 0;
+    double total_ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+std::mutex g_prof_mu;
+std::map<std::string, ProfEntry> g_prof;
+bool g_prof_timing = false;
+
+}  // namespace
+
+void prof_begin(const char *name, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfEntry &e = g_prof[name];
+    e.launches++;
+    if (g_prof_timing) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) {
+            cudaEventRecord(a, s);
+            e.pending.emplace_back(a, b);
+        }
+    }
+}
+
+void prof_end(const char *name, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_timing) return;
+    ProfEntry &e = g_prof[name];
+    if (!e.pending.empty()) cudaEventRecord(e.pending.back().second, s);
+}
+
+int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (cached[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
+}
+
+int32_t *status_word() {
+    static int32_t *cached[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!cached[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_dppix_status) != cudaSuccess) return nullptr;
+        cached[dev] = static_cast<int32_t *>(p);
+    }
+    return cached[dev];
+}
+
+namespace {
+
+int make_geom(const dp_pix_desc *d, Geom &g) {
+    memset(&g, 0, sizeof(g));
+    if (!d) return fail(DP_PIX_E_INVALID_ARG, "desc is NULL");
+    if (d->M < 1 || d->N < 1) return fail(DP_PIX_E_INVALID_ARG, "M and N must be >= 1");
+    if (d->C < 1 || d->C > 4) return fail(DP_PIX_E_INVALID_ARG, "C must be in 1..4");
+    if (d->K < 1 || d->K > kMaxK) return fail(DP_PIX_E_INVALID_ARG, "K must be in 1..8");
+    if (d->row_pitch < (int64_t)d->N * d->C) return fail(DP_PIX_E_INVALID_ARG, "row_pitch < N*C");
+    if (!(d->value_range > 0) || !(d->m > 0)) return fail(DP_PIX_E_INVALID_ARG, "value_range and m must be > 0");
+    if (d->pad_mode != DP_PIX_PAD_REFLECT && d->pad_mode != DP_PIX_PAD_SYMMETRIC)
+        return fail(DP_PIX_E_INVALID_ARG, "bad pad_mode");
+    if (d->region_source < 0 || d->region_source > 3) return fail(DP_PIX_E_INVALID_ARG, "bad region_source");
+    if (d->record_dtype < 0 || d->record_dtype > 2) return fail(DP_PIX_E_INVALID_ARG, "bad record_dtype");
+    if ((d->region_source == DP_PIX_SRC_MASK_U8 || d->region_source == DP_PIX_SRC_MATTE_F32) && d->K != 2)
+        return fail(DP_PIX_E_INVALID_ARG, "mask and matte sources need K == 2");
+    if (d->value_range > 255.0) return fail(DP_PIX_E_UNSUPPORTED, "u8 frames need value_range <= 255");
+    int64_t T = 1;
+    int64_t gg = 0;
+    int bmin = 1 << 30;
+    for (int r = 0; r < d->K; ++r) {
+        const int b = d->grid[r];
+        if (b < 1) return fail(DP_PIX_E_INVALID_ARG, "grid[%d] must be >= 1", r);
+        if (b > 64) return fail(DP_PIX_E_UNSUPPORTED, "grid[%d] = %d > 64", r, b);
+        if (!d->noise_free && !(d->eps[r] > 0)) return fail(DP_PIX_E_INVALID_ARG, "eps[%d] must be > 0", r);
+        T = T / gcd64(T, b) * b;
+        if (T > kMaxT) return fail(DP_PIX_E_UNSUPPORTED, "T = lcm(grids) > %d", kMaxT);
+        gg = gcd64(gg, b);
+        bmin = b < bmin ? b : bmin;
+    }
+    if (T * T * d->C > kMaxTileBytes) return fail(DP_PIX_E_UNSUPPORTED, "T*T*C > %d", kMaxTileBytes);
+    g.M = d->M; g.N = d->N; g.C = d->C; g.K = d->K; g.T = (int)T;
+    g.GR = (int)((d->M + T - 1) / T);
+    g.GC = (int)((d->N + T - 1) / T);
+    g.PR = (int)(g.GR * T - d->M);
+    g.PC = (int)(g.GC * T - d->N);
+    const int64_t lim_r = d->pad_mode == DP_PIX_PAD_REFLECT ? d->M - 1 : d->M;
+    const int64_t lim_c = d->pad_mode == DP_PIX_PAD_REFLECT ? d->N - 1 : d->N;
+    if (g.PR > lim_r || g.PC > lim_c)
+        return fail(DP_PIX_E_PAD_TOO_LARGE, "padding (%d, %d) reaches past the image (%d x %d)", g.PR, g.PC, d->M, d->N);
+    const uint64_t ntiles = (uint64_t)g.GR * (uint64_t)g.GC;
+    if (ntiles > (uint64_t)kMaxFrameTiles) return fail(DP_PIX_E_UNSUPPORTED, "more than %d tiles per frame", kMaxFrameTiles);
+    g.ntiles = (uint32_t)ntiles;
+    g.pad_mode = d->pad_mode;
+    g.source = d->region_source;
+    g.dtype = d->record_dtype;
+    g.noise_free = d->noise_free ? 1 : 0;
+    g.es = d->record_dtype == DP_PIX_REC_U8 ? 1 : 4;
+    g.pitch = d->row_pitch;
+    g.R = d->value_range;
+    g.R_f = (float)d->value_range;
+    g.m = d->m;
+    g.matte_thr = d->matte_threshold;
+    g.seed = d->seed;
+    uint64_t maxcells = 0;
+    for (int r = 0; r < d->K; ++r) {
+        const int b = d->grid[r];
+        g.grid[r] = b;
+        g.cells_side[r] = (int)(T / b);
+        g.eps[r] = d->eps[r];
+        // Eq. 12 with Eq. 8: sigma = R m / (b^2 eps)
+        g.sigma[r] = d->value_range * d->m / ((double)b * (double)b * d->eps[r]);
+        g.sigma_f[r] = (float)g.sigma[r];
+        g.b2_f[r] = (float)(b * b);
+        const uint64_t c = (uint64_t)g.cells_side[r] * g.cells_side[r];
+        maxcells = c > maxcells ? c : maxcells;
+    }
+    g.b_min = bmin;
+    g.g = (int)gg;
+    g.rowidx_offset = kHeaderBytes;
+    g.map_offset = g.rowidx_offset + a16((uint64_t)g.GR * g.K * 4);
+    g.payload_offset = g.map_offset + a16(ntiles);
+    g.record_cap = g.payload_offset + a16(ntiles * maxcells * g.C * g.es) + 16ull * g.K;
+    if (g.record_cap >= (1ull << 32)) return fail(DP_PIX_E_UNSUPPORTED, "record larger than 4 GiB");
+    const int TC = (int)T * g.C;
+    if (g.source == DP_PIX_SRC_VARIANCE) {
+        if (TC % 4 != 0) return fail(DP_PIX_E_UNSUPPORTED, "VARIANCE needs T*C to be a multiple of 4");
+        if (ntiles > (uint64_t)kMaxRankTiles) return fail(DP_PIX_E_UNSUPPORTED, "VARIANCE ranks at most %d tiles", kMaxRankTiles);
+        g.idx_bits = bits_for((unsigned __int128)(ntiles - 1));
+        if (g.idx_bits < 1) g.idx_bits = 1;
+        const unsigned __int128 n = (unsigned __int128)TC * (unsigned __int128)T;
+        const unsigned __int128 kmax = (n * 255u) * (n * 255u) / 4u + 1u;
+        if (bits_for(kmax) + g.idx_bits > 64) return fail(DP_PIX_E_UNSUPPORTED, "rank key does not fit 64 bits");
+        g.var_onepass = (g.g >= 4 && g.g <= 16) ? 1 : 0;
+    }
+    // workspace layout (per frame)
+    uint64_t off = 0;
+    g.ws_tileoff = off;
+    off = a256(off + 4ull * ntiles);
+    g.ws_keys = off;
+    if (g.source == DP_PIX_SRC_VARIANCE) off = a256(off + 8ull * ntiles);
+    g.ws_gsum = off;
+    if (g.var_onepass) {
+        const uint64_t per = (uint64_t)(T / g.g) * (T / g.g) * g.C;
+        g.gsum_per_tile = (uint32_t)((per + 7) & ~7ull);
+        off = a256(off + 2ull * ntiles * g.gsum_per_tile);
+    }
+    g.ws_per_frame = off;
+    // staged segment: S tiles of one tile row, S*T*C a multiple of 16 when possible
+    int s0 = 16 / (int)gcd64(TC, 16);
+    int S = s0 * (int)((384 + (int64_t)s0 * TC - 1) / ((int64_t)s0 * TC));
+    if (S > 16) S = 16 / s0 * s0;
+    if (S < 1) S = 1;
+    const int vb_rel = (int)T / bmin;
+    const int vb_stat = g.var_onepass ? (int)T / g.g : 0;
+    const int vbands = vb_rel > vb_stat ? vb_rel : vb_stat;
+    auto smem_for = [&](int s) { return (int64_t)T * (int64_t)a16((uint64_t)s * TC) + (int64_t)s * vbands * TC * 2; };
+    while (S > 1 && smem_for(S) > 96 * 1024) S = (S - s0 >= 1) ? S - s0 : S - 1;
+    if (smem_for(S) > 200 * 1024) return fail(DP_PIX_E_UNSUPPORTED, "tile too large to stage");
+    g.seg_tiles = S;
+    g.seg_per_row = (g.GC + S - 1) / S;
+    g.seg_rowstride = (int)a16((uint64_t)S * TC);
+    g.vbands = vb_rel;
+    if (g.var_onepass) {
+        int E = (int)(8192 / (g.gsum_per_tile * 2));
+        g.emit_tiles = E < 1 ? 1 : (E > 64 ? 64 : E);
+    }
+    return DP_PIX_OK;
+}
+
+int check_cuda_device() {
+    int n = 0;
+    const cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n < 1) return fail(DP_PIX_E_CUDA, "no CUDA device available: %s", cudaGetErrorString(e));
+    return DP_PIX_OK;
+}
+
+}  // namespace
+}  // namespace dppix
+
+using namespace dppix;
+
+extern "C" {
+
+int dp_pix_version(void) { return 10000; }
+
+const char *dp_pix_last_error(void) { return t_err; }
+
+int dp_pix_plan(const dp_pix_desc *d, dp_pix_plan_t *out, dp_pix_sizes *sz) {
+    t_err[0] = 0;
+    if (!out) return fail(DP_PIX_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    Geom g;
+    const int rc = make_geom(d, g);
+    if (rc) return rc;
+    dp_pix_plan_s *p = new (std::nothrow) dp_pix_plan_s;
+    if (!p) return fail(DP_PIX_E_INVALID_ARG, "out of host memory");
+    p->g = g;
+    *out = p;
+    if (sz) {
+        memset(sz, 0, sizeof(*sz));
+        sz->record_bytes = g.record_cap;
+        sz->workspace_per_frame = g.ws_per_frame;
+        sz->workspace_fixed = 0;
+        sz->T = g.T; sz->GR = g.GR; sz->GC = g.GC; sz->PR = g.PR; sz->PC = g.PC;
+        sz->num_tiles = g.ntiles;
+        uint64_t maxcells = 0;
+        for (int r = 0; r < g.K; ++r) {
+            const uint64_t c = (uint64_t)g.cells_side[r] * g.cells_side[r];
+            maxcells = c > maxcells ? c : maxcells;
+            sz->sigma[r] = g.sigma[r];
+        }
+        sz->max_values = (uint64_t)g.ntiles * maxcells * g.C;
+    }
+    return DP_PIX_OK;
+}
+
+int dp_pix_plan_destroy(dp_pix_plan_t plan) {
+    delete plan;
+    return DP_PIX_OK;
+}
+
+int dp_pix_release(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride, const void *d_region_src,
+                   int64_t src_pitch, int64_t src_frame_stride, uint32_t n_frames, uint32_t stream_id,
+                   uint64_t frame_idx0, void *d_records, int64_t record_stride, void *d_ws, uint64_t ws_bytes,
+                   void *cuda_stream) {
+    t_err[0] = 0;
+    if (!plan) return fail(DP_PIX_E_INVALID_ARG, "plan is NULL");
+    const Geom &g = plan->g;
+    if (n_frames == 0) return DP_PIX_OK;
+    if (!d_frames || !d_records || !d_ws) return fail(DP_PIX_E_INVALID_ARG, "frames, records and workspace are required");
+    if (stream_id >= (1u << 24)) return fail(DP_PIX_E_INVALID_ARG, "stream_id must be < 2^24");
+    if (n_frames > 65535) return fail(DP_PIX_E_INVALID_ARG, "at most 65535 frames per call");
+    if (n_frames > 1 && frame_stride < g.pitch * (int64_t)(g.M - 1) + (int64_t)g.N * g.C)
+        return fail(DP_PIX_E_INVALID_ARG, "frame_stride smaller than one frame");
+    if (record_stride < (int64_t)g.record_cap || record_stride % 16 != 0)
+        return fail(DP_PIX_E_BUFFER_TOO_SMALL, "record_stride %lld < record capacity %llu or not a multiple of 16",
+                    (long long)record_stride, (unsigned long long)g.record_cap);
+    if ((uintptr_t)d_records % 16 != 0) return fail(DP_PIX_E_INVALID_ARG, "records must be 16-byte aligned");
+    if ((uintptr_t)d_ws % 256 != 0) return fail(DP_PIX_E_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < (uint64_t)n_frames * g.ws_per_frame)
+        return fail(DP_PIX_E_BUFFER_TOO_SMALL, "workspace %llu < %llu", (unsigned long long)ws_bytes,
+                    (unsigned long long)((uint64_t)n_frames * g.ws_per_frame));
+    if (g.source != DP_PIX_SRC_VARIANCE && !d_region_src) return fail(DP_PIX_E_INVALID_ARG, "region source is required");
+    if (g.source == DP_PIX_SRC_MASK_U8 && src_pitch < g.N) return fail(DP_PIX_E_INVALID_ARG, "mask pitch < N");
+    if (g.source == DP_PIX_SRC_MATTE_F32 && (src_pitch < 4ll * g.N || src_pitch % 4 != 0 || (uintptr_t)d_region_src % 4))
+        return fail(DP_PIX_E_INVALID_ARG, "matte pitch < 4N or not 4-byte aligned");
+    if (n_frames > 1 && g.source != DP_PIX_SRC_VARIANCE && src_frame_stride <= 0)
+        return fail(DP_PIX_E_INVALID_ARG, "src_frame_stride required for several frames");
+    int rc = check_cuda_device();
+    if (rc) return rc;
+
+    CallArgs a;
+    memset(&a, 0, sizeof(a));
+    a.frames = static_cast<const uint8_t *>(d_frames);
+    a.frame_stride = frame_stride;
+    a.src = static_cast<const uint8_t *>(d_region_src);
+    a.src_pitch = src_pitch;
+    a.src_frame_stride = src_frame_stride;
+    a.n_frames = n_frames;
+    a.stream_id = stream_id;
+    a.frame_idx0 = frame_idx0;
+    a.records = static_cast<uint8_t *>(d_records);
+    a.record_stride = record_stride;
+    a.ws = static_cast<uint8_t *>(d_ws);
+    a.status = status_word();
+    const uintptr_t base = (uintptr_t)d_frames;
+    const int64_t fs = n_frames > 1 ? frame_stride : 0;
+    const int64_t seg_bytes = (int64_t)g.seg_tiles * g.T * g.C;
+    if (base % 16 == 0 && g.pitch % 16 == 0 && fs % 16 == 0 && seg_bytes % 16 == 0)
+        a.vec = 16;
+    else if (base % 4 == 0 && g.pitch % 4 == 0 && fs % 4 == 0 && seg_bytes % 4 == 0)
+        a.vec = 4;
+    else
+        a.vec = 1;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaSuccess;
+    switch (g.source) {
+        case DP_PIX_SRC_TILE_LABELS:
+            e = launch_finalize_labels(g, a, s);
+            if (e == cudaSuccess) e = launch_release(g, a, s);
+            break;
+        case DP_PIX_SRC_MASK_U8:
+        case DP_PIX_SRC_MATTE_F32:
+            e = launch_classify(g, a, s);
+            if (e == cudaSuccess) e = launch_finalize_map(g, a, s);
+            if (e == cudaSuccess) e = launch_release(g, a, s);
+            break;
+        case DP_PIX_SRC_VARIANCE:
+            e = launch_tile_stats(g, a, s);
+            if (e == cudaSuccess) e = launch_rank(g, a, s);
+            if (e == cudaSuccess) e = g.var_onepass ? launch_emit(g, a, s) : launch_release(g, a, s);
+            break;
+        default:
+            return fail(DP_PIX_E_INVALID_ARG, "bad region source");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "release launch");
+    return DP_PIX_OK;
+}
+
+int dp_pix_store(const void *d_record, void *dst, uint64_t cap, uint64_t *written, int dst_is_host,
+                 void *cuda_stream) {
+    t_err[0] = 0;
+    if (!d_record || !dst) return fail(DP_PIX_E_INVALID_ARG, "record and destination are required");
+    int rc = check_cuda_device();
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    dp_pix_record_header h;
+    cudaError_t e = cudaMemcpyAsync(&h, d_record, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "store: header read");
+    if (memcmp(h.magic, "DPPX", 4) != 0 || h.version != 1 || h.total_bytes < sizeof(h))
+        return fail(DP_PIX_E_BAD_RECORD, "store: not a record");
+    if (cap < h.total_bytes)
+        return fail(DP_PIX_E_BUFFER_TOO_SMALL, "store: record needs %llu bytes", (unsigned long long)h.total_bytes);
+    e = cudaMemcpyAsync(dst, d_record, h.total_bytes, dst_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "store: copy");
+    if (written) *written = h.total_bytes;
+    return DP_PIX_OK;
+}
+
+int dp_pix_store_batch(const void *d_records, int64_t record_stride, uint32_t n, void *h_dst, int64_t dst_stride,
+                       uint64_t *written, void *cuda_stream) {
+    t_err[0] = 0;
+    if (n == 0) return DP_PIX_OK;
+    if (!d_records || !h_dst) return fail(DP_PIX_E_INVALID_ARG, "records and destination are required");
+    if (record_stride < (int64_t)sizeof(dp_pix_record_header) || dst_stride < (int64_t)sizeof(dp_pix_record_header))
+        return fail(DP_PIX_E_INVALID_ARG, "strides must be >= 512");
+    int rc = check_cuda_device();
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<dp_pix_record_header> hdr(n);
+    cudaError_t e = cudaMemcpy2DAsync(hdr.data(), sizeof(dp_pix_record_header), d_records, (size_t)record_stride,
+                                      sizeof(dp_pix_record_header), n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "store_batch: header read");
+    for (uint32_t i = 0; i < n; ++i) {
+        const dp_pix_record_header &h = hdr[i];
+        if (memcmp(h.magic, "DPPX", 4) != 0 || h.version != 1 || h.total_bytes < sizeof(h) ||
+            h.total_bytes > (uint64_t)record_stride)
+            return fail(DP_PIX_E_BAD_RECORD, "store_batch: record %u is not a record", i);
+        if (h.total_bytes > (uint64_t)dst_stride)
+            return fail(DP_PIX_E_BUFFER_TOO_SMALL, "store_batch: record %u needs %llu bytes", i,
+                        (unsigned long long)h.total_bytes);
+    }
+    for (uint32_t i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(static_cast<uint8_t *>(h_dst) + (uint64_t)i * dst_stride,
+                            static_cast<const uint8_t *>(d_records) + (uint64_t)i * record_stride, hdr[i].total_bytes,
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "store_batch: copy");
+    if (written)
+        for (uint32_t i = 0; i < n; ++i) written[i] = hdr[i].total_bytes;
+    return DP_PIX_OK;
+}
+
+int dp_pix_reconstruct(const void *d_records, int64_t record_stride, uint32_t n_records, void *d_out,
+                       int64_t out_frame_stride, int64_t out_pitch, int out_type, int32_t max_M, int32_t max_N,
+                       int32_t max_C, void *cuda_stream) {
+    t_err[0] = 0;
+    if (n_records == 0) return DP_PIX_OK;
+    if (!d_records || !d_out) return fail(DP_PIX_E_INVALID_ARG, "records and output are required");
+    if (out_type != DP_PIX_OUT_U8 && out_type != DP_PIX_OUT_F32) return fail(DP_PIX_E_INVALID_ARG, "bad out_type");
+    if (max_M < 1 || max_N < 1 || max_C < 1 || max_C > 4) return fail(DP_PIX_E_INVALID_ARG, "bad max geometry");
+    const int oes = out_type == DP_PIX_OUT_F32 ? 4 : 1;
+    if (out_pitch < (int64_t)max_N * max_C * oes) return fail(DP_PIX_E_INVALID_ARG, "out_pitch < max_N * max_C * elem");
+    if (n_records > 1 && out_frame_stride < out_pitch * max_M) return fail(DP_PIX_E_INVALID_ARG, "out_frame_stride too small");
+    if (record_stride < DP_PIX_RECORD_HEADER_BYTES || record_stride % 16 != 0)
+        return fail(DP_PIX_E_INVALID_ARG, "record_stride must be >= 512 and a multiple of 16");
+    if ((uintptr_t)d_records % 16 != 0) return fail(DP_PIX_E_INVALID_ARG, "records must be 16-byte aligned");
+    if (out_type == DP_PIX_OUT_F32 && ((uintptr_t)d_out % 4 || out_pitch % 4 || (n_records > 1 && out_frame_stride % 4)))
+        return fail(DP_PIX_E_INVALID_ARG, "f32 output must be 4-byte aligned");
+    int rc = check_cuda_device();
+    if (rc) return rc;
+    int align = 16;
+    const uint64_t ob = (uint64_t)(uintptr_t)d_out;
+    while (align > 1 && (ob % align || out_pitch % align || (n_records > 1 && out_frame_stride % align))) align >>= 1;
+    const cudaError_t e = launch_reconstruct(static_cast<const uint8_t *>(d_records), record_stride, n_records,
+                                             static_cast<uint8_t *>(d_out), out_frame_stride, out_pitch, out_type,
+                                             max_M, max_N, max_C, align, status_word(),
+                                             static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "reconstruct launch");
+    return DP_PIX_OK;
+}
+
+int dp_pix_debug_noise(uint64_t seed, const uint32_t *d_ctr, uint64_t n, uint32_t *d_words, float *d_eta, float sigma,
+                       void *cuda_stream) {
+    t_err[0] = 0;
+    if (n == 0) return DP_PIX_OK;
+    if (!d_ctr) return fail(DP_PIX_E_INVALID_ARG, "counters are required");
+    int rc = check_cuda_device();
+    if (rc) return rc;
+    const cudaError_t e = launch_debug_noise(seed, d_ctr, n, d_words, d_eta, sigma, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "debug_noise launch");
+    return DP_PIX_OK;
+}
+
+int dp_pix_status(void *cuda_stream, uint32_t *detail) {
+    t_err[0] = 0;
+    int rc = check_cuda_device();
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "status: stream sync");
+    int32_t st[2] = {0, 0};
+    e = cudaMemcpyFromSymbol(st, g_dppix_status, sizeof(st));
+    if (e != cudaSuccess) return cuda_fail(e, "status: read");
+    if (detail) *detail = (uint32_t)st[1];
+    if (st[0] != 0) {
+        const int32_t zero[2] = {0, 0};
+        cudaMemcpyToSymbol(g_dppix_status, zero, sizeof(zero));
+        return fail(st[0], "device-side check failed (detail 0x%x)", (unsigned)st[1]);
+    }
+    return DP_PIX_OK;
+}
+
+int dp_pix_prof_enable(int timing) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_timing = timing != 0;
+    return DP_PIX_OK;
+}
+
+int dp_pix_prof_read(dp_pix_prof_entry *out, int cap) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int i = 0;
+    for (auto &kv : g_prof) {
+        ProfEntry &e = kv.second;
+        for (auto &p : e.pending) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(p.second) == cudaSuccess && cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess)
+                e.total_ms += ms;
+            cudaEventDestroy(p.first);
+            cudaEventDestroy(p.second);
+        }
+        e.pending.clear();
+        if (out && i < cap) {
+            memset(&out[i], 0, sizeof(out[i]));
+            strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
+            out[i].launches = e.launches;
+            out[i].total_ms = e.total_ms;
+        }
+        ++i;
+    }
+    return i;
+}
+
+int dp_pix_prof_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &kv : g_prof)
+        for (auto &p : kv.second.pending) {
+            cudaEventDestroy(p.first);
+            cudaEventDestroy(p.second);
+        }
+    g_prof.clear();
+    return DP_PIX_OK;
+}
+
+}  // extern "C"

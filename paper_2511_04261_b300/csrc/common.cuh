@@ -1,0 +1,158 @@
+// common.cuh -- internal types and device helpers of libdppix (region-adaptive DP pixelization).
+//
+// Plain-old-data structs passed by value to every kernel, the counter-based generator, the Laplace
+// sampler and the mirror-padding index.  Nothing here allocates; nothing here is shared with the oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dppix.h"
+
+namespace dppix {
+
+constexpr int kMaxK = DP_PIX_MAX_REGIONS;
+constexpr int kMaxT = 128;
+constexpr int kMaxTileBytes = 49152;     // T*T*C limit (one staged tile)
+constexpr int kMaxRankTiles = 16384;     // VARIANCE: tiles of one frame ranked in shared memory
+constexpr int kMaxFrameTiles = 200000;   // tiles of one frame (the map is finalised in shared memory)
+constexpr int kHeaderBytes = DP_PIX_RECORD_HEADER_BYTES;
+
+// Geometry and constants of a plan (Alg. 2 steps 1-3, Alg. 3 steps 1-2, Eq. 12).
+struct Geom {
+    int32_t M, N, C, K, T, GR, GC, PR, PC;
+    int32_t pad_mode, source, dtype, noise_free;
+    int32_t es;                       // record element bytes
+    int64_t pitch;                    // frame row pitch
+    int32_t grid[kMaxK];
+    int32_t cells_side[kMaxK];        // T / b_r
+    float sigma_f[kMaxK];
+    float b2_f[kMaxK];                // b_r^2 as float (exact)
+    double sigma[kMaxK];
+    double eps[kMaxK];
+    double R, m;
+    float R_f;
+    float matte_thr;
+    uint64_t seed;
+    uint32_t ntiles;
+    int32_t g;                        // gcd of the grids (variance path granularity)
+    int32_t var_onepass;              // VARIANCE with 4 <= g <= 16: g-cell sums kept, image read once
+    int32_t b_min;
+    int32_t idx_bits;                 // bits for the tile index in a packed rank key
+    uint64_t rowidx_offset, map_offset, payload_offset, record_cap;
+    // workspace layout, per frame
+    uint64_t ws_per_frame, ws_tileoff, ws_keys, ws_gsum;
+    uint32_t gsum_per_tile;           // u16 values per tile: (T/g)^2 * C
+    // launch shapes
+    int32_t seg_tiles;                // tiles per staged segment of a tile row
+    int32_t seg_per_row;              // ceil(GC / seg_tiles)
+    int32_t seg_rowstride;            // bytes per staged row (multiple of 16)
+    int32_t vbands;                   // max bands of a staged tile = T / b_min (or T / g for stats)
+    int32_t emit_tiles;               // tiles per CTA in the g-cell emit kernel
+};
+
+// Per-call arguments of a release.
+struct CallArgs {
+    const uint8_t *frames;
+    int64_t frame_stride;
+    const uint8_t *src;
+    int64_t src_pitch, src_frame_stride;
+    uint32_t n_frames;
+    uint32_t stream_id;
+    uint64_t frame_idx0;
+    uint8_t *records;
+    int64_t record_stride;
+    uint8_t *ws;
+    int32_t vec;                      // widest safe global load for frame rows: 16, 4 or 1 bytes
+    int32_t *status;                  // device status word
+};
+
+// ---------------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64 multiplies with the
+// published multipliers, the key bumped by the published Weyl constants between rounds.
+// ---------------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &w, int i) {
+    return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w));
+}
+
+// Counter of the noise draw of one cell: (cell index in the frame's padded b_r-grid, r | stream << 8,
+// frame mod 2^32, frame >> 32); key (seed mod 2^32, seed >> 32).  Output word ch is channel ch.
+__device__ __forceinline__ uint4 cell_noise_words(uint64_t seed, uint32_t cell_idx, uint32_t region,
+                                                  uint32_t stream_id, uint64_t frame) {
+    return philox4x32_10(make_uint4(cell_idx, region | (stream_id << 8), (uint32_t)frame, (uint32_t)(frame >> 32)),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// Laplace(0, sigma) by the inverse CDF at u = (x + 1/2) / 2^32 (Eq. 9).  With k = x (lower half) or
+// k = 2^32-1-x (upper half, sign flipped), ln(2u) or ln(2(1-u)) is ln t, t = (k + 1/2) / 2^31.  For
+// t < 1/2 logf(t) is well conditioned; for t >= 1/2 ln t = log1pf(-(j + 1/2) / 2^31) with the exact
+// integer j = 2^31-1-k, so no cancellation happens near t = 1.
+__device__ __forceinline__ float laplace_from_word(uint32_t x, float sigma) {
+    const bool upper = (x >> 31) != 0u;
+    const uint32_t k = upper ? ~x : x;
+    float lnt;
+    if (k < (1u << 30)) {
+        const float t = (__uint2float_rn(k) + 0.5f) * 0x1p-31f;
+        lnt = logf(t);
+    } else {
+        const uint32_t j = 0x7FFFFFFFu - k;
+        const float omt = (__uint2float_rn(j) + 0.5f) * 0x1p-31f;
+        lnt = log1pf(-omt);
+    }
+    return upper ? -sigma * lnt : sigma * lnt;
+}
+
+// Clipped noisy mean (Sec. III-D; Alg. 2 steps 6-9): v = min(max(S / b^2 + eta, 0), R).
+__device__ __forceinline__ float noisy_mean(uint32_t S, float b2, float eta, float R) {
+    const float mu = __fdiv_rn(__uint2float_rn(S), b2);
+    const float v = __fadd_rn(mu, eta);
+    return fminf(fmaxf(v, 0.0f), R);
+}
+
+// Mirror padding by index: padded index p >= n maps back into [0, n) (Alg. 2 step 4).
+__device__ __forceinline__ int reflect_idx(int p, int n, int pad_mode) {
+    if (p < n) return p;
+    return pad_mode == DP_PIX_PAD_REFLECT ? 2 * (n - 1) - p : 2 * n - 1 - p;
+}
+
+__device__ __forceinline__ uint64_t align16_u64(uint64_t x) { return (x + 15ull) & ~15ull; }
+
+// Device status word (st[0] = first error code, st[1] = detail), cleared by dp_pix_status().  Kernels get
+// its address as an argument; it lives in api.cu.
+__device__ __forceinline__ void raise_status(int32_t *st, int32_t code, uint32_t detail) {
+    if (st != nullptr && atomicCAS(reinterpret_cast<int *>(st), 0, code) == 0) st[1] = (int32_t)detail;
+}
+
+// Launchers (one per kernel file); return cudaError_t of the launch.
+cudaError_t launch_classify(const Geom &g, const CallArgs &a, cudaStream_t s);
+cudaError_t launch_finalize_labels(const Geom &g, const CallArgs &a, cudaStream_t s);
+cudaError_t launch_finalize_map(const Geom &g, const CallArgs &a, cudaStream_t s);
+cudaError_t launch_release(const Geom &g, const CallArgs &a, cudaStream_t s);
+cudaError_t launch_tile_stats(const Geom &g, const CallArgs &a, cudaStream_t s);
+cudaError_t launch_rank(const Geom &g, const CallArgs &a, cudaStream_t s);
+cudaError_t launch_emit(const Geom &g, const CallArgs &a, cudaStream_t s);
+cudaError_t launch_reconstruct(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out,
+                               int64_t out_frame_stride, int64_t out_pitch, int out_type, int max_M, int max_N,
+                               int max_C, int out_align, int32_t *status, cudaStream_t s);
+cudaError_t launch_debug_noise(uint64_t seed, const uint32_t *ctr, uint64_t n, uint32_t *words, float *eta,
+                               float sigma, cudaStream_t s);
+
+// Host-side launch accounting (api.cu).
+void prof_begin(const char *name, cudaStream_t s);
+void prof_end(const char *name, cudaStream_t s);
+int sm_count();
+int32_t *status_word();  // device address of the status word on the current device (nullptr on failure)
+
+}  // namespace dppix

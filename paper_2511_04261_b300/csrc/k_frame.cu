@@ -1,0 +1,246 @@
+// k_frame.cu -- per-frame kernels: region-map finalisation and variance-quantile ranking.
+//
+// One CTA per frame.  Given the frame's u8 tile -> region map, the CTA counts tiles per region, lays out
+// the region-major payload (Table 3: mu'_G then mu'_Gs, generalised to K regions), writes each tile's
+// payload byte offset to the workspace, writes the tile-row index and the 512-byte header into the
+// record.  The rank kernel first builds the map from the per-tile variance keys (exact integers) by a
+// bitonic sort of (key, tile index) in shared memory.
+#include <cstring>
+
+#include "common.cuh"
+
+namespace dppix {
+
+namespace {
+
+constexpr int kFrameThreads = 1024;
+
+// Exclusive scan of kMaxK counters per thread across the block.  warp_tot: smem [32][kMaxK].
+__device__ void block_excl_scan_k(uint32_t (&v)[kMaxK], uint32_t (&excl)[kMaxK], uint32_t (&total)[kMaxK],
+                                  uint32_t (*warp_tot)[kMaxK]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+    uint32_t incl[kMaxK];
+#pragma unroll
+    for (int r = 0; r < kMaxK; ++r) incl[r] = v[r];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+        for (int r = 0; r < kMaxK; ++r) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl[r], off);
+            if (lane >= off) incl[r] += t;
+        }
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int r = 0; r < kMaxK; ++r) warp_tot[warp][r] = incl[r];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int r = 0; r < kMaxK; ++r) {
+            uint32_t x = lane < nwarps ? warp_tot[lane][r] : 0u;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, x, off);
+                if (lane >= off) x += t;
+            }
+            if (lane < nwarps) warp_tot[lane][r] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kMaxK; ++r) {
+        const uint32_t base = warp > 0 ? warp_tot[warp - 1][r] : 0u;
+        excl[r] = base + incl[r] - v[r];
+        total[r] = warp_tot[nwarps - 1][r];
+    }
+    __syncthreads();
+}
+
+struct FinalizeSmem {
+    uint32_t warp_tot[32][kMaxK];
+    uint64_t roff[kMaxK];
+    uint64_t tile_bytes[kMaxK];
+    uint32_t count[kMaxK];
+    dp_pix_record_header hdr;
+};
+
+// Lays out the record of frame f from the map in shared memory (see file comment).
+__device__ void finalize_frame(const Geom &g, const CallArgs &a, uint32_t f, const uint8_t *map_s, bool write_map,
+                               FinalizeSmem &sm) {
+    const uint32_t n = g.ntiles;
+    const uint32_t chunk = (n + blockDim.x - 1) / blockDim.x;
+    const uint32_t c0 = min(n, threadIdx.x * chunk), c1 = min(n, c0 + chunk);
+    uint32_t cnt[kMaxK], excl[kMaxK], total[kMaxK];
+#pragma unroll
+    for (int r = 0; r < kMaxK; ++r) cnt[r] = 0;
+    for (uint32_t i = c0; i < c1; ++i) {
+        const uint32_t r = map_s[i];
+#pragma unroll
+        for (int q = 0; q < kMaxK; ++q) cnt[q] += (r == (uint32_t)q);
+    }
+    block_excl_scan_k(cnt, excl, total, sm.warp_tot);
+
+    uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
+    if (threadIdx.x == 0) {
+        uint64_t off = g.payload_offset;
+        for (int r = 0; r < g.K; ++r) {
+            const uint64_t cs = (uint64_t)g.cells_side[r];
+            sm.tile_bytes[r] = cs * cs * (uint64_t)g.C * (uint64_t)g.es;
+            sm.roff[r] = off;
+            sm.count[r] = total[r];
+            off = align16_u64(off + (uint64_t)total[r] * sm.tile_bytes[r]);
+        }
+        dp_pix_record_header &h = sm.hdr;
+        memset(&h, 0, sizeof(h));
+        h.magic[0] = 'D'; h.magic[1] = 'P'; h.magic[2] = 'P'; h.magic[3] = 'X';
+        h.version = 1;
+        h.header_bytes = kHeaderBytes;
+        h.flags = g.noise_free ? 1u : 0u;
+        h.M = g.M; h.N = g.N; h.C = g.C; h.T = g.T; h.K = g.K; h.GR = g.GR; h.GC = g.GC;
+        h.pad_mode = g.pad_mode; h.record_dtype = g.dtype; h.region_source = g.source; h.stream_id = a.stream_id;
+        h.seed = g.seed;
+        h.frame_idx = a.frame_idx0 + f;
+        h.value_range = g.R; h.m = g.m;
+        h.total_bytes = off;
+        h.map_offset = g.map_offset;
+        for (int r = 0; r < g.K; ++r) {
+            h.grid[r] = g.grid[r];
+            h.eps[r] = g.eps[r];
+            h.sigma[r] = g.sigma[r];
+            h.count[r] = total[r];
+            h.region_offset[r] = sm.roff[r];
+        }
+        h.rowidx_offset = g.rowidx_offset;
+        h.payload_offset = g.payload_offset;
+    }
+    __syncthreads();
+    // header out: 32 x 16 bytes
+    if (threadIdx.x < kHeaderBytes / 16)
+        reinterpret_cast<uint4 *>(rec)[threadIdx.x] = reinterpret_cast<const uint4 *>(&sm.hdr)[threadIdx.x];
+    // per-tile offsets and tile-row index
+    uint32_t *tileoff = reinterpret_cast<uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff);
+    uint32_t *rowidx = reinterpret_cast<uint32_t *>(rec + g.rowidx_offset);
+    uint32_t run[kMaxK];
+#pragma unroll
+    for (int r = 0; r < kMaxK; ++r) run[r] = excl[r];
+    for (uint32_t i = c0; i < c1; ++i) {
+        if (i % (uint32_t)g.GC == 0) {
+            const uint32_t ty = i / (uint32_t)g.GC;
+#pragma unroll
+            for (int r = 0; r < kMaxK; ++r)
+                if (r < g.K) rowidx[ty * g.K + r] = run[r];
+        }
+        const uint32_t r = map_s[i];
+        uint32_t ri = 0;
+#pragma unroll
+        for (int q = 0; q < kMaxK; ++q)
+            if (r == (uint32_t)q) { ri = run[q]; run[q] = ri + 1; }
+        tileoff[i] = (uint32_t)(sm.roff[r] + (uint64_t)ri * sm.tile_bytes[r]);
+    }
+    if (write_map) {
+        uint8_t *map = rec + g.map_offset;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) map[i] = map_s[i];
+    }
+}
+
+// Map given by the caller (tile labels) or already written into the record by k_classify.
+__global__ void __launch_bounds__(kFrameThreads) k_finalize(const Geom g, const CallArgs a, int from_labels) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    FinalizeSmem &sm = *reinterpret_cast<FinalizeSmem *>(dyn);
+    uint8_t *map_s = dyn + sizeof(FinalizeSmem);
+    const uint32_t f = blockIdx.x;
+    const uint8_t *src = from_labels ? a.src + (uint64_t)f * (uint64_t)a.src_frame_stride
+                                     : a.records + (uint64_t)f * (uint64_t)a.record_stride + g.map_offset;
+    for (uint32_t i = threadIdx.x; i < g.ntiles; i += blockDim.x) {
+        uint8_t r = src[i];
+        if (r >= (uint32_t)g.K) {
+            raise_status(a.status, DP_PIX_E_DEVICE, 0x100u | r);
+            r = 0;
+        }
+        map_s[i] = r;
+    }
+    __syncthreads();
+    finalize_frame(g, a, f, map_s, from_labels != 0, sm);
+}
+
+// VARIANCE classes: rank tiles by (key, index) ascending, class q = floor(K * rank / n).
+__global__ void __launch_bounds__(kFrameThreads) k_rank(const Geom g, const CallArgs a, uint32_t npow2) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    FinalizeSmem &sm = *reinterpret_cast<FinalizeSmem *>(dyn);
+    uint64_t *keys_s = reinterpret_cast<uint64_t *>(dyn + sizeof(FinalizeSmem));
+    uint8_t *map_s = reinterpret_cast<uint8_t *>(keys_s + npow2);
+    const uint32_t f = blockIdx.x, n = g.ntiles;
+    const uint64_t *keys = reinterpret_cast<const uint64_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_keys);
+    for (uint32_t i = threadIdx.x; i < npow2; i += blockDim.x)
+        keys_s[i] = i < n ? ((keys[i] << g.idx_bits) | (uint64_t)i) : ~0ull;
+    __syncthreads();
+    for (uint32_t k = 2; k <= npow2; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < npow2; i += blockDim.x) {
+                const uint32_t ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t x = keys_s[i], y = keys_s[ixj];
+                    const bool ascending = (i & k) == 0;
+                    if ((x > y) == ascending) {
+                        keys_s[i] = y;
+                        keys_s[ixj] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const uint64_t mask = (1ull << g.idx_bits) - 1ull;
+    for (uint32_t p = threadIdx.x; p < n; p += blockDim.x) {
+        const uint32_t idx = (uint32_t)(keys_s[p] & mask);
+        map_s[idx] = (uint8_t)(((uint64_t)g.K * p) / n);
+    }
+    __syncthreads();
+    finalize_frame(g, a, f, map_s, true, sm);
+}
+
+}  // namespace
+
+cudaError_t launch_finalize_labels(const Geom &g, const CallArgs &a, cudaStream_t s) {
+    const size_t smem = sizeof(FinalizeSmem) + g.ntiles;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr_set = true;
+    }
+    prof_begin("k_finalize", s);
+    k_finalize<<<a.n_frames, kFrameThreads, smem, s>>>(g, a, 1);
+    prof_end("k_finalize", s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_map(const Geom &g, const CallArgs &a, cudaStream_t s) {
+    const size_t smem = sizeof(FinalizeSmem) + g.ntiles;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr_set = true;
+    }
+    prof_begin("k_finalize", s);
+    k_finalize<<<a.n_frames, kFrameThreads, smem, s>>>(g, a, 0);
+    prof_end("k_finalize", s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rank(const Geom &g, const CallArgs &a, cudaStream_t s) {
+    uint32_t npow2 = 1;
+    while (npow2 < g.ntiles) npow2 <<= 1;
+    const size_t smem = sizeof(FinalizeSmem) + (size_t)npow2 * 8 + g.ntiles;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr_set = true;
+    }
+    prof_begin("k_rank", s);
+    k_rank<<<a.n_frames, kFrameThreads, smem, s>>>(g, a, npow2);
+    prof_end("k_rank", s);
+    return cudaGetLastError();
+}
+
+}  // namespace dppix

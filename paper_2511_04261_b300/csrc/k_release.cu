@@ -1,0 +1,454 @@
+// k_release.cu -- the streaming kernels of the release path.
+//
+// All three kernels work on "segments": one tile row (T image rows) times `seg_tiles` consecutive tiles of
+// one frame.  A segment is staged into shared memory once (16-byte cp.async when rows are aligned), with
+// the mirror padding of the last tile row/column resolved by index while staging (Alg. 2 step 4, Alg. 3
+// step 3; the padded image is never materialised).  Then, from shared memory:
+//  - column sums over the rows of each cell band, four byte lanes at a time in 16-bit SIMD lanes
+//    (vertical pass), and per-(cell, channel) sums over the band's columns (horizontal pass): exact u32
+//    cell sums of the b_r x b_r cells (Eq. 2; Alg. 2 step 6; Alg. 3 steps 8 and 14);
+//  - k_release: Laplace noise from the in-register Philox, clip, write the record payload (Alg. 3 steps
+//    9-10 and 15-17);
+//  - k_tile_stats: per-tile S, Q for the variance classes and, when the grids share a divisor g >= 4, the
+//    g x g cell sums from which any b_r-cell sum is later assembled (image read once);
+//  - k_emit: g-cell sums -> b_r-cell sums -> noise -> record.
+#include "common.cuh"
+
+namespace dppix {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Stage rows ty*T .. ty*T+T-1 (mirrored past M) and pixel columns [x0, x0 + ns*T) (mirrored past N) of
+// frame f into raw[j * rowstride + byte], then barrier.
+__device__ void stage_segment(const Geom &g, const CallArgs &a, uint32_t f, int ty, int tx0, int ns, uint8_t *raw) {
+    const int T = g.T, C = g.C, rs = g.seg_rowstride;
+    const int x0 = tx0 * T;
+    const int W = ns * T;
+    const int xv = min(W, g.N - x0);  // in-image columns of the segment (>= 1)
+    const int vb = xv * C;
+    const uint8_t *fbase = a.frames + (uint64_t)f * (uint64_t)a.frame_stride + (int64_t)x0 * C;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int done = 0;  // bytes per row covered by vector copies
+    if (a.vec == 16) {
+        const int nv = vb >> 4;
+        for (int idx = tid; idx < T * nv; idx += nt) {
+            const int j = idx / nv, v = idx - j * nv;
+            const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
+            cp_async16(raw + j * rs + 16 * v, fbase + (int64_t)sy * g.pitch + 16 * v);
+        }
+        done = nv << 4;
+    } else if (a.vec == 4) {
+        const int nv = vb >> 2;
+        for (int idx = tid; idx < T * nv; idx += nt) {
+            const int j = idx / nv, v = idx - j * nv;
+            const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
+            cp_async4(raw + j * rs + 4 * v, fbase + (int64_t)sy * g.pitch + 4 * v);
+        }
+        done = nv << 2;
+    }
+    const int tail = vb - done;
+    if (tail > 0) {
+        for (int idx = tid; idx < T * tail; idx += nt) {
+            const int j = idx / tail, k = done + (idx - j * tail);
+            const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
+            raw[j * rs + k] = fbase[(int64_t)sy * g.pitch + k];
+        }
+    }
+    const int pb = (W - xv) * C;  // mirrored bytes past the right edge
+    if (pb > 0) {
+        const uint8_t *fb0 = a.frames + (uint64_t)f * (uint64_t)a.frame_stride;
+        for (int idx = tid; idx < T * pb; idx += nt) {
+            const int j = idx / pb, k = idx - j * pb;
+            const int px = xv + k / C, ch = k - (k / C) * C;
+            const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
+            const int sx = reflect_idx(x0 + px, g.N, g.pad_mode);
+            raw[j * rs + px * C + ch] = fb0[(int64_t)sy * g.pitch + (int64_t)sx * C + ch];
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+}
+
+// Vertical pass of one (tile, band, word column): sums `rows` staged rows of 4 bytes in 16-bit lanes and
+// stores the 4 column sums as u16 into vdst[0..3].
+__device__ __forceinline__ void band_word_sums(const uint8_t *raw, int rs, int row0, int rows, int byte0,
+                                               uint32_t *vdst) {
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(raw + row0 * rs + byte0);
+    const int step = rs >> 2;
+    uint32_t lo = 0, hi = 0;
+    for (int i = 0; i < rows; ++i) {
+        const uint32_t w = src[i * step];
+        lo += __byte_perm(w, 0u, 0x4240);  // bytes 0, 2 -> 16-bit lanes
+        hi += __byte_perm(w, 0u, 0x4341);  // bytes 1, 3
+    }
+    vdst[0] = __byte_perm(lo, hi, 0x5410);  // (col 0, col 1)
+    vdst[1] = __byte_perm(lo, hi, 0x7632);  // (col 2, col 3)
+}
+
+struct SegInfo {
+    int32_t b[16];
+    int32_t cs[16];
+    int32_t region[16];
+    uint32_t tileoff[16];
+    int32_t startA[17];
+    int32_t startB[17];
+};
+
+// ------------------------------------------------------------------------------------------------------
+// k_release: staged segment -> exact cell sums of each tile's own grid -> noise -> clip -> record.
+// ------------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_release(const Geom g, const CallArgs a) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ SegInfo si;
+    const int T = g.T, C = g.C, TC = T * C, rs = g.seg_rowstride;
+    uint8_t *raw = dyn;
+    uint16_t *V = reinterpret_cast<uint16_t *>(dyn + (size_t)T * rs);
+    const bool word_path = (TC & 3) == 0;
+    const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row;
+    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const uint32_t sg = item % g.seg_per_row;
+        const uint32_t fr = item / g.seg_per_row;
+        const int ty = (int)(fr % g.GR);
+        const uint32_t f = fr / g.GR;
+        const int tx0 = (int)sg * g.seg_tiles;
+        const int ns = min(g.seg_tiles, g.GC - tx0);
+        uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
+        if (threadIdx.x == 0) {
+            const uint8_t *map = rec + g.map_offset + (uint64_t)ty * g.GC + tx0;
+            const uint32_t *toff =
+                reinterpret_cast<const uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff) + ty * g.GC + tx0;
+            int sa = 0, sb = 0;
+            for (int t = 0; t < ns; ++t) {
+                int r = map[t];
+                if (r >= g.K) r = 0;
+                const int b = g.grid[r];
+                si.b[t] = b;
+                si.cs[t] = T / b;
+                si.region[t] = r;
+                si.tileoff[t] = toff[t];
+                si.startA[t] = sa;
+                si.startB[t] = sb;
+                sa += (T / b) * (word_path ? (TC >> 2) : TC);
+                sb += (T / b) * (T / b);
+            }
+            si.startA[ns] = sa;
+            si.startB[ns] = sb;
+        }
+        stage_segment(g, a, f, ty, tx0, ns, raw);  // ends with a barrier (also covers si)
+
+        // vertical pass
+        const int totalA = si.startA[ns];
+        for (int it = threadIdx.x; it < totalA; it += blockDim.x) {
+            int t = 0;
+            while (t + 1 < ns && it >= si.startA[t + 1]) ++t;
+            const int rem = it - si.startA[t];
+            const int b = si.b[t];
+            if (word_path) {
+                const int wcs = TC >> 2;
+                const int band = rem / wcs, wc = rem - band * wcs;
+                uint32_t *vdst = reinterpret_cast<uint32_t *>(V + ((size_t)(t * g.vbands + band) * TC)) + 2 * wc;
+                band_word_sums(raw, rs, band * b, b, t * TC + 4 * wc, vdst);
+            } else {
+                const int band = rem / TC, k = rem - band * TC;
+                uint32_t s = 0;
+                for (int i = 0; i < b; ++i) s += raw[(band * b + i) * rs + t * TC + k];
+                V[(size_t)(t * g.vbands + band) * TC + k] = (uint16_t)s;
+            }
+        }
+        __syncthreads();
+
+        // horizontal pass, noise, clip, store
+        const int totalB = si.startB[ns];
+        const uint64_t frame = a.frame_idx0 + f;
+        for (int it = threadIdx.x; it < totalB; it += blockDim.x) {
+            int t = 0;
+            while (t + 1 < ns && it >= si.startB[t + 1]) ++t;
+            const int cell = it - si.startB[t];
+            const int cs = si.cs[t], b = si.b[t], r = si.region[t];
+            const int cy = cell / cs, cx = cell - cy * cs;
+            const uint16_t *vrow = V + (size_t)(t * g.vbands + cy) * TC + cx * b * C;
+            uint32_t S[4] = {0u, 0u, 0u, 0u};
+            for (int i = 0; i < b; ++i) {
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch)
+                    if (ch < C) S[ch] += vrow[i * C + ch];
+            }
+            const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)((tx0 + t) * cs + cx);
+            uint4 words = make_uint4(0, 0, 0, 0);
+            if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
+                words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, a.stream_id, frame);
+            uint8_t *dst = rec + si.tileoff[t] + (uint64_t)cell * C * g.es;
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                if (ch >= C) break;
+                if (g.dtype == DP_PIX_REC_SUM_U32) {
+                    reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
+                } else {
+                    const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), g.sigma_f[r]);
+                    const float v = noisy_mean(S[ch], g.b2_f[r], eta, g.R_f);
+                    if (g.dtype == DP_PIX_REC_F32)
+                        reinterpret_cast<float *>(dst)[ch] = v;
+                    else
+                        dst[ch] = (uint8_t)__float2uint_rn(v);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// k_tile_stats: per tile S = sum x, Q = sum x^2 over the C*T*T padded samples -> key = n*Q - S^2 (exact);
+// with `gsum`, also the g x g cell sums (u16) of every tile into the workspace.
+// ------------------------------------------------------------------------------------------------------
+template <bool kGsum>
+__global__ void __launch_bounds__(kThreads) k_tile_stats(const Geom g, const CallArgs a) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ uint32_t S_s[16];
+    __shared__ unsigned long long Q_s[16];
+    const int T = g.T, C = g.C, TC = T * C, rs = g.seg_rowstride;
+    uint8_t *raw = dyn;
+    uint16_t *V = reinterpret_cast<uint16_t *>(dyn + (size_t)T * rs);
+    const int gg = kGsum ? g.g : T;          // band height
+    const int bands = T / gg;
+    const int wcs = TC >> 2;                 // word columns (TC % 4 == 0 required on this path)
+    const int per_tile = ((bands * wcs + 31) / 32) * 32;  // warp-aligned items per tile
+    const int gcs = T / g.g;                 // g-cells per tile side
+    const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const uint32_t sg = item % g.seg_per_row;
+        const uint32_t fr = item / g.seg_per_row;
+        const int ty = (int)(fr % g.GR);
+        const uint32_t f = fr / g.GR;
+        const int tx0 = (int)sg * g.seg_tiles;
+        const int ns = min(g.seg_tiles, g.GC - tx0);
+        if (threadIdx.x < 16) {
+            S_s[threadIdx.x] = 0u;
+            Q_s[threadIdx.x] = 0ull;
+        }
+        stage_segment(g, a, f, ty, tx0, ns, raw);
+
+        const int totalA = ns * per_tile;
+        for (int it = threadIdx.x; it - lane < totalA; it += blockDim.x) {
+            // all lanes of a warp share one tile (per_tile is a multiple of 32)
+            const int t = it / per_tile;
+            const int rem = it - t * per_tile;
+            uint32_t s = 0, q = 0;
+            if (it < totalA && rem < bands * wcs) {
+                const int band = rem / wcs, wc = rem - band * wcs;
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(raw + band * gg * rs + t * TC + 4 * wc);
+                const int step = rs >> 2;
+                uint32_t lo = 0, hi = 0;
+                for (int i = 0; i < gg; ++i) {
+                    const uint32_t w = src[i * step];
+                    q = __dp4a(w, w, q);
+                    s = __dp4a(w, 0x01010101u, s);
+                    if (kGsum) {
+                        lo += __byte_perm(w, 0u, 0x4240);
+                        hi += __byte_perm(w, 0u, 0x4341);
+                    }
+                }
+                if (kGsum) {
+                    uint32_t *vdst = reinterpret_cast<uint32_t *>(V + ((size_t)(t * bands + band) * TC)) + 2 * wc;
+                    vdst[0] = __byte_perm(lo, hi, 0x5410);
+                    vdst[1] = __byte_perm(lo, hi, 0x7632);
+                }
+            }
+            const uint32_t sw = __reduce_add_sync(0xffffffffu, s);
+            unsigned long long qw = q;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) qw += __shfl_xor_sync(0xffffffffu, qw, off);
+            if (lane == 0 && t < ns) {
+                atomicAdd(&S_s[t], sw);
+                atomicAdd(&Q_s[t], qw);
+            }
+        }
+        __syncthreads();
+
+        const uint32_t tile0 = (uint32_t)ty * g.GC + tx0;
+        if (kGsum) {
+            uint16_t *gsum = reinterpret_cast<uint16_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_gsum);
+            const int cells = gcs * gcs;
+            const int gstride = g.gsum_per_tile;  // u16 per tile (padded)
+            for (int it = threadIdx.x; it < ns * cells; it += blockDim.x) {
+                const int t = it / cells, cell = it - t * cells;
+                const int cy = cell / gcs, cx = cell - cy * gcs;
+                const uint16_t *vrow = V + (size_t)(t * bands + cy) * TC + cx * g.g * C;
+                uint32_t S[4] = {0u, 0u, 0u, 0u};
+                for (int i = 0; i < g.g; ++i) {
+#pragma unroll
+                    for (int ch = 0; ch < 4; ++ch)
+                        if (ch < C) S[ch] += vrow[i * C + ch];
+                }
+                uint16_t *dst = gsum + (size_t)(tile0 + t) * gstride + (size_t)cell * C;
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch)
+                    if (ch < C) dst[ch] = (uint16_t)S[ch];
+            }
+        }
+        if (threadIdx.x < ns) {
+            const int t = threadIdx.x;
+            const unsigned long long n = (unsigned long long)TC * (unsigned long long)T;
+            const unsigned long long S = S_s[t];
+            uint64_t *keys = reinterpret_cast<uint64_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_keys);
+            keys[tile0 + t] = n * Q_s[t] - S * S;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// k_emit: per tile, assemble each b_r-cell sum from its (b_r/g)^2 g-cell sums, then noise, clip, store.
+// ------------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs a) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ int32_t t_region[64];
+    __shared__ uint32_t t_off[64];
+    __shared__ int32_t t_start[65];
+    const int E = g.emit_tiles, C = g.C, T = g.T, gcs = T / g.g;
+    const int gstride = g.gsum_per_tile;
+    uint16_t *gs = reinterpret_cast<uint16_t *>(dyn);
+    const uint32_t groups_per_frame = (g.ntiles + E - 1) / E;
+    const uint32_t items = a.n_frames * groups_per_frame;
+    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const uint32_t f = item / groups_per_frame;
+        const uint32_t tile0 = (item - f * groups_per_frame) * E;
+        const int ne = (int)min((uint32_t)E, g.ntiles - tile0);
+        uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
+        if (threadIdx.x == 0) {
+            const uint8_t *map = rec + g.map_offset + tile0;
+            const uint32_t *toff =
+                reinterpret_cast<const uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff) + tile0;
+            int sb = 0;
+            for (int t = 0; t < ne; ++t) {
+                int r = map[t];
+                if (r >= g.K) r = 0;
+                t_region[t] = r;
+                t_off[t] = toff[t];
+                t_start[t] = sb;
+                const int cs = g.cells_side[r];
+                sb += cs * cs;
+            }
+            t_start[ne] = sb;
+        }
+        // g-cell sums of the group's tiles are contiguous in the workspace
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_gsum +
+                                                           (uint64_t)tile0 * gstride * 2);
+        const int nvec = ne * gstride * 2 / 16;
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) reinterpret_cast<uint4 *>(gs)[i] = src[i];
+        __syncthreads();
+        const int total = t_start[ne];
+        const uint64_t frame = a.frame_idx0 + f;
+        for (int it = threadIdx.x; it < total; it += blockDim.x) {
+            int t = 0;
+            while (t + 1 < ne && it >= t_start[t + 1]) ++t;
+            const int r = t_region[t];
+            const int cell = it - t_start[t];
+            const int cs = g.cells_side[r], nb = g.grid[r] / g.g;
+            const int cy = cell / cs, cx = cell - cy * cs;
+            const uint16_t *tg = gs + (size_t)t * gstride;
+            uint32_t S[4] = {0u, 0u, 0u, 0u};
+            for (int yy = 0; yy < nb; ++yy) {
+                const uint16_t *row = tg + ((cy * nb + yy) * gcs + cx * nb) * C;
+                for (int xx = 0; xx < nb; ++xx) {
+#pragma unroll
+                    for (int ch = 0; ch < 4; ++ch)
+                        if (ch < C) S[ch] += row[xx * C + ch];
+                }
+            }
+            const uint32_t tile = tile0 + t;
+            const uint32_t ty = tile / g.GC, tx = tile - ty * g.GC;
+            const uint32_t cell_idx = (ty * cs + cy) * (uint32_t)(g.GC * cs) + tx * cs + cx;
+            uint4 words = make_uint4(0, 0, 0, 0);
+            if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
+                words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, a.stream_id, frame);
+            uint8_t *dst = rec + t_off[t] + (uint64_t)cell * C * g.es;
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                if (ch >= C) break;
+                if (g.dtype == DP_PIX_REC_SUM_U32) {
+                    reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
+                } else {
+                    const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), g.sigma_f[r]);
+                    const float v = noisy_mean(S[ch], g.b2_f[r], eta, g.R_f);
+                    if (g.dtype == DP_PIX_REC_F32)
+                        reinterpret_cast<float *>(dst)[ch] = v;
+                    else
+                        dst[ch] = (uint8_t)__float2uint_rn(v);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+size_t seg_smem(const Geom &g, int bands_per_tile) {
+    return (size_t)g.T * g.seg_rowstride + (size_t)g.seg_tiles * bands_per_tile * g.T * g.C * 2;
+}
+
+template <typename K>
+int grid_for(K kernel, size_t smem, uint32_t items) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const uint64_t cap = (uint64_t)per_sm * (uint64_t)sm_count();
+    return (int)(items < cap ? items : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_release(const Geom &g, const CallArgs &a, cudaStream_t s) {
+    const size_t smem = seg_smem(g, g.vbands);
+    cudaFuncSetAttribute(k_release, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row;
+    const int grid = grid_for(k_release, smem, items);
+    prof_begin("k_release", s);
+    k_release<<<grid, kThreads, smem, s>>>(g, a);
+    prof_end("k_release", s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_stats(const Geom &g, const CallArgs &a, cudaStream_t s) {
+    const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row;
+    if (g.var_onepass) {
+        const size_t smem = seg_smem(g, g.T / g.g);
+        cudaFuncSetAttribute(k_tile_stats<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int grid = grid_for(k_tile_stats<true>, smem, items);
+        prof_begin("k_tile_stats_gsum", s);
+        k_tile_stats<true><<<grid, kThreads, smem, s>>>(g, a);
+        prof_end("k_tile_stats_gsum", s);
+    } else {
+        const size_t smem = seg_smem(g, 0);
+        cudaFuncSetAttribute(k_tile_stats<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int grid = grid_for(k_tile_stats<false>, smem, items);
+        prof_begin("k_tile_stats", s);
+        k_tile_stats<false><<<grid, kThreads, smem, s>>>(g, a);
+        prof_end("k_tile_stats", s);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const Geom &g, const CallArgs &a, cudaStream_t s) {
+    const size_t smem = (size_t)g.emit_tiles * g.gsum_per_tile * 2;
+    cudaFuncSetAttribute(k_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const uint32_t items = a.n_frames * ((g.ntiles + g.emit_tiles - 1) / g.emit_tiles);
+    const int grid = grid_for(k_emit, smem, items);
+    prof_begin("k_emit", s);
+    k_emit<<<grid, kThreads, smem, s>>>(g, a);
+    prof_end("k_emit", s);
+    return cudaGetLastError();
+}
+
+}  // namespace dppix

@@ -1,0 +1,112 @@
+"""The C-ABI library on a machine without a GPU: it loads, exports every declared entry point, and its
+host-only plan agrees with the oracle's geometry and validation (no compute call is made here)."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2511_04261_b300 as P
+from paper_2511_04261_b300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^DPPIX_API\s+[\w\s\*]+?\b(dp_pix_\w+)\s*\(", txt, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_symbols()
+    assert {"dp_pix_plan", "dp_pix_release", "dp_pix_store", "dp_pix_reconstruct"} <= names
+    lib = ct.CDLL(_lib.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_version_and_last_error():
+    L = _lib.lib()
+    assert L.dp_pix_version() >= 10000
+    with pytest.raises(P.DppixError) as e:
+        P.Plan(M=0, N=5, C=3, grids=[4], eps=[1])
+    assert e.value.code == _lib.E_INVALID_ARG
+    assert b"M and N" in L.dp_pix_last_error()
+
+
+def test_compute_calls_fail_loudly_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("has a GPU")
+    L = _lib.lib()
+    rc = L.dp_pix_status(None, None)
+    assert rc == _lib.E_CUDA
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_plan_geometry_matches_oracle(seed):
+    rng = np.random.default_rng(seed)
+    K = int(rng.integers(1, 5))
+    pool = [1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24, 32]
+    grids = [int(rng.choice(pool)) for _ in range(K)]
+    M, N, C = int(rng.integers(1, 300)), int(rng.integers(1, 300)), int(rng.choice([1, 3, 4]))
+    eps = [float(rng.uniform(0.1, 3)) for _ in range(K)]
+    pad = int(rng.integers(0, 2))
+    dtype = int(rng.integers(0, 3))
+    kw = dict(M=M, N=N, C=C, grids=grids, eps=eps, pad_mode=pad, dtype=dtype, m=float(rng.uniform(1, 64)))
+    orc = O.geometry_rc(**kw)
+    try:
+        plan = P.Plan(**kw)
+    except P.DppixError as e:
+        # the library may refuse what it does not support; a padding refusal must be the oracle's too
+        assert e.code in (_lib.E_UNSUPPORTED, _lib.E_PAD_TOO_LARGE), e
+        if e.code == _lib.E_PAD_TOO_LARGE:
+            assert orc == -2
+        return
+    assert orc == 0
+    g = O.geometry(**kw)
+    assert (plan.T, plan.GR, plan.GC) == (g["T"], g["GR"], g["GC"])
+    assert plan.record_bytes == g["capacity"]
+    np.testing.assert_allclose(plan.sigma, g["sigma"], rtol=1e-15)
+
+
+def test_plan_limits():
+    with pytest.raises(P.DppixError) as e:
+        P.Plan(M=100, N=100, C=3, grids=[65], eps=[1])
+    assert e.value.code == _lib.E_UNSUPPORTED
+    with pytest.raises(P.DppixError) as e:
+        P.Plan(M=100, N=100, C=3, grids=[64, 3], eps=[1, 1])  # T = 192
+    assert e.value.code == _lib.E_UNSUPPORTED
+    with pytest.raises(P.DppixError) as e:
+        P.Plan(M=100, N=100, C=3, grids=[8, 4], eps=[1, 1], source=_lib.SRC_MASK_U8, pad_mode=7)
+    assert e.value.code == _lib.E_INVALID_ARG
+    with pytest.raises(P.DppixError) as e:
+        P.Plan(M=100, N=100, C=3, grids=[8, 4, 2], eps=[1, 1, 1], source=_lib.SRC_MASK_U8)
+    assert e.value.code == _lib.E_INVALID_ARG
+    with pytest.raises(P.DppixError) as e:
+        P.Plan(M=4000, N=4000, C=3, grids=[32, 16], eps=[1, 1], source=_lib.SRC_VARIANCE)  # 15625 tiles ok
+        P.Plan(M=8000, N=8000, C=3, grids=[32, 16], eps=[1, 1], source=_lib.SRC_VARIANCE)  # 62500 > 16384
+    assert e.value.code == _lib.E_UNSUPPORTED
+    with pytest.raises(P.DppixError) as e:
+        P.Plan(M=10, N=10, C=3, grids=[8], eps=[-1])
+    assert e.value.code == _lib.E_INVALID_ARG
+    P.Plan(M=10, N=10, C=3, grids=[8], eps=[0], noise_free=True)
+
+
+def test_variance_plan_paths():
+    one = P.Plan(M=1080, N=1920, C=3, grids=[32, 16, 8, 4], eps=[2, 1, .5, .25], source=_lib.SRC_VARIANCE)
+    two = P.Plan(M=1080, N=1920, C=3, grids=[6, 20], eps=[.5, 1.5], source=_lib.SRC_VARIANCE)
+    # one-pass keeps (T/g)^2 * C u16 g-cell sums per tile in the workspace; two-pass keeps only keys/offsets
+    assert one.ws_per_frame > 2040 * 64 * 3 * 2
+    assert two.ws_per_frame < 20 * 1024

@@ -1,0 +1,274 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element on seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy import stats
+
+import oracle as O
+import paper_2511_04261_b300 as P
+from paper_2511_04261_b300 import synth
+from tests.gpu_util import REL_TOL, compare_records, gpu_release
+
+pytestmark = pytest.mark.gpu
+
+
+def _labels(rng, M, N, grids):
+    T = math.lcm(*grids)
+    return rng.integers(0, len(grids), size=(-(-M // T), -(-N // T)), dtype=np.uint8)
+
+
+# ------------------------------------------------------------------------------------------------------
+# Noise: Philox words bit-exact, Laplace draws within tolerance, KS
+# ------------------------------------------------------------------------------------------------------
+def test_philox_words_bit_exact_and_laplace():
+    rng = np.random.default_rng(1)
+    n = 4096
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64)
+    ctr[:4] = [[0, 0, 0, 0], [2**32 - 1] * 4, [1, 0, 0, 0], [0, 0, 0, 1]]
+    seed = 0x1234567890ABCDEF
+    sigma = 127.5
+    words, eta = P.dp_pix_debug_noise(seed, torch.from_numpy(ctr.astype(np.int64)).cuda(), sigma)
+    words = words.cpu().numpy()
+    eta = eta.cpu().numpy().astype(np.float64)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for i in range(n):
+        exp = O.philox4x32_10(ctr[i].astype(np.uint32), key)
+        assert np.array_equal(words[i].astype(np.uint32), exp), i
+        for j in range(4):
+            e = O.laplace_from_word(int(exp[j]), sigma)
+            assert abs(eta[i, j] - e) <= 1e-6 * abs(e) + 1e-7 * sigma
+
+
+def test_gpu_laplace_ks():
+    n = 50000
+    ctr = torch.zeros((n, 4), dtype=torch.int64, device="cuda")
+    ctr[:, 0] = torch.arange(n, device="cuda")
+    ctr[:, 1] = 5
+    _, eta = P.dp_pix_debug_noise(99, ctr, 1.0)
+    e = eta.cpu().numpy().reshape(-1).astype(np.float64)
+    assert stats.kstest(e, "laplace").pvalue > 0.01
+    assert np.mean(np.abs(e)) == pytest.approx(1.0, rel=0.02)
+
+
+# ------------------------------------------------------------------------------------------------------
+# Release parity across sources, grids, channels, paddings and record types
+# ------------------------------------------------------------------------------------------------------
+CASES_LABELS = [
+    (100, 130, 3, [24, 8], 0), (61, 67, 1, [6, 20], 0), (37, 53, 4, [4, 8, 16], 1), (70, 90, 3, [5], 0),
+    (33, 47, 3, [12, 6, 4], 0), (64, 64, 3, [32, 16, 8, 4], 1), (150, 97, 3, [2, 3], 0), (45, 200, 3, [1, 4], 0),
+]
+
+
+@pytest.mark.parametrize("M,N,C,grids,pad", CASES_LABELS)
+@pytest.mark.parametrize("dtype", [O.DT_F32, O.DT_U8, O.DT_SUM])
+def test_release_tile_labels(M, N, C, grids, pad, dtype):
+    rng = np.random.default_rng(M * 1000 + N + dtype)
+    img = rng.integers(0, 256, size=(M, N, C), dtype=np.uint8)
+    lab = _labels(rng, M, N, grids)
+    kw = dict(M=M, N=N, C=C, grids=grids, eps=[0.5 + 0.25 * i for i in range(len(grids))], pad_mode=pad,
+              source=O.SRC_TILE_LABELS, dtype=dtype, seed=12345, m=16)
+    _, _, recs = gpu_release(img, lab, **kw)
+    rec, means, sums, etas = O.release(img, lab, frame_idx=0, stream_id=0, **kw)
+    compare_records(recs[0], rec, means, sums, etas, dtype)
+
+
+@pytest.mark.parametrize("M,N,pad", [(200, 260, 0), (576, 768, 0), (131, 157, 1)])
+def test_release_mask(M, N, pad):
+    img, mask = synth.rect_frame(seed=1001 + M, M=M, N=N)
+    kw = dict(M=M, N=N, C=3, grids=[24, 8], eps=[1.0, 0.5], pad_mode=pad, source=O.SRC_MASK, dtype=O.DT_F32,
+              seed=1, m=16)
+    _, _, recs = gpu_release(img, mask, **kw)
+    rec, means, sums, etas = O.release(img, mask, **kw)
+    compare_records(recs[0], rec, means, sums, etas, O.DT_F32)
+
+
+@pytest.mark.parametrize("M,N", [(180, 250), (333, 421)])
+def test_release_matte(M, N):
+    img, alpha = synth.portrait(np.random.default_rng(M), M, N)
+    kw = dict(M=M, N=N, C=3, grids=[20, 6], eps=[1.5, 0.5], source=O.SRC_MATTE, dtype=O.DT_F32, seed=3, m=32,
+              matte_thr=0.5)
+    _, _, recs = gpu_release(img, alpha, **kw)
+    rec, means, sums, etas = O.release(img, alpha, **kw)
+    compare_records(recs[0], rec, means, sums, etas, O.DT_F32)
+
+
+@pytest.mark.parametrize("M,N,grids,eps", [
+    (200, 330, [32, 16, 8, 4], [2, 1, .5, .25]),     # g = 4: g-cell sums, one read of the image
+    (130, 250, [16, 8], [1, .5]),                     # g = 8
+    (121, 245, [6, 20], [.5, 1.5]),                   # g = 2: statistics pass, then a second read
+    (64, 96, [32, 32], [1, 1]),                       # g = 32 > 16: two passes
+])
+@pytest.mark.parametrize("dtype", [O.DT_F32, O.DT_SUM])
+def test_release_variance(M, N, grids, eps, dtype):
+    img = synth.moving_rect_clip(seed=7 + M, frames=1, M=M, N=N)[0]
+    kw = dict(M=M, N=N, C=3, grids=grids, eps=eps, source=O.SRC_VARIANCE, dtype=dtype, seed=2, m=16)
+    _, _, recs = gpu_release(img, None, **kw)
+    rec, means, sums, etas = O.release(img, None, **kw)
+    compare_records(recs[0], rec, means, sums, etas, dtype)
+
+
+def test_release_batch_frames_stream_and_frame_index():
+    rng = np.random.default_rng(3)
+    F, M, N = 5, 75, 110
+    imgs = rng.integers(0, 256, size=(F, M, N, 3), dtype=np.uint8)
+    kw = dict(M=M, N=N, C=3, grids=[32, 16, 8, 4], eps=[2, 1, .5, .25], source=O.SRC_VARIANCE, dtype=O.DT_F32,
+              seed=77, m=16)
+    _, _, recs = gpu_release(imgs, None, frame_idx0=7, stream_id=3, **kw)
+    for i in range(F):
+        rec, means, sums, etas = O.release(imgs[i], None, frame_idx=7 + i, stream_id=3, **kw)
+        h = compare_records(recs[i], rec, means, sums, etas, O.DT_F32)
+        assert h["frame_idx"] == 7 + i and h["stream_id"] == 3
+
+
+@pytest.mark.parametrize("pitch_extra,offset", [(13, 0), (16 * 5 - 0, 0), (3, 3)])
+def test_release_row_pitch_and_alignment(pitch_extra, offset):
+    rng = np.random.default_rng(pitch_extra + offset)
+    M, N, C = 90, 125, 3
+    pitch = N * C + pitch_extra
+    buf = rng.integers(0, 256, size=(M * pitch + offset + 64,), dtype=np.uint8)
+    img2d = buf[offset:offset + M * pitch].reshape(M, pitch)
+    lab = _labels(rng, M, N, [24, 8])
+    kw = dict(M=M, N=N, C=C, grids=[24, 8], eps=[1, .5], source=O.SRC_TILE_LABELS, dtype=O.DT_SUM, seed=4, m=16)
+    plan = P.Plan(pitch=pitch, **kw)
+    tb = torch.from_numpy(buf).cuda()
+    t = tb[offset:offset + M * pitch].view(M, pitch)
+    recs = plan.release(t, torch.from_numpy(lab).cuda())
+    got = P.dp_pix_store(recs[0])
+    rec, means, sums, etas = O.release(img2d, lab, pitch=pitch, **kw)
+    compare_records(got, rec, means, sums, etas, O.DT_SUM)
+
+
+def test_noise_free_release_is_block_mean():
+    rng = np.random.default_rng(8)
+    M, N = 97, 131
+    img = rng.integers(0, 256, size=(M, N, 3), dtype=np.uint8)
+    lab = _labels(rng, M, N, [24, 8])
+    kw = dict(M=M, N=N, C=3, grids=[24, 8], eps=[1, 1], source=O.SRC_TILE_LABELS, dtype=O.DT_F32, noise_free=True)
+    plan, recs_d, recs = gpu_release(img, lab, **kw)
+    rec, means, sums, etas = O.release(img, lab, **kw)
+    compare_records(recs[0], rec, means, sums, etas, O.DT_F32)
+    out = P.dp_pix_reconstruct(recs_d, M, N, 3, P.OUT_F32).cpu().numpy()[0]
+    assert np.allclose(out, O.reconstruct(rec, 2), rtol=0, atol=255 * 2**-23)
+
+
+# ------------------------------------------------------------------------------------------------------
+# Reconstruction: bit-exact against the oracle's reconstruction of the same (GPU) record
+# ------------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("M,N,C,grids,src", [
+    (100, 130, 3, [24, 8], O.SRC_TILE_LABELS), (61, 67, 1, [6, 20], O.SRC_TILE_LABELS),
+    (200, 330, 3, [32, 16, 8, 4], O.SRC_VARIANCE), (37, 53, 4, [4, 8, 16], O.SRC_TILE_LABELS),
+    (45, 200, 3, [1, 4], O.SRC_TILE_LABELS),
+])
+@pytest.mark.parametrize("dtype", [O.DT_F32, O.DT_U8, O.DT_SUM])
+def test_reconstruct_bit_exact(M, N, C, grids, src, dtype):
+    rng = np.random.default_rng(M + N + C)
+    F = 3
+    imgs = rng.integers(0, 256, size=(F, M, N, C), dtype=np.uint8)
+    lab = np.stack([_labels(rng, M, N, grids) for _ in range(F)]) if src == O.SRC_TILE_LABELS else None
+    kw = dict(M=M, N=N, C=C, grids=grids, eps=[0.5] * len(grids), source=src, dtype=dtype, seed=5, m=16)
+    plan, recs_d, recs = gpu_release(imgs, lab, **kw)
+    for ot, npdt in [(P.OUT_U8, np.uint8), (P.OUT_F32, np.float32)]:
+        out = P.dp_pix_reconstruct(recs_d, M, N, C, ot).cpu().numpy()
+        for i in range(F):
+            exp = O.reconstruct(np.frombuffer(recs[i], np.uint8), 0 if ot == P.OUT_U8 else 1)
+            assert np.array_equal(out[i], exp), (i, ot)
+    assert P.dp_pix_status() == 0
+
+
+def test_reconstruct_strided_output():
+    rng = np.random.default_rng(11)
+    M, N = 50, 70
+    img = rng.integers(0, 256, size=(M, N, 3), dtype=np.uint8)
+    lab = _labels(rng, M, N, [8, 4])
+    plan, recs_d, recs = gpu_release(img, lab, M=M, N=N, C=3, grids=[8, 4], eps=[1, 1], seed=1)
+    big = torch.zeros((M, N + 7, 3), dtype=torch.uint8, device="cuda")
+    view = big[:, 3:3 + N, :]
+    P.dp_pix_reconstruct(recs_d[0], M, N, 3, P.OUT_U8, out=view)
+    exp = O.reconstruct(np.frombuffer(recs[0], np.uint8), 0)
+    got = big.cpu().numpy()
+    assert np.array_equal(got[:, 3:3 + N], exp)
+    assert not got[:, :3].any() and not got[:, 3 + N:].any()
+
+
+# ------------------------------------------------------------------------------------------------------
+# Edge cases
+# ------------------------------------------------------------------------------------------------------
+def test_edge_one_pixel_and_exact_tile():
+    for (M, N, grids) in [(1, 1, [1]), (24, 24, [24, 8]), (8, 8, [8]), (2, 3, [2])]:
+        pad = 0
+        rng = np.random.default_rng(M * N)
+        img = rng.integers(0, 256, size=(M, N, 3), dtype=np.uint8)
+        lab = _labels(rng, M, N, grids)
+        kw = dict(M=M, N=N, C=3, grids=grids, eps=[1] * len(grids), source=O.SRC_TILE_LABELS, dtype=O.DT_F32,
+                  seed=9, pad_mode=pad)
+        plan, recs_d, recs = gpu_release(img, lab, **kw)
+        rec, means, sums, etas = O.release(img, lab, **kw)
+        compare_records(recs[0], rec, means, sums, etas, O.DT_F32)
+        out = P.dp_pix_reconstruct(recs_d, M, N, 3).cpu().numpy()[0]
+        assert np.array_equal(out, O.reconstruct(np.frombuffer(recs[0], np.uint8), 0))
+
+
+def test_zero_frames_is_noop_and_bad_labels_flag_status():
+    plan = P.Plan(M=32, N=32, C=3, grids=[16], eps=[1])
+    img = torch.zeros((0, 32, 32, 3), dtype=torch.uint8, device="cuda")
+    recs = plan.release(img, torch.zeros((0, 2, 2), dtype=torch.uint8, device="cuda"))
+    assert recs.shape[0] == 0
+    img = torch.zeros((32, 32, 3), dtype=torch.uint8, device="cuda")
+    bad = torch.full((2, 2), 5, dtype=torch.uint8, device="cuda")  # label >= K
+    plan.release(img, bad)
+    with pytest.raises(P.DppixError) as e:
+        P.dp_pix_status()
+    assert e.value.code == -8
+    assert P.dp_pix_status() == 0  # cleared
+
+
+def test_reconstruct_rejects_malformed_record():
+    rec = torch.zeros((1, 4096), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((1, 8, 8, 3), dtype=torch.uint8, device="cuda")
+    P.dp_pix_reconstruct(rec, 8, 8, 3, out=out)
+    with pytest.raises(P.DppixError):
+        P.dp_pix_status()
+    assert not out.any()
+
+
+# ------------------------------------------------------------------------------------------------------
+# Full-size workloads at the benchmark's launch configuration, sampled against the oracle
+# ------------------------------------------------------------------------------------------------------
+def test_config1_full_frame():
+    """768 x 576 RGB, 6 rectangles, fg b=8 eps=.5, bg b=24 eps=1, m=16, seed 1: complete record + image."""
+    img, mask = synth.rect_frame(seed=1001)
+    kw = dict(M=576, N=768, C=3, grids=[24, 8], eps=[1.0, 0.5], source=O.SRC_MASK, dtype=O.DT_F32, seed=1, m=16)
+    plan, recs_d, recs = gpu_release(img, mask, **kw)
+    rec, means, sums, etas = O.release(img, mask, **kw)
+    compare_records(recs[0], rec, means, sums, etas, O.DT_F32)
+    out = P.dp_pix_reconstruct(recs_d, 576, 768, 3).cpu().numpy()[0]
+    assert np.array_equal(out, O.reconstruct(np.frombuffer(recs[0], np.uint8), 0))
+
+
+def test_config2_full_clip_sampled():
+    """64 frames 1920 x 1080, 4 variance classes (b 32/16/8/4, eps 2/1/.5/.25), one launch sequence as in the
+    benchmark; frames 0, 31 and 63 compared completely with the oracle, invariants on all frames."""
+    F, M, N = 64, 1080, 1920
+    clip = synth.moving_rect_clip(seed=1002, frames=F, M=M, N=N)
+    kw = dict(M=M, N=N, C=3, grids=[32, 16, 8, 4], eps=[2, 1, .5, .25], source=O.SRC_VARIANCE, dtype=O.DT_F32,
+              seed=2, m=16)
+    plan = P.Plan(**kw)
+    frames = torch.from_numpy(clip).cuda()
+    recs_d = plan.release(frames, None)
+    outs = P.dp_pix_reconstruct(recs_d, M, N, 3)
+    torch.cuda.synchronize()
+    assert P.dp_pix_status() == 0
+    for i in [0, 31, 63]:
+        got = P.dp_pix_store(recs_d[i])
+        rec, means, sums, etas = O.release(clip[i], None, frame_idx=i, **kw)
+        compare_records(got, rec, means, sums, etas, O.DT_F32)
+        assert np.array_equal(outs[i].cpu().numpy(), O.reconstruct(np.frombuffer(got, np.uint8), 0))
+    # every frame: 2040 tiles in four equal classes of 510, record size by the C4 formula
+    a16 = lambda x: (x + 15) // 16 * 16
+    for i in range(F):
+        h = P.record_header(P.dp_pix_store(recs_d[i]))
+        assert h["count"] == [510, 510, 510, 510]
+        exp = 512 + a16(34 * 4 * 4) + a16(2040) + sum(a16(510 * (32 // b) ** 2 * 12) for b in [32, 16, 8, 4])
+        assert h["total_bytes"] == exp
