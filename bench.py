@@ -87,7 +87,7 @@ class ClockSampler:
             self.nv, self.h = nv, h
             self.max_mhz = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
             self.ok = True
-        except Exception as e:  # no NVML: report what is known
+        except Exception as e:  # no NVML: fall back to nvidia-smi around the timed region
             self.err = repr(e)
 
     def _reasons(self):
@@ -114,9 +114,27 @@ class ClockSampler:
         self._t = threading.Thread(target=self._run, daemon=True)
         self._t.start()
 
+    @staticmethod
+    def smi_query():
+        import subprocess
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            out = subprocess.run(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits"],
+                                 capture_output=True, text=True, timeout=20).stdout.strip().splitlines()
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+            row = out[int(vis) if vis.isdigit() and int(vis) < len(out) else 0].split(",")
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = [n for n, v in zip(names, row[2:]) if v.strip() == "Active"]
+            return float(row[0]), float(row[1]), reasons
+        except Exception:
+            return None, None, []
+
     def stop(self):
         if not self.ok:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "NVML unavailable"}
+            sm, smax, reasons = self.smi_query()
+            return {"sm_mhz": sm, "sm_max_mhz": smax, "reasons": reasons,
+                    "note": "NVML unavailable (%s); nvidia-smi queried right after the timed region" % self.err}
         self._stop.set()
         self._t.join()
         s = self.samples

@@ -2,12 +2,12 @@
  * dppix.h -- C ABI of libdppix: region-adaptive differentially private pixelization on NVIDIA B300.
  *
  * The calls follow the paper's statement of the problem (Alg. 3 inputs: image I, grid sizes, privacy
- * budget eps, max variation m, region mask; outputs: the compact noisy-statistics record of Table 3 and
+ * budget eps, max variation m, region mask; outputs: the compact noisy-statistics record of Table IV and
  * the restored image I').  A frame is M x N pixels of C interleaved uint8 samples (C = 1..4).  The frame
  * is split into K <= 8 regions; region r gets grid side b_r and budget eps_r, and every b_r x b_r cell of
- * it is released as clip(mean + Laplace(0, sigma_r), 0, R) with sigma_r = R*m / (b_r^2 eps_r) (Eq. 12,
+ * it is released as clip(mean + Laplace(0, sigma_r), 0, R) with sigma_r = R*m / (b_r^2 eps_r) (Eq. 11,
  * Eq. 8).  Regions live on square tiles of side T = lcm{b_r}; each tile belongs to one region (the
- * paper's b x b grid with its subgrids, Eq. 14).
+ * paper's b x b grid with its subgrids, Eq. 16).
  *
  * Conventions shared by every call:
  *  - Every pointer named d_* is a device pointer owned by the caller; the library never allocates device
@@ -109,7 +109,7 @@ typedef struct dp_pix_sizes {
     double sigma[DP_PIX_MAX_REGIONS]; /* Laplace scale of each region */
 } dp_pix_sizes;
 
-/* The 512-byte record header, little-endian, at the start of every record (Table 3 generalised).
+/* The 512-byte record header, little-endian, at the start of every record (Table IV generalised).
  * The tile-row index, map and payload follow at the offsets it gives. */
 typedef struct dp_pix_record_header {
     char magic[4];                /* "DPPX" */
@@ -149,7 +149,7 @@ DPPIX_API int dp_pix_plan_destroy(dp_pix_plan_t plan);
  * key (seed mod 2^32, seed >> 32) and counter (cell index in the frame's padded b_r-grid,
  * r | stream_id << 8, frame mod 2^32, frame >> 32) -- word ch for channel ch, inverse-CDF sampler
  * eta = +-sigma_r * ln((k + 1/2) / 2^31) -- clips to [0, R] and writes one self-describing record per
- * frame (Table 3 generalised).
+ * frame (Table IV generalised).
  *   d_frames:         frame i starts at d_frames + i*frame_stride (bytes); rows are row_pitch apart.
  *   d_region_src:     per the plan's region_source: u8 labels [G_R][G_C] (src_pitch ignored, frames
  *                     src_frame_stride apart), u8 mask / f32 matte rows src_pitch bytes apart, or NULL
@@ -188,7 +188,7 @@ DPPIX_API int dp_pix_store_batch(const void *d_records, int64_t record_stride, u
                                  int64_t dst_stride, uint64_t *written, void *cuda_stream);
 
 /*
- * Rebuilds the pixelized frames from their records alone (Sec. V-E: the stored metadata suffice;
+ * Rebuilds the pixelized frames from their records alone (Sec. VI-F: the stored metadata suffice;
  * Alg. 2 steps 10-11): every pixel of a cell takes the cell's stored value; the padding is cropped.
  * Geometry is read from each record's header on the device, so no plan and no host sync are needed.
  *   d_records:   n_records records, record_stride bytes apart (>= 512, multiple of 16); record_stride is

@@ -8,14 +8,14 @@
  *
  * Everything is computed in double precision with exact 64-bit integer pixel sums, cell by cell, in the
  * order the paper states the method:
- *   - pixelization: b x b cell means broadcast over the cell (Sec. III-A, Eq. 1-4);
- *   - Laplace mechanism: sigma = sensitivity / eps, eta ~ Laplace(0, sigma) (Sec. III-B, Eq. 7-9);
- *   - sensitivity of the pixelization 255*m/b^2 -- here R*m/b^2 for a value range R (Sec. III-D, Eq. 12);
- *   - noisy mean clipped to [0, R] (Sec. III-D; Alg. 1 and Alg. 2);
+ *   - pixelization: b x b cell means broadcast over the cell (Sec. IV-A, Eq. 1-4);
+ *   - Laplace mechanism: sigma = sensitivity / eps, eta ~ Laplace(0, sigma) (Sec. IV-B, Eq. 7-9);
+ *   - sensitivity of the pixelization 255*m/b^2 -- here R*m/b^2 for a value range R (Sec. IV-D, Eq. 11);
+ *   - noisy mean clipped to [0, R] (Sec. IV-D; Alg. 1 and Alg. 2);
  *   - mirror padding to whole grids, mean, noise, clip, repeat, crop (Alg. 2);
  *   - mask mean per grid, simple (> 1/2) / complex (<= 1/2) split, per-region grid and noise (Alg. 3,
- *     Sec. V-A..D, Eq. 14-15), generalised to K regions on tiles of side T = lcm{b_r};
- *   - compact record of noisy statistics and reconstruction by broadcast (Table 2, Table 3, Sec. V-E).
+ *     Sec. VI-A..D, Eq. 16-17), generalised to K regions on tiles of side T = lcm{b_r};
+ *   - compact record of noisy statistics and reconstruction by broadcast (Table III, Table IV, Sec. VI-F).
  *
  * Readings of points the paper leaves open (channels, tie rule, sampler, keying, record layout, variance
  * classes, soft layer) are the ones listed for this build; each function names the reading it follows.
@@ -149,8 +149,8 @@ static uint64_t align16(uint64_t x) { return (x + 15u) & ~(uint64_t)15u; }
 
 static int dtype_bytes(int dtype) { return dtype == 1 ? 1 : 4; }
 
-/* Sec. IV Alg. 2 steps 1-3 and Alg. 3 steps 1-2, with T = lcm{b_r} as the tile (the paper's b when one
- * region's grid divides the other's, Eq. 14). sigma_r = R*m/(b_r^2 eps_r) (Eq. 12 with Eq. 8). */
+/* Sec. V-B: Alg. 2 steps 1-3 and Alg. 3 steps 1-2, with T = lcm{b_r} as the tile (the paper's b when one
+ * region's grid divides the other's, Eq. 16). sigma_r = R*m/(b_r^2 eps_r) (Eq. 11 with Eq. 8). */
 int ora_geometry(const ora_desc *d, ora_geom *g)
 {
     if (!d || !g) return ORA_E_INVALID;
@@ -335,7 +335,7 @@ static int64_t cell_sum(const ora_desc *d, const uint8_t *img, int64_t y0, int64
 }
 
 /*
- * Full release of one frame into a record (Alg. 3 generalised to K regions; record per Table 3).
+ * Full release of one frame into a record (Alg. 3 generalised to K regions; record per Table IV).
  * Record order: region-major (the paper stores mu'_G, then mu'_Gs), then tiles of that region in row-major
  * tile order, then cells row-major inside the tile, then the C channels.
  * Noise key (sampler reading): Philox4x32-10 with key (seed mod 2^32, seed >> 32) and counter
@@ -453,7 +453,7 @@ int ora_release(const ora_desc *d, const uint8_t *img, const void *src, int64_t 
 }
 
 /* ------------------------------------------------------------------------------------------------ */
-/* Reconstruction from a record alone (Sec. V-E: metadata suffice; Alg. 2 steps 10-11).              */
+/* Reconstruction from a record alone (Sec. VI-F: metadata suffice; Alg. 2 steps 10-11).              */
 /* ------------------------------------------------------------------------------------------------ */
 
 /* Reads the geometry out of a record header; checks the fields the reconstruction relies on. */
@@ -477,6 +477,7 @@ int ora_record_info(const uint8_t *rec, uint64_t len, int32_t out[16])
 /*
  * out_type 0: u8 image M x N x C (round half to even of the stored value), out_pitch bytes per row.
  * out_type 1: f32 image, out_pitch bytes per row.  out_type 2: f64 image.
+ * A record of exact sums (dtype 2) reconstructs to the noise-free block means.
  * The tile-row index stored in the record is recomputed from the map and must agree.
  */
 int ora_reconstruct(const uint8_t *rec, uint64_t len, int out_type, void *out, int64_t out_pitch)
@@ -527,7 +528,8 @@ int ora_reconstruct(const uint8_t *rec, uint64_t len, int out_type, void *out, i
                 double v;
                 if (dtype == 0) v = (double)get_f32(src);
                 else if (dtype == 1) v = (double)*src;
-                else v = (double)get_u32(src);
+                else /* exact-sum record: the noise-free mean S / b^2 (Eq. 2), in the f32 precision of the means */
+                    v = (double)((float)get_u32(src) / (float)(b[r] * b[r]));
                 if (out_type == 0) {
                     ((uint8_t *)out)[y * out_pitch + x * C + ch] = (uint8_t)rint(v);
                 } else if (out_type == 1) {

@@ -181,7 +181,7 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
         g.grid[r] = b;
         g.cells_side[r] = (int)(T / b);
         g.eps[r] = d->eps[r];
-        // Eq. 12 with Eq. 8: sigma = R m / (b^2 eps)
+        // Eq. 11 with Eq. 8: sigma = R m / (b^2 eps)
         g.sigma[r] = d->value_range * d->m / ((double)b * (double)b * d->eps[r]);
         g.sigma_f[r] = (float)g.sigma[r];
         g.b2_f[r] = (float)(b * b);

@@ -18,7 +18,7 @@ constexpr int kMaxRankTiles = 16384;     // VARIANCE: tiles of one frame ranked 
 constexpr int kMaxFrameTiles = 200000;   // tiles of one frame (the map is finalised in shared memory)
 constexpr int kHeaderBytes = DP_PIX_RECORD_HEADER_BYTES;
 
-// Geometry and constants of a plan (Alg. 2 steps 1-3, Alg. 3 steps 1-2, Eq. 12).
+// Geometry and constants of a plan (Alg. 2 steps 1-3, Alg. 3 steps 1-2, Eq. 11).
 struct Geom {
     int32_t M, N, C, K, T, GR, GC, PR, PC;
     int32_t pad_mode, source, dtype, noise_free;
@@ -114,7 +114,7 @@ __device__ __forceinline__ float laplace_from_word(uint32_t x, float sigma) {
     return upper ? -sigma * lnt : sigma * lnt;
 }
 
-// Clipped noisy mean (Sec. III-D; Alg. 2 steps 6-9): v = min(max(S / b^2 + eta, 0), R).
+// Clipped noisy mean (Sec. IV-D; Alg. 2 steps 6-9): v = min(max(S / b^2 + eta, 0), R).
 __device__ __forceinline__ float noisy_mean(uint32_t S, float b2, float eta, float R) {
     const float mu = __fdiv_rn(__uint2float_rn(S), b2);
     const float v = __fadd_rn(mu, eta);

@@ -1,7 +1,7 @@
 // k_frame.cu -- per-frame kernels: region-map finalisation and variance-quantile ranking.
 //
 // One CTA per frame.  Given the frame's u8 tile -> region map, the CTA counts tiles per region, lays out
-// the region-major payload (Table 3: mu'_G then mu'_Gs, generalised to K regions), writes each tile's
+// the region-major payload (Table IV: mu'_G then mu'_Gs, generalised to K regions), writes each tile's
 // payload byte offset to the workspace, writes the tile-row index and the 512-byte header into the
 // record.  The rank kernel first builds the map from the per-tile variance keys (exact integers) by a
 // bitonic sort of (key, tile index) in shared memory.
@@ -141,6 +141,15 @@ __device__ void finalize_frame(const Geom &g, const CallArgs &a, uint32_t f, con
     if (write_map) {
         uint8_t *map = rec + g.map_offset;
         for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) map[i] = map_s[i];
+    }
+    // zero the alignment gaps so that a record is a deterministic byte string
+    const uint64_t row_end = g.rowidx_offset + (uint64_t)g.GR * g.K * 4;
+    for (uint64_t i = row_end + threadIdx.x; i < g.map_offset; i += blockDim.x) rec[i] = 0;
+    for (uint64_t i = g.map_offset + n + threadIdx.x; i < g.payload_offset; i += blockDim.x) rec[i] = 0;
+    if (threadIdx.x < (unsigned)g.K) {
+        const int r = threadIdx.x;
+        const uint64_t end = sm.roff[r] + (uint64_t)sm.count[r] * sm.tile_bytes[r];
+        for (uint64_t i = end; i < align16_u64(end); ++i) rec[i] = 0;
     }
 }
 

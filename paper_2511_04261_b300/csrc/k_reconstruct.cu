@@ -1,4 +1,4 @@
-// k_reconstruct.cu -- rebuild pixelized frames from their records alone (Sec. V-E; Alg. 2 steps 10-11).
+// k_reconstruct.cu -- rebuild pixelized frames from their records alone (Sec. VI-F; Alg. 2 steps 10-11).
 //
 // Geometry comes from each record's header on the device, so one launch serves any mix of records.
 // Work item = (record, tile row, segment of tiles).  All output rows of a segment that lie in the same
@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(kThreads)
             // widest unit that keeps every row segment start aligned
             int U = out_align;
             while (U > 1 && (((int64_t)rg.SR * T * C * oes) % U != 0)) U >>= 1;
+            if (U == 2) U = 1;  // copies move 16, 8, 4 or 1 bytes
             const int nu = row_bytes / U;
             const int tail0 = nu * U;
             const int jmax = min(T, rg.M - ty * T);

@@ -44,9 +44,13 @@ def compare_records(rec_gpu: bytes, rec_ora: np.ndarray, means, sums, etas, dtyp
             np.testing.assert_allclose(hg[k], ho[k], rtol=1e-15)
         else:
             assert hg[k] == ho[k], (k, hg[k], ho[k])
-    # tile-row index and map: bit-exact
+    # header, tile-row index, map and the alignment gaps: bit-exact
     pay = ho["payload_offset"]
-    assert np.array_equal(g[512:pay], o[512:pay])
+    assert np.array_equal(g[:pay], o[:pay])
+    es = 1 if dtype == O.DT_U8 else 4
+    for r in range(ho["K"]):  # zero gap after each region's payload
+        end = ho["region_offset"][r] + ho["count"][r] * ho["cells_side"][r] ** 2 * ho["C"] * es
+        assert not g[end:(end + 15) // 16 * 16].any()
     vg = O.record_payload(g)
     vo = O.record_payload(o)
     if dtype == O.DT_SUM:

@@ -91,7 +91,7 @@ def test_laplace_ks_and_scale():
 
 
 # ------------------------------------------------------------------------------------------------------
-# Geometry, padding and sensitivity (Eq. 12, Alg. 2 steps 1-4, Alg. 3 steps 1-3, Eq. 14-15)
+# Geometry, padding and sensitivity (Eq. 11, Alg. 2 steps 1-4, Alg. 3 steps 1-3, Eq. 16-17)
 # ------------------------------------------------------------------------------------------------------
 def test_reflect_matches_numpy_pad():
     for n in range(1, 40):
@@ -110,12 +110,12 @@ def test_geometry_closed_forms():
         settings = json.load(f)["settings"]
     for s in settings:
         g = O.geometry(M=s["M"], N=s["N"], C=1, grids=[s["b"]], eps=[s["eps"]], m=s["m"])
-        # Eq. 12 with Eq. 8: sigma = 255 m / (b^2 eps)
+        # Eq. 11 with Eq. 8: sigma = 255 m / (b^2 eps)
         assert g["sigma"][0] * s["b"] ** 2 * s["eps"] == pytest.approx(255 * s["m"], rel=1e-15)
-        # G_R = ceil(M / b), P_R = G_R b - M (Table 1, Alg. 3 steps 1-2)
+        # G_R = ceil(M / b), P_R = G_R b - M (Table II, Alg. 3 steps 1-2)
         assert g["GR"] == -(-s["M"] // s["b"]) and g["GC"] == -(-s["N"] // s["b"])
         assert g["PR"] == g["GR"] * s["b"] - s["M"] and g["PC"] == g["GC"] * s["b"] - s["N"]
-    # Eq. 14-15: b = n s_b, Delta = Delta_s / n^2, T = b (the simple grid) when s_b divides b
+    # Eq. 16-17: b = n s_b, Delta = Delta_s / n^2, T = b (the simple grid) when s_b divides b
     for b, n in [(32, 8), (24, 3), (16, 4), (128, 8), (12, 1)]:
         sb = b // n
         g = O.geometry(M=300, N=400, C=3, grids=[b, sb], eps=[0.5, 0.5], m=32)
@@ -231,6 +231,20 @@ def test_noise_free_reconstruction_is_block_mean(grids):
     assert np.array_equal(got8, np.rint(exp.astype(np.float32)).astype(np.uint8))
 
 
+def test_sum_record_reconstructs_block_mean():
+    """A record of exact sums rebuilds the noise-free block means (Eq. 2-3), in f32 like the means."""
+    rng = np.random.default_rng(31)
+    M, N, grids = 61, 77, [6, 20]
+    img = rng.integers(0, 256, size=(M, N, 3), dtype=np.uint8)
+    labels = rng.integers(0, 2, size=(2, 2), dtype=np.uint8)
+    rec, means, sums, eta = O.release(img, labels, grids=grids, eps=[1, 1], source=O.SRC_TILE_LABELS,
+                                      dtype=O.DT_SUM)
+    exp = _np_block_mean_image(img, labels, grids, 60, 0)
+    got = O.reconstruct(rec, 1)
+    assert np.allclose(got, exp.astype(np.float32), rtol=2**-23, atol=0)
+    assert np.array_equal(O.reconstruct(rec, 0), np.rint(exp.astype(np.float32)).astype(np.uint8))
+
+
 def test_uniform_special_cases():
     """n = 1 (b = s_b) makes Alg. 3 equal Alg. 2; b = 1 keeps every sample (no pixelization)."""
     rng = np.random.default_rng(2)
@@ -315,7 +329,7 @@ def test_variance_ties_ranked_by_tile_index():
 
 
 # ------------------------------------------------------------------------------------------------------
-# Record (Table 2 / Table 3, C4 size formula) and reconstruction
+# Record (Table III / Table IV, size formula of Sec. VI-F) and reconstruction
 # ------------------------------------------------------------------------------------------------------
 def test_record_size_formula_and_layout():
     rng = np.random.default_rng(4)
@@ -340,7 +354,7 @@ def test_record_size_formula_and_layout():
 
 
 def test_reconstruct_broadcasts_record_values():
-    """Reconstruction puts each stored value on every pixel of its cell (Sec. V-E), built here from the
+    """Reconstruction puts each stored value on every pixel of its cell (Sec. VI-F), built here from the
     record's documented order by numpy repeat."""
     rng = np.random.default_rng(5)
     M, N, grids = 64, 90, [16, 4]
@@ -363,7 +377,7 @@ def test_reconstruct_broadcasts_record_values():
 
 
 # ------------------------------------------------------------------------------------------------------
-# Privacy invariants: noise scale, parallel composition (Thm 1, 3, 5), sensitivity (Eq. 12)
+# Privacy invariants: noise scale, parallel composition (Thm 1, 3, 5), sensitivity (Eq. 11)
 # ------------------------------------------------------------------------------------------------------
 def test_noise_residuals_are_laplace_with_region_scale():
     rng = np.random.default_rng(6)
@@ -409,7 +423,7 @@ def test_parallel_composition_cells_independent():
 
 def test_sensitivity_bound():
     """Neighbouring images differing in at most m samples by at most 255 change the noise-free
-    pixelization vector by at most 255 m / b^2 in L1 (Eq. 12), away from mirrored samples."""
+    pixelization vector by at most 255 m / b^2 in L1 (Eq. 11), away from mirrored samples."""
     rng = np.random.default_rng(10)
     M, N, b, m = 64, 64, 8, 16
     img = rng.integers(0, 256, size=(M, N, 1), dtype=np.uint8)
