@@ -170,6 +170,27 @@ DPPIX_API int dp_pix_release(dp_pix_plan_t plan, const void *d_frames, int64_t f
                    void *cuda_stream);
 
 /*
+ * dp_pix_release without a workspace argument, for callers that cannot allocate device memory: code
+ * running while a CUDA graph is captured (cudaMalloc is not allowed there), plug-ins whose host framework
+ * owns every device allocation and passes in only inputs and outputs, and real-time loops that must not
+ * enter an allocator.  The paper has no counterpart; this is a deployment convenience.
+ *   Arguments, results and errors are those of dp_pix_release; the workspace is a 16 MiB array built into
+ *   the library (each GPU that loads the library holds it until the process exits).  A call whose frames
+ *   need more (n_frames * sizes.workspace_per_frame > 16 MiB) is rejected with DP_PIX_E_BUFFER_TOO_SMALL
+ *   and a message; nothing is launched.  This entry point calls no cudaMalloc, cudaFree or other allocating
+ *   routine.
+ *   The first call on a device looks up that device's address of the array (cudaGetSymbolAddress); make
+ *   that first call before any stream capture.
+ *   Every call shares the one array and it keeps the last call's contents (the kernels overwrite every
+ *   byte they read, so nothing needs clearing).  Calls whose work overlaps on the GPU (different streams,
+ *   or host threads without ordering) race on the array: order them on one stream.
+ */
+DPPIX_API int dp_pix_release_noalloc(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
+                                     const void *d_region_src, int64_t src_pitch, int64_t src_frame_stride,
+                                     uint32_t n_frames, uint32_t stream_id, uint64_t frame_idx0, void *d_records,
+                                     int64_t record_stride, void *cuda_stream);
+
+/*
  * Copies one record's used bytes (header total_bytes, <= capacity) from device memory to `dst` (host if
  * dst_is_host, else device) and writes that count to *written.  Synchronizes on cuda_stream to read the
  * header.  Errors: BAD_RECORD, BUFFER_TOO_SMALL (cap < total_bytes), CUDA.

@@ -109,6 +109,10 @@ int sm_count() {
     return cached[dev];
 }
 
+uint64_t plan_ws_per_frame(const dp_pix_plan_s *plan) { return plan ? plan->g.ws_per_frame : 0; }
+
+int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 int32_t *status_word() {
     static int32_t *cached[64] = {nullptr};
     int dev = 0;

@@ -154,5 +154,10 @@ void prof_begin(const char *name, cudaStream_t s);
 void prof_end(const char *name, cudaStream_t s);
 int sm_count();
 int32_t *status_word();  // device address of the status word on the current device (nullptr on failure)
+}  // namespace dppix
+struct dp_pix_plan_s;
+namespace dppix {
+uint64_t plan_ws_per_frame(const dp_pix_plan_s *plan);  // workspace bytes per frame of a plan (0 for NULL)
+int set_last_error(int code, const char *msg);          // sets this thread's dp_pix_last_error(), returns code
 
 }  // namespace dppix
