@@ -218,9 +218,9 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     if (g.source == DP_PIX_SRC_VARIANCE) off = a256(off + 8ull * ntiles);
     g.ws_gsum = off;
     if (g.var_onepass) {
-        const uint64_t per = (uint64_t)(T / g.g) * (T / g.g) * g.C;
-        g.gsum_per_tile = (uint32_t)((per + 7) & ~7ull);
-        off = a256(off + 2ull * ntiles * g.gsum_per_tile);
+        g.gx_cells = (int)(g.GC * T / g.g);
+        g.gy_cells = (int)(g.GR * T / g.g);
+        off = a256(off + 2ull * (uint64_t)g.gx_cells * g.gy_cells * g.C);
     }
     g.ws_per_frame = off;
     // staged segment: S tiles of one tile row, S*T*C a multiple of 16 when possible
@@ -238,10 +238,6 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     g.seg_per_row = (g.GC + S - 1) / S;
     g.seg_rowstride = (int)a16((uint64_t)S * TC);
     g.vbands = vb_rel;
-    if (g.var_onepass) {
-        int E = (int)(8192 / (g.gsum_per_tile * 2));
-        g.emit_tiles = E < 1 ? 1 : (E > 64 ? 64 : E);
-    }
     return DP_PIX_OK;
 }
 

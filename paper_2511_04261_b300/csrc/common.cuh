@@ -42,13 +42,12 @@ struct Geom {
     uint64_t rowidx_offset, map_offset, payload_offset, record_cap;
     // workspace layout, per frame
     uint64_t ws_per_frame, ws_tileoff, ws_keys, ws_gsum;
-    uint32_t gsum_per_tile;           // u16 values per tile: (T/g)^2 * C
+    int32_t gx_cells, gy_cells;       // g-image: (GR*T/g) rows of (GC*T/g) g-cells, C u16 sums each
     // launch shapes
     int32_t seg_tiles;                // tiles per staged segment of a tile row
     int32_t seg_per_row;              // ceil(GC / seg_tiles)
     int32_t seg_rowstride;            // bytes per staged row (multiple of 16)
     int32_t vbands;                   // max bands of a staged tile = T / b_min (or T / g for stats)
-    int32_t emit_tiles;               // tiles per CTA in the g-cell emit kernel
 };
 
 // Per-call arguments of a release.
@@ -141,6 +140,7 @@ cudaError_t launch_finalize_labels(const Geom &g, const CallArgs &a, cudaStream_
 cudaError_t launch_finalize_map(const Geom &g, const CallArgs &a, cudaStream_t s);
 cudaError_t launch_release(const Geom &g, const CallArgs &a, cudaStream_t s);
 cudaError_t launch_tile_stats(const Geom &g, const CallArgs &a, cudaStream_t s);
+cudaError_t launch_tile_stats_fast(const Geom &g, const CallArgs &a, cudaStream_t s);  // NotSupported: no instance
 cudaError_t launch_rank(const Geom &g, const CallArgs &a, cudaStream_t s);
 cudaError_t launch_emit(const Geom &g, const CallArgs &a, cudaStream_t s);
 cudaError_t launch_reconstruct(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out,

@@ -1,20 +1,29 @@
 // k_reconstruct.cu -- rebuild pixelized frames from their records alone (Sec. VI-F; Alg. 2 steps 10-11).
 //
 // Geometry comes from each record's header on the device, so one launch serves any mix of records.
-// Work item = (record, tile row, segment of tiles).  All output rows of a segment that lie in the same
-// cell band of every tile are identical, so the CTA builds that row once in shared memory (each pixel
-// takes its cell's stored value; u8 output rounds half to even) and streams it to every row of the band
-// with the widest aligned stores.  Rows and columns past M, N (the padding) are cropped.
+// Work item = (record, tile row, segment of tiles).  Every pixel of a cell takes the cell's stored value
+// (u8 output rounds half to even); rows and columns past M, N (the padding) are cropped.
+//
+// Fast path (records with the launch's channel count, 16-byte aligned output rows): the segment -- a whole
+// tile row when it fits -- has its cell values converted once into shared memory; each thread owns
+// 16-byte columns of the output rows, assembles its vector from the cells it covers, and stores the same
+// vector to every row of the current cell band before rebuilding it, so the write phase has no barrier
+// and every warp store is coalesced.
+// Generic path (anything else): the CTA builds each distinct output row in shared memory and copies it out
+// with the widest aligned stores.
 #include "common.cuh"
 
 namespace dppix {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kRowBytes = 2048;  // shared-memory row pattern
+constexpr int kRowBytes = 2048;     // generic path: shared-memory row pattern
+constexpr int kStageBytes = 32768;  // fast path: staged cell values of one segment
+constexpr int kMaxSegPx = 2048;     // fast path: pixel columns of one segment
+constexpr int kMaxSegTiles = 64;    // tiles of one segment
 
 struct RecGeom {
-    int32_t ok;
+    int32_t ok, fast;
     int32_t M, N, C, T, K, GR, GC, dtype, es, SR, nseg;
     int32_t grid[kMaxK];
     uint32_t count[kMaxK];
@@ -22,10 +31,21 @@ struct RecGeom {
     uint64_t region_offset[kMaxK];
 };
 
-// Reads and checks a record header: geometry within the caller's bounds, and every section (tile-row
-// index, map, region payloads) inside total_bytes <= cap, so that no later read leaves the record.
-__device__ bool read_header(const uint8_t *rec, uint64_t cap, int max_M, int max_N, int max_C, RecGeom &rg, int oes) {
-    const dp_pix_record_header *h = reinterpret_cast<const dp_pix_record_header *>(rec);
+__device__ __forceinline__ int gcd_i(int a, int b) {
+    while (b) {
+        const int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Checks a record header (a shared-memory copy): geometry within the caller's bounds, and every section
+// (tile-row index, map, region payloads) inside total_bytes <= cap, so that no later read leaves the
+// record.  Chooses the fast path when the record has fast_C channels, output rows are 16-byte aligned,
+// and a segment's cell values fit the staging buffer.
+__device__ bool read_header(const dp_pix_record_header *h, uint64_t cap, int max_M, int max_N, int max_C, RecGeom &rg,
+                            int oes, int fast_C, int out_align) {
     if (h->magic[0] != 'D' || h->magic[1] != 'P' || h->magic[2] != 'P' || h->magic[3] != 'X' || h->version != 1)
         return false;
     rg.M = (int)h->M; rg.N = (int)h->N; rg.C = (int)h->C; rg.T = (int)h->T; rg.K = (int)h->K;
@@ -36,6 +56,7 @@ __device__ bool read_header(const uint8_t *rec, uint64_t cap, int max_M, int max
     const uint64_t total = h->total_bytes;
     if (total > cap) return false;
     rg.es = rg.dtype == DP_PIX_REC_U8 ? 1 : 4;
+    int bmin = rg.T;
     for (int r = 0; r < rg.K; ++r) {
         rg.grid[r] = (int)h->grid[r];
         rg.count[r] = h->count[r];
@@ -44,6 +65,7 @@ __device__ bool read_header(const uint8_t *rec, uint64_t cap, int max_M, int max
         const uint64_t cs = (uint64_t)(rg.T / rg.grid[r]);
         if (rg.region_offset[r] > total || (uint64_t)rg.count[r] * cs * cs * rg.C * rg.es > total - rg.region_offset[r])
             return false;
+        bmin = rg.grid[r] < bmin ? rg.grid[r] : bmin;
     }
     rg.map_offset = h->map_offset;
     rg.rowidx_offset = h->rowidx_offset;
@@ -51,131 +73,359 @@ __device__ bool read_header(const uint8_t *rec, uint64_t cap, int max_M, int max
     if (rg.map_offset > total || ntiles > total - rg.map_offset) return false;
     if (rg.rowidx_offset > total || (uint64_t)rg.GR * rg.K * 4 > total - rg.rowidx_offset || rg.rowidx_offset % 4)
         return false;
-    const int tile_row_bytes = rg.T * rg.C * oes;
-    int sr = kRowBytes / tile_row_bytes;
-    rg.SR = sr < 1 ? 1 : (sr > 16 ? 16 : sr);
+    rg.fast = 0;
+    const int trb = rg.T * rg.C * oes;  // bytes of one tile row of output
+    if (rg.C == fast_C && out_align == 16 && trb >= 16) {
+        // S tiles per segment, S a multiple of s0 so that segment starts stay 16-byte aligned, and as many
+        // tiles as the staging buffers take (a whole tile row of a 1080p frame)
+        const int s0 = 16 / gcd_i(trb, 16);
+        const int csmax = rg.T / bmin;
+        const int vb = oes == 4 ? 16 : 4;  // staged bytes per cell
+        int S = min(kMaxSegTiles, ((rg.GC + s0 - 1) / s0) * s0) / s0 * s0;
+        while (S > 0 && ((int64_t)S * csmax * csmax * vb > kStageBytes || S * rg.T > kMaxSegPx)) S -= s0;
+        if (S > 0) {
+            rg.fast = 1;
+            rg.SR = S;
+        }
+    }
+    if (!rg.fast) {
+        const int sr = kRowBytes / trb;
+        rg.SR = sr < 1 ? 1 : (sr > 16 ? 16 : sr);
+    }
     rg.nseg = (rg.GC + rg.SR - 1) / rg.SR;
     return true;
 }
 
+// Stored value of one (cell, channel) as the output element's float.
+__device__ __forceinline__ float record_value(const uint8_t *src, int dtype, int b) {
+    if (dtype == DP_PIX_REC_F32) return *reinterpret_cast<const float *>(src);
+    if (dtype == DP_PIX_REC_U8) return (float)*src;
+    return __fdiv_rn(__uint2float_rn(*reinterpret_cast<const uint32_t *>(src)), (float)(b * b));
+}
+
+__device__ __forceinline__ uint32_t to_u8(float v) { return __float2uint_rn(fminf(fmaxf(v, 0.0f), 255.0f)); }
+
+// Per-segment tile table shared by both paths.
+struct SegTiles {
+    int32_t b[kMaxSegTiles], cs[kMaxSegTiles], base[kMaxSegTiles + 1];
+    uint64_t off[kMaxSegTiles];
+};
+
+// Tile table of the segment [tx0, tx0 + ns) of tile row ty: region, grid, payload offset.  The number of
+// region-r tiles before the segment comes from the record's tile-row index plus a block-parallel count
+// over the map row, so no thread walks the row alone.
+__device__ void seg_tile_info(const uint8_t *rec, const RecGeom &rg, int ty, int tx0, int ns, uint32_t rec_i,
+                              int32_t *status, SegTiles &st, uint32_t *cnt_s) {
+    const uint8_t *maprow = rec + rg.map_offset + (uint64_t)ty * rg.GC;
+    if (threadIdx.x < kMaxK) cnt_s[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int x = threadIdx.x; x < tx0; x += blockDim.x) {
+        const int r = maprow[x];
+        if (r < rg.K) atomicAdd(&cnt_s[r], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < ns) {
+        const int t = threadIdx.x;
+        int r = maprow[tx0 + t];
+        if (r >= rg.K) r = 0;
+        uint32_t before = reinterpret_cast<const uint32_t *>(rec + rg.rowidx_offset)[ty * rg.K + r] + cnt_s[r];
+        for (int x = tx0; x < tx0 + t; ++x) before += (maprow[x] == r);
+        int b = rg.grid[r], cs = rg.T / b;
+        uint64_t off = rg.region_offset[r] + (uint64_t)before * (uint64_t)(cs * cs * rg.C * rg.es);
+        if (before >= rg.count[r]) {  // inconsistent index: read the header instead of leaving the record
+            raise_status(status, DP_PIX_E_DEVICE, 0x300u | (rec_i & 0xFFu));
+            b = rg.T;
+            cs = 1;
+            off = 0;
+        }
+        st.b[t] = b;
+        st.cs[t] = cs;
+        st.off[t] = off;
+    }
+    __syncthreads();
+}
+
+// ---- fast path: vector assembly -----------------------------------------------------------------------
+// Output element i of a 16-byte chunk whose first element is channel P of local pixel 0 belongs to local
+// pixel (P + i) / C, channel (P + i) % C -- compile-time once P and C are.
+template <int C>
+struct FastK {
+    static constexpr int NPX8 = (C - 1 + 16) / C + 1;  // pixels a u8 chunk can touch (upper bound)
+    static constexpr int NPXF = (C - 1 + 4) / C + 1;   // pixels an f32 chunk can touch (upper bound)
+};
+
+template <int C, int P>
+__device__ __forceinline__ uint4 build_u8(const uint32_t *pv) {
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const uint32_t byte = (pv[(P + i) / C] >> (8 * ((P + i) % C))) & 0xFFu;
+        w[i / 4] |= byte << (8 * (i % 4));
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+template <int C, int P>
+__device__ __forceinline__ uint4 build_f32(const float4 *pv) {
+    float o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 v = pv[(P + i) / C];
+        const int ch = (P + i) % C;
+        o[i] = ch == 0 ? v.x : (ch == 1 ? v.y : (ch == 2 ? v.z : v.w));
+    }
+    return make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]), __float_as_uint(o[3]));
+}
+
+template <int C>
+__device__ __forceinline__ uint4 build_u8_phase(int p, const uint32_t *pv) {
+    if (p == 0) return build_u8<C, 0>(pv);
+    if (C > 1 && p == 1) return build_u8<C, (C > 1 ? 1 : 0)>(pv);
+    if (C > 2 && p == 2) return build_u8<C, (C > 2 ? 2 : 0)>(pv);
+    return build_u8<C, (C > 3 ? 3 : 0)>(pv);
+}
+
+template <int C>
+__device__ __forceinline__ uint4 build_f32_phase(int p, const float4 *pv) {
+    if (p == 0) return build_f32<C, 0>(pv);
+    if (C > 1 && p == 1) return build_f32<C, (C > 1 ? 1 : 0)>(pv);
+    if (C > 2 && p == 2) return build_f32<C, (C > 2 ? 2 : 0)>(pv);
+    return build_f32<C, (C > 3 ? 3 : 0)>(pv);
+}
+
+template <int C, int kOutF32>
+__device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i, int ty, int sg, uint8_t *obase,
+                          int64_t out_pitch, uint8_t *stage, uint32_t *colinfo, SegTiles &st, uint32_t *cnt_s,
+                          int32_t *status) {
+    constexpr int oes = kOutF32 ? 4 : 1;
+    const int T = rg.T;
+    const int tx0 = sg * rg.SR;
+    const int ns = min(rg.SR, rg.GC - tx0);
+    seg_tile_info(rec, rg, ty, tx0, ns, rec_i, status, st, cnt_s);
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int t = 0; t < ns; ++t) {
+            st.base[t] = acc;
+            acc += st.cs[t] * st.cs[t];
+        }
+        st.base[ns] = acc;
+    }
+    // pixel column -> (tile, cell column)
+    for (int px = threadIdx.x; px < ns * T; px += blockDim.x) {
+        const int t = px / T;
+        colinfo[px] = ((uint32_t)t << 16) | (uint32_t)((px - t * T) / st.b[t]);
+    }
+    __syncthreads();
+    // cell values of the segment, converted once
+    const int ncell = st.base[ns];
+    for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
+        int lo = 0, hi = ns - 1;  // last tile with base <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (st.base[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const int t = lo;
+        const int c = e - st.base[t];
+        const uint8_t *src = rec + st.off[t] + (uint64_t)c * C * rg.es;
+        if (kOutF32) {
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) v[ch] = record_value(src + ch * rg.es, rg.dtype, st.b[t]);
+            reinterpret_cast<float4 *>(stage)[e] = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+            uint32_t pk = 0;
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) pk |= to_u8(record_value(src + ch * rg.es, rg.dtype, st.b[t])) << (8 * ch);
+            reinterpret_cast<uint32_t *>(stage)[e] = pk;
+        }
+    }
+    __syncthreads();
+    // write phase: thread = (16-byte column chunk, group of rows); no barrier until the next item
+    const int x0 = tx0 * T;
+    const int vpx = min(ns * T, rg.N - x0);
+    const int row_bytes = vpx * C * oes;
+    const int nch = (row_bytes + 15) >> 4;
+    const int jmax = min(T, rg.M - ty * T);
+    int RG = (2 * kThreads + nch - 1) / nch;  // about two (chunk, row group) units per thread
+    RG = RG < 1 ? 1 : (RG > jmax ? jmax : RG);
+    const int rpg = (jmax + RG - 1) / RG;
+    uint8_t *orow0 = obase + (int64_t)(ty * T) * out_pitch + (int64_t)x0 * C * oes;
+    const int last_px = ns * T - 1;
+    constexpr int kElems = 16 / oes;
+    constexpr int NPX = kOutF32 ? FastK<C>::NPXF : FastK<C>::NPX8;
+    for (int w = threadIdx.x; w < nch * RG; w += blockDim.x) {
+        const int k = w % nch, grp = w / nch;
+        const int j0 = grp * rpg, j1 = min(jmax, j0 + rpg);
+        if (j0 >= j1) continue;
+        const int o = k << 4;
+        const int e0 = o / oes;  // first output element of the chunk
+        const int p = e0 % C;
+        const int l0 = e0 / C;   // first pixel column
+        uint32_t ci[NPX];
+#pragma unroll
+        for (int l = 0; l < NPX; ++l) ci[l] = colinfo[min(l0 + l, last_px)];
+        // the chunk's real pixels lie in at most two tiles (a tile row has >= 16 bytes); a trailing entry of
+        // ci[] may lie past them and is never used by the vector builder
+        const int tA = ci[0] >> 16;
+        const int tB = colinfo[min((e0 + kElems - 1) / C, last_px)] >> 16;
+        const int bA = st.b[tA], bB = st.b[tB];
+        const bool full = o + 16 <= row_bytes;
+        int j = j0;
+        while (j < j1) {
+            const int bandA = j / bA, bandB = j / bB;
+            const int jn = min(j1, min((bandA + 1) * bA, (bandB + 1) * bB));
+            const int baseA = st.base[tA] + bandA * st.cs[tA], baseB = st.base[tB] + bandB * st.cs[tB];
+            uint4 vec;
+            if (kOutF32) {
+                float4 pv[NPX];
+#pragma unroll
+                for (int l = 0; l < NPX; ++l) {
+                    const int bb = (int)(ci[l] >> 16) == tA ? baseA : baseB;
+                    pv[l] = reinterpret_cast<const float4 *>(stage)[min(bb + (int)(ci[l] & 0xFFFFu), ncell - 1)];
+                }
+                vec = build_f32_phase<C>(p, pv);
+            } else {
+                uint32_t pv[NPX];
+#pragma unroll
+                for (int l = 0; l < NPX; ++l) {
+                    const int bb = (int)(ci[l] >> 16) == tA ? baseA : baseB;
+                    pv[l] = reinterpret_cast<const uint32_t *>(stage)[min(bb + (int)(ci[l] & 0xFFFFu), ncell - 1)];
+                }
+                vec = build_u8_phase<C>(p, pv);
+            }
+            for (int rr = j; rr < jn; ++rr) {
+                uint8_t *dst = orow0 + (int64_t)rr * out_pitch + o;
+                if (full) {
+                    *reinterpret_cast<uint4 *>(dst) = vec;
+                } else {
+                    for (int i = 0; o + i < row_bytes; ++i) {
+                        const uint32_t wv = i < 4 ? vec.x : (i < 8 ? vec.y : (i < 12 ? vec.z : vec.w));
+                        dst[i] = (uint8_t)(wv >> (8 * (i & 3)));
+                    }
+                }
+            }
+            j = jn;
+        }
+    }
+    __syncthreads();
+}
+
+// ---- generic path ------------------------------------------------------------------------------------
 template <int kOutF32>
+__device__ void generic_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i, int ty, int sg, uint8_t *obase,
+                             int64_t out_pitch, int out_align, uint8_t *rowpat, SegTiles &st, uint32_t *cnt_s,
+                             int32_t *status) {
+    constexpr int oes = kOutF32 ? 4 : 1;
+    const int T = rg.T, C = rg.C, es = rg.es;
+    const int tx0 = sg * rg.SR;
+    const int ns = min(rg.SR, rg.GC - tx0);
+    seg_tile_info(rec, rg, ty, tx0, ns, rec_i, status, st, cnt_s);
+    const int x0 = tx0 * T;
+    const int vpx = min(ns * T, rg.N - x0);
+    const int row_bytes = vpx * C * oes;
+    uint8_t *orow0 = obase + (uint64_t)x0 * C * oes;
+    // widest unit that keeps every row segment start aligned
+    int U = out_align;
+    while (U > 1 && (((int64_t)rg.SR * T * C * oes) % U != 0)) U >>= 1;
+    if (U == 2) U = 1;  // copies move 16, 8, 4 or 1 bytes
+    const int nu = row_bytes / U;
+    const int tail0 = nu * U;
+    const int jmax = min(T, rg.M - ty * T);
+    int j = 0;
+    while (j < jmax) {
+        // next row where some tile enters a new cell band
+        int jn = jmax;
+        for (int t = 0; t < ns; ++t) {
+            const int nb = (j / st.b[t] + 1) * st.b[t];
+            jn = min(jn, nb);
+        }
+        // build the row pattern of rows [j, jn)
+        const int elems = ns * T * C;
+        for (int e = threadIdx.x; e < elems; e += blockDim.x) {
+            const int t = e / (T * C);
+            const int rem = e - t * (T * C);
+            const int px = rem / C, ch = rem - px * C;
+            const int b = st.b[t], cs = st.cs[t];
+            const int cell = (j / b) * cs + px / b;
+            const float v = record_value(rec + st.off[t] + ((uint64_t)cell * C + ch) * es, rg.dtype, b);
+            if (kOutF32)
+                reinterpret_cast<float *>(rowpat)[e] = v;
+            else
+                rowpat[e] = (uint8_t)to_u8(v);
+        }
+        __syncthreads();
+        const int rows = jn - j;
+        const int per_row = nu + (row_bytes - tail0);
+        for (int q = threadIdx.x; q < rows * per_row; q += blockDim.x) {
+            const int rr = q / per_row, u = q - rr * per_row;
+            uint8_t *orow = orow0 + (int64_t)(ty * T + j + rr) * out_pitch;
+            if (u < nu) {
+                const int o = u * U;
+                if (U == 16)
+                    *reinterpret_cast<uint4 *>(orow + o) = *reinterpret_cast<const uint4 *>(rowpat + o);
+                else if (U == 8)
+                    *reinterpret_cast<uint2 *>(orow + o) = *reinterpret_cast<const uint2 *>(rowpat + o);
+                else if (U == 4)
+                    *reinterpret_cast<uint32_t *>(orow + o) = *reinterpret_cast<const uint32_t *>(rowpat + o);
+                else
+                    orow[o] = rowpat[o];
+            } else {
+                const int o = tail0 + (u - nu);
+                orow[o] = rowpat[o];
+            }
+        }
+        __syncthreads();
+        j = jn;
+    }
+}
+
+// kFastC: channel count served by the fast path in this launch (0: generic only).
+// CTAs are dealt to records: with n <= gridDim records each record gets gridDim / n CTAs that split its
+// work items into contiguous runs; with more records than CTAs, CTA c takes records c, c + gridDim, ...
+// Each CTA parses a record header once (one parallel 512-byte copy into shared memory).
+template <int kOutF32, int kFastC>
 __global__ void __launch_bounds__(kThreads)
     k_reconstruct(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out, int64_t out_frame_stride,
                   int64_t out_pitch, int max_M, int max_N, int max_C, int out_align, int32_t *status) {
+    extern __shared__ __align__(16) uint8_t dyn[];  // fast path: stage[kStageBytes] then colinfo[kMaxSegPx]
     __shared__ __align__(16) uint8_t rowpat[kRowBytes];
+    __shared__ __align__(16) dp_pix_record_header hdr_s;
     __shared__ RecGeom rg;
-    __shared__ int32_t t_b[16], t_cs[16];
-    __shared__ uint64_t t_off[16];
+    __shared__ SegTiles st;
+    __shared__ uint32_t cnt_s[kMaxK];
     constexpr int oes = kOutF32 ? 4 : 1;
-    uint64_t base = 0;  // global item index of the current record's first item
-    for (uint32_t i = 0; i < n; ++i) {
+    uint8_t *stage = dyn;
+    uint32_t *colinfo = reinterpret_cast<uint32_t *>(dyn + kStageBytes);
+    const uint32_t G = gridDim.x;
+    const uint32_t per_rec = n <= G ? G / n : 1u;  // CTAs per record
+    const uint32_t slots = n <= G ? n : G;         // records handled concurrently
+    if (blockIdx.x >= per_rec * slots) return;     // spare CTAs (whole block)
+    const uint32_t sub = blockIdx.x / slots, slot = blockIdx.x % slots;
+    for (uint32_t i = slot; i < n; i += slots) {
         const uint8_t *rec = records + (uint64_t)i * (uint64_t)record_stride;
+        if (threadIdx.x < kHeaderBytes / 16)
+            reinterpret_cast<uint4 *>(&hdr_s)[threadIdx.x] = reinterpret_cast<const uint4 *>(rec)[threadIdx.x];
+        __syncthreads();
         if (threadIdx.x == 0) {
-            rg.ok = read_header(rec, (uint64_t)record_stride, max_M, max_N, max_C, rg, oes) ? 1 : 0;
-            if (!rg.ok && blockIdx.x == 0) raise_status(status, DP_PIX_E_DEVICE, 0x200u | (i & 0xFFu));
+            rg.ok = read_header(&hdr_s, (uint64_t)record_stride, max_M, max_N, max_C, rg, oes, kFastC, out_align) ? 1
+                                                                                                                  : 0;
+            if (!rg.ok && sub == 0) raise_status(status, DP_PIX_E_DEVICE, 0x200u | (i & 0xFFu));
         }
         __syncthreads();
-        if (!rg.ok) {
-            __syncthreads();
-            continue;
-        }
-        const uint64_t items = (uint64_t)rg.GR * rg.nseg;
-        // items of this record handled by this CTA: global index = base + k, k in [0, items)
-        uint64_t first = (blockIdx.x >= base % gridDim.x) ? blockIdx.x - base % gridDim.x
-                                                          : blockIdx.x + gridDim.x - base % gridDim.x;
-        const int T = rg.T, C = rg.C;
-        const int es = rg.es;
-        uint8_t *obase = out + (uint64_t)i * (uint64_t)out_frame_stride;
-        for (uint64_t k = first; k < items; k += gridDim.x) {
-            const int ty = (int)(k / rg.nseg), sg = (int)(k - (uint64_t)ty * rg.nseg);
-            const int tx0 = sg * rg.SR;
-            const int ns = min(rg.SR, rg.GC - tx0);
-            if (threadIdx.x < ns) {
-                const int t = threadIdx.x;
-                const uint8_t *maprow = rec + rg.map_offset + (uint64_t)ty * rg.GC;
-                int r = maprow[tx0 + t];
-                if (r >= rg.K) r = 0;
-                uint32_t before = reinterpret_cast<const uint32_t *>(rec + rg.rowidx_offset)[ty * rg.K + r];
-                for (int x = 0; x < tx0 + t; ++x) before += (maprow[x] == r);
-                int b = rg.grid[r], cs = T / b;
-                uint64_t off = rg.region_offset[r] + (uint64_t)before * (uint64_t)(cs * cs * C * es);
-                if (before >= rg.count[r]) {  // inconsistent index: read the header instead of leaving the record
-                    raise_status(status, DP_PIX_E_DEVICE, 0x300u | (i & 0xFFu));
-                    b = T;
-                    cs = 1;
-                    off = 0;
-                }
-                t_b[t] = b;
-                t_cs[t] = cs;
-                t_off[t] = off;
-            }
-            __syncthreads();
-            const int x0 = tx0 * T;
-            const int vpx = min(ns * T, rg.N - x0);
-            const int row_bytes = vpx * C * oes;
-            uint8_t *orow0 = obase + (uint64_t)x0 * C * oes;
-            // widest unit that keeps every row segment start aligned
-            int U = out_align;
-            while (U > 1 && (((int64_t)rg.SR * T * C * oes) % U != 0)) U >>= 1;
-            if (U == 2) U = 1;  // copies move 16, 8, 4 or 1 bytes
-            const int nu = row_bytes / U;
-            const int tail0 = nu * U;
-            const int jmax = min(T, rg.M - ty * T);
-            int j = 0;
-            while (j < jmax) {
-                // next row where some tile enters a new cell band
-                int jn = jmax;
-                for (int t = 0; t < ns; ++t) {
-                    const int nb = (j / t_b[t] + 1) * t_b[t];
-                    jn = min(jn, nb);
-                }
-                // build the row pattern of rows [j, jn)
-                const int elems = ns * T * C;
-                for (int e = threadIdx.x; e < elems; e += blockDim.x) {
-                    const int t = e / (T * C);
-                    const int rem = e - t * (T * C);
-                    const int px = rem / C, ch = rem - px * C;
-                    const int b = t_b[t], cs = t_cs[t];
-                    const int cell = (j / b) * cs + px / b;
-                    const uint8_t *src = rec + t_off[t] + ((uint64_t)cell * C + ch) * es;
-                    float v;
-                    if (rg.dtype == DP_PIX_REC_F32)
-                        v = *reinterpret_cast<const float *>(src);
-                    else if (rg.dtype == DP_PIX_REC_U8)
-                        v = (float)*src;
-                    else
-                        v = __fdiv_rn(__uint2float_rn(*reinterpret_cast<const uint32_t *>(src)), (float)(b * b));
-                    if (kOutF32)
-                        reinterpret_cast<float *>(rowpat)[e] = v;
-                    else
-                        rowpat[e] = (uint8_t)__float2uint_rn(fminf(fmaxf(v, 0.0f), 255.0f));
-                }
-                __syncthreads();
-                const int rows = jn - j;
-                const int per_row = nu + (row_bytes - tail0);
-                for (int q = threadIdx.x; q < rows * per_row; q += blockDim.x) {
-                    const int rr = q / per_row, u = q - rr * per_row;
-                    uint8_t *orow = orow0 + (int64_t)(ty * T + j + rr) * out_pitch;
-                    if (u < nu) {
-                        const int o = u * U;
-                        if (U == 16)
-                            *reinterpret_cast<uint4 *>(orow + o) = *reinterpret_cast<const uint4 *>(rowpat + o);
-                        else if (U == 8)
-                            *reinterpret_cast<uint2 *>(orow + o) = *reinterpret_cast<const uint2 *>(rowpat + o);
-                        else if (U == 4)
-                            *reinterpret_cast<uint32_t *>(orow + o) = *reinterpret_cast<const uint32_t *>(rowpat + o);
-                        else
-                            orow[o] = rowpat[o];
-                    } else {
-                        const int o = tail0 + (u - nu);
-                        orow[o] = rowpat[o];
-                    }
-                }
-                __syncthreads();
-                j = jn;
+        if (rg.ok) {
+            const uint64_t items = (uint64_t)rg.GR * rg.nseg;
+            const uint64_t chunk = (items + per_rec - 1) / per_rec;
+            const uint64_t k0 = (uint64_t)sub * chunk, k1 = min(items, k0 + chunk);
+            uint8_t *obase = out + (uint64_t)i * (uint64_t)out_frame_stride;
+            for (uint64_t k = k0; k < k1; ++k) {
+                const int ty = (int)(k / rg.nseg), sg = (int)(k - (uint64_t)ty * rg.nseg);
+                if (kFastC > 0 && rg.fast)
+                    fast_item<(kFastC > 0 ? kFastC : 1), kOutF32>(rec, rg, i, ty, sg, obase, out_pitch, stage, colinfo,
+                                                                   st, cnt_s, status);
+                else
+                    generic_item<kOutF32>(rec, rg, i, ty, sg, obase, out_pitch, out_align, rowpat, st, cnt_s, status);
             }
         }
-        base += items;
         __syncthreads();
     }
 }
@@ -196,30 +446,51 @@ __global__ void k_debug_noise(uint64_t seed, const uint32_t *ctr, uint64_t n, ui
     }
 }
 
+template <int kOutF32, int kFastC>
+cudaError_t launch_rc(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out, int64_t out_frame_stride,
+                      int64_t out_pitch, int max_M, int max_N, int max_C, int out_align, int32_t *status,
+                      cudaStream_t s) {
+    const size_t smem = kStageBytes + kMaxSegPx * 4;
+    auto kern = k_reconstruct<kOutF32, kFastC>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int grid = per_sm * sm_count();
+    const char *name = kOutF32 ? "k_reconstruct_f32" : "k_reconstruct_u8";
+    prof_begin(name, s);
+    kern<<<grid, kThreads, smem, s>>>(records, record_stride, n, out, out_frame_stride, out_pitch, max_M, max_N, max_C,
+                                      out_align, status);
+    prof_end(name, s);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_reconstruct(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out,
                                int64_t out_frame_stride, int64_t out_pitch, int out_type, int max_M, int max_N,
                                int max_C, int out_align, int32_t *status, cudaStream_t s) {
-    int per_sm = 0;
-    if (out_type == DP_PIX_OUT_F32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_reconstruct<1>, kThreads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_reconstruct<0>, kThreads, 0);
-    if (per_sm < 1) per_sm = 1;
-    const int grid = per_sm * sm_count();
+    const int fc = out_align == 16 ? max_C : 0;
+#define DPPIX_RC(F, FC) \
+    return launch_rc<F, FC>(records, record_stride, n, out, out_frame_stride, out_pitch, max_M, max_N, max_C, out_align, \
+                            status, s)
     if (out_type == DP_PIX_OUT_F32) {
-        prof_begin("k_reconstruct_f32", s);
-        k_reconstruct<1><<<grid, kThreads, 0, s>>>(records, record_stride, n, out, out_frame_stride, out_pitch, max_M,
-                                                   max_N, max_C, out_align, status);
-        prof_end("k_reconstruct_f32", s);
-    } else {
-        prof_begin("k_reconstruct_u8", s);
-        k_reconstruct<0><<<grid, kThreads, 0, s>>>(records, record_stride, n, out, out_frame_stride, out_pitch, max_M,
-                                                   max_N, max_C, out_align, status);
-        prof_end("k_reconstruct_u8", s);
+        switch (fc) {
+            case 1: DPPIX_RC(1, 1);
+            case 2: DPPIX_RC(1, 2);
+            case 3: DPPIX_RC(1, 3);
+            case 4: DPPIX_RC(1, 4);
+            default: DPPIX_RC(1, 0);
+        }
     }
-    return cudaGetLastError();
+    switch (fc) {
+        case 1: DPPIX_RC(0, 1);
+        case 2: DPPIX_RC(0, 2);
+        case 3: DPPIX_RC(0, 3);
+        case 4: DPPIX_RC(0, 4);
+        default: DPPIX_RC(0, 0);
+    }
+#undef DPPIX_RC
 }
 
 cudaError_t launch_debug_noise(uint64_t seed, const uint32_t *ctr, uint64_t n, uint32_t *words, float *eta,

@@ -12,6 +12,8 @@
 //  - k_tile_stats: per-tile S, Q for the variance classes and, when the grids share a divisor g >= 4, the
 //    g x g cell sums from which any b_r-cell sum is later assembled (image read once);
 //  - k_emit: g-cell sums -> b_r-cell sums -> noise -> record.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace dppix {
@@ -124,19 +126,21 @@ __global__ void __launch_bounds__(kThreads) k_release(const Geom g, const CallAr
         const int tx0 = (int)sg * g.seg_tiles;
         const int ns = min(g.seg_tiles, g.GC - tx0);
         uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
+        if (threadIdx.x < ns) {  // one thread per tile loads its region and payload offset
+            const int t = threadIdx.x;
+            int r = rec[g.map_offset + (uint64_t)ty * g.GC + tx0 + t];
+            if (r >= g.K) r = 0;
+            si.region[t] = r;
+            si.tileoff[t] =
+                reinterpret_cast<const uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff)[ty * g.GC + tx0 + t];
+        }
+        stage_segment(g, a, f, ty, tx0, ns, raw);  // ends with a barrier (also covers si)
         if (threadIdx.x == 0) {
-            const uint8_t *map = rec + g.map_offset + (uint64_t)ty * g.GC + tx0;
-            const uint32_t *toff =
-                reinterpret_cast<const uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff) + ty * g.GC + tx0;
             int sa = 0, sb = 0;
             for (int t = 0; t < ns; ++t) {
-                int r = map[t];
-                if (r >= g.K) r = 0;
-                const int b = g.grid[r];
+                const int b = g.grid[si.region[t]];
                 si.b[t] = b;
                 si.cs[t] = T / b;
-                si.region[t] = r;
-                si.tileoff[t] = toff[t];
                 si.startA[t] = sa;
                 si.startB[t] = sb;
                 sa += (T / b) * (word_path ? (TC >> 2) : TC);
@@ -145,7 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_release(const Geom g, const CallAr
             si.startA[ns] = sa;
             si.startB[ns] = sb;
         }
-        stage_segment(g, a, f, ty, tx0, ns, raw);  // ends with a barrier (also covers si)
+        __syncthreads();
 
         // vertical pass
         const int totalA = si.startA[ns];
@@ -279,9 +283,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats(const Geom g, const Cal
 
         const uint32_t tile0 = (uint32_t)ty * g.GC + tx0;
         if (kGsum) {
-            uint16_t *gsum = reinterpret_cast<uint16_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_gsum);
+            uint16_t *gimg = reinterpret_cast<uint16_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_gsum);
             const int cells = gcs * gcs;
-            const int gstride = g.gsum_per_tile;  // u16 per tile (padded)
             for (int it = threadIdx.x; it < ns * cells; it += blockDim.x) {
                 const int t = it / cells, cell = it - t * cells;
                 const int cy = cell / gcs, cx = cell - cy * gcs;
@@ -292,7 +295,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats(const Geom g, const Cal
                     for (int ch = 0; ch < 4; ++ch)
                         if (ch < C) S[ch] += vrow[i * C + ch];
                 }
-                uint16_t *dst = gsum + (size_t)(tile0 + t) * gstride + (size_t)cell * C;
+                // g-image position of g-cell (cy, cx) of tile (ty, tx0 + t)
+                uint16_t *dst = gimg + ((size_t)(ty * gcs + cy) * g.gx_cells + (size_t)(tx0 + t) * gcs + cx) * C;
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch)
                     if (ch < C) dst[ch] = (uint16_t)S[ch];
@@ -309,89 +313,182 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats(const Geom g, const Cal
     }
 }
 
-// ------------------------------------------------------------------------------------------------------
-// k_emit: per tile, assemble each b_r-cell sum from its (b_r/g)^2 g-cell sums, then noise, clip, store.
-// ------------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs a) {
-    extern __shared__ __align__(16) uint8_t dyn[];
-    __shared__ int32_t t_region[64];
-    __shared__ uint32_t t_off[64];
-    __shared__ int32_t t_start[65];
-    const int E = g.emit_tiles, C = g.C, T = g.T, gcs = T / g.g;
-    const int gstride = g.gsum_per_tile;
-    uint16_t *gs = reinterpret_cast<uint16_t *>(dyn);
-    const uint32_t groups_per_frame = (g.ntiles + E - 1) / E;
-    const uint32_t items = a.n_frames * groups_per_frame;
-    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const uint32_t f = item / groups_per_frame;
-        const uint32_t tile0 = (item - f * groups_per_frame) * E;
-        const int ne = (int)min((uint32_t)E, g.ntiles - tile0);
-        uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
-        if (threadIdx.x == 0) {
-            const uint8_t *map = rec + g.map_offset + tile0;
-            const uint32_t *toff =
-                reinterpret_cast<const uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff) + tile0;
-            int sb = 0;
-            for (int t = 0; t < ne; ++t) {
-                int r = map[t];
-                if (r >= g.K) r = 0;
-                t_region[t] = r;
-                t_off[t] = toff[t];
-                t_start[t] = sb;
-                const int cs = g.cells_side[r];
-                sb += cs * cs;
-            }
-            t_start[ne] = sb;
-        }
-        // g-cell sums of the group's tiles are contiguous in the workspace
-        const uint4 *src = reinterpret_cast<const uint4 *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_gsum +
-                                                           (uint64_t)tile0 * gstride * 2);
-        const int nvec = ne * gstride * 2 / 16;
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) reinterpret_cast<uint4 *>(gs)[i] = src[i];
-        __syncthreads();
-        const int total = t_start[ne];
-        const uint64_t frame = a.frame_idx0 + f;
-        for (int it = threadIdx.x; it < total; it += blockDim.x) {
-            int t = 0;
-            while (t + 1 < ne && it >= t_start[t + 1]) ++t;
-            const int r = t_region[t];
-            const int cell = it - t_start[t];
-            const int cs = g.cells_side[r], nb = g.grid[r] / g.g;
-            const int cy = cell / cs, cx = cell - cy * cs;
-            const uint16_t *tg = gs + (size_t)t * gstride;
-            uint32_t S[4] = {0u, 0u, 0u, 0u};
-            for (int yy = 0; yy < nb; ++yy) {
-                const uint16_t *row = tg + ((cy * nb + yy) * gcs + cx * nb) * C;
-                for (int xx = 0; xx < nb; ++xx) {
+// Noise, clip and store of one (cell, channel) set (Alg. 3 steps 9-10 and 15-17).
+__device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint8_t *dst, const uint32_t *S, int r,
+                                          uint32_t cell_idx, uint64_t frame) {
+    const int C = g.C;
+    uint4 words = make_uint4(0, 0, 0, 0);
+    if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
+        words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, a.stream_id, frame);
 #pragma unroll
-                    for (int ch = 0; ch < 4; ++ch)
-                        if (ch < C) S[ch] += row[xx * C + ch];
-                }
-            }
-            const uint32_t tile = tile0 + t;
-            const uint32_t ty = tile / g.GC, tx = tile - ty * g.GC;
-            const uint32_t cell_idx = (ty * cs + cy) * (uint32_t)(g.GC * cs) + tx * cs + cx;
-            uint4 words = make_uint4(0, 0, 0, 0);
-            if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
-                words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, a.stream_id, frame);
-            uint8_t *dst = rec + t_off[t] + (uint64_t)cell * C * g.es;
-#pragma unroll
-            for (int ch = 0; ch < 4; ++ch) {
-                if (ch >= C) break;
-                if (g.dtype == DP_PIX_REC_SUM_U32) {
-                    reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
-                } else {
-                    const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), g.sigma_f[r]);
-                    const float v = noisy_mean(S[ch], g.b2_f[r], eta, g.R_f);
-                    if (g.dtype == DP_PIX_REC_F32)
-                        reinterpret_cast<float *>(dst)[ch] = v;
-                    else
-                        dst[ch] = (uint8_t)__float2uint_rn(v);
-                }
-            }
+    for (int ch = 0; ch < 4; ++ch) {
+        if (ch >= C) break;
+        if (g.dtype == DP_PIX_REC_SUM_U32) {
+            reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
+        } else {
+            const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), g.sigma_f[r]);
+            const float v = noisy_mean(S[ch], g.b2_f[r], eta, g.R_f);
+            if (g.dtype == DP_PIX_REC_F32)
+                reinterpret_cast<float *>(dst)[ch] = v;
+            else
+                dst[ch] = (uint8_t)__float2uint_rn(v);
         }
-        __syncthreads();
     }
+}
+
+// Sum of the nb x nb g-cells of one b_r-cell, split over L lanes of a warp (all 32 lanes call it).
+// src: g-cell (0, 0) of the cell; stride: u16 values between g-image rows.
+__device__ __forceinline__ void gcell_block_sum(const uint16_t *src, int stride, int nb, int C, int lig, int L,
+                                                bool active, uint32_t *S) {
+    S[0] = S[1] = S[2] = S[3] = 0u;
+    if (active) {
+        const int ng = nb * nb;
+        const bool pow2 = (nb & (nb - 1)) == 0;
+        const int lg = __ffs(nb) - 1;
+        for (int gi = lig; gi < ng; gi += L) {
+            const int yy = pow2 ? (gi >> lg) : gi / nb;
+            const int xx = gi - yy * nb;
+            const uint16_t *p = src + (size_t)yy * stride + (size_t)xx * C;
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch)
+                if (ch < C) S[ch] += p[ch];
+        }
+    }
+    for (int off = L >> 1; off > 0; off >>= 1) {
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) S[ch] += __shfl_xor_sync(0xffffffffu, S[ch], off);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// k_emit_row: one CTA per (frame, tile row).  The row's g-cell sums are one contiguous band of the g-image;
+// it is copied into shared memory with coalesced loads.  Phase 1: one warp per tile assembles each b_r-cell
+// sum from its (b_r/g)^2 g-cells (L lanes per cell, combined by shuffles) into shared memory.  Phase 2:
+// one thread per cell draws the noise, clips and stores, so every lane works in the costly noise step.
+// ------------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_emit_row(const Geom g, const CallArgs a) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    const int C = g.C, gcs = g.T / g.g, GX = g.gx_cells, GC = g.GC;
+    const uint32_t f = blockIdx.x / g.GR;
+    const int ty = (int)(blockIdx.x - f * g.GR);
+    const uint64_t band_vals = (uint64_t)gcs * GX * C;  // u16 values in the band
+    int maxcells = 1;
+    for (int r = 0; r < g.K; ++r) maxcells = max(maxcells, g.cells_side[r] * g.cells_side[r]);
+    uint16_t *band = reinterpret_cast<uint16_t *>(dyn);
+    uint32_t *sums = reinterpret_cast<uint32_t *>(dyn + ((band_vals * 2 + 15) & ~15ull));  // [tile][cell][C]
+    uint32_t *toff_s = sums + (size_t)GC * maxcells * C;
+    int32_t *base_s = reinterpret_cast<int32_t *>(toff_s + GC);  // [GC + 1] cell prefix
+    uint8_t *map_s = reinterpret_cast<uint8_t *>(base_s + GC + 1);
+    const uint8_t *wsf = a.ws + (uint64_t)f * g.ws_per_frame;
+    const uint16_t *src = reinterpret_cast<const uint16_t *>(wsf + g.ws_gsum) + (uint64_t)ty * band_vals;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (band_vals * 2) % 16 == 0) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        for (uint64_t i = threadIdx.x; i < band_vals * 2 / 16; i += blockDim.x) reinterpret_cast<uint4 *>(band)[i] = s4[i];
+    } else {
+        for (uint64_t i = threadIdx.x; i < band_vals; i += blockDim.x) band[i] = src[i];
+    }
+    uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
+    const uint32_t *toff = reinterpret_cast<const uint32_t *>(wsf + g.ws_tileoff) + (uint64_t)ty * GC;
+    for (int tx = threadIdx.x; tx < GC; tx += blockDim.x) {
+        toff_s[tx] = toff[tx];
+        int r = rec[g.map_offset + (uint64_t)ty * GC + tx];
+        map_s[tx] = (uint8_t)(r < g.K ? r : 0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int tx = 0; tx < GC; ++tx) {
+            base_s[tx] = acc;
+            const int cs = g.cells_side[map_s[tx]];
+            acc += cs * cs;
+        }
+        base_s[GC] = acc;
+    }
+    // phase 1: cell sums
+    const int lane = threadIdx.x & 31;
+    for (int tx = threadIdx.x >> 5; tx < GC; tx += kThreads / 32) {
+        const int r = map_s[tx];
+        const int cs = g.cells_side[r], nb = g.grid[r] / g.g, cells = cs * cs;
+        int L = 1;
+        while (2 * L * cells <= 32) L *= 2;
+        const int per_pass = 32 / L;
+        for (int c0 = 0; c0 < cells; c0 += per_pass) {
+            const int c = c0 + lane / L, lig = lane & (L - 1);
+            const bool active = c < cells;
+            const int cy = active ? c / cs : 0, cx = active ? c - cy * cs : 0;
+            uint32_t S[4];
+            gcell_block_sum(band + ((size_t)cy * nb * GX + (size_t)tx * gcs + (size_t)cx * nb) * C, GX * C, nb, C,
+                            lig, L, active, S);
+            if (active && lig == 0) {
+                uint32_t *d = sums + ((size_t)tx * maxcells + c) * C;
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch)
+                    if (ch < C) d[ch] = S[ch];
+            }
+        }
+    }
+    __syncthreads();
+    // phase 2: one thread per cell of the row
+    const int total = base_s[GC];
+    const uint64_t frame = a.frame_idx0 + f;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        int lo = 0, hi = GC - 1;  // last tile whose first cell is <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (base_s[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const int tx = lo, c = e - base_s[tx];
+        const int r = map_s[tx], cs = g.cells_side[r];
+        const int cy = c / cs, cx = c - cy * cs;
+        const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(GC * cs) + (uint32_t)(tx * cs + cx);
+        const uint32_t *d = sums + ((size_t)tx * maxcells + c) * C;
+        uint32_t S[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch)
+            if (ch < C) S[ch] = d[ch];
+        emit_cell(g, a, rec + toff_s[tx] + (uint64_t)c * C * g.es, S, r, cell_idx, frame);
+    }
+}
+
+// k_emit: fallback for tile rows whose g-image band does not fit shared memory; one warp per tile, reading
+// the g-image in global memory.
+__global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t wid = (uint64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (wid >= (uint64_t)a.n_frames * g.ntiles) return;  // whole warp
+    const uint32_t f = (uint32_t)(wid / g.ntiles);
+    const uint32_t tile = (uint32_t)(wid - (uint64_t)f * g.ntiles);
+    const uint32_t ty = tile / g.GC, tx = tile - ty * g.GC;
+    uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
+    int r = rec[g.map_offset + tile];
+    if (r >= g.K) r = 0;
+    const uint32_t toff =
+        reinterpret_cast<const uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff)[tile];
+    const uint16_t *gimg = reinterpret_cast<const uint16_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_gsum);
+    const int C = g.C, gcs = g.T / g.g;
+    const int cs = g.cells_side[r], nb = g.grid[r] / g.g, cells = cs * cs;
+    int L = 1;
+    while (2 * L * cells <= 32) L *= 2;
+    const int per_pass = 32 / L;
+    const uint64_t frame = a.frame_idx0 + f;
+    for (int c0 = 0; c0 < cells; c0 += per_pass) {
+        const int c = c0 + lane / L, lig = lane & (L - 1);
+        const bool active = c < cells;
+        const int cy = active ? c / cs : 0, cx = active ? c - cy * cs : 0;
+        uint32_t S[4];
+        gcell_block_sum(gimg + (((size_t)ty * gcs + (size_t)cy * nb) * g.gx_cells + (size_t)tx * gcs + (size_t)cx * nb) * C,
+                        g.gx_cells * C, nb, C, lig, L, active, S);
+        if (active && lig == 0)
+            emit_cell(g, a, rec + toff + (uint64_t)c * C * g.es, S, r,
+                      (ty * cs + cy) * (uint32_t)(g.GC * cs) + tx * cs + cx, frame);
+    }
+}
+
+size_t emit_row_smem(const Geom &g) {
+    int maxcells = 1;
+    for (int r = 0; r < g.K; ++r) maxcells = std::max(maxcells, g.cells_side[r] * g.cells_side[r]);
+    const uint64_t band = (((uint64_t)(g.T / g.g) * g.gx_cells * g.C * 2 + 15) & ~15ull);
+    return band + (uint64_t)g.GC * maxcells * g.C * 4 + 4ull * g.GC + 4ull * (g.GC + 1) + g.GC;
 }
 
 size_t seg_smem(const Geom &g, int bands_per_tile) {
@@ -422,6 +519,8 @@ cudaError_t launch_release(const Geom &g, const CallArgs &a, cudaStream_t s) {
 
 cudaError_t launch_tile_stats(const Geom &g, const CallArgs &a, cudaStream_t s) {
     const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row;
+    const cudaError_t fe = launch_tile_stats_fast(g, a, s);
+    if (fe != cudaErrorNotSupported) return fe;
     if (g.var_onepass) {
         const size_t smem = seg_smem(g, g.T / g.g);
         cudaFuncSetAttribute(k_tile_stats<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -441,12 +540,18 @@ cudaError_t launch_tile_stats(const Geom &g, const CallArgs &a, cudaStream_t s) 
 }
 
 cudaError_t launch_emit(const Geom &g, const CallArgs &a, cudaStream_t s) {
-    const size_t smem = (size_t)g.emit_tiles * g.gsum_per_tile * 2;
-    cudaFuncSetAttribute(k_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const uint32_t items = a.n_frames * ((g.ntiles + g.emit_tiles - 1) / g.emit_tiles);
-    const int grid = grid_for(k_emit, smem, items);
+    const size_t smem = emit_row_smem(g);
+    if (smem <= 160 * 1024) {
+        cudaFuncSetAttribute(k_emit_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        prof_begin("k_emit", s);
+        k_emit_row<<<a.n_frames * (unsigned)g.GR, kThreads, smem, s>>>(g, a);
+        prof_end("k_emit", s);
+        return cudaGetLastError();
+    }
+    const uint64_t warps = (uint64_t)a.n_frames * g.ntiles;
+    const uint64_t blocks = (warps + kThreads / 32 - 1) / (kThreads / 32);
     prof_begin("k_emit", s);
-    k_emit<<<grid, kThreads, smem, s>>>(g, a);
+    k_emit<<<(unsigned)blocks, kThreads, 0, s>>>(g, a);
     prof_end("k_emit", s);
     return cudaGetLastError();
 }

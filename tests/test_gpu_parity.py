@@ -109,6 +109,27 @@ def test_release_variance(M, N, grids, eps, dtype):
     compare_records(recs[0], rec, means, sums, etas, dtype)
 
 
+@pytest.mark.parametrize("M,N,C,grids,eps", [
+    (96, 256, 3, [32, 16, 8, 4], [2, 1, .5, .25]),   # no padding
+    (100, 256, 3, [32, 16, 8, 4], [2, 1, .5, .25]),  # mirrored rows
+    (130, 128, 1, [16, 8], [1, .5]),                  # g = 8, one 16-byte chunk per tile
+    (70, 64, 4, [8, 4], [1, .5]),                     # C = 4
+    (64, 192, 3, [16], [1]),                          # g = 16, K = 1 (Alg. 2)
+])
+@pytest.mark.parametrize("dtype", [O.DT_F32, O.DT_SUM])
+def test_release_variance_aligned_frames(M, N, C, grids, eps, dtype):
+    """Frames without column padding and with 16-byte rows: the statistics pass reads them directly."""
+    rng = np.random.default_rng(M + N + C)
+    F = 3
+    imgs = rng.integers(0, 256, size=(F, M, N, C), dtype=np.uint8)
+    imgs[:, : M // 2] //= 4  # give the tiles different spreads
+    kw = dict(M=M, N=N, C=C, grids=grids, eps=eps, source=O.SRC_VARIANCE, dtype=dtype, seed=8, m=16)
+    _, _, recs = gpu_release(imgs, None, frame_idx0=3, **kw)
+    for i in range(F):
+        rec, means, sums, etas = O.release(imgs[i], None, frame_idx=3 + i, **kw)
+        compare_records(recs[i], rec, means, sums, etas, dtype)
+
+
 def test_release_batch_frames_stream_and_frame_index():
     rng = np.random.default_rng(3)
     F, M, N = 5, 75, 110
@@ -174,6 +195,39 @@ def test_reconstruct_bit_exact(M, N, C, grids, src, dtype):
         for i in range(F):
             exp = O.reconstruct(np.frombuffer(recs[i], np.uint8), 0 if ot == P.OUT_U8 else 1)
             assert np.array_equal(out[i], exp), (i, ot)
+    assert P.dp_pix_status() == 0
+
+
+@pytest.mark.parametrize("M,N,C,grids,src", [
+    (100, 130, 3, [24, 8], O.SRC_TILE_LABELS), (61, 67, 1, [6, 20], O.SRC_TILE_LABELS),
+    (200, 330, 3, [32, 16, 8, 4], O.SRC_VARIANCE), (37, 53, 4, [4, 8, 16], O.SRC_TILE_LABELS),
+    (45, 200, 3, [1, 4], O.SRC_TILE_LABELS), (96, 256, 3, [32, 16, 8, 4], O.SRC_VARIANCE),
+    (70, 90, 3, [5], O.SRC_TILE_LABELS), (64, 80, 3, [2, 8], O.SRC_TILE_LABELS),
+    (50, 2100, 3, [32, 16, 8, 4], O.SRC_TILE_LABELS),
+])
+@pytest.mark.parametrize("dtype", [O.DT_F32, O.DT_U8, O.DT_SUM])
+def test_reconstruct_aligned_rows_bit_exact(M, N, C, grids, src, dtype):
+    """Output rows 16-byte aligned (a padded pitch), the layout the vectorised reconstruction serves."""
+    rng = np.random.default_rng(M * 7 + N + C)
+    F = 2
+    imgs = rng.integers(0, 256, size=(F, M, N, C), dtype=np.uint8)
+    lab = np.stack([_labels(rng, M, N, grids) for _ in range(F)]) if src == O.SRC_TILE_LABELS else None
+    kw = dict(M=M, N=N, C=C, grids=grids, eps=[0.5] * len(grids), source=src, dtype=dtype, seed=6, m=16)
+    plan, recs_d, recs = gpu_release(imgs, lab, **kw)
+    for ot, oes in [(P.OUT_U8, 1), (P.OUT_F32, 4)]:
+        dt = torch.uint8 if ot == P.OUT_U8 else torch.float32
+        Np = N
+        while (Np * C * oes) % 16:
+            Np += 1
+        Np += 16 // math.gcd(16, C * oes)  # always leave a margin past the row
+        big = torch.full((F, M, Np, C), 7, dtype=dt, device="cuda")
+        view = big[:, :, :N, :]
+        P.dp_pix_reconstruct(recs_d, M, N, C, ot, out=view)
+        got = big.cpu().numpy()
+        for i in range(F):
+            exp = O.reconstruct(np.frombuffer(recs[i], np.uint8), 0 if ot == P.OUT_U8 else 1)
+            assert np.array_equal(got[i, :, :N], exp), (i, ot)
+            assert np.all(got[i, :, N:] == 7)  # nothing written past the row
     assert P.dp_pix_status() == 0
 
 
