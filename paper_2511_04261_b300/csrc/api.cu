@@ -189,6 +189,7 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
         g.sigma[r] = d->value_range * d->m / ((double)b * (double)b * d->eps[r]);
         g.sigma_f[r] = (float)g.sigma[r];
         g.b2_f[r] = (float)(b * b);
+        g.inv_b2_f[r] = (b & (b - 1)) == 0 ? 1.0f / (float)(b * b) : 0.0f;
         const uint64_t c = (uint64_t)g.cells_side[r] * g.cells_side[r];
         maxcells = c > maxcells ? c : maxcells;
     }

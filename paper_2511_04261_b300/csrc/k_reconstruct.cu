@@ -154,13 +154,33 @@ struct FastK {
     static constexpr int NPXF = (C - 1 + 4) / C + 1;   // pixels an f32 chunk can touch (upper bound)
 };
 
+// Byte-permute selector for output word K of a chunk with phase P: byte i of the word is element
+// e = P + 4K + i, i.e. channel e % C of pixel e / C, which for C >= 2 is one of the two adjacent pixels
+// a = (P + 4K) / C and a + 1 (selector nibbles 0-3 and 4-7).
+template <int C>
+__host__ __device__ constexpr uint32_t word_sel(int e0) {
+    uint32_t sel = 0;
+    for (int i = 0; i < 4; ++i) {
+        const int pix = (e0 + i) / C - e0 / C, ch = (e0 + i) % C;
+        sel |= (uint32_t)(pix * 4 + ch) << (4 * i);
+    }
+    return sel;
+}
+
 template <int C, int P>
 __device__ __forceinline__ uint4 build_u8(const uint32_t *pv) {
-    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    uint32_t w[4];
+    if (C == 1) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const uint32_t byte = (pv[(P + i) / C] >> (8 * ((P + i) % C))) & 0xFFu;
-        w[i / 4] |= byte << (8 * (i % 4));
+        for (int k = 0; k < 4; ++k)
+            w[k] = __byte_perm(__byte_perm(pv[4 * k], pv[4 * k + 1], 0x0040), __byte_perm(pv[4 * k + 2], pv[4 * k + 3], 0x0040),
+                               0x5410);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int a = (P + 4 * k) / C;
+            w[k] = __byte_perm(pv[a], pv[a + 1], word_sel<C>(P + 4 * k));
+        }
     }
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
@@ -293,8 +313,8 @@ __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i,
                 }
                 vec = build_u8_phase<C>(p, pv);
             }
-            for (int rr = j; rr < jn; ++rr) {
-                uint8_t *dst = orow0 + (int64_t)rr * out_pitch + o;
+            uint8_t *dst = orow0 + (int64_t)j * out_pitch + o;
+            for (int rr = j; rr < jn; ++rr, dst += out_pitch) {
                 if (full) {
                     *reinterpret_cast<uint4 *>(dst) = vec;
                 } else {

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) k_release(const Geom g, const CallAr
                     reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
                 } else {
                     const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), g.sigma_f[r]);
-                    const float v = noisy_mean(S[ch], g.b2_f[r], eta, g.R_f);
+                    const float v = noisy_mean(S[ch], g.b2_f[r], g.inv_b2_f[r], eta, g.R_f);
                     if (g.dtype == DP_PIX_REC_F32)
                         reinterpret_cast<float *>(dst)[ch] = v;
                     else
@@ -327,7 +327,7 @@ __device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint
             reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
         } else {
             const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), g.sigma_f[r]);
-            const float v = noisy_mean(S[ch], g.b2_f[r], eta, g.R_f);
+            const float v = noisy_mean(S[ch], g.b2_f[r], g.inv_b2_f[r], eta, g.R_f);
             if (g.dtype == DP_PIX_REC_F32)
                 reinterpret_cast<float *>(dst)[ch] = v;
             else
@@ -366,7 +366,9 @@ __device__ __forceinline__ void gcell_block_sum(const uint16_t *src, int stride,
 // sum from its (b_r/g)^2 g-cells (L lanes per cell, combined by shuffles) into shared memory.  Phase 2:
 // one thread per cell draws the noise, clips and stores, so every lane works in the costly noise step.
 // ------------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_emit_row(const Geom g, const CallArgs a) {
+constexpr int kEmitThreads = 512;
+
+__global__ void __launch_bounds__(kEmitThreads) k_emit_row(const Geom g, const CallArgs a) {
     extern __shared__ __align__(16) uint8_t dyn[];
     const int C = g.C, gcs = g.T / g.g, GX = g.gx_cells, GC = g.GC;
     const uint32_t f = blockIdx.x / g.GR;
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(kThreads) k_emit_row(const Geom g, const CallA
     }
     // phase 1: cell sums
     const int lane = threadIdx.x & 31;
-    for (int tx = threadIdx.x >> 5; tx < GC; tx += kThreads / 32) {
+    for (int tx = threadIdx.x >> 5; tx < GC; tx += kEmitThreads / 32) {
         const int r = map_s[tx];
         const int cs = g.cells_side[r], nb = g.grid[r] / g.g, cells = cs * cs;
         int L = 1;
@@ -439,7 +441,7 @@ __global__ void __launch_bounds__(kThreads) k_emit_row(const Geom g, const CallA
         }
         const int tx = lo, c = e - base_s[tx];
         const int r = map_s[tx], cs = g.cells_side[r];
-        const int cy = c / cs, cx = c - cy * cs;
+        const int cy = (cs & (cs - 1)) == 0 ? c >> (__ffs(cs) - 1) : c / cs, cx = c - cy * cs;
         const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(GC * cs) + (uint32_t)(tx * cs + cx);
         const uint32_t *d = sums + ((size_t)tx * maxcells + c) * C;
         uint32_t S[4] = {0u, 0u, 0u, 0u};
@@ -544,7 +546,7 @@ cudaError_t launch_emit(const Geom &g, const CallArgs &a, cudaStream_t s) {
     if (smem <= 160 * 1024) {
         cudaFuncSetAttribute(k_emit_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         prof_begin("k_emit", s);
-        k_emit_row<<<a.n_frames * (unsigned)g.GR, kThreads, smem, s>>>(g, a);
+        k_emit_row<<<a.n_frames * (unsigned)g.GR, kEmitThreads, smem, s>>>(g, a);
         prof_end("k_emit", s);
         return cudaGetLastError();
     }
