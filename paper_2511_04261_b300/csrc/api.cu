@@ -215,6 +215,8 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     uint64_t off = 0;
     g.ws_tileoff = off;
     off = a256(off + 4ull * ntiles);
+    g.ws_tilelist = off;
+    off = a256(off + 4ull * ntiles);
     g.ws_keys = off;
     if (g.source == DP_PIX_SRC_VARIANCE) off = a256(off + 8ull * ntiles);
     g.ws_gsum = off;

@@ -42,7 +42,7 @@ struct Geom {
     int32_t idx_bits;                 // bits for the tile index in a packed rank key
     uint64_t rowidx_offset, map_offset, payload_offset, record_cap;
     // workspace layout, per frame
-    uint64_t ws_per_frame, ws_tileoff, ws_keys, ws_gsum;
+    uint64_t ws_per_frame, ws_tileoff, ws_tilelist, ws_keys, ws_gsum;
     int32_t gx_cells, gy_cells;       // g-image: (GR*T/g) rows of (GC*T/g) g-cells, C u16 sums each
     // launch shapes
     int32_t seg_tiles;                // tiles per staged segment of a tile row

@@ -62,10 +62,12 @@ struct FinalizeSmem {
     uint64_t roff[kMaxK];
     uint64_t tile_bytes[kMaxK];
     uint32_t count[kMaxK];
+    uint32_t tstart[kMaxK];  // first position of region r's tiles in the region-ordered tile list
     dp_pix_record_header hdr;
 };
 
-// Lays out the record of frame f from the map in shared memory (see file comment).
+// Lays out the record of frame f from the map in shared memory (see file comment); also writes the
+// workspace's per-tile payload offsets and the tile ids in record order (region-major, row-major).
 __device__ void finalize_frame(const Geom &g, const CallArgs &a, uint32_t f, const uint8_t *map_s, bool write_map,
                                FinalizeSmem &sm) {
     const uint32_t n = g.ntiles;
@@ -84,11 +86,14 @@ __device__ void finalize_frame(const Geom &g, const CallArgs &a, uint32_t f, con
     uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
     if (threadIdx.x == 0) {
         uint64_t off = g.payload_offset;
+        uint32_t tacc = 0;
         for (int r = 0; r < g.K; ++r) {
             const uint64_t cs = (uint64_t)g.cells_side[r];
             sm.tile_bytes[r] = cs * cs * (uint64_t)g.C * (uint64_t)g.es;
             sm.roff[r] = off;
             sm.count[r] = total[r];
+            sm.tstart[r] = tacc;
+            tacc += total[r];
             off = align16_u64(off + (uint64_t)total[r] * sm.tile_bytes[r]);
         }
         dp_pix_record_header &h = sm.hdr;
@@ -121,6 +126,7 @@ __device__ void finalize_frame(const Geom &g, const CallArgs &a, uint32_t f, con
     // per-tile offsets and tile-row index
     uint32_t *tileoff = reinterpret_cast<uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff);
     uint32_t *rowidx = reinterpret_cast<uint32_t *>(rec + g.rowidx_offset);
+    uint32_t *tilelist = reinterpret_cast<uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tilelist);
     uint32_t run[kMaxK];
 #pragma unroll
     for (int r = 0; r < kMaxK; ++r) run[r] = excl[r];
@@ -137,6 +143,7 @@ __device__ void finalize_frame(const Geom &g, const CallArgs &a, uint32_t f, con
         for (int q = 0; q < kMaxK; ++q)
             if (r == (uint32_t)q) { ri = run[q]; run[q] = ri + 1; }
         tileoff[i] = (uint32_t)(sm.roff[r] + (uint64_t)ri * sm.tile_bytes[r]);
+        tilelist[sm.tstart[r] + ri] = i;  // tiles in record (payload) order
     }
     if (write_map) {
         uint8_t *map = rec + g.map_offset;

@@ -107,7 +107,7 @@ __device__ __forceinline__ uint32_t to_u8(float v) { return __float2uint_rn(fmin
 
 // Per-segment tile table shared by both paths.
 struct SegTiles {
-    int32_t b[kMaxSegTiles], cs[kMaxSegTiles], base[kMaxSegTiles + 1];
+    int32_t reg[kMaxSegTiles], b[kMaxSegTiles], cs[kMaxSegTiles], base[kMaxSegTiles + 1];
     uint64_t off[kMaxSegTiles];
 };
 
@@ -118,6 +118,10 @@ __device__ void seg_tile_info(const uint8_t *rec, const RecGeom &rg, int ty, int
                               int32_t *status, SegTiles &st, uint32_t *cnt_s) {
     const uint8_t *maprow = rec + rg.map_offset + (uint64_t)ty * rg.GC;
     if (threadIdx.x < kMaxK) cnt_s[threadIdx.x] = 0u;
+    if (threadIdx.x < ns) {
+        const int r = maprow[tx0 + threadIdx.x];
+        st.reg[threadIdx.x] = r < rg.K ? r : 0;
+    }
     __syncthreads();
     for (int x = threadIdx.x; x < tx0; x += blockDim.x) {
         const int r = maprow[x];
@@ -126,10 +130,9 @@ __device__ void seg_tile_info(const uint8_t *rec, const RecGeom &rg, int ty, int
     __syncthreads();
     if (threadIdx.x < ns) {
         const int t = threadIdx.x;
-        int r = maprow[tx0 + t];
-        if (r >= rg.K) r = 0;
+        const int r = st.reg[t];
         uint32_t before = reinterpret_cast<const uint32_t *>(rec + rg.rowidx_offset)[ty * rg.K + r] + cnt_s[r];
-        for (int x = tx0; x < tx0 + t; ++x) before += (maprow[x] == r);
+        for (int x = 0; x < t; ++x) before += (st.reg[x] == r);  // the segment's region ids, in shared memory
         int b = rg.grid[r], cs = rg.T / b;
         uint64_t off = rg.region_offset[r] + (uint64_t)before * (uint64_t)(cs * cs * rg.C * rg.es);
         if (before >= rg.count[r]) {  // inconsistent index: read the header instead of leaving the record
@@ -222,18 +225,28 @@ __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i,
     const int tx0 = sg * rg.SR;
     const int ns = min(rg.SR, rg.GC - tx0);
     seg_tile_info(rec, rg, ty, tx0, ns, rec_i, status, st, cnt_s);
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int t = 0; t < ns; ++t) {
-            st.base[t] = acc;
-            acc += st.cs[t] * st.cs[t];
+    if (threadIdx.x < 32) {  // exclusive prefix of the tiles' cell counts, two tiles per lane
+        const int l = threadIdx.x;
+        const int c0 = 2 * l < ns ? st.cs[2 * l] * st.cs[2 * l] : 0;
+        const int c1 = 2 * l + 1 < ns ? st.cs[2 * l + 1] * st.cs[2 * l + 1] : 0;
+        int incl = c0 + c1;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (l >= off) incl += v;
         }
-        st.base[ns] = acc;
+        const int excl = incl - c0 - c1;
+        if (2 * l <= ns) st.base[2 * l] = excl;
+        if (2 * l + 1 <= ns) st.base[2 * l + 1] = excl + c0;
+        if (l == 31) st.base[ns] = incl;  // the total (ns may be 64)
     }
     // pixel column -> (tile, cell column)
+    const bool tp2 = (T & (T - 1)) == 0;
+    const int lt = __ffs(T) - 1;
     for (int px = threadIdx.x; px < ns * T; px += blockDim.x) {
-        const int t = px / T;
-        colinfo[px] = ((uint32_t)t << 16) | (uint32_t)((px - t * T) / st.b[t]);
+        const int t = tp2 ? px >> lt : px / T;
+        const int b = st.b[t], pt = px - t * T;
+        colinfo[px] = ((uint32_t)t << 16) | (uint32_t)((b & (b - 1)) == 0 ? pt >> (__ffs(b) - 1) : pt / b);
     }
     __syncthreads();
     // cell values of the segment, converted once

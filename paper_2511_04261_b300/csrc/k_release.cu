@@ -336,161 +336,66 @@ __device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint
     }
 }
 
-// Sum of the nb x nb g-cells of one b_r-cell, split over L lanes of a warp (all 32 lanes call it).
-// src: g-cell (0, 0) of the cell; stride: u16 values between g-image rows.
-__device__ __forceinline__ void gcell_block_sum(const uint16_t *src, int stride, int nb, int C, int lig, int L,
-                                                bool active, uint32_t *S) {
-    S[0] = S[1] = S[2] = S[3] = 0u;
-    if (active) {
-        const int ng = nb * nb;
-        const bool pow2 = (nb & (nb - 1)) == 0;
-        const int lg = __ffs(nb) - 1;
-        for (int gi = lig; gi < ng; gi += L) {
-            const int yy = pow2 ? (gi >> lg) : gi / nb;
-            const int xx = gi - yy * nb;
-            const uint16_t *p = src + (size_t)yy * stride + (size_t)xx * C;
-#pragma unroll
-            for (int ch = 0; ch < 4; ++ch)
-                if (ch < C) S[ch] += p[ch];
-        }
-    }
-    for (int off = L >> 1; off > 0; off >>= 1) {
-#pragma unroll
-        for (int ch = 0; ch < 4; ++ch) S[ch] += __shfl_xor_sync(0xffffffffu, S[ch], off);
-    }
-}
-
 // ------------------------------------------------------------------------------------------------------
-// k_emit_row: one CTA per (frame, tile row).  The row's g-cell sums are one contiguous band of the g-image;
-// it is copied into shared memory with coalesced loads.  Phase 1: one warp per tile assembles each b_r-cell
-// sum from its (b_r/g)^2 g-cells (L lanes per cell, combined by shuffles) into shared memory.  Phase 2:
-// one thread per cell draws the noise, clips and stores, so every lane works in the costly noise step.
+// k_emit: walks each record's payload in order, one thread per cell.  Element e of the payload lies in the
+// region whose cumulative cell count passes e; the region-ordered tile list gives its tile, and the cell
+// sum is assembled from the tile's (b_r/g)^2 g-cell sums in the g-image.  Consecutive threads therefore
+// write consecutive record bytes and share one region, so a warp's lanes do equal work.
 // ------------------------------------------------------------------------------------------------------
-constexpr int kEmitThreads = 512;
-
-__global__ void __launch_bounds__(kEmitThreads) k_emit_row(const Geom g, const CallArgs a) {
-    extern __shared__ __align__(16) uint8_t dyn[];
-    const int C = g.C, gcs = g.T / g.g, GX = g.gx_cells, GC = g.GC;
-    const uint32_t f = blockIdx.x / g.GR;
-    const int ty = (int)(blockIdx.x - f * g.GR);
-    const uint64_t band_vals = (uint64_t)gcs * GX * C;  // u16 values in the band
-    int maxcells = 1;
-    for (int r = 0; r < g.K; ++r) maxcells = max(maxcells, g.cells_side[r] * g.cells_side[r]);
-    uint16_t *band = reinterpret_cast<uint16_t *>(dyn);
-    uint32_t *sums = reinterpret_cast<uint32_t *>(dyn + ((band_vals * 2 + 15) & ~15ull));  // [tile][cell][C]
-    uint32_t *toff_s = sums + (size_t)GC * maxcells * C;
-    int32_t *base_s = reinterpret_cast<int32_t *>(toff_s + GC);  // [GC + 1] cell prefix
-    uint8_t *map_s = reinterpret_cast<uint8_t *>(base_s + GC + 1);
-    const uint8_t *wsf = a.ws + (uint64_t)f * g.ws_per_frame;
-    const uint16_t *src = reinterpret_cast<const uint16_t *>(wsf + g.ws_gsum) + (uint64_t)ty * band_vals;
-    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (band_vals * 2) % 16 == 0) {
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-        for (uint64_t i = threadIdx.x; i < band_vals * 2 / 16; i += blockDim.x) reinterpret_cast<uint4 *>(band)[i] = s4[i];
-    } else {
-        for (uint64_t i = threadIdx.x; i < band_vals; i += blockDim.x) band[i] = src[i];
-    }
+__global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs a) {
+    __shared__ uint32_t cstart[kMaxK + 1], tstart[kMaxK + 1];
+    __shared__ uint64_t roff[kMaxK];
+    const uint32_t f = blockIdx.y;
     uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
-    const uint32_t *toff = reinterpret_cast<const uint32_t *>(wsf + g.ws_tileoff) + (uint64_t)ty * GC;
-    for (int tx = threadIdx.x; tx < GC; tx += blockDim.x) {
-        toff_s[tx] = toff[tx];
-        int r = rec[g.map_offset + (uint64_t)ty * GC + tx];
-        map_s[tx] = (uint8_t)(r < g.K ? r : 0);
+    if (threadIdx.x == 0) {
+        const dp_pix_record_header *h = reinterpret_cast<const dp_pix_record_header *>(rec);
+        uint32_t c = 0, t = 0;
+        for (int r = 0; r < g.K; ++r) {
+            const uint32_t n = min(h->count[r], g.ntiles);
+            cstart[r] = c;
+            tstart[r] = t;
+            roff[r] = h->region_offset[r];
+            c += n * (uint32_t)(g.cells_side[r] * g.cells_side[r]);
+            t += n;
+        }
+        cstart[g.K] = c;
+        tstart[g.K] = t;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int tx = 0; tx < GC; ++tx) {
-            base_s[tx] = acc;
-            const int cs = g.cells_side[map_s[tx]];
-            acc += cs * cs;
-        }
-        base_s[GC] = acc;
-    }
-    // phase 1: cell sums
-    const int lane = threadIdx.x & 31;
-    for (int tx = threadIdx.x >> 5; tx < GC; tx += kEmitThreads / 32) {
-        const int r = map_s[tx];
-        const int cs = g.cells_side[r], nb = g.grid[r] / g.g, cells = cs * cs;
-        int L = 1;
-        while (2 * L * cells <= 32) L *= 2;
-        const int per_pass = 32 / L;
-        for (int c0 = 0; c0 < cells; c0 += per_pass) {
-            const int c = c0 + lane / L, lig = lane & (L - 1);
-            const bool active = c < cells;
-            const int cy = active ? c / cs : 0, cx = active ? c - cy * cs : 0;
-            uint32_t S[4];
-            gcell_block_sum(band + ((size_t)cy * nb * GX + (size_t)tx * gcs + (size_t)cx * nb) * C, GX * C, nb, C,
-                            lig, L, active, S);
-            if (active && lig == 0) {
-                uint32_t *d = sums + ((size_t)tx * maxcells + c) * C;
+    const uint32_t total = tstart[g.K] <= g.ntiles ? cstart[g.K] : 0u;
+    const uint8_t *wsf = a.ws + (uint64_t)f * g.ws_per_frame;
+    const uint32_t *tilelist = reinterpret_cast<const uint32_t *>(wsf + g.ws_tilelist);
+    const uint16_t *gimg = reinterpret_cast<const uint16_t *>(wsf + g.ws_gsum);
+    const int C = g.C, gcs = g.T / g.g;
+    const size_t rowvals = (size_t)g.gx_cells * C;
+    const uint64_t frame = a.frame_idx0 + f;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        int r = 0;
+        while (r + 1 < g.K && e >= cstart[r + 1]) ++r;
+        const uint32_t local = e - cstart[r];
+        const int cs = g.cells_side[r];
+        const bool p2 = (cs & (cs - 1)) == 0;
+        const int lcs = __ffs(cs) - 1;
+        const uint32_t cells = (uint32_t)(cs * cs);
+        const uint32_t k = p2 ? local >> (2 * lcs) : local / cells;
+        const int c = (int)(local - k * cells);
+        const int cy = p2 ? c >> lcs : c / cs, cx = c - cy * cs;
+        const uint32_t tile = tilelist[tstart[r] + k];
+        const uint32_t ty = tile / (uint32_t)g.GC, tx = tile - ty * (uint32_t)g.GC;
+        const int nb = g.grid[r] / g.g;
+        const uint16_t *p0 = gimg + ((size_t)(ty * gcs + cy * nb)) * rowvals + ((size_t)tx * gcs + (size_t)cx * nb) * C;
+        uint32_t S[4] = {0u, 0u, 0u, 0u};
+        for (int yy = 0; yy < nb; ++yy) {
+            const uint16_t *p = p0 + (size_t)yy * rowvals;
+            for (int xx = 0; xx < nb; ++xx) {
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch)
-                    if (ch < C) d[ch] = S[ch];
+                    if (ch < C) S[ch] += p[xx * C + ch];
             }
         }
+        const uint32_t cell_idx = (ty * cs + cy) * (uint32_t)(g.GC * cs) + tx * cs + cx;
+        emit_cell(g, a, rec + roff[r] + (uint64_t)local * C * g.es, S, r, cell_idx, frame);
     }
-    __syncthreads();
-    // phase 2: one thread per cell of the row
-    const int total = base_s[GC];
-    const uint64_t frame = a.frame_idx0 + f;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        int lo = 0, hi = GC - 1;  // last tile whose first cell is <= e
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (base_s[mid] <= e) lo = mid; else hi = mid - 1;
-        }
-        const int tx = lo, c = e - base_s[tx];
-        const int r = map_s[tx], cs = g.cells_side[r];
-        const int cy = (cs & (cs - 1)) == 0 ? c >> (__ffs(cs) - 1) : c / cs, cx = c - cy * cs;
-        const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(GC * cs) + (uint32_t)(tx * cs + cx);
-        const uint32_t *d = sums + ((size_t)tx * maxcells + c) * C;
-        uint32_t S[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int ch = 0; ch < 4; ++ch)
-            if (ch < C) S[ch] = d[ch];
-        emit_cell(g, a, rec + toff_s[tx] + (uint64_t)c * C * g.es, S, r, cell_idx, frame);
-    }
-}
-
-// k_emit: fallback for tile rows whose g-image band does not fit shared memory; one warp per tile, reading
-// the g-image in global memory.
-__global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs a) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t wid = (uint64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    if (wid >= (uint64_t)a.n_frames * g.ntiles) return;  // whole warp
-    const uint32_t f = (uint32_t)(wid / g.ntiles);
-    const uint32_t tile = (uint32_t)(wid - (uint64_t)f * g.ntiles);
-    const uint32_t ty = tile / g.GC, tx = tile - ty * g.GC;
-    uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
-    int r = rec[g.map_offset + tile];
-    if (r >= g.K) r = 0;
-    const uint32_t toff =
-        reinterpret_cast<const uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff)[tile];
-    const uint16_t *gimg = reinterpret_cast<const uint16_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_gsum);
-    const int C = g.C, gcs = g.T / g.g;
-    const int cs = g.cells_side[r], nb = g.grid[r] / g.g, cells = cs * cs;
-    int L = 1;
-    while (2 * L * cells <= 32) L *= 2;
-    const int per_pass = 32 / L;
-    const uint64_t frame = a.frame_idx0 + f;
-    for (int c0 = 0; c0 < cells; c0 += per_pass) {
-        const int c = c0 + lane / L, lig = lane & (L - 1);
-        const bool active = c < cells;
-        const int cy = active ? c / cs : 0, cx = active ? c - cy * cs : 0;
-        uint32_t S[4];
-        gcell_block_sum(gimg + (((size_t)ty * gcs + (size_t)cy * nb) * g.gx_cells + (size_t)tx * gcs + (size_t)cx * nb) * C,
-                        g.gx_cells * C, nb, C, lig, L, active, S);
-        if (active && lig == 0)
-            emit_cell(g, a, rec + toff + (uint64_t)c * C * g.es, S, r,
-                      (ty * cs + cy) * (uint32_t)(g.GC * cs) + tx * cs + cx, frame);
-    }
-}
-
-size_t emit_row_smem(const Geom &g) {
-    int maxcells = 1;
-    for (int r = 0; r < g.K; ++r) maxcells = std::max(maxcells, g.cells_side[r] * g.cells_side[r]);
-    const uint64_t band = (((uint64_t)(g.T / g.g) * g.gx_cells * g.C * 2 + 15) & ~15ull);
-    return band + (uint64_t)g.GC * maxcells * g.C * 4 + 4ull * g.GC + 4ull * (g.GC + 1) + g.GC;
 }
 
 size_t seg_smem(const Geom &g, int bands_per_tile) {
@@ -542,18 +447,14 @@ cudaError_t launch_tile_stats(const Geom &g, const CallArgs &a, cudaStream_t s) 
 }
 
 cudaError_t launch_emit(const Geom &g, const CallArgs &a, cudaStream_t s) {
-    const size_t smem = emit_row_smem(g);
-    if (smem <= 160 * 1024) {
-        cudaFuncSetAttribute(k_emit_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        prof_begin("k_emit", s);
-        k_emit_row<<<a.n_frames * (unsigned)g.GR, kEmitThreads, smem, s>>>(g, a);
-        prof_end("k_emit", s);
-        return cudaGetLastError();
-    }
-    const uint64_t warps = (uint64_t)a.n_frames * g.ntiles;
-    const uint64_t blocks = (warps + kThreads / 32 - 1) / (kThreads / 32);
+    // enough resident threads per frame to cover the GPU a few times over, looping over the cells
+    int per_frame = (8 * sm_count() + (int)a.n_frames - 1) / (int)a.n_frames;
+    int maxcells = 1;
+    for (int r = 0; r < g.K; ++r) maxcells = std::max(maxcells, g.cells_side[r] * g.cells_side[r]);
+    const int need = (int)(((uint64_t)g.ntiles * maxcells + kThreads - 1) / kThreads);
+    per_frame = std::max(1, std::min(per_frame, need));
     prof_begin("k_emit", s);
-    k_emit<<<(unsigned)blocks, kThreads, 0, s>>>(g, a);
+    k_emit<<<dim3(per_frame, a.n_frames), kThreads, 0, s>>>(g, a);
     prof_end("k_emit", s);
     return cudaGetLastError();
 }
