@@ -191,8 +191,11 @@ __global__ void __launch_bounds__(kFrameThreads) k_rank(const Geom g, const Call
     for (uint32_t i = threadIdx.x; i < npow2; i += blockDim.x)
         keys_s[i] = i < n ? ((keys[i] << g.idx_bits) | (uint64_t)i) : ~0ull;
     __syncthreads();
+    // bitonic sort; partner distances >= 32 go through shared memory, the rest of each merge level is done
+    // in registers with warp shuffles (npow2 is a multiple of 32, so every warp is full)
     for (uint32_t k = 2; k <= npow2; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        uint32_t j = k >> 1;
+        for (; j >= 32; j >>= 1) {
             for (uint32_t i = threadIdx.x; i < npow2; i += blockDim.x) {
                 const uint32_t ixj = i ^ j;
                 if (ixj > i) {
@@ -206,6 +209,17 @@ __global__ void __launch_bounds__(kFrameThreads) k_rank(const Geom g, const Call
             }
             __syncthreads();
         }
+        for (uint32_t i = threadIdx.x; i < npow2; i += blockDim.x) {
+            uint64_t x = keys_s[i];
+            const bool ascending = (i & k) == 0;
+            for (uint32_t jj = j; jj > 0; jj >>= 1) {
+                const uint64_t y = __shfl_xor_sync(0xffffffffu, x, (int)jj);
+                const bool lower = (i & jj) == 0;
+                x = (lower == ascending) ? (x < y ? x : y) : (x < y ? y : x);
+            }
+            keys_s[i] = x;
+        }
+        __syncthreads();
     }
     const uint64_t mask = (1ull << g.idx_bits) - 1ull;
     for (uint32_t p = threadIdx.x; p < n; p += blockDim.x) {
@@ -245,7 +259,7 @@ cudaError_t launch_finalize_map(const Geom &g, const CallArgs &a, cudaStream_t s
 }
 
 cudaError_t launch_rank(const Geom &g, const CallArgs &a, cudaStream_t s) {
-    uint32_t npow2 = 1;
+    uint32_t npow2 = 32;  // at least one full warp for the shuffle stages
     while (npow2 < g.ntiles) npow2 <<= 1;
     const size_t smem = sizeof(FinalizeSmem) + (size_t)npow2 * 8 + g.ntiles;
     static bool attr_set = false;
