@@ -40,6 +40,7 @@ struct Geom {
     int32_t var_onepass;              // VARIANCE with 4 <= g <= 16: g-cell sums kept, image read once
     int32_t b_min;
     int32_t idx_bits;                 // bits for the tile index in a packed rank key
+    int32_t val_bits;                 // bits of a packed (key, tile index) value
     uint64_t rowidx_offset, map_offset, payload_offset, record_cap;
     // workspace layout, per frame
     uint64_t ws_per_frame, ws_tileoff, ws_tilelist, ws_keys, ws_gsum;

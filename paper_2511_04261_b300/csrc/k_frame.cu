@@ -180,51 +180,71 @@ __global__ void __launch_bounds__(kFrameThreads) k_finalize(const Geom g, const 
     finalize_frame(g, a, f, map_s, from_labels != 0, sm);
 }
 
-// VARIANCE classes: rank tiles by (key, index) ascending, class q = floor(K * rank / n).
-__global__ void __launch_bounds__(kFrameThreads) k_rank(const Geom g, const CallArgs a, uint32_t npow2) {
+// VARIANCE classes: tiles ranked by (key, index) ascending get class q = floor(K * rank / n).  Only the
+// K - 1 class boundaries matter: the tile of rank ceil(q n / K) starts class q.  Each boundary value is
+// found exactly by a radix select over the unique packed values key << idx_bits | index (8-bit digits from
+// the top); a tile's class is then the number of boundaries not above its value.
+__global__ void __launch_bounds__(kFrameThreads) k_rank(const Geom g, const CallArgs a) {
     extern __shared__ __align__(16) uint8_t dyn[];
     FinalizeSmem &sm = *reinterpret_cast<FinalizeSmem *>(dyn);
-    uint64_t *keys_s = reinterpret_cast<uint64_t *>(dyn + sizeof(FinalizeSmem));
-    uint8_t *map_s = reinterpret_cast<uint8_t *>(keys_s + npow2);
     const uint32_t f = blockIdx.x, n = g.ntiles;
+    uint64_t *vals = reinterpret_cast<uint64_t *>(dyn + sizeof(FinalizeSmem));
+    uint8_t *map_s = reinterpret_cast<uint8_t *>(vals + n);
+    __shared__ uint32_t hist[kMaxK - 1][256];
+    __shared__ uint64_t prefix[kMaxK - 1];
+    __shared__ uint32_t target[kMaxK - 1];
+    const int Q = g.K - 1;
     const uint64_t *keys = reinterpret_cast<const uint64_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_keys);
-    for (uint32_t i = threadIdx.x; i < npow2; i += blockDim.x)
-        keys_s[i] = i < n ? ((keys[i] << g.idx_bits) | (uint64_t)i) : ~0ull;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) vals[i] = (keys[i] << g.idx_bits) | (uint64_t)i;
+    if ((int)threadIdx.x < Q) {
+        prefix[threadIdx.x] = 0ull;
+        target[threadIdx.x] = (uint32_t)(((uint64_t)(threadIdx.x + 1) * n + g.K - 1) / g.K);  // 0-based rank
+    }
     __syncthreads();
-    // bitonic sort; partner distances >= 32 go through shared memory, the rest of each merge level is done
-    // in registers with warp shuffles (npow2 is a multiple of 32, so every warp is full)
-    for (uint32_t k = 2; k <= npow2; k <<= 1) {
-        uint32_t j = k >> 1;
-        for (; j >= 32; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < npow2; i += blockDim.x) {
-                const uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t x = keys_s[i], y = keys_s[ixj];
-                    const bool ascending = (i & k) == 0;
-                    if ((x > y) == ascending) {
-                        keys_s[i] = y;
-                        keys_s[ixj] = x;
-                    }
-                }
-            }
-            __syncthreads();
+    const int passes = Q > 0 ? (g.val_bits + 7) / 8 : 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * (passes - 1 - pass);
+        for (int i = threadIdx.x; i < Q * 256; i += blockDim.x) hist[i >> 8][i & 255] = 0u;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint64_t v = vals[i];
+            const uint64_t hi = shift + 8 >= 64 ? 0ull : v >> (shift + 8);
+            const uint32_t d = (uint32_t)(v >> shift) & 255u;
+            for (int q = 0; q < Q; ++q)
+                if (hi == prefix[q]) atomicAdd(&hist[q][d], 1u);
         }
-        for (uint32_t i = threadIdx.x; i < npow2; i += blockDim.x) {
-            uint64_t x = keys_s[i];
-            const bool ascending = (i & k) == 0;
-            for (uint32_t jj = j; jj > 0; jj >>= 1) {
-                const uint64_t y = __shfl_xor_sync(0xffffffffu, x, (int)jj);
-                const bool lower = (i & jj) == 0;
-                x = (lower == ascending) ? (x < y ? x : y) : (x < y ? y : x);
+        __syncthreads();
+        if (warp < Q) {  // warp q finds the digit bucket that holds its target rank
+            uint32_t c[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                c[j] = hist[warp][8 * lane + j];
+                sum += c[j];
             }
-            keys_s[i] = x;
+            uint32_t incl = sum;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += t;
+            }
+            const uint32_t excl = incl - sum, t = target[warp];
+            if (excl <= t && t < incl) {
+                uint32_t acc = excl;
+                int j = 0;
+                while (j < 7 && acc + c[j] <= t) acc += c[j++];
+                prefix[warp] = (prefix[warp] << 8) | (uint64_t)(8 * lane + j);
+                target[warp] = t - acc;
+            }
         }
         __syncthreads();
     }
     const uint64_t mask = (1ull << g.idx_bits) - 1ull;
-    for (uint32_t p = threadIdx.x; p < n; p += blockDim.x) {
-        const uint32_t idx = (uint32_t)(keys_s[p] & mask);
-        map_s[idx] = (uint8_t)(((uint64_t)g.K * p) / n);
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint64_t v = vals[i];
+        int cls = 0;
+        for (int q = 0; q < Q; ++q) cls += v >= prefix[q] ? 1 : 0;
+        map_s[v & mask] = (uint8_t)cls;
     }
     __syncthreads();
     finalize_frame(g, a, f, map_s, true, sm);
@@ -259,16 +279,10 @@ cudaError_t launch_finalize_map(const Geom &g, const CallArgs &a, cudaStream_t s
 }
 
 cudaError_t launch_rank(const Geom &g, const CallArgs &a, cudaStream_t s) {
-    uint32_t npow2 = 32;  // at least one full warp for the shuffle stages
-    while (npow2 < g.ntiles) npow2 <<= 1;
-    const size_t smem = sizeof(FinalizeSmem) + (size_t)npow2 * 8 + g.ntiles;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr_set = true;
-    }
+    const size_t smem = sizeof(FinalizeSmem) + (size_t)g.ntiles * 8 + g.ntiles;
+    cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prof_begin("k_rank", s);
-    k_rank<<<a.n_frames, kFrameThreads, smem, s>>>(g, a, npow2);
+    k_rank<<<a.n_frames, kFrameThreads, smem, s>>>(g, a);
     prof_end("k_rank", s);
     return cudaGetLastError();
 }

@@ -336,6 +336,34 @@ __device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint
     }
 }
 
+// Sum of an nb x nb block of g-cells (C u16 channel sums each; rows rowvals values apart) into S[0..C).
+// With nb even and 4-byte alignment a pair of g-cells is C whole words whose halves map to compile-time
+// channels, so each row is read with C * nb / 2 word loads that can all be in flight together.
+template <int C>
+__device__ __forceinline__ void gblock_sum(const uint16_t *p0, size_t rowvals, int nb, uint32_t *S) {
+    const bool pairs = (nb % 2 == 0) && (reinterpret_cast<uintptr_t>(p0) & 3) == 0 && (rowvals & 1) == 0;
+    for (int yy = 0; yy < nb; ++yy) {
+        const uint16_t *p = p0 + (size_t)yy * rowvals;
+        if (pairs) {
+            const uint32_t *w = reinterpret_cast<const uint32_t *>(p);
+#pragma unroll 4
+            for (int pr = 0; pr < nb / 2; ++pr) {
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const uint32_t x = w[pr * C + k];
+                    S[(2 * k) % C] += x & 0xFFFFu;
+                    S[(2 * k + 1) % C] += x >> 16;
+                }
+            }
+        } else {
+            for (int xx = 0; xx < nb; ++xx) {
+#pragma unroll
+                for (int ch = 0; ch < C; ++ch) S[ch] += p[xx * C + ch];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------------------
 // k_emit: walks each record's payload in order, one thread per cell.  Element e of the payload lies in the
 // region whose cumulative cell count passes e; the region-ordered tile list gives its tile, and the cell
@@ -385,13 +413,11 @@ __global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs 
         const int nb = g.grid[r] / g.g;
         const uint16_t *p0 = gimg + ((size_t)(ty * gcs + cy * nb)) * rowvals + ((size_t)tx * gcs + (size_t)cx * nb) * C;
         uint32_t S[4] = {0u, 0u, 0u, 0u};
-        for (int yy = 0; yy < nb; ++yy) {
-            const uint16_t *p = p0 + (size_t)yy * rowvals;
-            for (int xx = 0; xx < nb; ++xx) {
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch)
-                    if (ch < C) S[ch] += p[xx * C + ch];
-            }
+        switch (C) {
+            case 1: gblock_sum<1>(p0, rowvals, nb, S); break;
+            case 2: gblock_sum<2>(p0, rowvals, nb, S); break;
+            case 3: gblock_sum<3>(p0, rowvals, nb, S); break;
+            default: gblock_sum<4>(p0, rowvals, nb, S); break;
         }
         const uint32_t cell_idx = (ty * cs + cy) * (uint32_t)(g.GC * cs) + tx * cs + cx;
         emit_cell(g, a, rec + roff[r] + (uint64_t)local * C * g.es, S, r, cell_idx, frame);
