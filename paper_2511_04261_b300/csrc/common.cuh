@@ -97,21 +97,28 @@ __device__ __forceinline__ uint4 cell_noise_words(uint64_t seed, uint32_t cell_i
 }
 
 // Laplace(0, sigma) by the inverse CDF at u = (x + 1/2) / 2^32 (Eq. 9).  With k = x (lower half) or
-// k = 2^32-1-x (upper half, sign flipped), ln(2u) or ln(2(1-u)) is ln t, t = (k + 1/2) / 2^31.  For
-// t < 1/2 logf(t) is well conditioned; for t >= 1/2 ln t = log1pf(-(j + 1/2) / 2^31) with the exact
-// integer j = 2^31-1-k, so no cancellation happens near t = 1.
+// k = 2^32-1-x (upper half, sign flipped), ln(2u) or ln(2(1-u)) is ln t, t = (k + 1/2) / 2^31.  Both halves
+// use one log1pf call so that a warp whose lanes fall in different halves runs it once:
+//  - t < 1/2: t = 2^e * m with m in [1, 2) read from the float's exponent and mantissa, so
+//    ln t = e ln 2 + log1p(m - 1) with m - 1 exact;
+//  - t >= 1/2: ln t = log1p(-(j + 1/2) / 2^31) with the exact integer j = 2^31-1-k, so nothing cancels
+//    near t = 1.
 __device__ __forceinline__ float laplace_from_word(uint32_t x, float sigma) {
     const bool upper = (x >> 31) != 0u;
     const uint32_t k = upper ? ~x : x;
-    float lnt;
+    float arg, off;
     if (k < (1u << 30)) {
-        const float t = (__uint2float_rn(k) + 0.5f) * 0x1p-31f;
-        lnt = logf(t);
+        const float t = (__uint2float_rn(k) + 0.5f) * 0x1p-31f;  // a normal float in [2^-32, 1/2)
+        const int bits = __float_as_int(t);
+        const int e = ((bits >> 23) & 0xFF) - 127;
+        arg = __int_as_float((bits & 0x007FFFFF) | 0x3F800000) - 1.0f;
+        off = (float)e * 0.693147180559945309f;
     } else {
         const uint32_t j = 0x7FFFFFFFu - k;
-        const float omt = (__uint2float_rn(j) + 0.5f) * 0x1p-31f;
-        lnt = log1pf(-omt);
+        arg = -(__uint2float_rn(j) + 0.5f) * 0x1p-31f;
+        off = 0.0f;
     }
+    const float lnt = off + log1pf(arg);
     return upper ? -sigma * lnt : sigma * lnt;
 }
 

@@ -294,36 +294,39 @@ __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i,
         const int e0 = o / oes;  // first output element of the chunk
         const int p = e0 % C;
         const int l0 = e0 / C;   // first pixel column
-        uint32_t ci[NPX];
+        // the chunk's real pixels lie in at most two tiles (a tile row has >= 16 bytes); trailing entries past
+        // them are never used by the vector builder and are pointed at the last real pixel
+        const int lastp = min((e0 + kElems - 1) / C, last_px);
+        const uint32_t cl = colinfo[lastp];
+        const int tA = colinfo[min(l0, last_px)] >> 16;
+        const int tB = cl >> 16;
+        int cc[NPX];
+        bool inB[NPX];
 #pragma unroll
-        for (int l = 0; l < NPX; ++l) ci[l] = colinfo[min(l0 + l, last_px)];
-        // the chunk's real pixels lie in at most two tiles (a tile row has >= 16 bytes); a trailing entry of
-        // ci[] may lie past them and is never used by the vector builder
-        const int tA = ci[0] >> 16;
-        const int tB = colinfo[min((e0 + kElems - 1) / C, last_px)] >> 16;
-        const int bA = st.b[tA], bB = st.b[tB];
+        for (int l = 0; l < NPX; ++l) {
+            const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
+            cc[l] = (int)(v & 0xFFFFu);
+            inB[l] = (int)(v >> 16) != tA;
+        }
+        const int bA = st.b[tA], bB = st.b[tB], csA = st.cs[tA], csB = st.cs[tB];
         const bool full = o + 16 <= row_bytes;
+        // cell bands followed incrementally: band of row j, and the row where it ends
+        int bandA = j0 / bA, bandB = j0 / bB;
+        int endA = (bandA + 1) * bA, endB = (bandB + 1) * bB;
         int j = j0;
         while (j < j1) {
-            const int bandA = j / bA, bandB = j / bB;
-            const int jn = min(j1, min((bandA + 1) * bA, (bandB + 1) * bB));
-            const int baseA = st.base[tA] + bandA * st.cs[tA], baseB = st.base[tB] + bandB * st.cs[tB];
+            const int jn = min(j1, min(endA, endB));
+            const int baseA = st.base[tA] + bandA * csA, baseB = st.base[tB] + bandB * csB;
             uint4 vec;
             if (kOutF32) {
                 float4 pv[NPX];
 #pragma unroll
-                for (int l = 0; l < NPX; ++l) {
-                    const int bb = (int)(ci[l] >> 16) == tA ? baseA : baseB;
-                    pv[l] = reinterpret_cast<const float4 *>(stage)[min(bb + (int)(ci[l] & 0xFFFFu), ncell - 1)];
-                }
+                for (int l = 0; l < NPX; ++l) pv[l] = reinterpret_cast<const float4 *>(stage)[(inB[l] ? baseB : baseA) + cc[l]];
                 vec = build_f32_phase<C>(p, pv);
             } else {
                 uint32_t pv[NPX];
 #pragma unroll
-                for (int l = 0; l < NPX; ++l) {
-                    const int bb = (int)(ci[l] >> 16) == tA ? baseA : baseB;
-                    pv[l] = reinterpret_cast<const uint32_t *>(stage)[min(bb + (int)(ci[l] & 0xFFFFu), ncell - 1)];
-                }
+                for (int l = 0; l < NPX; ++l) pv[l] = reinterpret_cast<const uint32_t *>(stage)[(inB[l] ? baseB : baseA) + cc[l]];
                 vec = build_u8_phase<C>(p, pv);
             }
             uint8_t *dst = orow0 + (int64_t)j * out_pitch + o;
@@ -338,6 +341,14 @@ __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i,
                 }
             }
             j = jn;
+            if (j == endA) {
+                ++bandA;
+                endA += bA;
+            }
+            if (j == endB) {
+                ++bandB;
+                endB += bB;
+            }
         }
     }
     __syncthreads();
