@@ -11,7 +11,7 @@
 // and every warp store is coalesced.
 // Generic path (anything else): the CTA builds each distinct output row in shared memory and copies it out
 // with the widest aligned stores.
-#include "common.cuh"
+#include "seg_write.cuh"
 
 namespace dppix {
 namespace {
@@ -19,8 +19,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kRowBytes = 2048;     // generic path: shared-memory row pattern
 constexpr int kStageBytes = 32768;  // fast path: staged cell values of one segment
-constexpr int kMaxSegPx = 2048;     // fast path: pixel columns of one segment
-constexpr int kMaxSegTiles = 64;    // tiles of one segment
+constexpr int kMaxSegPx = kSegMaxPx;
+constexpr int kMaxSegTiles = kSegMaxTiles;
 
 struct RecGeom {
     int32_t ok, fast;
@@ -103,13 +103,6 @@ __device__ __forceinline__ float record_value(const uint8_t *src, int dtype, int
     return __fdiv_rn(__uint2float_rn(*reinterpret_cast<const uint32_t *>(src)), (float)(b * b));
 }
 
-__device__ __forceinline__ uint32_t to_u8(float v) { return __float2uint_rn(fminf(fmaxf(v, 0.0f), 255.0f)); }
-
-// Per-segment tile table shared by both paths.
-struct SegTiles {
-    int32_t reg[kMaxSegTiles], b[kMaxSegTiles], cs[kMaxSegTiles], base[kMaxSegTiles + 1];
-    uint64_t off[kMaxSegTiles];
-};
 
 // Tile table of the segment [tx0, tx0 + ns) of tile row ty: region, grid, payload offset.  The number of
 // region-r tiles before the segment comes from the record's tile-row index plus a block-parallel count
@@ -148,74 +141,6 @@ __device__ void seg_tile_info(const uint8_t *rec, const RecGeom &rg, int ty, int
     __syncthreads();
 }
 
-// ---- fast path: vector assembly -----------------------------------------------------------------------
-// Output element i of a 16-byte chunk whose first element is channel P of local pixel 0 belongs to local
-// pixel (P + i) / C, channel (P + i) % C -- compile-time once P and C are.
-template <int C>
-struct FastK {
-    static constexpr int NPX8 = (C - 1 + 16) / C + 1;  // pixels a u8 chunk can touch (upper bound)
-    static constexpr int NPXF = (C - 1 + 4) / C + 1;   // pixels an f32 chunk can touch (upper bound)
-};
-
-// Byte-permute selector for output word K of a chunk with phase P: byte i of the word is element
-// e = P + 4K + i, i.e. channel e % C of pixel e / C, which for C >= 2 is one of the two adjacent pixels
-// a = (P + 4K) / C and a + 1 (selector nibbles 0-3 and 4-7).
-template <int C>
-__host__ __device__ constexpr uint32_t word_sel(int e0) {
-    uint32_t sel = 0;
-    for (int i = 0; i < 4; ++i) {
-        const int pix = (e0 + i) / C - e0 / C, ch = (e0 + i) % C;
-        sel |= (uint32_t)(pix * 4 + ch) << (4 * i);
-    }
-    return sel;
-}
-
-template <int C, int P>
-__device__ __forceinline__ uint4 build_u8(const uint32_t *pv) {
-    uint32_t w[4];
-    if (C == 1) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            w[k] = __byte_perm(__byte_perm(pv[4 * k], pv[4 * k + 1], 0x0040), __byte_perm(pv[4 * k + 2], pv[4 * k + 3], 0x0040),
-                               0x5410);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int a = (P + 4 * k) / C;
-            w[k] = __byte_perm(pv[a], pv[a + 1], word_sel<C>(P + 4 * k));
-        }
-    }
-    return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-template <int C, int P>
-__device__ __forceinline__ uint4 build_f32(const float4 *pv) {
-    float o[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 v = pv[(P + i) / C];
-        const int ch = (P + i) % C;
-        o[i] = ch == 0 ? v.x : (ch == 1 ? v.y : (ch == 2 ? v.z : v.w));
-    }
-    return make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]), __float_as_uint(o[3]));
-}
-
-template <int C>
-__device__ __forceinline__ uint4 build_u8_phase(int p, const uint32_t *pv) {
-    if (p == 0) return build_u8<C, 0>(pv);
-    if (C > 1 && p == 1) return build_u8<C, (C > 1 ? 1 : 0)>(pv);
-    if (C > 2 && p == 2) return build_u8<C, (C > 2 ? 2 : 0)>(pv);
-    return build_u8<C, (C > 3 ? 3 : 0)>(pv);
-}
-
-template <int C>
-__device__ __forceinline__ uint4 build_f32_phase(int p, const float4 *pv) {
-    if (p == 0) return build_f32<C, 0>(pv);
-    if (C > 1 && p == 1) return build_f32<C, (C > 1 ? 1 : 0)>(pv);
-    if (C > 2 && p == 2) return build_f32<C, (C > 2 ? 2 : 0)>(pv);
-    return build_f32<C, (C > 3 ? 3 : 0)>(pv);
-}
-
 template <int C, int kOutF32>
 __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i, int ty, int sg, uint8_t *obase,
                           int64_t out_pitch, uint8_t *stage, uint32_t *colinfo, SegTiles &st, uint32_t *cnt_s,
@@ -225,29 +150,7 @@ __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i,
     const int tx0 = sg * rg.SR;
     const int ns = min(rg.SR, rg.GC - tx0);
     seg_tile_info(rec, rg, ty, tx0, ns, rec_i, status, st, cnt_s);
-    if (threadIdx.x < 32) {  // exclusive prefix of the tiles' cell counts, two tiles per lane
-        const int l = threadIdx.x;
-        const int c0 = 2 * l < ns ? st.cs[2 * l] * st.cs[2 * l] : 0;
-        const int c1 = 2 * l + 1 < ns ? st.cs[2 * l + 1] * st.cs[2 * l + 1] : 0;
-        int incl = c0 + c1;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, off);
-            if (l >= off) incl += v;
-        }
-        const int excl = incl - c0 - c1;
-        if (2 * l <= ns) st.base[2 * l] = excl;
-        if (2 * l + 1 <= ns) st.base[2 * l + 1] = excl + c0;
-        if (l == 31) st.base[ns] = incl;  // the total (ns may be 64)
-    }
-    // pixel column -> (tile, cell column)
-    const bool tp2 = (T & (T - 1)) == 0;
-    const int lt = __ffs(T) - 1;
-    for (int px = threadIdx.x; px < ns * T; px += blockDim.x) {
-        const int t = tp2 ? px >> lt : px / T;
-        const int b = st.b[t], pt = px - t * T;
-        colinfo[px] = ((uint32_t)t << 16) | (uint32_t)((b & (b - 1)) == 0 ? pt >> (__ffs(b) - 1) : pt / b);
-    }
+    seg_prefix_colinfo(st, ns, T, colinfo);
     __syncthreads();
     // cell values of the segment, converted once
     const int ncell = st.base[ns];
@@ -273,84 +176,10 @@ __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i,
         }
     }
     __syncthreads();
-    // write phase: thread = (16-byte column chunk, group of rows); no barrier until the next item
+    // write phase: no barrier until the next item
     const int x0 = tx0 * T;
-    const int vpx = min(ns * T, rg.N - x0);
-    const int row_bytes = vpx * C * oes;
-    const int nch = (row_bytes + 15) >> 4;
-    const int jmax = min(T, rg.M - ty * T);
-    int RG = (2 * kThreads + nch - 1) / nch;  // about two (chunk, row group) units per thread
-    RG = RG < 1 ? 1 : (RG > jmax ? jmax : RG);
-    const int rpg = (jmax + RG - 1) / RG;
-    uint8_t *orow0 = obase + (int64_t)(ty * T) * out_pitch + (int64_t)x0 * C * oes;
-    const int last_px = ns * T - 1;
-    constexpr int kElems = 16 / oes;
-    constexpr int NPX = kOutF32 ? FastK<C>::NPXF : FastK<C>::NPX8;
-    for (int w = threadIdx.x; w < nch * RG; w += blockDim.x) {
-        const int k = w % nch, grp = w / nch;
-        const int j0 = grp * rpg, j1 = min(jmax, j0 + rpg);
-        if (j0 >= j1) continue;
-        const int o = k << 4;
-        const int e0 = o / oes;  // first output element of the chunk
-        const int p = e0 % C;
-        const int l0 = e0 / C;   // first pixel column
-        // the chunk's real pixels lie in at most two tiles (a tile row has >= 16 bytes); trailing entries past
-        // them are never used by the vector builder and are pointed at the last real pixel
-        const int lastp = min((e0 + kElems - 1) / C, last_px);
-        const uint32_t cl = colinfo[lastp];
-        const int tA = colinfo[min(l0, last_px)] >> 16;
-        const int tB = cl >> 16;
-        int cc[NPX];
-        bool inB[NPX];
-#pragma unroll
-        for (int l = 0; l < NPX; ++l) {
-            const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
-            cc[l] = (int)(v & 0xFFFFu);
-            inB[l] = (int)(v >> 16) != tA;
-        }
-        const int bA = st.b[tA], bB = st.b[tB], csA = st.cs[tA], csB = st.cs[tB];
-        const bool full = o + 16 <= row_bytes;
-        // cell bands followed incrementally: band of row j, and the row where it ends
-        int bandA = j0 / bA, bandB = j0 / bB;
-        int endA = (bandA + 1) * bA, endB = (bandB + 1) * bB;
-        int j = j0;
-        while (j < j1) {
-            const int jn = min(j1, min(endA, endB));
-            const int baseA = st.base[tA] + bandA * csA, baseB = st.base[tB] + bandB * csB;
-            uint4 vec;
-            if (kOutF32) {
-                float4 pv[NPX];
-#pragma unroll
-                for (int l = 0; l < NPX; ++l) pv[l] = reinterpret_cast<const float4 *>(stage)[(inB[l] ? baseB : baseA) + cc[l]];
-                vec = build_f32_phase<C>(p, pv);
-            } else {
-                uint32_t pv[NPX];
-#pragma unroll
-                for (int l = 0; l < NPX; ++l) pv[l] = reinterpret_cast<const uint32_t *>(stage)[(inB[l] ? baseB : baseA) + cc[l]];
-                vec = build_u8_phase<C>(p, pv);
-            }
-            uint8_t *dst = orow0 + (int64_t)j * out_pitch + o;
-            for (int rr = j; rr < jn; ++rr, dst += out_pitch) {
-                if (full) {
-                    *reinterpret_cast<uint4 *>(dst) = vec;
-                } else {
-                    for (int i = 0; o + i < row_bytes; ++i) {
-                        const uint32_t wv = i < 4 ? vec.x : (i < 8 ? vec.y : (i < 12 ? vec.z : vec.w));
-                        dst[i] = (uint8_t)(wv >> (8 * (i & 3)));
-                    }
-                }
-            }
-            j = jn;
-            if (j == endA) {
-                ++bandA;
-                endA += bA;
-            }
-            if (j == endB) {
-                ++bandB;
-                endB += bB;
-            }
-        }
-    }
+    seg_write_rows<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T),
+                               obase + (int64_t)(ty * T) * out_pitch + (int64_t)x0 * C * oes, out_pitch);
     __syncthreads();
 }
 

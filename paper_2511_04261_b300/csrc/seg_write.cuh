@@ -1,0 +1,202 @@
+// seg_write.cuh -- shared-memory segment machinery of the reconstruction (Sec. VI-F), used by the
+// stand-alone reconstruction and by the fused release + reconstruction.
+//
+// A segment is ns consecutive tiles of one tile row.  Its cell values sit in shared memory ("stage"),
+// tile by tile in row-major cell order (st.base[t] = first cell of tile t); colinfo maps each pixel column
+// of the segment to (tile, cell column).  The write loop gives each thread 16-byte columns of the output
+// rows: it assembles the vector once per cell band and stores it to every row of the band.
+#pragma once
+
+#include "common.cuh"
+
+namespace dppix {
+
+constexpr int kSegMaxTiles = 64;    // tiles of one segment
+constexpr int kSegMaxPx = 2048;     // pixel columns of one segment
+
+__device__ __forceinline__ uint32_t to_u8(float v) { return __float2uint_rn(fminf(fmaxf(v, 0.0f), 255.0f)); }
+
+struct SegTiles {
+    int32_t reg[kSegMaxTiles], b[kSegMaxTiles], cs[kSegMaxTiles], base[kSegMaxTiles + 1];
+    uint64_t off[kSegMaxTiles];
+};
+
+// ---- vector assembly ----------------------------------------------------------------------------------
+// Output element i of a 16-byte chunk whose first element is channel P of local pixel 0 belongs to local
+// pixel (P + i) / C, channel (P + i) % C -- compile-time once P and C are.
+template <int C>
+struct FastK {
+    static constexpr int NPX8 = (C - 1 + 16) / C + 1;  // pixels a u8 chunk can touch (upper bound)
+    static constexpr int NPXF = (C - 1 + 4) / C + 1;   // pixels an f32 chunk can touch (upper bound)
+};
+
+// Byte-permute selector for output word K of a chunk with phase P: byte i of the word is element
+// e = P + 4K + i, i.e. channel e % C of pixel e / C, which for C >= 2 is one of the two adjacent pixels
+// a = (P + 4K) / C and a + 1 (selector nibbles 0-3 and 4-7).
+template <int C>
+__host__ __device__ constexpr uint32_t word_sel(int e0) {
+    uint32_t sel = 0;
+    for (int i = 0; i < 4; ++i) {
+        const int pix = (e0 + i) / C - e0 / C, ch = (e0 + i) % C;
+        sel |= (uint32_t)(pix * 4 + ch) << (4 * i);
+    }
+    return sel;
+}
+
+template <int C, int P>
+__device__ __forceinline__ uint4 build_u8(const uint32_t *pv) {
+    uint32_t w[4];
+    if (C == 1) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            w[k] = __byte_perm(__byte_perm(pv[4 * k], pv[4 * k + 1], 0x0040), __byte_perm(pv[4 * k + 2], pv[4 * k + 3], 0x0040),
+                               0x5410);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int a = (P + 4 * k) / C;
+            w[k] = __byte_perm(pv[a], pv[a + 1], word_sel<C>(P + 4 * k));
+        }
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+template <int C, int P>
+__device__ __forceinline__ uint4 build_f32(const float4 *pv) {
+    float o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 v = pv[(P + i) / C];
+        const int ch = (P + i) % C;
+        o[i] = ch == 0 ? v.x : (ch == 1 ? v.y : (ch == 2 ? v.z : v.w));
+    }
+    return make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]), __float_as_uint(o[3]));
+}
+
+template <int C>
+__device__ __forceinline__ uint4 build_u8_phase(int p, const uint32_t *pv) {
+    if (p == 0) return build_u8<C, 0>(pv);
+    if (C > 1 && p == 1) return build_u8<C, (C > 1 ? 1 : 0)>(pv);
+    if (C > 2 && p == 2) return build_u8<C, (C > 2 ? 2 : 0)>(pv);
+    return build_u8<C, (C > 3 ? 3 : 0)>(pv);
+}
+
+template <int C>
+__device__ __forceinline__ uint4 build_f32_phase(int p, const float4 *pv) {
+    if (p == 0) return build_f32<C, 0>(pv);
+    if (C > 1 && p == 1) return build_f32<C, (C > 1 ? 1 : 0)>(pv);
+    if (C > 2 && p == 2) return build_f32<C, (C > 2 ? 2 : 0)>(pv);
+    return build_f32<C, (C > 3 ? 3 : 0)>(pv);
+}
+
+// Cell prefix st.base[0..ns] (warp 0, two tiles per lane; ns <= 64) and the pixel-column map; needs st.b
+// and st.cs.  Ends without a barrier.
+__device__ __forceinline__ void seg_prefix_colinfo(SegTiles &st, int ns, int T, uint32_t *colinfo) {
+    if (threadIdx.x < 32) {  // exclusive prefix of the tiles' cell counts, two tiles per lane
+        const int l = threadIdx.x;
+        const int c0 = 2 * l < ns ? st.cs[2 * l] * st.cs[2 * l] : 0;
+        const int c1 = 2 * l + 1 < ns ? st.cs[2 * l + 1] * st.cs[2 * l + 1] : 0;
+        int incl = c0 + c1;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (l >= off) incl += v;
+        }
+        const int excl = incl - c0 - c1;
+        if (2 * l <= ns) st.base[2 * l] = excl;
+        if (2 * l + 1 <= ns) st.base[2 * l + 1] = excl + c0;
+        if (l == 31) st.base[ns] = incl;  // the total (ns may be 64)
+    }
+    // pixel column -> (tile, cell column)
+    const bool tp2 = (T & (T - 1)) == 0;
+    const int lt = __ffs(T) - 1;
+    for (int px = threadIdx.x; px < ns * T; px += blockDim.x) {
+        const int t = tp2 ? px >> lt : px / T;
+        const int b = st.b[t], pt = px - t * T;
+        colinfo[px] = ((uint32_t)t << 16) | (uint32_t)((b & (b - 1)) == 0 ? pt >> (__ffs(b) - 1) : pt / b);
+    }
+}
+
+// Writes the jmax output rows of a segment whose first output byte is orow0 (16-byte aligned) and
+// whose rows hold vpx pixels; stage holds the segment's cell values (packed u8 or float4).
+template <int C, int kOutF32>
+__device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, const uint8_t *stage, int ns, int T, int vpx,
+                               int jmax, uint8_t *orow0, int64_t out_pitch) {
+    constexpr int oes = kOutF32 ? 4 : 1;
+    // write phase: thread = (16-byte column chunk, group of rows); no barrier until the next item
+    const int row_bytes = vpx * C * oes;
+    const int nch = (row_bytes + 15) >> 4;
+    int RG = (2 * (int)blockDim.x + nch - 1) / nch;  // about two (chunk, row group) units per thread
+    RG = RG < 1 ? 1 : (RG > jmax ? jmax : RG);
+    const int rpg = (jmax + RG - 1) / RG;
+    const int last_px = ns * T - 1;
+    constexpr int kElems = 16 / oes;
+    constexpr int NPX = kOutF32 ? FastK<C>::NPXF : FastK<C>::NPX8;
+    for (int w = threadIdx.x; w < nch * RG; w += blockDim.x) {
+        const int k = w % nch, grp = w / nch;
+        const int j0 = grp * rpg, j1 = min(jmax, j0 + rpg);
+        if (j0 >= j1) continue;
+        const int o = k << 4;
+        const int e0 = o / oes;  // first output element of the chunk
+        const int p = e0 % C;
+        const int l0 = e0 / C;   // first pixel column
+        // the chunk's real pixels lie in at most two tiles (a tile row has >= 16 bytes); trailing entries past
+        // them are never used by the vector builder and are pointed at the last real pixel
+        const int lastp = min((e0 + kElems - 1) / C, last_px);
+        const uint32_t cl = colinfo[lastp];
+        const int tA = colinfo[min(l0, last_px)] >> 16;
+        const int tB = cl >> 16;
+        int cc[NPX];
+        bool inB[NPX];
+#pragma unroll
+        for (int l = 0; l < NPX; ++l) {
+            const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
+            cc[l] = (int)(v & 0xFFFFu);
+            inB[l] = (int)(v >> 16) != tA;
+        }
+        const int bA = st.b[tA], bB = st.b[tB], csA = st.cs[tA], csB = st.cs[tB];
+        const bool full = o + 16 <= row_bytes;
+        // cell bands followed incrementally: band of row j, and the row where it ends
+        int bandA = j0 / bA, bandB = j0 / bB;
+        int endA = (bandA + 1) * bA, endB = (bandB + 1) * bB;
+        int j = j0;
+        while (j < j1) {
+            const int jn = min(j1, min(endA, endB));
+            const int baseA = st.base[tA] + bandA * csA, baseB = st.base[tB] + bandB * csB;
+            uint4 vec;
+            if (kOutF32) {
+                float4 pv[NPX];
+#pragma unroll
+                for (int l = 0; l < NPX; ++l) pv[l] = reinterpret_cast<const float4 *>(stage)[(inB[l] ? baseB : baseA) + cc[l]];
+                vec = build_f32_phase<C>(p, pv);
+            } else {
+                uint32_t pv[NPX];
+#pragma unroll
+                for (int l = 0; l < NPX; ++l) pv[l] = reinterpret_cast<const uint32_t *>(stage)[(inB[l] ? baseB : baseA) + cc[l]];
+                vec = build_u8_phase<C>(p, pv);
+            }
+            uint8_t *dst = orow0 + (int64_t)j * out_pitch + o;
+            for (int rr = j; rr < jn; ++rr, dst += out_pitch) {
+                if (full) {
+                    *reinterpret_cast<uint4 *>(dst) = vec;
+                } else {
+                    for (int i = 0; o + i < row_bytes; ++i) {
+                        const uint32_t wv = i < 4 ? vec.x : (i < 8 ? vec.y : (i < 12 ? vec.z : vec.w));
+                        dst[i] = (uint8_t)(wv >> (8 * (i & 3)));
+                    }
+                }
+            }
+            j = jn;
+            if (j == endA) {
+                ++bandA;
+                endA += bA;
+            }
+            if (j == endB) {
+                ++bandB;
+                endB += bB;
+            }
+        }
+    }
+}
+
+}  // namespace dppix
