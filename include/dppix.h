@@ -170,6 +170,23 @@ DPPIX_API int dp_pix_release(dp_pix_plan_t plan, const void *d_frames, int64_t f
                    void *cuda_stream);
 
 /*
+ * dp_pix_release followed by dp_pix_reconstruct of the same frames, in one call (Alg. 3 with its
+ * restoring steps; Sec. VI-F).  Writes the same records and the same images as the two calls would.
+ * When the images' rows are 16-byte aligned and the release uses variance classes with a common grid
+ * divisor g in 4..16, the noisy cell means are turned into image rows in the same kernel that writes the
+ * records, so the records are not read back; otherwise the two calls run in turn.
+ *   Release arguments: as dp_pix_release.  Image arguments: as dp_pix_reconstruct, with the plan's M, N, C
+ *   as the bounds: image i at d_out + i*out_frame_stride, rows out_pitch bytes apart, out_type DP_PIX_OUT_*.
+ *   The caller owns every buffer.  Returns DP_PIX_OK, or the error codes of the two calls (argument
+ *   errors are found before anything is launched; kernel-side errors arrive through dp_pix_status()).
+ */
+DPPIX_API int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
+                                         const void *d_region_src, int64_t src_pitch, int64_t src_frame_stride,
+                                         uint32_t n_frames, uint32_t stream_id, uint64_t frame_idx0, void *d_records,
+                                         int64_t record_stride, void *d_out, int64_t out_frame_stride, int64_t out_pitch,
+                                         int out_type, void *d_ws, uint64_t ws_bytes, void *cuda_stream);
+
+/*
  * dp_pix_release without a workspace argument, for callers that cannot allocate device memory: code
  * running while a CUDA graph is captured (cudaMalloc is not allowed there), plug-ins whose host framework
  * owns every device allocation and passes in only inputs and outputs, and real-time loops that must not

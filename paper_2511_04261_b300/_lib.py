@@ -68,6 +68,8 @@ def lib():
     L.dp_pix_plan.argtypes = [ct.POINTER(Desc), ct.POINTER(P), ct.POINTER(Sizes)]
     L.dp_pix_plan_destroy.argtypes = [P]
     L.dp_pix_release.argtypes = [P, P, I64, P, I64, I64, U32, U32, U64, P, I64, P, U64, P]
+    L.dp_pix_release_reconstruct.argtypes = [P, P, I64, P, I64, I64, U32, U32, U64, P, I64, P, I64, I64, ct.c_int, P,
+                                             U64, P]
     L.dp_pix_release_noalloc.argtypes = [P, P, I64, P, I64, I64, U32, U32, U64, P, I64, P]
     L.dp_pix_store.argtypes = [P, P, U64, ct.POINTER(U64), ct.c_int, P]
     L.dp_pix_store_batch.argtypes = [P, I64, U32, P, I64, P, P]
@@ -80,7 +82,8 @@ def lib():
     L.dp_pix_prof_enable.argtypes = [ct.c_int]
     L.dp_pix_prof_read.argtypes = [ct.POINTER(ProfEntry), ct.c_int]
     L.dp_pix_prof_reset.argtypes = []
-    for name in ("dp_pix_plan", "dp_pix_plan_destroy", "dp_pix_release", "dp_pix_release_noalloc", "dp_pix_store",
+    for name in ("dp_pix_plan", "dp_pix_plan_destroy", "dp_pix_release", "dp_pix_release_reconstruct",
+                 "dp_pix_release_noalloc", "dp_pix_store",
                  "dp_pix_store_batch",
                  "dp_pix_reconstruct",
                  "dp_pix_debug_noise", "dp_pix_status", "dp_pix_prof_enable", "dp_pix_prof_read",

@@ -11,7 +11,7 @@ import torch
 
 from . import _lib as L
 
-__all__ = ["Plan", "dp_pix_plan", "dp_pix_release", "dp_pix_store", "dp_pix_store_batch", "dp_pix_reconstruct", "dp_pix_debug_noise",
+__all__ = ["Plan", "dp_pix_plan", "dp_pix_release", "dp_pix_release_reconstruct", "dp_pix_store", "dp_pix_store_batch", "dp_pix_reconstruct", "dp_pix_debug_noise",
            "dp_pix_status", "prof_enable", "prof_read", "prof_reset", "record_header", "DppixError"]
 
 DppixError = L.DppixError
@@ -103,14 +103,20 @@ class Plan:
         the tensor is [F, M, pitch] / [M, pitch]).  Returns the records tensor [F, record_stride]."""
         return dp_pix_release(self, frames, region_src, stream_id, frame_idx0, records, ws, stream)
 
+    def release_reconstruct(self, frames: torch.Tensor, region_src: Optional[torch.Tensor] = None,
+                            stream_id: int = 0, frame_idx0: int = 0, out_type: int = L.OUT_U8,
+                            records: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+                            ws: Optional[torch.Tensor] = None, stream: Optional[torch.cuda.Stream] = None):
+        """Release and reconstruct in one call; returns (records [F, stride], images [F, M, N, C])."""
+        return dp_pix_release_reconstruct(self, frames, region_src, stream_id, frame_idx0, out_type, records, out,
+                                          ws, stream)
+
 
 def dp_pix_plan(**kw) -> Plan:
     return Plan(**kw)
 
 
-def dp_pix_release(plan: Plan, frames: torch.Tensor, region_src: Optional[torch.Tensor] = None, stream_id: int = 0,
-                   frame_idx0: int = 0, records: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None,
-                   stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+def _release_args(plan: Plan, frames: torch.Tensor, region_src, records, ws):
     if frames.device.type != "cuda" or frames.dtype != torch.uint8:
         raise ValueError("frames must be a uint8 CUDA tensor")
     spec = plan.spec
@@ -130,12 +136,43 @@ def dp_pix_release(plan: Plan, frames: torch.Tensor, region_src: Optional[torch.
         records = plan.alloc_records(n, device=frames.device)
     if ws is None:
         ws = plan.alloc_workspace(n, device=frames.device)
+    return single, fr, n, frame_stride, region_src, src_pitch, src_frame_stride, records, ws
+
+
+def dp_pix_release(plan: Plan, frames: torch.Tensor, region_src: Optional[torch.Tensor] = None, stream_id: int = 0,
+                   frame_idx0: int = 0, records: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None,
+                   stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    _, fr, n, frame_stride, region_src, src_pitch, src_frame_stride, records, ws = _release_args(
+        plan, frames, region_src, records, ws)
     rc = L.lib().dp_pix_release(plan.handle, _ptr(fr), frame_stride, _ptr(region_src), src_pitch, src_frame_stride,
                                 n, int(stream_id), int(frame_idx0) & (2**64 - 1), _ptr(records),
                                 records.stride(0) * records.element_size(), _ptr(ws), ws.numel() * ws.element_size(),
                                 _stream_handle(stream))
     L.check(rc, "dp_pix_release")
     return records
+
+
+def dp_pix_release_reconstruct(plan: Plan, frames: torch.Tensor, region_src: Optional[torch.Tensor] = None,
+                               stream_id: int = 0, frame_idx0: int = 0, out_type: int = L.OUT_U8,
+                               records: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+                               ws: Optional[torch.Tensor] = None, stream: Optional[torch.cuda.Stream] = None):
+    """dp_pix_release then dp_pix_reconstruct in one call.  out: [F, M, N, C] (or [M, N, C]) u8 / f32 with
+    rows of any pitch.  Returns (records, images)."""
+    single, fr, n, frame_stride, region_src, src_pitch, src_frame_stride, records, ws = _release_args(
+        plan, frames, region_src, records, ws)
+    spec = plan.spec
+    dt = torch.uint8 if out_type == L.OUT_U8 else torch.float32
+    if out is None:
+        out = torch.empty((n, spec.M, spec.N, spec.C), dtype=dt, device=frames.device)
+    o = out.unsqueeze(0) if out.dim() == 3 else out
+    es = o.element_size()
+    rc = L.lib().dp_pix_release_reconstruct(
+        plan.handle, _ptr(fr), frame_stride, _ptr(region_src), src_pitch, src_frame_stride, n, int(stream_id),
+        int(frame_idx0) & (2**64 - 1), _ptr(records), records.stride(0) * records.element_size(), _ptr(o),
+        o.stride(0) * es, o.stride(1) * es, int(out_type), _ptr(ws), ws.numel() * ws.element_size(),
+        _stream_handle(stream))
+    L.check(rc, "dp_pix_release_reconstruct")
+    return records, (out[0] if single and out.dim() == 4 else out)
 
 
 def dp_pix_store(record: torch.Tensor, stream: Optional[torch.cuda.Stream] = None) -> bytes:

@@ -297,11 +297,22 @@ int dp_pix_plan_destroy(dp_pix_plan_t plan) {
     return DP_PIX_OK;
 }
 
-int dp_pix_release(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride, const void *d_region_src,
-                   int64_t src_pitch, int64_t src_frame_stride, uint32_t n_frames, uint32_t stream_id,
-                   uint64_t frame_idx0, void *d_records, int64_t record_stride, void *d_ws, uint64_t ws_bytes,
-                   void *cuda_stream) {
-    t_err[0] = 0;
+}  // extern "C"
+
+namespace {
+
+// Output of the fused release + reconstruction; `fused` tells whether the kernels wrote it.
+struct FusedOut {
+    uint8_t *out;
+    int64_t frame_stride, pitch;
+    int type, align;
+    bool fused;
+};
+
+int release_impl(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride, const void *d_region_src,
+                 int64_t src_pitch, int64_t src_frame_stride, uint32_t n_frames, uint32_t stream_id, uint64_t frame_idx0,
+                 void *d_records, int64_t record_stride, void *d_ws, uint64_t ws_bytes, void *cuda_stream,
+                 FusedOut *fo) {
     if (!plan) return fail(DP_PIX_E_INVALID_ARG, "plan is NULL");
     const Geom &g = plan->g;
     if (n_frames == 0) return DP_PIX_OK;
@@ -366,13 +377,61 @@ int dp_pix_release(dp_pix_plan_t plan, const void *d_frames, int64_t frame_strid
         case DP_PIX_SRC_VARIANCE:
             e = launch_tile_stats(g, a, s);
             if (e == cudaSuccess) e = launch_rank(g, a, s);
-            if (e == cudaSuccess) e = g.var_onepass ? launch_emit(g, a, s) : launch_release(g, a, s);
+            if (e == cudaSuccess && g.var_onepass && fo) {
+                e = launch_emit_recon(g, a, fo->out, fo->frame_stride, fo->pitch, fo->type, fo->align, s);
+                fo->fused = e == cudaSuccess;
+                if (e == cudaErrorNotSupported) e = launch_emit(g, a, s);
+            } else if (e == cudaSuccess) {
+                e = g.var_onepass ? launch_emit(g, a, s) : launch_release(g, a, s);
+            }
             break;
         default:
             return fail(DP_PIX_E_INVALID_ARG, "bad region source");
     }
     if (e != cudaSuccess) return cuda_fail(e, "release launch");
     return DP_PIX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dp_pix_release(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride, const void *d_region_src,
+                   int64_t src_pitch, int64_t src_frame_stride, uint32_t n_frames, uint32_t stream_id,
+                   uint64_t frame_idx0, void *d_records, int64_t record_stride, void *d_ws, uint64_t ws_bytes,
+                   void *cuda_stream) {
+    t_err[0] = 0;
+    return release_impl(plan, d_frames, frame_stride, d_region_src, src_pitch, src_frame_stride, n_frames, stream_id,
+                        frame_idx0, d_records, record_stride, d_ws, ws_bytes, cuda_stream, nullptr);
+}
+
+int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
+                               const void *d_region_src, int64_t src_pitch, int64_t src_frame_stride,
+                               uint32_t n_frames, uint32_t stream_id, uint64_t frame_idx0, void *d_records,
+                               int64_t record_stride, void *d_out, int64_t out_frame_stride, int64_t out_pitch,
+                               int out_type, void *d_ws, uint64_t ws_bytes, void *cuda_stream) {
+    t_err[0] = 0;
+    if (!plan) return fail(DP_PIX_E_INVALID_ARG, "plan is NULL");
+    if (n_frames == 0) return DP_PIX_OK;
+    const Geom &g = plan->g;
+    if (!d_out) return fail(DP_PIX_E_INVALID_ARG, "output is required");
+    if (out_type != DP_PIX_OUT_U8 && out_type != DP_PIX_OUT_F32) return fail(DP_PIX_E_INVALID_ARG, "bad out_type");
+    const int oes = out_type == DP_PIX_OUT_F32 ? 4 : 1;
+    if (out_pitch < (int64_t)g.N * g.C * oes) return fail(DP_PIX_E_INVALID_ARG, "out_pitch < N * C * elem");
+    if (n_frames > 1 && out_frame_stride < out_pitch * g.M) return fail(DP_PIX_E_INVALID_ARG, "out_frame_stride too small");
+    if (out_type == DP_PIX_OUT_F32 &&
+        ((uintptr_t)d_out % 4 || out_pitch % 4 || (n_frames > 1 && out_frame_stride % 4)))
+        return fail(DP_PIX_E_INVALID_ARG, "f32 output must be 4-byte aligned");
+    int align = 16;
+    while (align > 1 &&
+           ((uintptr_t)d_out % align || out_pitch % align || (n_frames > 1 && out_frame_stride % align)))
+        align >>= 1;
+    FusedOut fo{static_cast<uint8_t *>(d_out), n_frames > 1 ? out_frame_stride : 0, out_pitch, out_type, align, false};
+    int rc = release_impl(plan, d_frames, frame_stride, d_region_src, src_pitch, src_frame_stride, n_frames, stream_id,
+                          frame_idx0, d_records, record_stride, d_ws, ws_bytes, cuda_stream, &fo);
+    if (rc || fo.fused) return rc;
+    return dp_pix_reconstruct(d_records, record_stride, n_frames, d_out, out_frame_stride, out_pitch, out_type, g.M,
+                              g.N, g.C, cuda_stream);
 }
 
 int dp_pix_store(const void *d_record, void *dst, uint64_t cap, uint64_t *written, int dst_is_host,

@@ -153,6 +153,8 @@ cudaError_t launch_tile_stats(const Geom &g, const CallArgs &a, cudaStream_t s);
 cudaError_t launch_tile_stats_fast(const Geom &g, const CallArgs &a, cudaStream_t s);  // NotSupported: no instance
 cudaError_t launch_rank(const Geom &g, const CallArgs &a, cudaStream_t s);
 cudaError_t launch_emit(const Geom &g, const CallArgs &a, cudaStream_t s);
+cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, int64_t out_frame_stride,
+                              int64_t out_pitch, int out_type, int out_align, cudaStream_t s);  // NotSupported: fall back
 cudaError_t launch_reconstruct(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out,
                                int64_t out_frame_stride, int64_t out_pitch, int out_type, int max_M, int max_N,
                                int max_C, int out_align, int32_t *status, cudaStream_t s);

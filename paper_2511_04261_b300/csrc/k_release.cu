@@ -14,7 +14,7 @@
 //  - k_emit: g-cell sums -> b_r-cell sums -> noise -> record.
 #include <algorithm>
 
-#include "common.cuh"
+#include "seg_write.cuh"
 
 namespace dppix {
 namespace {
@@ -314,8 +314,9 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats(const Geom g, const Cal
 }
 
 // Noise, clip and store of one (cell, channel) set (Alg. 3 steps 9-10 and 15-17).
+// ov (optional) receives the value a reconstruction reads back from the stored element (Sec. VI-F).
 __device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint8_t *dst, const uint32_t *S, int r,
-                                          uint32_t cell_idx, uint64_t frame) {
+                                          uint32_t cell_idx, uint64_t frame, float *ov = nullptr) {
     const int C = g.C;
     uint4 words = make_uint4(0, 0, 0, 0);
     if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
@@ -325,13 +326,18 @@ __device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint
         if (ch >= C) break;
         if (g.dtype == DP_PIX_REC_SUM_U32) {
             reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
+            if (ov) ov[ch] = __fdiv_rn(__uint2float_rn(S[ch]), g.b2_f[r]);
         } else {
             const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), g.sigma_f[r]);
             const float v = noisy_mean(S[ch], g.b2_f[r], g.inv_b2_f[r], eta, g.R_f);
-            if (g.dtype == DP_PIX_REC_F32)
+            if (g.dtype == DP_PIX_REC_F32) {
                 reinterpret_cast<float *>(dst)[ch] = v;
-            else
-                dst[ch] = (uint8_t)__float2uint_rn(v);
+                if (ov) ov[ch] = v;
+            } else {
+                const uint32_t q = __float2uint_rn(v);
+                dst[ch] = (uint8_t)q;
+                if (ov) ov[ch] = (float)q;
+            }
         }
     }
 }
@@ -424,10 +430,6 @@ __global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs 
     }
 }
 
-size_t seg_smem(const Geom &g, int bands_per_tile) {
-    return (size_t)g.T * g.seg_rowstride + (size_t)g.seg_tiles * bands_per_tile * g.T * g.C * 2;
-}
-
 template <typename K>
 int grid_for(K kernel, size_t smem, uint32_t items) {
     int per_sm = 0;
@@ -436,6 +438,104 @@ int grid_for(K kernel, size_t smem, uint32_t items) {
     const uint64_t cap = (uint64_t)per_sm * (uint64_t)sm_count();
     return (int)(items < cap ? items : cap);
 }
+
+// ------------------------------------------------------------------------------------------------------
+// k_emit_recon: the emit and the reconstruction fused, for one (frame, tile-row segment) per item.  Each
+// cell's noisy mean is computed from the g-image as in k_emit and written to the record; the value a
+// reconstruction would read back is staged in shared memory, and the segment's output rows are written
+// from there (seg_write.cuh) -- the record is never read back.
+// ------------------------------------------------------------------------------------------------------
+constexpr int kFusedStage = 32768;
+
+template <int C, int kOutF32>
+__global__ void __launch_bounds__(kThreads)
+    k_emit_recon(const Geom g, const CallArgs a, uint8_t *out, int64_t out_frame_stride, int64_t out_pitch, int seg) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ SegTiles st;
+    constexpr int oes = kOutF32 ? 4 : 1;
+    uint8_t *stage = dyn;
+    uint32_t *colinfo = reinterpret_cast<uint32_t *>(dyn + kFusedStage);
+    const int T = g.T, gcs = T / g.g;
+    const size_t rowvals = (size_t)g.gx_cells * C;
+    const uint32_t nseg = (uint32_t)((g.GC + seg - 1) / seg);
+    const uint32_t items = a.n_frames * (uint32_t)g.GR * nseg;
+    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const uint32_t sg = item % nseg, fr = item / nseg;
+        const int ty = (int)(fr % g.GR);
+        const uint32_t f = fr / g.GR;
+        const int tx0 = (int)sg * seg;
+        const int ns = min(seg, g.GC - tx0);
+        uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
+        const uint8_t *wsf = a.ws + (uint64_t)f * g.ws_per_frame;
+        if ((int)threadIdx.x < ns) {
+            const int t = threadIdx.x;
+            const uint32_t tile = (uint32_t)ty * g.GC + tx0 + t;
+            int r = rec[g.map_offset + tile];
+            if (r >= g.K) r = 0;
+            st.reg[t] = r;
+            st.b[t] = g.grid[r];
+            st.cs[t] = g.cells_side[r];
+            st.off[t] = reinterpret_cast<const uint32_t *>(wsf + g.ws_tileoff)[tile];
+        }
+        __syncthreads();
+        seg_prefix_colinfo(st, ns, T, colinfo);
+        __syncthreads();
+        const int ncell = st.base[ns];
+        const uint16_t *gimg = reinterpret_cast<const uint16_t *>(wsf + g.ws_gsum);
+        const uint64_t frame = a.frame_idx0 + f;
+        for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
+            int lo = 0, hi = ns - 1;  // last tile whose first cell is <= e
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (st.base[mid] <= e) lo = mid; else hi = mid - 1;
+            }
+            const int t = lo, c = e - st.base[t];
+            const int r = st.reg[t], cs = st.cs[t];
+            const int cy = (cs & (cs - 1)) == 0 ? c >> (__ffs(cs) - 1) : c / cs, cx = c - cy * cs;
+            const int tx = tx0 + t, nb = st.b[t] / g.g;
+            uint32_t S[4] = {0u, 0u, 0u, 0u};
+            gblock_sum<C>(gimg + (size_t)(ty * gcs + cy * nb) * rowvals + ((size_t)tx * gcs + (size_t)cx * nb) * C,
+                          rowvals, nb, S);
+            const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)(tx * cs + cx);
+            float ov[4] = {0.f, 0.f, 0.f, 0.f};
+            emit_cell(g, a, rec + st.off[t] + (uint64_t)c * C * g.es, S, r, cell_idx, frame, ov);
+            if (kOutF32) {
+                reinterpret_cast<float4 *>(stage)[e] = make_float4(ov[0], ov[1], ov[2], ov[3]);
+            } else {
+                uint32_t pk = 0;
+#pragma unroll
+                for (int ch = 0; ch < C; ++ch) pk |= to_u8(ov[ch]) << (8 * ch);
+                reinterpret_cast<uint32_t *>(stage)[e] = pk;
+            }
+        }
+        __syncthreads();
+        const int x0 = tx0 * T;
+        seg_write_rows<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, g.N - x0), min(T, g.M - ty * T),
+                                   out + (uint64_t)f * (uint64_t)out_frame_stride + (int64_t)(ty * T) * out_pitch +
+                                       (int64_t)x0 * C * oes,
+                                   out_pitch);
+        __syncthreads();
+    }
+}
+
+template <int C, int kOutF32>
+cudaError_t launch_er(const Geom &g, const CallArgs &a, uint8_t *out, int64_t ofs, int64_t op, int seg, cudaStream_t s) {
+    const size_t smem = kFusedStage + (size_t)kSegMaxPx * 4;
+    auto kern = k_emit_recon<C, kOutF32>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)((g.GC + seg - 1) / seg);
+    const int grid = grid_for(kern, smem, items);
+    const char *name = kOutF32 ? "k_emit_recon_f32" : "k_emit_recon_u8";
+    prof_begin(name, s);
+    kern<<<grid, kThreads, smem, s>>>(g, a, out, ofs, op, seg);
+    prof_end(name, s);
+    return cudaGetLastError();
+}
+
+size_t seg_smem(const Geom &g, int bands_per_tile) {
+    return (size_t)g.T * g.seg_rowstride + (size_t)g.seg_tiles * bands_per_tile * g.T * g.C * 2;
+}
+
 
 }  // namespace
 
@@ -470,6 +570,47 @@ cudaError_t launch_tile_stats(const Geom &g, const CallArgs &a, cudaStream_t s) 
         prof_end("k_tile_stats", s);
     }
     return cudaGetLastError();
+}
+
+int gcd_int(int a, int b) {
+    while (b) {
+        const int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Fused emit + reconstruction when the output layout allows the vectorised write (16-byte aligned rows) and
+// a segment's cells fit the staging buffer; cudaErrorNotSupported (nothing launched) otherwise.
+cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, int64_t out_frame_stride,
+                              int64_t out_pitch, int out_type, int out_align, cudaStream_t s) {
+    const int oes = out_type == DP_PIX_OUT_F32 ? 4 : 1;
+    const int trb = g.T * g.C * oes;
+    if (!g.var_onepass || out_align != 16 || trb < 16) return cudaErrorNotSupported;
+    const int s0 = 16 / gcd_int(trb, 16);
+    int csmax = 1;
+    for (int r = 0; r < g.K; ++r) csmax = std::max(csmax, g.cells_side[r]);
+    const int vb = oes == 4 ? 16 : 4;
+    int seg = std::min(kSegMaxTiles, (g.GC + s0 - 1) / s0 * s0) / s0 * s0;
+    while (seg > 0 && ((int64_t)seg * csmax * csmax * vb > kFusedStage || seg * g.T > kSegMaxPx)) seg -= s0;
+    if (seg <= 0) return cudaErrorNotSupported;
+#define DPPIX_ER(CC, F) return launch_er<CC, F>(g, a, out, out_frame_stride, out_pitch, seg, s)
+    if (oes == 4) {
+        switch (g.C) {
+            case 1: DPPIX_ER(1, 1);
+            case 2: DPPIX_ER(2, 1);
+            case 3: DPPIX_ER(3, 1);
+            default: DPPIX_ER(4, 1);
+        }
+    }
+    switch (g.C) {
+        case 1: DPPIX_ER(1, 0);
+        case 2: DPPIX_ER(2, 0);
+        case 3: DPPIX_ER(3, 0);
+        default: DPPIX_ER(4, 0);
+    }
+#undef DPPIX_ER
 }
 
 cudaError_t launch_emit(const Geom &g, const CallArgs &a, cudaStream_t s) {

@@ -326,3 +326,76 @@ def test_config2_full_clip_sampled():
         assert h["count"] == [510, 510, 510, 510]
         exp = 512 + a16(34 * 4 * 4) + a16(2040) + sum(a16(510 * (32 // b) ** 2 * 12) for b in [32, 16, 8, 4])
         assert h["total_bytes"] == exp
+
+
+# ------------------------------------------------------------------------------------------------------
+# Release and reconstruction in one call (Alg. 3 with the restoring steps of Sec. VI-F)
+# ------------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("M,N,C,grids,src,padded", [
+    (96, 256, 3, [32, 16, 8, 4], O.SRC_VARIANCE, False),    # fused kernel, g = 4
+    (100, 256, 3, [32, 16, 8, 4], O.SRC_VARIANCE, True),    # fused kernel, mirrored rows, padded pitch
+    (130, 128, 1, [16, 8], O.SRC_VARIANCE, True),           # fused kernel, g = 8, C = 1
+    (70, 64, 4, [8, 4], O.SRC_VARIANCE, False),             # fused kernel, C = 4
+    (64, 192, 3, [16], O.SRC_VARIANCE, True),               # fused kernel, g = 16, K = 1
+    (200, 330, 3, [32, 16, 8, 4], O.SRC_VARIANCE, False),   # column padding: release, then reconstruct
+    (121, 245, 3, [6, 20], O.SRC_VARIANCE, True),           # g = 2: release, then reconstruct
+    (100, 130, 3, [24, 8], O.SRC_TILE_LABELS, True),        # labels: release, then reconstruct
+])
+@pytest.mark.parametrize("dtype", [O.DT_F32, O.DT_U8, O.DT_SUM])
+@pytest.mark.parametrize("ot", [P.OUT_U8, P.OUT_F32])
+def test_release_reconstruct_matches_two_calls(M, N, C, grids, src, padded, dtype, ot):
+    """The fused call writes the records dp_pix_release writes and the images dp_pix_reconstruct makes from
+    them, bit for bit; the images also equal the oracle's reconstruction of the oracle-checked records."""
+    rng = np.random.default_rng(M * 3 + N + C + dtype)
+    F = 3
+    imgs = rng.integers(0, 256, size=(F, M, N, C), dtype=np.uint8)
+    imgs[:, : M // 3] //= 8
+    lab = np.stack([_labels(rng, M, N, grids) for _ in range(F)]) if src == O.SRC_TILE_LABELS else None
+    kw = dict(M=M, N=N, C=C, grids=grids, eps=[0.5 + 0.25 * i for i in range(len(grids))], source=src, dtype=dtype,
+              seed=12, m=16)
+    plan, recs_d, recs = gpu_release(imgs, lab, frame_idx0=5, **kw)
+    oes = 1 if ot == P.OUT_U8 else 4
+    dt = torch.uint8 if ot == P.OUT_U8 else torch.float32
+    Np = N
+    if padded:
+        while (Np * C * oes) % 16:
+            Np += 1
+        Np += 16 // math.gcd(16, C * oes)
+    big = torch.full((F, M, Np, C), 7, dtype=dt, device="cuda")
+    view = big[:, :, :N, :]
+    t = torch.from_numpy(imgs).cuda()
+    s = torch.from_numpy(lab).cuda() if lab is not None else None
+    recs2 = torch.full_like(recs_d, 0xAB)
+    plan.release_reconstruct(t, s, frame_idx0=5, out_type=ot, records=recs2, out=view)
+    torch.cuda.synchronize()
+    assert P.dp_pix_status() == 0
+    ref = P.dp_pix_reconstruct(recs_d, M, N, C, ot)
+    got = big.cpu().numpy()
+    assert np.array_equal(got[:, :, :N], ref.cpu().numpy())
+    if Np > N:
+        assert np.all(got[:, :, N:] == 7)
+    for i in range(F):
+        assert P.dp_pix_store(recs2[i]) == recs[i]
+        exp = O.reconstruct(np.frombuffer(recs[i], np.uint8), 0 if ot == P.OUT_U8 else 1)
+        assert np.array_equal(got[i, :, :N], exp), i
+    rec, means, sums, etas = O.release(imgs[0], lab[0] if lab is not None else None, frame_idx=5, **kw)
+    compare_records(recs[0], rec, means, sums, etas, dtype)
+
+
+def test_release_reconstruct_config2_sampled():
+    """A 1080p clip through the fused call: records equal to dp_pix_release's, images equal to
+    dp_pix_reconstruct's, and sampled frames checked against the oracle."""
+    F, M, N = 6, 1080, 1920
+    clip = synth.moving_rect_clip(seed=21, frames=F, M=M, N=N)
+    kw = dict(M=M, N=N, C=3, grids=[32, 16, 8, 4], eps=[2, 1, .5, .25], source=O.SRC_VARIANCE, dtype=O.DT_F32,
+              seed=4, m=16)
+    plan, recs_d, recs = gpu_release(clip, None, **kw)
+    t = torch.from_numpy(clip).cuda()
+    r2, img = plan.release_reconstruct(t)
+    torch.cuda.synchronize()
+    assert P.dp_pix_status() == 0
+    assert torch.equal(r2, recs_d) or all(P.dp_pix_store(r2[i]) == recs[i] for i in range(F))
+    assert torch.equal(img, P.dp_pix_reconstruct(recs_d, M, N, 3, P.OUT_U8))
+    for i in (0, F - 1):
+        rec, means, sums, etas = O.release(clip[i], None, frame_idx=i, **kw)
+        compare_records(recs[i], rec, means, sums, etas, O.DT_F32)
