@@ -42,7 +42,7 @@ def set_frames(n):
 def config(extra=None):
     c = {"workload": WORKLOAD, "frames": F, "M": M, "N": N, "C": C, "grids": GRIDS, "eps": EPS, "m": MVAR,
          "region_source": "variance quantiles on 32x32 tiles", "record": "f32 means + u8 tile map",
-         "step": "dp_pix_release + dp_pix_reconstruct of all frames",
+         "step": "release (records) + reconstruction (pixelized u8 frames) of all frames",
          "l2": "inputs larger than L2 (%.0f MB of frames read and written per step)" % (F * M * N * C / 1e6),
          "generator_seed": 1002,
          "philox_seed": SEED}
@@ -192,6 +192,8 @@ def algorithmic_bytes(plan, payload_bytes):
         "k_emit": F * ntiles * (gsum_tile + 4 + 1) + payload_bytes,
         # frames written; record payload and maps read
         "k_reconstruct_u8": frame_bytes + payload_bytes + F * ntiles,
+        # fused: g-cell sums, offsets and map read; record payload and frames written
+        "k_emit_recon_u8": frame_bytes + F * ntiles * (gsum_tile + 4 + 1) + payload_bytes,
         # keys read; map, offsets, index and header written
         "k_rank": F * ntiles * (8 + 1 + 4) + F * (512 + plan.GR * 16),
     }
@@ -284,9 +286,13 @@ def run_ours(args):
     out = torch.empty((F, M, N, C), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(fr, frame_idx0):
-        plan.release(fr, None, stream_id=rank, frame_idx0=frame_idx0, records=records, ws=ws)
-        P.dp_pix_reconstruct(records, M, N, C, P.OUT_U8, out=out)
+    def step(fr, frame_idx0, recs=records, o=out, w=ws):
+        if args.path == "fused":
+            plan.release_reconstruct(fr, None, stream_id=rank, frame_idx0=frame_idx0, out_type=P.OUT_U8, records=recs,
+                                     out=o, ws=w)
+        else:
+            plan.release(fr, None, stream_id=rank, frame_idx0=frame_idx0, records=recs, ws=w)
+            P.dp_pix_reconstruct(recs, M, N, C, P.OUT_U8, out=o)
 
     for w in range(args.warmup):
         step(frames, w * F)
@@ -343,8 +349,7 @@ def run_ours(args):
     for i in range(60):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        plan.release(frames[i % F], None, stream_id=rank, frame_idx0=10**6 + i, records=rec1, ws=ws1)
-        P.dp_pix_reconstruct(rec1, M, N, C, P.OUT_U8, out=out1)
+        step(frames[i % F], 10**6 + i, rec1, out1, ws1)
         b.record(stream)
         b.synchronize()
         if i >= 10:
@@ -385,7 +390,8 @@ def run_e2e(args, P, torch, plan, clip, frames, records, step, world):
     e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / e2e_steps, world)
     return {"value": world * F * M * N / 1e6 / (e2e_ms / 1e3), "unit": "Mpx/s", "ms_per_step": e2e_ms,
             "h2d_bytes_per_step": F * M * N * C, "d2h_bytes_per_step": int(sum(written)) + F * 512,
-            "path": "pinned host frames -> device copy, dp_pix_release, dp_pix_reconstruct, dp_pix_store_batch"}
+            "path": "pinned host frames -> device copy, %s, dp_pix_store_batch" % (
+                "dp_pix_release_reconstruct" if args.path == "fused" else "dp_pix_release, dp_pix_reconstruct")}
 
 
 def finish(args, rank, world, value, ms_max, roofline, cpu, e2e, clocks, launches, latency):
@@ -394,7 +400,9 @@ def finish(args, rank, world, value, ms_max, roofline, cpu, e2e, clocks, launche
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                 "config": config({"parallelism": "replicas: one clip per GPU, no collective" if world > 1 else "1 GPU",
-                                  "arith": "u8 samples, exact u32 cell sums, f32 noise/mean"}),
+                                  "arith": "u8 samples, exact u32 cell sums, f32 noise/mean",
+                                  "path": "dp_pix_release_reconstruct" if args.path == "fused" else
+                                  "dp_pix_release + dp_pix_reconstruct"}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                 "latency": latency}
         print(json.dumps(line), flush=True)
@@ -414,6 +422,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--frames", type=int, default=64, help="frames per step (64 = the benchmark workload)")
+    ap.add_argument("--path", choices=["fused", "two-call"], default="fused",
+                    help="fused: dp_pix_release_reconstruct; two-call: dp_pix_release then dp_pix_reconstruct")
     args = ap.parse_args()
     set_frames(args.frames)
     if args.warmup < 3:

@@ -337,7 +337,8 @@ def test_config2_full_clip_sampled():
     (130, 128, 1, [16, 8], O.SRC_VARIANCE, True),           # fused kernel, g = 8, C = 1
     (70, 64, 4, [8, 4], O.SRC_VARIANCE, False),             # fused kernel, C = 4
     (64, 192, 3, [16], O.SRC_VARIANCE, True),               # fused kernel, g = 16, K = 1
-    (200, 330, 3, [32, 16, 8, 4], O.SRC_VARIANCE, False),   # column padding: release, then reconstruct
+    (200, 330, 3, [32, 16, 8, 4], O.SRC_VARIANCE, True),    # fused kernel, mirrored columns (staged statistics)
+    (200, 330, 3, [32, 16, 8, 4], O.SRC_VARIANCE, False),   # rows not 16-byte aligned: release, then reconstruct
     (121, 245, 3, [6, 20], O.SRC_VARIANCE, True),           # g = 2: release, then reconstruct
     (100, 130, 3, [24, 8], O.SRC_TILE_LABELS, True),        # labels: release, then reconstruct
 ])
