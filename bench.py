@@ -161,6 +161,11 @@ def dist_setup(n_gpus):
     return world, rank, local
 
 
+def whole_job_mpx_per_s(world, ms_max):
+    """Megapixels of all ranks' clips (one clip of F frames per rank per step) over the slowest rank's time."""
+    return world * F * M * N / 1e6 / (ms_max / 1e3)
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -319,7 +324,7 @@ def run_ours(args):
     P.dp_pix_status()
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = max_over_ranks(ms, world)
-    value = world * F * M * N / 1e6 / (ms_max / 1e3)
+    value = whole_job_mpx_per_s(world, ms_max)
     launches = sum(v[0] for v in prof.values())
 
     # ---- roofline of the dominant kernel (its own launch durations, from events on its stream) ----
