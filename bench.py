@@ -3,9 +3,9 @@
 
 Workload (one step): a clip of 64 frames of 1920x1080 RGB u8 (moving-rectangle generator), four
 local-variance classes on 32x32 tiles with grids {32, 16, 8, 4} and budgets {2, 1, 0.5, 0.25}, m = 16:
-classify + exact cell sums + Laplace noise + clip + compact record (dp_pix_release), then the
-pixelized frames rebuilt from the records (dp_pix_reconstruct).  Inputs (398 MB per step) are larger than
-the 126 MB L2.
+classify + exact cell sums + Laplace noise + clip + compact record, and the pixelized frames rebuilt from
+the records, in one dp_pix_release_reconstruct call (`--path two-call`: dp_pix_release then
+dp_pix_reconstruct).  Inputs (398 MB per step) are larger than the 126 MB L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -69,9 +69,18 @@ REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_c
 
 
 class ClockSampler:
+    """SM clock and throttle reasons sampled during the timed region: NVML from a thread when pynvml imports,
+    else an `nvidia-smi -lms` subprocess whose samples are kept from the window around the region."""
+    SMI_FIELDS = ("timestamp,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_power_cap")
+    SMI_NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
     def __init__(self, device_index=0, period=0.002):
         self.samples, self.reasons, self.ok, self.period = [], set(), False, period
         self.max_mhz = None
+        self.err = None
+        self.proc = None
         try:
             import pynvml as nv
             import torch
@@ -87,7 +96,7 @@ class ClockSampler:
             self.nv, self.h = nv, h
             self.max_mhz = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
             self.ok = True
-        except Exception as e:  # no NVML: fall back to nvidia-smi around the timed region
+        except Exception as e:
             self.err = repr(e)
 
     def _reasons(self):
@@ -108,38 +117,55 @@ class ClockSampler:
             time.sleep(self.period)
 
     def start(self):
-        if not self.ok:
+        self.t0 = time.time()
+        if self.ok:
+            self._stop = threading.Event()
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
             return
-        self._stop = threading.Event()
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        import subprocess
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self._smi_index(), "--query-gpu=" + self.SMI_FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)  # the first sample lands before the timed region starts
+        except Exception as e:
+            self.err = "%s; nvidia-smi: %r" % (self.err, e)
+            self.proc = None
 
     @staticmethod
-    def smi_query():
-        import subprocess
-        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-        try:
-            out = subprocess.run(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits"],
-                                 capture_output=True, text=True, timeout=20).stdout.strip().splitlines()
-            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
-            row = out[int(vis) if vis.isdigit() and int(vis) < len(out) else 0].split(",")
-            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-            reasons = [n for n, v in zip(names, row[2:]) if v.strip() == "Active"]
-            return float(row[0]), float(row[1]), reasons
-        except Exception:
-            return None, None, []
+    def _smi_index():
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+        return vis if vis.isdigit() else "0"
 
     def stop(self):
-        if not self.ok:
-            sm, smax, reasons = self.smi_query()
-            return {"sm_mhz": sm, "sm_max_mhz": smax, "reasons": reasons,
-                    "note": "NVML unavailable (%s); nvidia-smi queried right after the timed region" % self.err}
-        self._stop.set()
-        self._t.join()
-        s = self.samples
-        return {"sm_mhz": statistics.median(s) if s else None, "sm_max_mhz": self.max_mhz,
-                "reasons": sorted(self.reasons - {"gpu_idle"}), "samples": len(s)}
+        t1 = time.time()
+        if self.ok:
+            self._stop.set()
+            self._t.join()
+            s = self.samples
+            return {"sm_mhz": statistics.median(s) if s else None, "sm_max_mhz": self.max_mhz,
+                    "reasons": sorted(self.reasons - {"gpu_idle"}), "samples": len(s), "source": "nvml"}
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "note": "no NVML (%s) and no nvidia-smi" % self.err}
+        time.sleep(0.1)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        for line in out.strip().splitlines():
+            row = [x.strip() for x in line.split(",")]
+            if len(row) < 7:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax = float(row[2])
+            except ValueError:
+                continue
+            reasons |= {n for n, v in zip(self.SMI_NAMES, row[3:7]) if v == "Active"}
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm), "window_s": round(t1 - self.t0 + 0.4, 3),
+                "source": "nvidia-smi -lms 20 from 0.3 s before to 0.1 s after the timed region (NVML: %s)" % self.err}
 
 
 # ------------------------------------------------------------------------------------------------------
@@ -420,8 +446,8 @@ def finish(args, rank, world, value, ms_max, roofline, cpu, e2e, clocks, launche
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
