@@ -311,6 +311,10 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     clip = synth.moving_rect_clip(seed=1002 + rank, frames=F, M=M, N=N)
     plan = P.Plan(M=M, N=N, C=C, grids=GRIDS, eps=EPS, m=MVAR, source=P.SRC_VARIANCE, dtype=P.REC_F32, seed=SEED)
+    if args.fused_px:
+        plan.tune(P.TUNE_FUSED_PX, args.fused_px)
+    if args.fused_threads:
+        plan.tune(P.TUNE_FUSED_THREADS, args.fused_threads)
     frames = torch.from_numpy(clip).to(dev)
     records = plan.alloc_records(F, device=dev)
     ws = plan.alloc_workspace(F, device=dev)
@@ -349,6 +353,7 @@ def run_ours(args):
     P.prof_enable(False)
     P.dp_pix_status()
     ms = e0.elapsed_time(e1) / args.steps
+    args.tuning = {"fused_px": plan.tuning(P.TUNE_FUSED_PX), "fused_threads": plan.tuning(P.TUNE_FUSED_THREADS)}
     ms_max = max_over_ranks(ms, world)
     value = whole_job_mpx_per_s(world, ms_max)
     launches = sum(v[0] for v in prof.values())
@@ -433,7 +438,7 @@ def finish(args, rank, world, value, ms_max, roofline, cpu, e2e, clocks, launche
                 "config": config({"parallelism": "replicas: one clip per GPU, no collective" if world > 1 else "1 GPU",
                                   "arith": "u8 samples, exact u32 cell sums, f32 noise/mean",
                                   "path": "dp_pix_release_reconstruct" if args.path == "fused" else
-                                  "dp_pix_release + dp_pix_reconstruct"}),
+                                  "dp_pix_release + dp_pix_reconstruct", "tuning": getattr(args, "tuning", None)}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                 "latency": latency}
         print(json.dumps(line), flush=True)
@@ -453,6 +458,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--frames", type=int, default=64, help="frames per step (64 = the benchmark workload)")
+    ap.add_argument("--fused-px", type=int, default=None, help="DP_PIX_TUNE_FUSED_PX (default: the plan's)")
+    ap.add_argument("--fused-threads", type=int, default=None, help="DP_PIX_TUNE_FUSED_THREADS (default: the plan's)")
     ap.add_argument("--path", choices=["fused", "two-call"], default="fused",
                     help="fused: dp_pix_release_reconstruct; two-call: dp_pix_release then dp_pix_reconstruct")
     args = ap.parse_args()

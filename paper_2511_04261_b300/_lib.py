@@ -22,6 +22,7 @@ PAD_REFLECT, PAD_SYMMETRIC = 0, 1
 SRC_TILE_LABELS, SRC_MASK_U8, SRC_MATTE_F32, SRC_VARIANCE = 0, 1, 2, 3
 REC_F32, REC_U8, REC_SUM_U32 = 0, 1, 2
 OUT_U8, OUT_F32 = 0, 1
+TUNE_FUSED_PX, TUNE_FUSED_THREADS = 1, 2
 
 
 class Desc(ct.Structure):
@@ -67,6 +68,8 @@ def lib():
     P, I32, I64, U32, U64 = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_uint32, ct.c_uint64
     L.dp_pix_plan.argtypes = [ct.POINTER(Desc), ct.POINTER(P), ct.POINTER(Sizes)]
     L.dp_pix_plan_destroy.argtypes = [P]
+    L.dp_pix_plan_tune.argtypes = [P, ct.c_int, ct.c_int]
+    L.dp_pix_plan_tuning.argtypes = [P, ct.c_int, ct.POINTER(ct.c_int)]
     L.dp_pix_release.argtypes = [P, P, I64, P, I64, I64, U32, U32, U64, P, I64, P, U64, P]
     L.dp_pix_release_reconstruct.argtypes = [P, P, I64, P, I64, I64, U32, U32, U64, P, I64, P, I64, I64, ct.c_int, P,
                                              U64, P]
@@ -82,7 +85,7 @@ def lib():
     L.dp_pix_prof_enable.argtypes = [ct.c_int]
     L.dp_pix_prof_read.argtypes = [ct.POINTER(ProfEntry), ct.c_int]
     L.dp_pix_prof_reset.argtypes = []
-    for name in ("dp_pix_plan", "dp_pix_plan_destroy", "dp_pix_release", "dp_pix_release_reconstruct",
+    for name in ("dp_pix_plan", "dp_pix_plan_destroy", "dp_pix_plan_tune", "dp_pix_plan_tuning", "dp_pix_release", "dp_pix_release_reconstruct",
                  "dp_pix_release_noalloc", "dp_pix_store",
                  "dp_pix_store_batch",
                  "dp_pix_reconstruct",

@@ -87,6 +87,16 @@ class Plan:
     def handle(self):
         return self._h
 
+    def tune(self, knob: int, value: int) -> "Plan":
+        """dp_pix_plan_tune: set a launch-shape knob (TUNE_FUSED_PX, TUNE_FUSED_THREADS); results never change."""
+        L.check(L.lib().dp_pix_plan_tune(self._h, int(knob), int(value)), "dp_pix_plan_tune")
+        return self
+
+    def tuning(self, knob: int) -> int:
+        v = ct.c_int(0)
+        L.check(L.lib().dp_pix_plan_tuning(self._h, int(knob), ct.byref(v)), "dp_pix_plan_tuning")
+        return int(v.value)
+
     def record_stride(self) -> int:
         return (self.record_bytes + 255) // 256 * 256
 

@@ -224,9 +224,12 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     if (g.var_onepass) {
         g.gx_cells = (int)(g.GC * T / g.g);
         g.gy_cells = (int)(g.GR * T / g.g);
-        off = a256(off + 2ull * (uint64_t)g.gx_cells * g.gy_cells * g.C);
+        g.gpitch = (g.gx_cells * g.C + 7) / 8 * 8;
+        off = a256(off + 2ull * (uint64_t)g.gpitch * g.gy_cells);
     }
     g.ws_per_frame = off;
+    g.fused_px = 512;
+    g.fused_threads = 256;
     // staged segment: S tiles of one tile row, S*T*C a multiple of 16 when possible
     int s0 = 16 / (int)gcd64(TC, 16);
     int S = s0 * (int)((384 + (int64_t)s0 * TC - 1) / ((int64_t)s0 * TC));
@@ -295,6 +298,33 @@ int dp_pix_plan(const dp_pix_desc *d, dp_pix_plan_t *out, dp_pix_sizes *sz) {
 int dp_pix_plan_destroy(dp_pix_plan_t plan) {
     delete plan;
     return DP_PIX_OK;
+}
+
+int dp_pix_plan_tune(dp_pix_plan_t plan, int knob, int value) {
+    t_err[0] = 0;
+    if (!plan) return fail(DP_PIX_E_INVALID_ARG, "plan is NULL");
+    switch (knob) {
+        case DP_PIX_TUNE_FUSED_PX:
+            if (value < 64 || value > 2048) return fail(DP_PIX_E_INVALID_ARG, "fused pixel columns must be 64..2048");
+            plan->g.fused_px = value;
+            return DP_PIX_OK;
+        case DP_PIX_TUNE_FUSED_THREADS:
+            if (value != 128 && value != 256) return fail(DP_PIX_E_INVALID_ARG, "fused threads must be 128 or 256");
+            plan->g.fused_threads = value;
+            return DP_PIX_OK;
+        default:
+            return fail(DP_PIX_E_INVALID_ARG, "unknown knob %d", knob);
+    }
+}
+
+int dp_pix_plan_tuning(dp_pix_plan_t plan, int knob, int *value) {
+    t_err[0] = 0;
+    if (!plan || !value) return fail(DP_PIX_E_INVALID_ARG, "plan or value is NULL");
+    switch (knob) {
+        case DP_PIX_TUNE_FUSED_PX: *value = plan->g.fused_px; return DP_PIX_OK;
+        case DP_PIX_TUNE_FUSED_THREADS: *value = plan->g.fused_threads; return DP_PIX_OK;
+        default: return fail(DP_PIX_E_INVALID_ARG, "unknown knob %d", knob);
+    }
 }
 
 }  // extern "C"

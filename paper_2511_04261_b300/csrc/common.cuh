@@ -45,11 +45,13 @@ struct Geom {
     // workspace layout, per frame
     uint64_t ws_per_frame, ws_tileoff, ws_tilelist, ws_keys, ws_gsum;
     int32_t gx_cells, gy_cells;       // g-image: (GR*T/g) rows of (GC*T/g) g-cells, C u16 sums each
+    int32_t gpitch;                   // u16 values per g-image row: gx_cells * C rounded up to 16 bytes
     // launch shapes
     int32_t seg_tiles;                // tiles per staged segment of a tile row
     int32_t seg_per_row;              // ceil(GC / seg_tiles)
     int32_t seg_rowstride;            // bytes per staged row (multiple of 16)
     int32_t vbands;                   // max bands of a staged tile = T / b_min (or T / g for stats)
+    int32_t fused_px, fused_threads;  // launch shape of the fused release + reconstruction (tunable)
 };
 
 // Per-call arguments of a release.

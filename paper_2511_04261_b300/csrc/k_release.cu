@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats(const Geom g, const Cal
                         if (ch < C) S[ch] += vrow[i * C + ch];
                 }
                 // g-image position of g-cell (cy, cx) of tile (ty, tx0 + t)
-                uint16_t *dst = gimg + ((size_t)(ty * gcs + cy) * g.gx_cells + (size_t)(tx0 + t) * gcs + cx) * C;
+                uint16_t *dst = gimg + (size_t)(ty * gcs + cy) * g.gpitch + ((size_t)(tx0 + t) * gcs + cx) * C;
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch)
                     if (ch < C) dst[ch] = (uint16_t)S[ch];
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs 
     const uint32_t *tilelist = reinterpret_cast<const uint32_t *>(wsf + g.ws_tilelist);
     const uint16_t *gimg = reinterpret_cast<const uint16_t *>(wsf + g.ws_gsum);
     const int C = g.C, gcs = g.T / g.g;
-    const size_t rowvals = (size_t)g.gx_cells * C;
+    const size_t rowvals = (size_t)g.gpitch;
     const uint64_t frame = a.frame_idx0 + f;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         int r = 0;
@@ -440,23 +440,32 @@ int grid_for(K kernel, size_t smem, uint32_t items) {
 }
 
 // ------------------------------------------------------------------------------------------------------
-// k_emit_recon: the emit and the reconstruction fused, for one (frame, tile-row segment) per item.  Each
-// cell's noisy mean is computed from the g-image as in k_emit and written to the record; the value a
-// reconstruction would read back is staged in shared memory, and the segment's output rows are written
-// from there (seg_write.cuh) -- the record is never read back.
+// k_emit_recon: the emit and the reconstruction fused, for one (frame, tile-row segment) per item.
+//  A. the segment's tile table (map byte, payload offset) and its block of the g-image (T/g rows of
+//     ns*T/g g-cells) are fetched together with 16-byte loads into shared memory -- one round trip;
+//  B. one thread per cell: the b_r-cell sum from the shared g-cells, noise, clip, the record element,
+//     and the value a reconstruction would read back (Sec. VI-F) staged in shared memory;
+//  C. the segment's output rows are written from the stage (seg_write.cuh) -- the record is never read back.
+// Shared memory: g-cells [T/g][gseg_bytes] | stage | colinfo, sized by the launcher.
 // ------------------------------------------------------------------------------------------------------
-constexpr int kFusedStage = 32768;
+struct FusedShape {
+    int seg;            // tiles per item
+    int gseg_bytes;     // bytes per g-image row of a segment (multiple of 16)
+    int stage_off, colinfo_off, smem;
+};
 
-template <int C, int kOutF32>
-__global__ void __launch_bounds__(kThreads)
-    k_emit_recon(const Geom g, const CallArgs a, uint8_t *out, int64_t out_frame_stride, int64_t out_pitch, int seg) {
+template <int C, int kOutF32, int kThr>
+__global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
+    k_emit_recon(const Geom g, const CallArgs a, uint8_t *out, int64_t out_frame_stride, int64_t out_pitch,
+                 const FusedShape fs) {
     extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ SegTiles st;
     constexpr int oes = kOutF32 ? 4 : 1;
-    uint8_t *stage = dyn;
-    uint32_t *colinfo = reinterpret_cast<uint32_t *>(dyn + kFusedStage);
-    const int T = g.T, gcs = T / g.g;
-    const size_t rowvals = (size_t)g.gx_cells * C;
+    uint8_t *gseg = dyn;
+    uint8_t *stage = dyn + fs.stage_off;
+    uint32_t *colinfo = reinterpret_cast<uint32_t *>(dyn + fs.colinfo_off);
+    const int T = g.T, gcs = T / g.g, seg = fs.seg;
+    const int gsv = fs.gseg_bytes >> 1;  // u16 values per shared g-image row
     const uint32_t nseg = (uint32_t)((g.GC + seg - 1) / seg);
     const uint32_t items = a.n_frames * (uint32_t)g.GR * nseg;
     for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
@@ -467,6 +476,7 @@ __global__ void __launch_bounds__(kThreads)
         const int ns = min(seg, g.GC - tx0);
         uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
         const uint8_t *wsf = a.ws + (uint64_t)f * g.ws_per_frame;
+        // ---- A: tile table and g-cells of the segment ----
         if ((int)threadIdx.x < ns) {
             const int t = threadIdx.x;
             const uint32_t tile = (uint32_t)ty * g.GC + tx0 + t;
@@ -477,13 +487,23 @@ __global__ void __launch_bounds__(kThreads)
             st.cs[t] = g.cells_side[r];
             st.off[t] = reinterpret_cast<const uint32_t *>(wsf + g.ws_tileoff)[tile];
         }
+        {
+            const int nvec = (ns * gcs * C * 2 + 15) >> 4;  // 16-byte chunks per row (the row pitch covers the last)
+            const uint8_t *src0 = wsf + g.ws_gsum + ((size_t)ty * gcs * g.gpitch + (size_t)tx0 * gcs * C) * 2;
+            for (int i = threadIdx.x; i < gcs * nvec; i += kThr) {
+                const int row = i / nvec, v = i - row * nvec;
+                const uint4 x = __ldcs(reinterpret_cast<const uint4 *>(src0 + (size_t)row * g.gpitch * 2) + v);
+                *reinterpret_cast<uint4 *>(gseg + row * fs.gseg_bytes + v * 16) = x;
+            }
+        }
         __syncthreads();
         seg_prefix_colinfo(st, ns, T, colinfo);
         __syncthreads();
+        // ---- B: cells ----
         const int ncell = st.base[ns];
-        const uint16_t *gimg = reinterpret_cast<const uint16_t *>(wsf + g.ws_gsum);
         const uint64_t frame = a.frame_idx0 + f;
-        for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
+        const uint16_t *gs16 = reinterpret_cast<const uint16_t *>(gseg);
+        for (int e = threadIdx.x; e < ncell; e += kThr) {
             int lo = 0, hi = ns - 1;  // last tile whose first cell is <= e
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -494,8 +514,7 @@ __global__ void __launch_bounds__(kThreads)
             const int cy = (cs & (cs - 1)) == 0 ? c >> (__ffs(cs) - 1) : c / cs, cx = c - cy * cs;
             const int tx = tx0 + t, nb = st.b[t] / g.g;
             uint32_t S[4] = {0u, 0u, 0u, 0u};
-            gblock_sum<C>(gimg + (size_t)(ty * gcs + cy * nb) * rowvals + ((size_t)tx * gcs + (size_t)cx * nb) * C,
-                          rowvals, nb, S);
+            gblock_sum<C>(gs16 + (size_t)(cy * nb) * gsv + (size_t)(t * gcs + cx * nb) * C, (size_t)gsv, nb, S);
             const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)(tx * cs + cx);
             float ov[4] = {0.f, 0.f, 0.f, 0.f};
             emit_cell(g, a, rec + st.off[t] + (uint64_t)c * C * g.es, S, r, cell_idx, frame, ov);
@@ -509,6 +528,7 @@ __global__ void __launch_bounds__(kThreads)
             }
         }
         __syncthreads();
+        // ---- C: output rows ----
         const int x0 = tx0 * T;
         seg_write_rows<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, g.N - x0), min(T, g.M - ty * T),
                                    out + (uint64_t)f * (uint64_t)out_frame_stride + (int64_t)(ty * T) * out_pitch +
@@ -518,16 +538,20 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-template <int C, int kOutF32>
-cudaError_t launch_er(const Geom &g, const CallArgs &a, uint8_t *out, int64_t ofs, int64_t op, int seg, cudaStream_t s) {
-    const size_t smem = kFusedStage + (size_t)kSegMaxPx * 4;
-    auto kern = k_emit_recon<C, kOutF32>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)((g.GC + seg - 1) / seg);
-    const int grid = grid_for(kern, smem, items);
+template <int C, int kOutF32, int kThr>
+cudaError_t launch_er(const Geom &g, const CallArgs &a, uint8_t *out, int64_t ofs, int64_t op, const FusedShape &fs,
+                      cudaStream_t s) {
+    auto kern = k_emit_recon<C, kOutF32, kThr>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, fs.smem);
+    const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)((g.GC + fs.seg - 1) / fs.seg);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThr, fs.smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const uint64_t cap = (uint64_t)per_sm * (uint64_t)sm_count();
+    const int grid = (int)(items < cap ? items : cap);
     const char *name = kOutF32 ? "k_emit_recon_f32" : "k_emit_recon_u8";
     prof_begin(name, s);
-    kern<<<grid, kThreads, smem, s>>>(g, a, out, ofs, op, seg);
+    kern<<<grid, kThr, fs.smem, s>>>(g, a, out, ofs, op, fs);
     prof_end(name, s);
     return cudaGetLastError();
 }
@@ -581,21 +605,40 @@ int gcd_int(int a, int b) {
     return a;
 }
 
-// Fused emit + reconstruction when the output layout allows the vectorised write (16-byte aligned rows) and
-// a segment's cells fit the staging buffer; cudaErrorNotSupported (nothing launched) otherwise.
+// Fused emit + reconstruction when the output layout allows the vectorised write (16-byte aligned rows)
+// and a segment fits shared memory; cudaErrorNotSupported (nothing launched) otherwise.  The segment is
+// the largest whole number of tiles with at most fused_px pixel columns whose output bytes and g-image
+// bytes both start on 16-byte boundaries.
 cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, int64_t out_frame_stride,
                               int64_t out_pitch, int out_type, int out_align, cudaStream_t s) {
     const int oes = out_type == DP_PIX_OUT_F32 ? 4 : 1;
     const int trb = g.T * g.C * oes;
-    if (!g.var_onepass || out_align != 16 || trb < 16) return cudaErrorNotSupported;
-    const int s0 = 16 / gcd_int(trb, 16);
+    if (!g.var_onepass || out_align != 16 || trb < 16 || (reinterpret_cast<uintptr_t>(a.ws) & 15) != 0)
+        return cudaErrorNotSupported;
+    const int gcs = g.T / g.g;
+    const int gtb = gcs * g.C * 2;  // g-image bytes of one tile in one g-row
+    const int s0 = 16 / gcd_int(trb, 16), s1 = 16 / gcd_int(gtb, 16);
+    const int sm = s0 / gcd_int(s0, s1) * s1;  // segment tile-count granularity
     int csmax = 1;
     for (int r = 0; r < g.K; ++r) csmax = std::max(csmax, g.cells_side[r]);
     const int vb = oes == 4 ? 16 : 4;
-    int seg = std::min(kSegMaxTiles, (g.GC + s0 - 1) / s0 * s0) / s0 * s0;
-    while (seg > 0 && ((int64_t)seg * csmax * csmax * vb > kFusedStage || seg * g.T > kSegMaxPx)) seg -= s0;
-    if (seg <= 0) return cudaErrorNotSupported;
-#define DPPIX_ER(CC, F) return launch_er<CC, F>(g, a, out, out_frame_stride, out_pitch, seg, s)
+    const int px = g.fused_px;
+    int seg = std::max(1, std::min(kSegMaxTiles, std::min(px, kSegMaxPx) / g.T) / sm) * sm;
+    FusedShape fs{};
+    for (; seg >= sm; seg -= sm) {
+        if (seg > kSegMaxTiles || seg * g.T > kSegMaxPx) continue;
+        fs.seg = seg;
+        fs.gseg_bytes = (seg * gtb + 15) / 16 * 16;
+        fs.stage_off = gcs * fs.gseg_bytes;
+        fs.colinfo_off = fs.stage_off + (seg * csmax * csmax * vb + 15) / 16 * 16;
+        fs.smem = fs.colinfo_off + seg * g.T * 4;
+        if (fs.smem <= 64 * 1024) break;
+    }
+    if (seg < sm) return cudaErrorNotSupported;
+    const int thr = g.fused_threads;
+#define DPPIX_ER(CC, F)                                                              \
+    return thr == 128 ? launch_er<CC, F, 128>(g, a, out, out_frame_stride, out_pitch, fs, s) \
+                      : launch_er<CC, F, 256>(g, a, out, out_frame_stride, out_pitch, fs, s)
     if (oes == 4) {
         switch (g.C) {
             case 1: DPPIX_ER(1, 1);

@@ -7,7 +7,7 @@
 //  - the tile's sum of squares (dp4a of a word with itself) and sum, reduced over the tile's threads by
 //    shuffles into the exact rank key n*Q - S^2.
 // The g-cell sums go to a "g-image" (rows of g-cells, C u16 each) so that neighbouring threads store
-// neighbouring bytes.  Used when the frame needs no column padding and rows are 16-byte aligned; the
+// neighbouring bytes (rows gpitch values apart).  Used when the frame needs no column padding and rows are 16-byte aligned; the
 // staged kernel in k_release.cu covers everything else.
 #include "common.cuh"
 
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats_fast(const Geom g, cons
     const uint32_t f = (uint32_t)(fr / g.GR);
     const uint8_t *fbase = a.frames + (uint64_t)f * (uint64_t)a.frame_stride + (uint64_t)q * K::BYTES;
     uint16_t *gimg = reinterpret_cast<uint16_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_gsum);
-    const int GX = g.gx_cells;
+    const int GP = g.gpitch;
     const int bands = T / G;
     uint32_t Ssum = 0, Qsum = 0;
     for (int band = 0; band < bands; ++band) {
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats_fast(const Geom g, cons
         }
         // g-cell sums of this band -> g-image row ty*T/G + band, cells q*NG .. q*NG+NG-1
         if (valid) {
-            uint16_t *dst = gimg + ((size_t)(ty * bands + band) * GX + (size_t)q * K::NG) * C;
+            uint16_t *dst = gimg + (size_t)(ty * bands + band) * GP + (size_t)q * K::NG * C;
             constexpr int NVAL = K::NG * C;
             if (NVAL % 2 == 0 && (reinterpret_cast<uintptr_t>(dst) & 3) == 0) {
 #pragma unroll

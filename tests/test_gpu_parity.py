@@ -400,3 +400,31 @@ def test_release_reconstruct_config2_sampled():
     for i in (0, F - 1):
         rec, means, sums, etas = O.release(clip[i], None, frame_idx=i, **kw)
         compare_records(recs[i], rec, means, sums, etas, O.DT_F32)
+
+
+@pytest.mark.parametrize("ot", [P.OUT_U8, P.OUT_F32])
+def test_release_reconstruct_launch_shapes_do_not_change_results(ot):
+    """Every fused launch shape (pixel columns per item, threads per block) gives the same bytes."""
+    F, M, N = 3, 200, 352
+    rng = np.random.default_rng(17)
+    imgs = rng.integers(0, 256, size=(F, M, N, 3), dtype=np.uint8)
+    imgs[:, :, : N // 2] //= 16
+    kw = dict(M=M, N=N, C=3, grids=[32, 16, 8, 4], eps=[2, 1, .5, .25], source=O.SRC_VARIANCE, dtype=O.DT_F32,
+              seed=23, m=16)
+    t = torch.from_numpy(imgs).cuda()
+    base = None
+    for px in (64, 96, 512, 2048):
+        for thr in (128, 256):
+            plan = P.Plan(**kw).tune(P.TUNE_FUSED_PX, px).tune(P.TUNE_FUSED_THREADS, thr)
+            recs, img = plan.release_reconstruct(t, out_type=ot)
+            torch.cuda.synchronize()
+            assert P.dp_pix_status() == 0
+            got = ([P.dp_pix_store(recs[i]) for i in range(F)], img.cpu().numpy())
+            if base is None:
+                base = got
+                for i in range(F):
+                    exp = O.reconstruct(np.frombuffer(got[0][i], np.uint8), 0 if ot == P.OUT_U8 else 1)
+                    assert np.array_equal(got[1][i], exp)
+            else:
+                assert got[0] == base[0], (px, thr)
+                assert np.array_equal(got[1], base[1]), (px, thr)
