@@ -146,8 +146,8 @@ DPPIX_API int dp_pix_plan_destroy(dp_pix_plan_t plan);
 /* Launch-shape knobs of a plan (no counterpart in the paper: they change speed, never results).  Set them
  * before the plan is shared; a call must not race with releases that use the plan.
  *   DP_PIX_TUNE_FUSED_PX       pixel columns per work item of the fused release + reconstruction,
- *                              64..2048 (default 512; rounded down to whole, aligned tiles)
- *   DP_PIX_TUNE_FUSED_THREADS  threads per block of that kernel, 128 or 256 (default 256)
+ *                              64..2048 (default 1024; rounded down to whole, aligned tiles)
+ *   DP_PIX_TUNE_FUSED_THREADS  threads per block of that kernel, 128 or 256 (default 128)
  * dp_pix_plan_tune returns INVALID_ARG for an unknown knob or a value out of range; dp_pix_plan_tuning
  * writes the current value to *value. */
 #define DP_PIX_TUNE_FUSED_PX 1

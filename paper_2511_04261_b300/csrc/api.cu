@@ -228,8 +228,8 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
         off = a256(off + 2ull * (uint64_t)g.gpitch * g.gy_cells);
     }
     g.ws_per_frame = off;
-    g.fused_px = 512;
-    g.fused_threads = 256;
+    g.fused_px = 1024;
+    g.fused_threads = 128;
     // staged segment: S tiles of one tile row, S*T*C a multiple of 16 when possible
     int s0 = 16 / (int)gcd64(TC, 16);
     int S = s0 * (int)((384 + (int64_t)s0 * TC - 1) / ((int64_t)s0 * TC));

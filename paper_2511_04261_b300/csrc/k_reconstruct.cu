@@ -150,7 +150,7 @@ __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i,
     const int tx0 = sg * rg.SR;
     const int ns = min(rg.SR, rg.GC - tx0);
     seg_tile_info(rec, rg, ty, tx0, ns, rec_i, status, st, cnt_s);
-    seg_prefix_colinfo(st, ns, T, colinfo);
+    seg_prefix_colinfo(st, ns, T, colinfo, threadIdx.x, blockDim.x);
     __syncthreads();
     // cell values of the segment, converted once
     const int ncell = st.base[ns];
@@ -179,7 +179,8 @@ __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i,
     // write phase: no barrier until the next item
     const int x0 = tx0 * T;
     seg_write_rows<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T),
-                               obase + (int64_t)(ty * T) * out_pitch + (int64_t)x0 * C * oes, out_pitch);
+                               obase + (int64_t)(ty * T) * out_pitch + (int64_t)x0 * C * oes, out_pitch, threadIdx.x,
+                               blockDim.x);
     __syncthreads();
 }
 

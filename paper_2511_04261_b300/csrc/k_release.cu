@@ -460,6 +460,8 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
                  const FusedShape fs) {
     extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ SegTiles st;
+    __shared__ uint8_t rlist[kSegMaxTiles];
+    __shared__ int32_t rtile[kMaxK], rcell[kMaxK + 1], rcs[kMaxK];
     constexpr int oes = kOutF32 ? 4 : 1;
     uint8_t *gseg = dyn;
     uint8_t *stage = dyn + fs.stage_off;
@@ -497,34 +499,59 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
             }
         }
         __syncthreads();
-        seg_prefix_colinfo(st, ns, T, colinfo);
+        seg_prefix_colinfo(st, ns, T, colinfo, threadIdx.x, kThr);  // warp 0 and all threads
+        if (threadIdx.x >= 32 && threadIdx.x < 64) {
+            // warp 1: the segment's tiles grouped by region (tile order kept), with region cell bases, so that
+            // the cell loop below hands a warp cells of one grid size (equal work per lane)
+            const int l = threadIdx.x - 32;
+            const int r0 = l < ns ? st.reg[l] : -1, r1 = l + 32 < ns ? st.reg[l + 32] : -1;
+            const unsigned lt = (1u << l) - 1u;
+            int tb = 0, cb = 0;
+            for (int r = 0; r < g.K; ++r) {
+                const unsigned m0 = __ballot_sync(0xffffffffu, r0 == r), m1 = __ballot_sync(0xffffffffu, r1 == r);
+                const int n0 = __popc(m0), n = n0 + __popc(m1);
+                if (r0 == r) rlist[tb + __popc(m0 & lt)] = (uint8_t)l;
+                if (r1 == r) rlist[tb + n0 + __popc(m1 & lt)] = (uint8_t)(l + 32);
+                const int cs = g.cells_side[r];
+                if (l == 0) {
+                    rtile[r] = tb;
+                    rcell[r] = cb;
+                    rcs[r] = cs;
+                }
+                tb += n;
+                cb += n * cs * cs;
+            }
+            if (l == 0) rcell[g.K] = cb;
+        }
         __syncthreads();
-        // ---- B: cells ----
-        const int ncell = st.base[ns];
+        // ---- B: cells, region by region ----
+        const int ncell = rcell[g.K];
         const uint64_t frame = a.frame_idx0 + f;
         const uint16_t *gs16 = reinterpret_cast<const uint16_t *>(gseg);
         for (int e = threadIdx.x; e < ncell; e += kThr) {
-            int lo = 0, hi = ns - 1;  // last tile whose first cell is <= e
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (st.base[mid] <= e) lo = mid; else hi = mid - 1;
-            }
-            const int t = lo, c = e - st.base[t];
-            const int r = st.reg[t], cs = st.cs[t];
-            const int cy = (cs & (cs - 1)) == 0 ? c >> (__ffs(cs) - 1) : c / cs, cx = c - cy * cs;
+            int r = 0;
+            while (r + 1 < g.K && e >= rcell[r + 1]) ++r;
+            const int cs = rcs[r], local = e - rcell[r];
+            const bool p2 = (cs & (cs - 1)) == 0;
+            const int lcs = __ffs(cs) - 1;
+            const int k = p2 ? local >> (2 * lcs) : local / (cs * cs);
+            const int c = local - k * cs * cs;
+            const int t = rlist[rtile[r] + k];
+            const int cy = p2 ? c >> lcs : c / cs, cx = c - cy * cs;
             const int tx = tx0 + t, nb = st.b[t] / g.g;
             uint32_t S[4] = {0u, 0u, 0u, 0u};
             gblock_sum<C>(gs16 + (size_t)(cy * nb) * gsv + (size_t)(t * gcs + cx * nb) * C, (size_t)gsv, nb, S);
             const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)(tx * cs + cx);
             float ov[4] = {0.f, 0.f, 0.f, 0.f};
             emit_cell(g, a, rec + st.off[t] + (uint64_t)c * C * g.es, S, r, cell_idx, frame, ov);
+            const int si = st.base[t] + c;  // the stage keeps segment order for the row writer
             if (kOutF32) {
-                reinterpret_cast<float4 *>(stage)[e] = make_float4(ov[0], ov[1], ov[2], ov[3]);
+                reinterpret_cast<float4 *>(stage)[si] = make_float4(ov[0], ov[1], ov[2], ov[3]);
             } else {
                 uint32_t pk = 0;
 #pragma unroll
                 for (int ch = 0; ch < C; ++ch) pk |= to_u8(ov[ch]) << (8 * ch);
-                reinterpret_cast<uint32_t *>(stage)[e] = pk;
+                reinterpret_cast<uint32_t *>(stage)[si] = pk;
             }
         }
         __syncthreads();
@@ -533,7 +560,7 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
         seg_write_rows<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, g.N - x0), min(T, g.M - ty * T),
                                    out + (uint64_t)f * (uint64_t)out_frame_stride + (int64_t)(ty * T) * out_pitch +
                                        (int64_t)x0 * C * oes,
-                                   out_pitch);
+                                   out_pitch, threadIdx.x, kThr);
         __syncthreads();
     }
 }

@@ -89,11 +89,12 @@ __device__ __forceinline__ uint4 build_f32_phase(int p, const float4 *pv) {
     return build_f32<C, (C > 3 ? 3 : 0)>(pv);
 }
 
-// Cell prefix st.base[0..ns] (warp 0, two tiles per lane; ns <= 64) and the pixel-column map; needs st.b
-// and st.cs.  Ends without a barrier.
-__device__ __forceinline__ void seg_prefix_colinfo(SegTiles &st, int ns, int T, uint32_t *colinfo) {
-    if (threadIdx.x < 32) {  // exclusive prefix of the tiles' cell counts, two tiles per lane
-        const int l = threadIdx.x;
+// Cell prefix st.base[0..ns] (the first warp of the group, two tiles per lane; ns <= 64) and the
+// pixel-column map; needs st.b and st.cs.  The group is threads tid = 0..nthr-1 (nthr a multiple of 32,
+// whole warps).  Ends without a barrier.
+__device__ __forceinline__ void seg_prefix_colinfo(SegTiles &st, int ns, int T, uint32_t *colinfo, int tid, int nthr) {
+    if (tid < 32) {  // exclusive prefix of the tiles' cell counts, two tiles per lane
+        const int l = tid;
         const int c0 = 2 * l < ns ? st.cs[2 * l] * st.cs[2 * l] : 0;
         const int c1 = 2 * l + 1 < ns ? st.cs[2 * l + 1] * st.cs[2 * l + 1] : 0;
         int incl = c0 + c1;
@@ -110,7 +111,7 @@ __device__ __forceinline__ void seg_prefix_colinfo(SegTiles &st, int ns, int T, 
     // pixel column -> (tile, cell column)
     const bool tp2 = (T & (T - 1)) == 0;
     const int lt = __ffs(T) - 1;
-    for (int px = threadIdx.x; px < ns * T; px += blockDim.x) {
+    for (int px = tid; px < ns * T; px += nthr) {
         const int t = tp2 ? px >> lt : px / T;
         const int b = st.b[t], pt = px - t * T;
         colinfo[px] = ((uint32_t)t << 16) | (uint32_t)((b & (b - 1)) == 0 ? pt >> (__ffs(b) - 1) : pt / b);
@@ -118,21 +119,22 @@ __device__ __forceinline__ void seg_prefix_colinfo(SegTiles &st, int ns, int T, 
 }
 
 // Writes the jmax output rows of a segment whose first output byte is orow0 (16-byte aligned) and
-// whose rows hold vpx pixels; stage holds the segment's cell values (packed u8 or float4).
+// whose rows hold vpx pixels; stage holds the segment's cell values (packed u8 or float4).  Threads
+// tid = 0..nthr-1 of the group share the work.
 template <int C, int kOutF32>
 __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, const uint8_t *stage, int ns, int T, int vpx,
-                               int jmax, uint8_t *orow0, int64_t out_pitch) {
+                               int jmax, uint8_t *orow0, int64_t out_pitch, int tid, int nthr) {
     constexpr int oes = kOutF32 ? 4 : 1;
     // write phase: thread = (16-byte column chunk, group of rows); no barrier until the next item
     const int row_bytes = vpx * C * oes;
     const int nch = (row_bytes + 15) >> 4;
-    int RG = (2 * (int)blockDim.x + nch - 1) / nch;  // about two (chunk, row group) units per thread
+    int RG = (2 * nthr + nch - 1) / nch;  // about two (chunk, row group) units per thread
     RG = RG < 1 ? 1 : (RG > jmax ? jmax : RG);
     const int rpg = (jmax + RG - 1) / RG;
     const int last_px = ns * T - 1;
     constexpr int kElems = 16 / oes;
     constexpr int NPX = kOutF32 ? FastK<C>::NPXF : FastK<C>::NPX8;
-    for (int w = threadIdx.x; w < nch * RG; w += blockDim.x) {
+    for (int w = tid; w < nch * RG; w += nthr) {
         const int k = w % nch, grp = w / nch;
         const int j0 = grp * rpg, j1 = min(jmax, j0 + rpg);
         if (j0 >= j1) continue;

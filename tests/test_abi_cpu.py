@@ -114,11 +114,11 @@ def test_variance_plan_paths():
 
 def test_plan_tuning_knobs():
     plan = P.Plan(M=1080, N=1920, C=3, grids=[32, 16, 8, 4], eps=[2, 1, .5, .25], source=P.SRC_VARIANCE)
-    assert plan.tuning(P.TUNE_FUSED_PX) == 512 and plan.tuning(P.TUNE_FUSED_THREADS) == 256
-    plan.tune(P.TUNE_FUSED_PX, 1024).tune(P.TUNE_FUSED_THREADS, 128)
     assert plan.tuning(P.TUNE_FUSED_PX) == 1024 and plan.tuning(P.TUNE_FUSED_THREADS) == 128
+    plan.tune(P.TUNE_FUSED_PX, 512).tune(P.TUNE_FUSED_THREADS, 256)
+    assert plan.tuning(P.TUNE_FUSED_PX) == 512 and plan.tuning(P.TUNE_FUSED_THREADS) == 256
     for knob, bad in [(P.TUNE_FUSED_PX, 63), (P.TUNE_FUSED_PX, 4096), (P.TUNE_FUSED_THREADS, 192), (99, 1)]:
         with pytest.raises(P.DppixError) as e:
             plan.tune(knob, bad)
         assert e.value.code == _lib.E_INVALID_ARG
-    assert plan.tuning(P.TUNE_FUSED_PX) == 1024
+    assert plan.tuning(P.TUNE_FUSED_PX) == 512
