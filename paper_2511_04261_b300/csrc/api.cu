@@ -230,7 +230,6 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     g.ws_per_frame = off;
     g.fused_px = 1024;
     g.fused_threads = 128;
-    g.fused_pbuf = 2;
     // staged segment: S tiles of one tile row, S*T*C a multiple of 16 when possible
     int s0 = 16 / (int)gcd64(TC, 16);
     int S = s0 * (int)((384 + (int64_t)s0 * TC - 1) / ((int64_t)s0 * TC));
@@ -313,10 +312,6 @@ int dp_pix_plan_tune(dp_pix_plan_t plan, int knob, int value) {
             if (value != 128 && value != 256) return fail(DP_PIX_E_INVALID_ARG, "fused threads must be 128 or 256");
             plan->g.fused_threads = value;
             return DP_PIX_OK;
-        case DP_PIX_TUNE_FUSED_PBUF:
-            if (value != 1 && value != 2) return fail(DP_PIX_E_INVALID_ARG, "fused pattern buffers must be 1 or 2");
-            plan->g.fused_pbuf = value;
-            return DP_PIX_OK;
         default:
             return fail(DP_PIX_E_INVALID_ARG, "unknown knob %d", knob);
     }
@@ -328,7 +323,6 @@ int dp_pix_plan_tuning(dp_pix_plan_t plan, int knob, int *value) {
     switch (knob) {
         case DP_PIX_TUNE_FUSED_PX: *value = plan->g.fused_px; return DP_PIX_OK;
         case DP_PIX_TUNE_FUSED_THREADS: *value = plan->g.fused_threads; return DP_PIX_OK;
-        case DP_PIX_TUNE_FUSED_PBUF: *value = plan->g.fused_pbuf; return DP_PIX_OK;
         default: return fail(DP_PIX_E_INVALID_ARG, "unknown knob %d", knob);
     }
 }

@@ -52,7 +52,6 @@ struct Geom {
     int32_t seg_rowstride;            // bytes per staged row (multiple of 16)
     int32_t vbands;                   // max bands of a staged tile = T / b_min (or T / g for stats)
     int32_t fused_px, fused_threads;  // launch shape of the fused release + reconstruction (tunable)
-    int32_t fused_pbuf;               // its row-pattern buffers: 1 or 2 (tunable)
 };
 
 // Per-call arguments of a release.

@@ -443,33 +443,25 @@ int grid_for(K kernel, size_t smem, uint32_t items) {
 // k_emit_recon: the emit and the reconstruction fused, for one (frame, tile-row segment) per item.
 //  A. the segment's tile table (map byte, payload offset) and its block of the g-image (T/g rows of
 //     ns*T/g g-cells) are fetched together with 16-byte loads into shared memory -- one round trip;
-//  B. cells, region by region: the b_r-cell sum from the shared g-cells, noise, clip, the record element,
+//  B. one thread per cell: the b_r-cell sum from the shared g-cells, noise, clip, the record element,
 //     and the value a reconstruction would read back (Sec. VI-F) staged in shared memory;
-//  C. the segment's distinct output rows (patterns) are assembled in shared memory and copied to every
-//     output row by the bulk-copy engine (seg_write.cuh) -- the record is never read back, and the pattern
-//     buffers alternate so that one item's copies run while the next item is computed.
-// Shared memory: g-cells [T/g][gseg_bytes] | stage | colinfo | npbuf pattern buffers, sized by the launcher.
+//  C. the segment's output rows are written from the stage (seg_write.cuh) -- the record is never read back.
+// Shared memory: g-cells [T/g][gseg_bytes] | stage | colinfo, sized by the launcher.
 // ------------------------------------------------------------------------------------------------------
 struct FusedShape {
     int seg;            // tiles per item
     int gseg_bytes;     // bytes per g-image row of a segment (multiple of 16)
-    int stage_off, colinfo_off, pat_off;
-    int prow;           // bytes per pattern row (multiple of 16)
-    int npat_max;       // patterns per buffer
-    int npbuf;          // pattern buffers (1 or 2)
-    int smem;
+    int stage_off, colinfo_off, smem;
 };
 
 template <int C, int kOutF32, int kThr>
-__global__ void __launch_bounds__(kThr, 1024 / kThr)
+__global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
     k_emit_recon(const Geom g, const CallArgs a, uint8_t *out, int64_t out_frame_stride, int64_t out_pitch,
                  const FusedShape fs) {
     extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ SegTiles st;
     __shared__ uint8_t rlist[kSegMaxTiles];
-    __shared__ int32_t rtile[kMaxK + 1], rcell[kMaxK + 1], rcs[kMaxK], rnb[kMaxK];
-    __shared__ uint8_t pstart[kMaxT], rowpat[kMaxT];
-    __shared__ int32_t npat_s;
+    __shared__ int32_t rtile[kMaxK], rcell[kMaxK + 1], rcs[kMaxK];
     constexpr int oes = kOutF32 ? 4 : 1;
     uint8_t *gseg = dyn;
     uint8_t *stage = dyn + fs.stage_off;
@@ -478,9 +470,7 @@ __global__ void __launch_bounds__(kThr, 1024 / kThr)
     const int gsv = fs.gseg_bytes >> 1;  // u16 values per shared g-image row
     const uint32_t nseg = (uint32_t)((g.GC + seg - 1) / seg);
     const uint32_t items = a.n_frames * (uint32_t)g.GR * nseg;
-    const int lane = threadIdx.x & 31;
-    int it = 0;
-    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x, ++it) {
+    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
         const uint32_t sg = item % nseg, fr = item / nseg;
         const int ty = (int)(fr % g.GR);
         const uint32_t f = fr / g.GR;
@@ -488,12 +478,6 @@ __global__ void __launch_bounds__(kThr, 1024 / kThr)
         const int ns = min(seg, g.GC - tx0);
         uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
         const uint8_t *wsf = a.ws + (uint64_t)f * g.ws_per_frame;
-        uint8_t *pat = dyn + fs.pat_off + (size_t)(fs.npbuf == 2 ? (it & 1) : 0) * fs.npat_max * fs.prow;
-        // the copies that last read this pattern buffer are done (each lane of warp 0 waits for its own)
-        if (threadIdx.x < 32) {
-            if (fs.npbuf == 2) bulk_wait_read<1>();
-            else bulk_wait_read<0>();
-        }
         // ---- A: tile table and g-cells of the segment ----
         if ((int)threadIdx.x < ns) {
             const int t = threadIdx.x;
@@ -519,7 +503,7 @@ __global__ void __launch_bounds__(kThr, 1024 / kThr)
         if (threadIdx.x >= 32 && threadIdx.x < 64) {
             // warp 1: the segment's tiles grouped by region (tile order kept), with region cell bases, so that
             // the cell loop below hands a warp cells of one grid size (equal work per lane)
-            const int l = lane;
+            const int l = threadIdx.x - 32;
             const int r0 = l < ns ? st.reg[l] : -1, r1 = l + 32 < ns ? st.reg[l + 32] : -1;
             const unsigned lt = (1u << l) - 1u;
             int tb = 0, cb = 0;
@@ -533,22 +517,14 @@ __global__ void __launch_bounds__(kThr, 1024 / kThr)
                     rtile[r] = tb;
                     rcell[r] = cb;
                     rcs[r] = cs;
-                    rnb[r] = g.grid[r] / g.g;
                 }
                 tb += n;
                 cb += n * cs * cs;
             }
-            if (l == 0) {
-                rtile[g.K] = tb;
-                rcell[g.K] = cb;
-            }
+            if (l == 0) rcell[g.K] = cb;
         }
         __syncthreads();
-        // ---- B: pattern rows (warp 0) and cells, region by region ----
-        if (threadIdx.x < 32) {
-            const int np = seg_patterns(g.grid, rtile, g.K, T, pstart, rowpat, lane);
-            if (lane == 0) npat_s = np;
-        }
+        // ---- B: cells, region by region ----
         const int ncell = rcell[g.K];
         const uint64_t frame = a.frame_idx0 + f;
         const uint16_t *gs16 = reinterpret_cast<const uint16_t *>(gseg);
@@ -562,13 +538,13 @@ __global__ void __launch_bounds__(kThr, 1024 / kThr)
             const int c = local - k * cs * cs;
             const int t = rlist[rtile[r] + k];
             const int cy = p2 ? c >> lcs : c / cs, cx = c - cy * cs;
-            const int tx = tx0 + t, nb = rnb[r];
+            const int tx = tx0 + t, nb = st.b[t] / g.g;
             uint32_t S[4] = {0u, 0u, 0u, 0u};
             gblock_sum<C>(gs16 + (size_t)(cy * nb) * gsv + (size_t)(t * gcs + cx * nb) * C, (size_t)gsv, nb, S);
             const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)(tx * cs + cx);
             float ov[4] = {0.f, 0.f, 0.f, 0.f};
             emit_cell(g, a, rec + st.off[t] + (uint64_t)c * C * g.es, S, r, cell_idx, frame, ov);
-            const int si = st.base[t] + c;  // the stage keeps segment order for the pattern builder
+            const int si = st.base[t] + c;  // the stage keeps segment order for the row writer
             if (kOutF32) {
                 reinterpret_cast<float4 *>(stage)[si] = make_float4(ov[0], ov[1], ov[2], ov[3]);
             } else {
@@ -579,32 +555,14 @@ __global__ void __launch_bounds__(kThr, 1024 / kThr)
             }
         }
         __syncthreads();
-        // ---- C: patterns, then the rows by bulk copy ----
+        // ---- C: output rows ----
         const int x0 = tx0 * T;
-        const int jmax = min(T, g.M - ty * T);
-        const int row_bytes = min(ns * T, g.N - x0) * C * oes;
-        const int nch = (row_bytes + 15) >> 4;
-        seg_build_patterns<C, kOutF32>(st, colinfo, stage, ns, T, nch, pstart, npat_s, jmax, pat, fs.prow, threadIdx.x,
-                                       kThr);
-        fence_proxy_async_shared();
+        seg_write_rows<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, g.N - x0), min(T, g.M - ty * T),
+                                   out + (uint64_t)f * (uint64_t)out_frame_stride + (int64_t)(ty * T) * out_pitch +
+                                       (int64_t)x0 * C * oes,
+                                   out_pitch, threadIdx.x, kThr);
         __syncthreads();
-        uint8_t *orow0 = out + (uint64_t)f * (uint64_t)out_frame_stride + (int64_t)(ty * T) * out_pitch +
-                         (int64_t)x0 * C * oes;
-        const int full = row_bytes & ~15, tail = row_bytes - full;
-        if (threadIdx.x < 32) {
-            if (full > 0)
-                for (int j = lane; j < jmax; j += 32)
-                    bulk_store(orow0 + (int64_t)j * out_pitch, pat + rowpat[j] * fs.prow, (uint32_t)full);
-            bulk_commit();
-        }
-        if (tail > 0)  // the last < 16 bytes of each row, with plain stores
-            for (int w = threadIdx.x; w < jmax * tail; w += kThr) {
-                const int j = w / tail, i = full + (w - j * tail);
-                orow0[(int64_t)j * out_pitch + i] = pat[rowpat[j] * fs.prow + i];
-            }
-        __syncthreads();  // the next item rewrites the tile table read above
     }
-    if (threadIdx.x < 32) bulk_wait_all();
 }
 
 template <int C, int kOutF32, int kThr>
@@ -693,12 +651,6 @@ cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, in
     const int vb = oes == 4 ? 16 : 4;
     const int px = g.fused_px;
     int seg = std::max(1, std::min(kSegMaxTiles, std::min(px, kSegMaxPx) / g.T) / sm) * sm;
-    int npat_max = 0;  // rows of a tile row where some grid's band starts
-    for (int j = 0; j < g.T; ++j) {
-        bool st = false;
-        for (int r = 0; r < g.K; ++r) st |= j % g.grid[r] == 0;
-        npat_max += st ? 1 : 0;
-    }
     FusedShape fs{};
     for (; seg >= sm; seg -= sm) {
         if (seg > kSegMaxTiles || seg * g.T > kSegMaxPx) continue;
@@ -706,12 +658,8 @@ cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, in
         fs.gseg_bytes = (seg * gtb + 15) / 16 * 16;
         fs.stage_off = gcs * fs.gseg_bytes;
         fs.colinfo_off = fs.stage_off + (seg * csmax * csmax * vb + 15) / 16 * 16;
-        fs.pat_off = fs.colinfo_off + (seg * g.T * 4 + 15) / 16 * 16;
-        fs.prow = (seg * g.T * g.C * oes + 15) / 16 * 16;
-        fs.npat_max = npat_max;
-        fs.npbuf = g.fused_pbuf;
-        fs.smem = fs.pat_off + fs.npbuf * fs.npat_max * fs.prow;
-        if (fs.smem <= 96 * 1024) break;
+        fs.smem = fs.colinfo_off + seg * g.T * 4;
+        if (fs.smem <= 64 * 1024) break;
     }
     if (seg < sm) return cudaErrorNotSupported;
     const int thr = g.fused_threads;

@@ -202,124 +202,3 @@ __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, cons
 }
 
 }  // namespace dppix
-
-namespace dppix {
-
-// ---- row patterns + bulk-copy row writes ----------------------------------------------------------------
-// The rows of a segment take only a few distinct values: row j of the tile row changes only where some
-// tile's cell band starts (j a multiple of its b).  Each distinct row ("pattern") is assembled once in
-// shared memory and then copied to every output row it covers by the bulk-copy engine
-// (cp.async.bulk shared -> global), so the SM issues one instruction per output row instead of one per
-// 16 bytes.
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory writes of this thread become visible to the bulk-copy (async) proxy.
-__device__ __forceinline__ void fence_proxy_async_shared() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-
-// bytes (a multiple of 16, > 0) from shared src to global dst, both 16-byte aligned.
-__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n"
-                 :
-                 : "l"(reinterpret_cast<uint64_t>(dst)), "r"(smem_u32(src)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-
-// Waits until at most N of this thread's committed bulk groups still read shared memory.
-template <int N>
-__device__ __forceinline__ void bulk_wait_read() {
-    asm volatile("cp.async.bulk.wait_group.read %0;\n" : : "n"(N) : "memory");
-}
-
-// Waits until all of this thread's bulk groups are complete (writes included).
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
-
-// Pattern rows of a segment (one warp, all 32 lanes): row j in [0, T) starts a pattern when some grid
-// present in the segment divides j.  Writes pstart[i] (first row of pattern i), rowpat[j] (pattern of
-// row j) and returns the pattern count (on every lane).  Region r is present when rtile[r+1] > rtile[r]
-// (rtile: first tile of each region in the segment's region-grouped tile list, K+1 entries).
-__device__ __forceinline__ int seg_patterns(const int32_t *grid, const int32_t *rtile, int K, int T, uint8_t *pstart,
-                                            uint8_t *rowpat, int lane) {
-    int cnt = 0;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int j0 = 0; j0 < T; j0 += 32) {
-        const int j = j0 + lane;
-        bool s = false;
-        if (j < T)
-            for (int r = 0; r < K; ++r) s |= rtile[r + 1] > rtile[r] && j % grid[r] == 0;
-        const unsigned m = __ballot_sync(0xffffffffu, s);
-        const int before = cnt + __popc(m & lt);
-        if (s) pstart[before] = (uint8_t)j;
-        if (j < T) rowpat[j] = (uint8_t)(before + (s ? 1 : 0) - 1);
-        cnt += __popc(m);
-    }
-    return cnt;
-}
-
-// Builds the 16-byte chunks k = tid, tid + nthr, ... of the npat pattern rows (pattern i is row pstart[i] of
-// the tile row; only patterns with pstart < jmax are built) from the staged cell values; pattern i lives at
-// pat + i * prow.  A chunk's pixels lie in at most two tiles (a tile row has >= 16 bytes); its vector is
-// re-gathered only when one of their cell bands changes.
-template <int C, int kOutF32>
-__device__ void seg_build_patterns(const SegTiles &st, const uint32_t *colinfo, const uint8_t *stage, int ns, int T,
-                                   int nch, const uint8_t *pstart, int npat, int jmax, uint8_t *pat, int prow, int tid,
-                                   int nthr) {
-    constexpr int oes = kOutF32 ? 4 : 1;
-    constexpr int kElems = 16 / oes;
-    constexpr int NPX = kOutF32 ? FastK<C>::NPXF : FastK<C>::NPX8;
-    const int last_px = ns * T - 1;
-    for (int k = tid; k < nch; k += nthr) {
-        const int o = k << 4;
-        const int e0 = o / oes;
-        const int p = e0 % C;
-        const int l0 = e0 / C;
-        const int lastp = min((e0 + kElems - 1) / C, last_px);
-        const uint32_t cl = colinfo[lastp];
-        const int tA = colinfo[min(l0, last_px)] >> 16;
-        const int tB = cl >> 16;
-        int cc[NPX];
-        bool inB[NPX];
-#pragma unroll
-        for (int l = 0; l < NPX; ++l) {
-            const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
-            cc[l] = (int)(v & 0xFFFFu);
-            inB[l] = (int)(v >> 16) != tA;
-        }
-        const int bA = st.b[tA], bB = st.b[tB], csA = st.cs[tA], csB = st.cs[tB];
-        const int b0A = st.base[tA], b0B = st.base[tB];
-        int prevA = -1, prevB = -1;
-        uint4 vec = make_uint4(0u, 0u, 0u, 0u);
-        for (int i = 0; i < npat; ++i) {
-            const int j = pstart[i];
-            if (j >= jmax) break;
-            const int bandA = j / bA, bandB = j / bB;
-            if (bandA != prevA || bandB != prevB) {
-                prevA = bandA;
-                prevB = bandB;
-                const int baseA = b0A + bandA * csA, baseB = b0B + bandB * csB;
-                if (kOutF32) {
-                    float4 pv[NPX];
-#pragma unroll
-                    for (int l = 0; l < NPX; ++l)
-                        pv[l] = reinterpret_cast<const float4 *>(stage)[(inB[l] ? baseB : baseA) + cc[l]];
-                    vec = build_f32_phase<C>(p, pv);
-                } else {
-                    uint32_t pv[NPX];
-#pragma unroll
-                    for (int l = 0; l < NPX; ++l)
-                        pv[l] = reinterpret_cast<const uint32_t *>(stage)[(inB[l] ? baseB : baseA) + cc[l]];
-                    vec = build_u8_phase<C>(p, pv);
-                }
-            }
-            *reinterpret_cast<uint4 *>(pat + i * prow + o) = vec;
-        }
-    }
-}
-
-}  // namespace dppix
