@@ -198,6 +198,46 @@ DPPIX_API int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frame
                                          int64_t record_stride, void *d_out, int64_t out_frame_stride, int64_t out_pitch,
                                          int out_type, void *d_ws, uint64_t ws_bytes, void *cuda_stream);
 
+/* ---- differentiable soft layer (a training pattern on top of the release; not in the paper) ------------ */
+/* y = w * P~_{b0}(x) + (1 - w) * P~_{b1}(x) on planar f32 images, where P~_b is the uniform release of
+ * Alg. 2 (mirror pad, cell mean, Laplace noise of scale R m / (b^2 eps) (Eq. 11 with Eq. 8), clip to [0, R],
+ * repeat, crop) of every channel plane.  The noise of grid j, cell (cy, cx) of image n is drawn with the
+ * Philox counter (cy * G_C,j + cx, j | stream_id << 8, (frame0 + n) mod 2^32, (frame0 + n) >> 32) and the
+ * release's sampler, so a backward pass sees the forward's draws (the noise is a constant of the layer). */
+typedef struct dp_pix_soft_desc {
+    int32_t B, C, H, W;           /* images, channels (1..4), rows, columns: x [B][C][H][W], w [B][1][H][W] */
+    int32_t grid[2];              /* b0 (weighted by w), b1 (weighted by 1 - w); 1..128 */
+    double eps[2];                /* eps_0, eps_1 > 0 (ignored when noise_free) */
+    double value_range;           /* R (1 for images in [0, 1]) */
+    double m;                     /* max-variation m */
+    int32_t pad_mode;             /* DP_PIX_PAD_* */
+    int32_t noise_free;           /* nonzero: eta = 0 */
+    uint32_t stream_id;
+    uint64_t seed;
+    uint64_t frame0;              /* image n uses frame index frame0 + n */
+} dp_pix_soft_desc;
+
+/* Bytes of the per-cell buffer `pre` (and of the backward's workspace): 4 * B * C * (G_R,0 G_C,0 + G_R,1 G_C,1).
+ * Host only.  Errors: INVALID_ARG, UNSUPPORTED (grid > 128), PAD_TOO_LARGE. */
+DPPIX_API int dp_pix_soft_sizes(const dp_pix_soft_desc *d, uint64_t *pre_bytes);
+
+/* Forward.  x, w, y: device f32, dense planar as in the desc.  pre (device, dp_pix_soft_sizes bytes,
+ * caller-owned) receives the unclipped noisy cell means, per image grid 0's [C][G_R,0][G_C,0] block then
+ * grid 1's; the backward needs it.  Asynchronous on cuda_stream.  Errors: as dp_pix_soft_sizes, CUDA. */
+DPPIX_API int dp_pix_soft_forward(const dp_pix_soft_desc *d, const float *x, const float *w, float *y, float *pre,
+                                  void *cuda_stream);
+
+/* Backward of L with dL/dy = gy, the noise held constant:
+ *   dw(p) = sum_ch gy(p) (P~_{b0}(p) - P~_{b1}(p));
+ *   dx(q) = sum_j sum over the cells c whose (mirror-padded) samples read q, once per such sample, of
+ *           [0 < pre_c < R] / b_j^2 * sum_{p in c inside the image} gy(p) w_j(p),   w_0 = w, w_1 = 1 - w.
+ * w, gy, pre: inputs (pre from dp_pix_soft_forward with the same desc); dx [B][C][H][W], dw [B][1][H][W]:
+ * outputs.  d_ws: dp_pix_soft_sizes bytes of scratch, needed unless both grids are powers of two in
+ * 4..128 with H a multiple of the larger, W a multiple of 128 and 16-byte aligned buffers (NULL is then
+ * allowed).  Asynchronous.  Errors: as dp_pix_soft_sizes, INVALID_ARG (missing buffer), CUDA. */
+DPPIX_API int dp_pix_soft_backward(const dp_pix_soft_desc *d, const float *w, const float *gy, const float *pre,
+                                   float *dx, float *dw, float *d_ws, void *cuda_stream);
+
 /*
  * dp_pix_release without a workspace argument, for callers that cannot allocate device memory: code
  * running while a CUDA graph is captured (cudaMalloc is not allowed there), plug-ins whose host framework

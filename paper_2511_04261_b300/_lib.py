@@ -25,6 +25,15 @@ OUT_U8, OUT_F32 = 0, 1
 TUNE_FUSED_PX, TUNE_FUSED_THREADS = 1, 2
 
 
+class SoftDesc(ct.Structure):
+    _fields_ = [
+        ("B", ct.c_int32), ("C", ct.c_int32), ("H", ct.c_int32), ("W", ct.c_int32),
+        ("grid", ct.c_int32 * 2), ("eps", ct.c_double * 2), ("value_range", ct.c_double), ("m", ct.c_double),
+        ("pad_mode", ct.c_int32), ("noise_free", ct.c_int32), ("stream_id", ct.c_uint32),
+        ("seed", ct.c_uint64), ("frame0", ct.c_uint64),
+    ]
+
+
 class Desc(ct.Structure):
     _fields_ = [
         ("M", ct.c_int32), ("N", ct.c_int32), ("C", ct.c_int32), ("K", ct.c_int32),
@@ -73,6 +82,9 @@ def lib():
     L.dp_pix_release.argtypes = [P, P, I64, P, I64, I64, U32, U32, U64, P, I64, P, U64, P]
     L.dp_pix_release_reconstruct.argtypes = [P, P, I64, P, I64, I64, U32, U32, U64, P, I64, P, I64, I64, ct.c_int, P,
                                              U64, P]
+    L.dp_pix_soft_sizes.argtypes = [ct.POINTER(SoftDesc), ct.POINTER(U64)]
+    L.dp_pix_soft_forward.argtypes = [ct.POINTER(SoftDesc), P, P, P, P, P]
+    L.dp_pix_soft_backward.argtypes = [ct.POINTER(SoftDesc), P, P, P, P, P, P, P]
     L.dp_pix_release_noalloc.argtypes = [P, P, I64, P, I64, I64, U32, U32, U64, P, I64, P]
     L.dp_pix_store.argtypes = [P, P, U64, ct.POINTER(U64), ct.c_int, P]
     L.dp_pix_store_batch.argtypes = [P, I64, U32, P, I64, P, P]
@@ -86,7 +98,8 @@ def lib():
     L.dp_pix_prof_read.argtypes = [ct.POINTER(ProfEntry), ct.c_int]
     L.dp_pix_prof_reset.argtypes = []
     for name in ("dp_pix_plan", "dp_pix_plan_destroy", "dp_pix_plan_tune", "dp_pix_plan_tuning", "dp_pix_release", "dp_pix_release_reconstruct",
-                 "dp_pix_release_noalloc", "dp_pix_store",
+                 "dp_pix_release_noalloc", "dp_pix_store", "dp_pix_soft_sizes", "dp_pix_soft_forward",
+                 "dp_pix_soft_backward",
                  "dp_pix_store_batch",
                  "dp_pix_reconstruct",
                  "dp_pix_debug_noise", "dp_pix_status", "dp_pix_prof_enable", "dp_pix_prof_read",

@@ -122,3 +122,23 @@ def test_plan_tuning_knobs():
             plan.tune(knob, bad)
         assert e.value.code == _lib.E_INVALID_ARG
     assert plan.tuning(P.TUNE_FUSED_PX) == 512
+
+
+def test_soft_sizes_and_validation():
+    """dp_pix_soft_sizes is host-only: the per-cell buffer size and the argument checks."""
+    spec = P.SoftSpec(grids=(8, 16), eps=(0.5, 1.0), R=1.0, m=16.0)
+    import torch
+    x = torch.empty((32, 3, 1024, 1024), device="meta")
+    d = spec.desc(x)
+    nb = ct.c_uint64(0)
+    assert _lib.lib().dp_pix_soft_sizes(ct.byref(d), ct.byref(nb)) == 0
+    assert nb.value == 4 * 32 * 3 * (128 * 128 + 64 * 64)
+    d.grid[1] = 0
+    assert _lib.lib().dp_pix_soft_sizes(ct.byref(d), ct.byref(nb)) == _lib.E_INVALID_ARG or \
+        _lib.lib().dp_pix_soft_sizes(ct.byref(d), ct.byref(nb)) == _lib.E_UNSUPPORTED
+    d.grid[1] = 16
+    d.H, d.W = 5, 5  # 16-pixel cells need 11 mirrored rows, more than a 5-row image has
+    assert _lib.lib().dp_pix_soft_sizes(ct.byref(d), ct.byref(nb)) == _lib.E_PAD_TOO_LARGE
+    d.H, d.W = 9, 9
+    assert _lib.lib().dp_pix_soft_sizes(ct.byref(d), ct.byref(nb)) == 0
+    assert nb.value == 4 * 32 * 3 * (2 * 2 + 1)
