@@ -448,6 +448,137 @@ def finish(args, rank, world, value, ms_max, roofline, cpu, e2e, clocks, launche
     return 0
 
 
+# ------------------------------------------------------------------------------------------------------
+# workload "soft": the differentiable layer on a 32 x 3 x 1024 x 1024 f32 batch (grids 8 and 16)
+# ------------------------------------------------------------------------------------------------------
+SOFT = dict(B=32, C=3, H=1024, W=1024, grids=(8, 16), eps=(0.5, 1.0), R=1.0, m=16.0, seed=4)
+SOFT_METRIC = "megapixels/sec through the soft DP-pixelization layer, forward + backward (1 B300); % HBM roofline"
+
+
+def soft_algorithmic_bytes():
+    B, C, H, W = SOFT["B"], SOFT["C"], SOFT["H"], SOFT["W"]
+    img, wgt = 4 * B * C * H * W, 4 * B * H * W
+    cells = 4 * B * C * ((H // 8) * (W // 8) + (H // 16) * (W // 16))
+    # forward: x and w read, y and the per-cell means written; backward: g and w read (+ means), dx and dw written
+    return {"k_soft_fwd": img + wgt + img + cells, "k_soft_bwd": img + wgt + cells + img + wgt}
+
+
+def soft_oracle_time(x, w, g, budget_s):
+    """Oracle forward + backward of whole images of the batch until the budget is used (at least one)."""
+    import oracle as O
+    kw = dict(grids=SOFT["grids"], eps=SOFT["eps"], R=SOFT["R"], m=SOFT["m"], seed=SOFT["seed"])
+    t0, done = time.perf_counter(), 0
+    while done < x.shape[0]:
+        O.soft_forward(x[done:done + 1], w[done:done + 1], frame0=done, **kw)
+        O.soft_backward(x[done:done + 1], w[done:done + 1], g[done:done + 1], frame0=done, **kw)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    return done, time.perf_counter() - t0
+
+
+def run_soft(args):
+    import torch
+    import paper_2511_04261_b300 as P
+    from paper_2511_04261_b300 import build, synth
+    build.build()
+    world, rank, _ = dist_setup(args.gpus)
+    B, C, H, W = SOFT["B"], SOFT["C"], SOFT["H"], SOFT["W"]
+    workload = "soft%d_%dx%dx%d_f32_b8_b16" % (B, C, H, W)
+    xh, wh, gh = synth.soft_batch(seed=1004 + rank, B=B, H=H, W=W, C=C)
+    x, w, g = (torch.from_numpy(a).cuda() for a in (xh, wh, gh))
+    spec = P.SoftSpec(grids=SOFT["grids"], eps=SOFT["eps"], R=SOFT["R"], m=SOFT["m"], seed=SOFT["seed"], stream_id=rank)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        y, pre = P.soft_forward(x, w, spec)
+        return P.soft_backward(w, g, pre, spec)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    barrier(world)
+    torch.cuda.synchronize()
+    P.prof_reset()
+    P.prof_enable(True)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    prof = P.prof_read()
+    P.prof_enable(False)
+    ms_max = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    value = world * B * H * W / 1e6 / (ms_max / 1e3)
+    hbm, peak_kind = measured_peaks()
+    algo = soft_algorithmic_bytes()
+    dom_name, (dom_launches, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    per_launch_ms = dom_ms / max(1, dom_launches)
+    achieved = algo[dom_name] / (per_launch_ms / 1e3) / 1e9
+    tot = sum(v[1] for v in prof.values())
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "algorithmic_bytes_per_launch": algo[dom_name],
+                "avg_launch_ms": per_launch_ms,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else
+                "fallback 6.4 TB/s",
+                "kernels": {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / max(1e-9, tot),
+                                "algorithmic_GBps": algo[k] / (v[1] / max(1, v[0]) / 1e3) / 1e9 if k in algo else None}
+                            for k, v in prof.items()}}
+    # end to end through the autograd wrapper: pinned host batch in, loss gradient read back
+    e2e = None
+    if not args.no_e2e:
+        xp, wp, gp = (torch.from_numpy(a).pin_memory() for a in (xh, wh, gh))
+        dxh = torch.empty_like(xp).pin_memory()
+
+        def e2e_step():
+            xd = xp.to("cuda", non_blocking=True).requires_grad_(True)
+            wd = wp.to("cuda", non_blocking=True).requires_grad_(True)
+            gd = gp.to("cuda", non_blocking=True)
+            y = P.soft_pixelize(xd, wd, spec)
+            torch.autograd.backward(y, gd)
+            dxh.copy_(xd.grad, non_blocking=True)
+            return float(wd.grad[0, 0, 0, 0])
+
+        e2e_step()
+        torch.cuda.synchronize()
+        n_e2e = max(3, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / n_e2e, world)
+        e2e = {"value": world * B * H * W / 1e6 / (e2e_ms / 1e3), "unit": "Mpx/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": xh.nbytes + wh.nbytes + gh.nbytes, "d2h_bytes_per_step": xh.nbytes + 4,
+               "path": "pinned host x, w, g -> device; soft_pixelize (autograd) forward + backward; dx -> host"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        done, dt = soft_oracle_time(xh, wh, gh, args.cpu_budget)
+        cpu = {"value": done * H * W / 1e6 / dt, "unit": "Mpx/s", "cores": 1, "kind": "oracle",
+               "sample": "%d of the %d images (oracle forward + backward, fp64, 1 thread, %.1f s)" % (done, B, dt)}
+    if rank == 0:
+        line = {"metric": SOFT_METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload, "B": B, "C": C, "H": H, "W": W, "grids": list(SOFT["grids"]),
+                           "eps": list(SOFT["eps"]), "R": SOFT["R"], "m": SOFT["m"],
+                           "step": "dp_pix_soft_forward + dp_pix_soft_backward of the batch",
+                           "l2": "inputs larger than L2 (%.0f MB read and written per step)" %
+                                 ((2 * algo["k_soft_fwd"] + algo["k_soft_bwd"] - algo["k_soft_fwd"]) / 1e6),
+                           "generator_seed": 1004, "parallelism": "1 GPU" if world == 1 else "replicas"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": sum(v[0] for v in prof.values())}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -462,12 +593,17 @@ def main():
     ap.add_argument("--fused-threads", type=int, default=None, help="DP_PIX_TUNE_FUSED_THREADS (default: the plan's)")
     ap.add_argument("--path", choices=["fused", "two-call"], default="fused",
                     help="fused: dp_pix_release_reconstruct; two-call: dp_pix_release then dp_pix_reconstruct")
+    ap.add_argument("--workload", choices=["clip", "soft"], default="clip",
+                    help="clip: the 64-frame 1080p release + reconstruction (the benchmark); soft: the differentiable "
+                         "layer on a 32 x 3 x 1024 x 1024 batch")
     args = ap.parse_args()
     set_frames(args.frames)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "soft":
+        return run_soft(args)
     return run_ours(args)
 
 
