@@ -198,6 +198,56 @@ DPPIX_API int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frame
                                          int64_t record_stride, void *d_out, int64_t out_frame_stride, int64_t out_pitch,
                                          int out_type, void *d_ws, uint64_t ws_bytes, void *cuda_stream);
 
+/* ---- ragged batches (no counterpart in the paper, which releases one frame at a time) ----------------- */
+/* Many images of different sizes released with one set of region parameters.  Each image is released
+ * exactly as dp_pix_release would release it alone with a plan for its size (same record bytes, same noise:
+ * its own stream_id and frame_idx key the draws); the batch runs each phase as one persistent launch over
+ * the work items of all images, largest images first, and replays the launches as a CUDA graph.  Region
+ * sources: TILE_LABELS, MASK_U8, MATTE_F32 (VARIANCE ranks a whole frame: UNSUPPORTED here). */
+typedef struct dp_pix_batch_s *dp_pix_batch_t;
+
+typedef struct dp_pix_batch_image {
+    const void *frame;            /* device u8 image, C interleaved samples per pixel */
+    int64_t row_pitch;            /* bytes between rows, >= N*C */
+    const void *region_src;       /* TILE_LABELS: u8 [G_R][G_C]; MASK_U8: u8 rows src_pitch apart; MATTE_F32:
+                                     f32 rows src_pitch apart (4-byte aligned) */
+    int64_t src_pitch;
+    void *record;                 /* device, dp_pix_batch_sizes bytes for this image, 16-byte aligned */
+    void *out;                    /* device reconstruction [M][N][C] (u8 or f32 per out_type), or NULL */
+    int64_t out_pitch;            /* bytes between output rows */
+    uint32_t stream_id;           /* < 2^24 */
+    uint64_t frame_idx;
+} dp_pix_batch_image;
+
+/* Plans a batch of n images, image i of M[i] x N[i] (host only).  common: the region parameters as for
+ * dp_pix_plan (its M, N and row_pitch are ignored).  Errors: as dp_pix_plan for any image; UNSUPPORTED for
+ * VARIANCE. */
+DPPIX_API int dp_pix_batch_plan(const dp_pix_desc *common, const int32_t *M, const int32_t *N, uint32_t n,
+                                dp_pix_batch_t *out);
+DPPIX_API int dp_pix_batch_destroy(dp_pix_batch_t b);
+
+/* record_bytes[i] (array of n, may be NULL): capacity to allocate for image i's record; ws_bytes: device
+ * workspace of the whole batch (the image table plus each image's workspace). */
+DPPIX_API int dp_pix_batch_sizes(dp_pix_batch_t b, uint64_t *record_bytes, uint64_t *ws_bytes);
+
+/* Binds the images (caller order) and a 256-byte aligned workspace, and uploads the image table on
+ * cuda_stream (the host array may be reused on return).  out_type: DP_PIX_OUT_U8 or DP_PIX_OUT_F32 for the
+ * images whose `out` is set.  Rebinding drops the captured graph.  Errors: INVALID_ARG (a missing buffer, a
+ * pitch or alignment), BUFFER_TOO_SMALL, CUDA. */
+DPPIX_API int dp_pix_batch_bind(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int out_type, void *d_ws,
+                                uint64_t ws_bytes, void *cuda_stream);
+
+/* Releases every bound image (and reconstructs those with an output), asynchronously on cuda_stream.
+ * use_graph != 0: the first call on a stream captures the launches into a CUDA graph, later calls replay it.
+ * Device-side problems (a bad label) arrive through dp_pix_status().  Errors: INVALID_ARG (not bound), CUDA. */
+DPPIX_API int dp_pix_batch_run(dp_pix_batch_t b, int use_graph, void *cuda_stream);
+
+/* Times the release's segment widths (tiles staged per work item) on the bound batch -- reps runs each,
+ * overwriting its records and outputs -- keeps the fastest, rebinds `imgs` (the images bound last) and drops
+ * the graph.  Synchronizes cuda_stream.  dp_pix_batch_tuning reports the width in use. */
+DPPIX_API int dp_pix_batch_autotune(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int reps, void *cuda_stream);
+DPPIX_API int dp_pix_batch_tuning(dp_pix_batch_t b, int *seg_tiles);
+
 /* ---- differentiable soft layer (a training pattern on top of the release; not in the paper) ------------ */
 /* y = w * P~_{b0}(x) + (1 - w) * P~_{b1}(x) on planar f32 images, where P~_b is the uniform release of
  * Alg. 2 (mirror pad, cell mean, Laplace noise of scale R m / (b^2 eps) (Eq. 11 with Eq. 8), clip to [0, R],

@@ -11,6 +11,7 @@ from .api import (Plan, dp_pix_debug_noise, dp_pix_plan, dp_pix_reconstruct, dp_
                   dp_pix_release_reconstruct, dp_pix_status,
                   dp_pix_store, dp_pix_store_batch, prof_enable, prof_read, prof_reset, record_header)
 
+from .batch import BatchPlan
 from .soft import SoftPixelize, SoftSpec, soft_backward, soft_forward, soft_pixelize
 
 __version__ = "0.1.0"

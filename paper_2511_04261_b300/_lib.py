@@ -34,6 +34,14 @@ class SoftDesc(ct.Structure):
     ]
 
 
+class BatchImage(ct.Structure):
+    _fields_ = [
+        ("frame", ct.c_void_p), ("row_pitch", ct.c_int64), ("region_src", ct.c_void_p), ("src_pitch", ct.c_int64),
+        ("record", ct.c_void_p), ("out", ct.c_void_p), ("out_pitch", ct.c_int64), ("stream_id", ct.c_uint32),
+        ("frame_idx", ct.c_uint64),
+    ]
+
+
 class Desc(ct.Structure):
     _fields_ = [
         ("M", ct.c_int32), ("N", ct.c_int32), ("C", ct.c_int32), ("K", ct.c_int32),
@@ -85,6 +93,13 @@ def lib():
     L.dp_pix_soft_sizes.argtypes = [ct.POINTER(SoftDesc), ct.POINTER(U64)]
     L.dp_pix_soft_forward.argtypes = [ct.POINTER(SoftDesc), P, P, P, P, P]
     L.dp_pix_soft_backward.argtypes = [ct.POINTER(SoftDesc), P, P, P, P, P, P, P]
+    L.dp_pix_batch_plan.argtypes = [ct.POINTER(Desc), ct.POINTER(I32), ct.POINTER(I32), U32, ct.POINTER(P)]
+    L.dp_pix_batch_destroy.argtypes = [P]
+    L.dp_pix_batch_sizes.argtypes = [P, ct.POINTER(U64), ct.POINTER(U64)]
+    L.dp_pix_batch_bind.argtypes = [P, ct.POINTER(BatchImage), ct.c_int, P, U64, P]
+    L.dp_pix_batch_run.argtypes = [P, ct.c_int, P]
+    L.dp_pix_batch_autotune.argtypes = [P, ct.POINTER(BatchImage), ct.c_int, P]
+    L.dp_pix_batch_tuning.argtypes = [P, ct.POINTER(ct.c_int)]
     L.dp_pix_release_noalloc.argtypes = [P, P, I64, P, I64, I64, U32, U32, U64, P, I64, P]
     L.dp_pix_store.argtypes = [P, P, U64, ct.POINTER(U64), ct.c_int, P]
     L.dp_pix_store_batch.argtypes = [P, I64, U32, P, I64, P, P]
@@ -99,7 +114,8 @@ def lib():
     L.dp_pix_prof_reset.argtypes = []
     for name in ("dp_pix_plan", "dp_pix_plan_destroy", "dp_pix_plan_tune", "dp_pix_plan_tuning", "dp_pix_release", "dp_pix_release_reconstruct",
                  "dp_pix_release_noalloc", "dp_pix_store", "dp_pix_soft_sizes", "dp_pix_soft_forward",
-                 "dp_pix_soft_backward",
+                 "dp_pix_soft_backward", "dp_pix_batch_plan", "dp_pix_batch_destroy", "dp_pix_batch_sizes",
+                 "dp_pix_batch_bind", "dp_pix_batch_run", "dp_pix_batch_autotune", "dp_pix_batch_tuning",
                  "dp_pix_store_batch",
                  "dp_pix_reconstruct",
                  "dp_pix_debug_noise", "dp_pix_status", "dp_pix_prof_enable", "dp_pix_prof_read",

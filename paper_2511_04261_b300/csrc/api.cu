@@ -80,7 +80,8 @@ void prof_begin(const char *name, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ProfEntry &e = g_prof[name];
     e.launches++;
-    if (g_prof_timing) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (g_prof_timing && cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
         cudaEvent_t a = nullptr, b = nullptr;
         if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) {
             cudaEventRecord(a, s);
@@ -92,6 +93,8 @@ void prof_begin(const char *name, cudaStream_t s) {
 void prof_end(const char *name, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_timing) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
     ProfEntry &e = g_prof[name];
     if (!e.pending.empty()) cudaEventRecord(e.pending.back().second, s);
 }
@@ -254,6 +257,13 @@ int check_cuda_device() {
     if (e != cudaSuccess || n < 1) return fail(DP_PIX_E_CUDA, "no CUDA device available: %s", cudaGetErrorString(e));
     return DP_PIX_OK;
 }
+
+}  // namespace
+
+int plan_geometry(const dp_pix_desc *d, Geom &g) { return make_geom(d, g); }
+int cuda_device_ok() { return check_cuda_device(); }
+
+namespace {
 
 }  // namespace
 }  // namespace dppix

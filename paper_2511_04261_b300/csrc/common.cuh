@@ -70,6 +70,44 @@ struct CallArgs {
     int32_t *status;                  // device status word
 };
 
+// One image of a ragged batch: its own geometry and call arguments, as a single-image release would get
+// them, plus where its work items start in each phase's flattened work list.
+struct BatchEntry {
+    Geom g;
+    CallArgs a;
+    uint8_t *out;                     // reconstruction target (NULL: none)
+    int64_t out_pitch;
+    uint64_t rec_cap;                 // bytes of the image's record buffer
+    uint32_t base[4];                 // first item: [0] classify rows, [1] finalize, [2] release items, [3] rebuild
+    uint32_t pad_;
+};
+
+struct BatchShared {
+    Geom g;
+    CallArgs a;
+};
+
+// Image owning global item `item` of phase `phase` (tab sorted by base[phase]); every thread of the block
+// computes it.
+__device__ __forceinline__ int batch_find(const BatchEntry *tab, uint32_t n, uint32_t item, int phase) {
+    int lo = 0, hi = (int)n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].base[phase] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Copies image i's geometry and arguments into shared memory (whole block; barriers on both sides).
+__device__ __forceinline__ void batch_load(const BatchEntry *tab, int i, BatchShared &bs) {
+    static_assert(sizeof(BatchShared) % 4 == 0, "word copy");
+    __syncthreads();
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&tab[i].g);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&bs);
+    for (int k = threadIdx.x; k < (int)(sizeof(BatchShared) / 4); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64 multiplies with the
 // published multipliers, the key bumped by the published Weyl constants between rounds.
@@ -160,6 +198,12 @@ cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, in
 cudaError_t launch_reconstruct(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out,
                                int64_t out_frame_stride, int64_t out_pitch, int out_type, int max_M, int max_N,
                                int max_C, int out_align, int32_t *status, cudaStream_t s);
+cudaError_t launch_batch_classify(const BatchEntry *tab, uint32_t n_img, uint32_t items, int max_gc, int matte,
+                                  cudaStream_t s);
+cudaError_t launch_batch_finalize(const BatchEntry *tab, uint32_t n_img, uint32_t max_tiles, cudaStream_t s);
+cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_reconstruct(const BatchEntry *tab, uint32_t n_img, uint32_t items, int out_type, int max_C,
+                                     int out_align, int32_t *status, cudaStream_t s);
 cudaError_t launch_debug_noise(uint64_t seed, const uint32_t *ctr, uint64_t n, uint32_t *words, float *eta,
                                float sigma, cudaStream_t s);
 
@@ -173,5 +217,7 @@ struct dp_pix_plan_s;
 namespace dppix {
 uint64_t plan_ws_per_frame(const dp_pix_plan_s *plan);  // workspace bytes per frame of a plan (0 for NULL)
 int set_last_error(int code, const char *msg);          // sets this thread's dp_pix_last_error(), returns code
+int plan_geometry(const dp_pix_desc *d, Geom &g);       // dp_pix_plan's validation and geometry (host)
+int cuda_device_ok();                                   // DP_PIX_OK, or DP_PIX_E_CUDA with the message set
 
 }  // namespace dppix

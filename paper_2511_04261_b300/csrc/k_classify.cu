@@ -4,6 +4,8 @@
 // column over the tile row's T mirror-padded rows, and adds the count to its tile's counter.  A tile is
 // simple (region 0) iff 2 * #simple > T^2 -- the paper's mask mean > 1/2 on exact integers, a tie going
 // to complex (region 1).  MASK_U8: nonzero = simple.  MATTE_F32: a pixel is complex iff alpha >= thr.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace dppix {
@@ -11,11 +13,9 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Tile row ty of frame f: the map bytes of its GC tiles.  cnt_s: GC counters in shared memory.
 template <bool kMatte>
-__global__ void __launch_bounds__(kThreads) k_classify(const Geom g, const CallArgs a) {
-    extern __shared__ uint32_t cnt_s[];  // [GC]
-    const int ty = blockIdx.x;
-    const uint32_t f = blockIdx.y;
+__device__ __forceinline__ void classify_row(const Geom &g, const CallArgs &a, int ty, uint32_t f, uint32_t *cnt_s) {
     const int T = g.T;
     for (int i = threadIdx.x; i < g.GC; i += blockDim.x) cnt_s[i] = 0u;
     __syncthreads();
@@ -42,7 +42,47 @@ __global__ void __launch_bounds__(kThreads) k_classify(const Geom g, const CallA
     for (int tx = threadIdx.x; tx < g.GC; tx += blockDim.x) map[tx] = (2u * cnt_s[tx] > half2) ? 0 : 1;
 }
 
+template <bool kMatte>
+__global__ void __launch_bounds__(kThreads) k_classify(const Geom g, const CallArgs a) {
+    extern __shared__ uint32_t cnt_s[];  // [GC]
+    classify_row<kMatte>(g, a, blockIdx.x, blockIdx.y, cnt_s);
+}
+
+// Batch: items = tile rows of every image (image i owns items [base_cls, base_cls + GR)).
+template <bool kMatte>
+__global__ void __launch_bounds__(kThreads) k_batch_classify(const BatchEntry *tab, uint32_t n_img, uint32_t items) {
+    extern __shared__ uint32_t cnt_s[];  // [max GC]
+    __shared__ BatchShared bs;
+    int cur = -1;
+    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int i = batch_find(tab, n_img, item, 0);
+        if (i != cur) {
+            batch_load(tab, i, bs);
+            cur = i;
+        }
+        classify_row<kMatte>(bs.g, bs.a, (int)(item - tab[i].base[0]), 0u, cnt_s);
+        __syncthreads();  // cnt_s and bs are reused by the next item
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_classify(const BatchEntry *tab, uint32_t n_img, uint32_t items, int max_gc, int matte,
+                                  cudaStream_t s) {
+    const size_t smem = (size_t)max_gc * 4;
+    const int per_sm = 4;
+    const int grid = (int)std::min<uint64_t>(items, (uint64_t)per_sm * sm_count());
+    if (matte) {
+        prof_begin("k_batch_classify", s);
+        k_batch_classify<true><<<grid, kThreads, smem, s>>>(tab, n_img, items);
+        prof_end("k_batch_classify", s);
+    } else {
+        prof_begin("k_batch_classify", s);
+        k_batch_classify<false><<<grid, kThreads, smem, s>>>(tab, n_img, items);
+        prof_end("k_batch_classify", s);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_classify(const Geom &g, const CallArgs &a, cudaStream_t s) {
     const dim3 grid(g.GR, a.n_frames);

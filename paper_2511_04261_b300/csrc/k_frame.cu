@@ -5,6 +5,7 @@
 // payload byte offset to the workspace, writes the tile-row index and the 512-byte header into the
 // record.  The rank kernel first builds the map from the per-tile variance keys (exact integers) by a
 // bitonic sort of (key, tile index) in shared memory.
+#include <algorithm>
 #include <cstring>
 
 #include "common.cuh"
@@ -180,6 +181,32 @@ __global__ void __launch_bounds__(kFrameThreads) k_finalize(const Geom g, const 
     finalize_frame(g, a, f, map_s, from_labels != 0, sm);
 }
 
+// Batch: one CTA per image (map written by k_batch_classify, or caller labels).
+__global__ void __launch_bounds__(kFrameThreads) k_batch_finalize(const BatchEntry *tab, uint32_t n_img) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ BatchShared bs;
+    FinalizeSmem &sm = *reinterpret_cast<FinalizeSmem *>(dyn);
+    uint8_t *map_s = dyn + sizeof(FinalizeSmem);
+    for (uint32_t i = blockIdx.x; i < n_img; i += gridDim.x) {
+        batch_load(tab, (int)i, bs);
+        const Geom &g = bs.g;
+        const CallArgs &a = bs.a;
+        const bool from_labels = g.source == DP_PIX_SRC_TILE_LABELS;
+        const uint8_t *src = from_labels ? a.src : a.records + g.map_offset;
+        for (uint32_t t = threadIdx.x; t < g.ntiles; t += blockDim.x) {
+            uint8_t r = src[t];
+            if (r >= (uint32_t)g.K) {
+                raise_status(a.status, DP_PIX_E_DEVICE, 0x100u | r);
+                r = 0;
+            }
+            map_s[t] = r;
+        }
+        __syncthreads();
+        finalize_frame(g, a, 0u, map_s, from_labels, sm);
+        __syncthreads();
+    }
+}
+
 // VARIANCE classes: tiles ranked by (key, index) ascending get class q = floor(K * rank / n).  Only the
 // K - 1 class boundaries matter: the tile of rank ceil(q n / K) starts class q.  Each boundary value is
 // found exactly by a radix select over the unique packed values key << idx_bits | index (8-bit digits from
@@ -275,6 +302,16 @@ cudaError_t launch_finalize_map(const Geom &g, const CallArgs &a, cudaStream_t s
     prof_begin("k_finalize", s);
     k_finalize<<<a.n_frames, kFrameThreads, smem, s>>>(g, a, 0);
     prof_end("k_finalize", s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finalize(const BatchEntry *tab, uint32_t n_img, uint32_t max_tiles, cudaStream_t s) {
+    const size_t smem = sizeof(FinalizeSmem) + max_tiles;
+    cudaFuncSetAttribute(k_batch_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = (int)std::min<uint32_t>(n_img, (uint32_t)sm_count());
+    prof_begin("k_batch_finalize", s);
+    k_batch_finalize<<<grid, kFrameThreads, smem, s>>>(tab, n_img);
+    prof_end("k_batch_finalize", s);
     return cudaGetLastError();
 }
 

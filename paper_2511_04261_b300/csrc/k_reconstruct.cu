@@ -11,6 +11,8 @@
 // and every warp store is coalesced.
 // Generic path (anything else): the CTA builds each distinct output row in shared memory and copies it out
 // with the widest aligned stores.
+#include <algorithm>
+
 #include "seg_write.cuh"
 
 namespace dppix {
@@ -304,6 +306,69 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// Batch: one item per (image, tile row), image i owning [base[3], base[3] + GR); the record and the output of
+// each image come from the batch table, and its header is parsed when a CTA moves to a new image.
+template <int kOutF32, int kFastC>
+__global__ void __launch_bounds__(kThreads)
+    k_batch_reconstruct(const BatchEntry *tab, uint32_t n_img, uint32_t items, int max_C, int out_align,
+                        int32_t *status) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ __align__(16) uint8_t rowpat[kRowBytes];
+    __shared__ __align__(16) dp_pix_record_header hdr_s;
+    __shared__ RecGeom rg;
+    __shared__ SegTiles st;
+    __shared__ uint32_t cnt_s[kMaxK];
+    constexpr int oes = kOutF32 ? 4 : 1;
+    uint8_t *stage = dyn;
+    uint32_t *colinfo = reinterpret_cast<uint32_t *>(dyn + kStageBytes);
+    int cur = -1;
+    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int i = batch_find(tab, n_img, item, 3);
+        const BatchEntry &e = tab[i];
+        const uint8_t *rec = e.a.records;
+        if (i != cur) {
+            __syncthreads();
+            if (threadIdx.x < kHeaderBytes / 16)
+                reinterpret_cast<uint4 *>(&hdr_s)[threadIdx.x] = reinterpret_cast<const uint4 *>(rec)[threadIdx.x];
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                rg.ok = read_header(&hdr_s, e.rec_cap, e.g.M, e.g.N, max_C, rg, oes, kFastC, out_align) ? 1 : 0;
+                if (!rg.ok) raise_status(status, DP_PIX_E_DEVICE, 0x300u | ((uint32_t)i & 0xFFu));
+            }
+            __syncthreads();
+            cur = i;
+        }
+        if (!rg.ok || e.out == nullptr) continue;
+        const int ty = (int)(item - e.base[3]);
+        if (ty >= rg.GR) continue;
+        for (int sg = 0; sg < rg.nseg; ++sg) {
+            if (kFastC > 0 && rg.fast)
+                fast_item<(kFastC > 0 ? kFastC : 1), kOutF32>(rec, rg, (uint32_t)i, ty, sg, e.out, e.out_pitch, stage,
+                                                               colinfo, st, cnt_s, status);
+            else
+                generic_item<kOutF32>(rec, rg, (uint32_t)i, ty, sg, e.out, e.out_pitch, out_align, rowpat, st, cnt_s,
+                                      status);
+        }
+    }
+}
+
+template <int kOutF32, int kFastC>
+cudaError_t launch_brc(const BatchEntry *tab, uint32_t n_img, uint32_t items, int max_C, int out_align,
+                       int32_t *status, cudaStream_t s) {
+    const size_t smem = kStageBytes + kMaxSegPx * 4;
+    auto kern = k_batch_reconstruct<kOutF32, kFastC>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int grid = (int)std::min<uint64_t>(items, (uint64_t)per_sm * sm_count());
+    const char *name = kOutF32 ? "k_batch_reconstruct_f32" : "k_batch_reconstruct_u8";
+    prof_begin(name, s);
+    kern<<<grid, kThreads, smem, s>>>(tab, n_img, items, max_C, out_align, status);
+    prof_end(name, s);
+    return cudaGetLastError();
+}
+
 __global__ void k_debug_noise(uint64_t seed, const uint32_t *ctr, uint64_t n, uint32_t *words, float *eta, float sigma) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
@@ -340,6 +405,29 @@ cudaError_t launch_rc(const uint8_t *records, int64_t record_stride, uint32_t n,
 }
 
 }  // namespace
+
+cudaError_t launch_batch_reconstruct(const BatchEntry *tab, uint32_t n_img, uint32_t items, int out_type, int max_C,
+                                     int out_align, int32_t *status, cudaStream_t s) {
+    const int fc = out_align == 16 ? max_C : 0;
+#define DPPIX_BRC(F, FC) return launch_brc<F, FC>(tab, n_img, items, max_C, out_align, status, s)
+    if (out_type == DP_PIX_OUT_F32) {
+        switch (fc) {
+            case 1: DPPIX_BRC(1, 1);
+            case 2: DPPIX_BRC(1, 2);
+            case 3: DPPIX_BRC(1, 3);
+            case 4: DPPIX_BRC(1, 4);
+            default: DPPIX_BRC(1, 0);
+        }
+    }
+    switch (fc) {
+        case 1: DPPIX_BRC(0, 1);
+        case 2: DPPIX_BRC(0, 2);
+        case 3: DPPIX_BRC(0, 3);
+        case 4: DPPIX_BRC(0, 4);
+        default: DPPIX_BRC(0, 0);
+    }
+#undef DPPIX_BRC
+}
 
 cudaError_t launch_reconstruct(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out,
                                int64_t out_frame_stride, int64_t out_pitch, int out_type, int max_M, int max_N,

@@ -110,20 +110,15 @@ struct SegInfo {
 // ------------------------------------------------------------------------------------------------------
 // k_release: staged segment -> exact cell sums of each tile's own grid -> noise -> clip -> record.
 // ------------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_release(const Geom g, const CallArgs a) {
-    extern __shared__ __align__(16) uint8_t dyn[];
-    __shared__ SegInfo si;
+// One work item: segment sg of tile row ty of frame f.  Shared memory: raw (T staged rows) | V (band sums).
+__device__ __forceinline__ void release_item(const Geom &g, const CallArgs &a, uint32_t f, int ty, int sg, uint8_t *dyn,
+                                             SegInfo &si) {
     const int T = g.T, C = g.C, TC = T * C, rs = g.seg_rowstride;
     uint8_t *raw = dyn;
     uint16_t *V = reinterpret_cast<uint16_t *>(dyn + (size_t)T * rs);
     const bool word_path = (TC & 3) == 0;
-    const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row;
-    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const uint32_t sg = item % g.seg_per_row;
-        const uint32_t fr = item / g.seg_per_row;
-        const int ty = (int)(fr % g.GR);
-        const uint32_t f = fr / g.GR;
-        const int tx0 = (int)sg * g.seg_tiles;
+    {
+        const int tx0 = sg * g.seg_tiles;
         const int ns = min(g.seg_tiles, g.GC - tx0);
         uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
         if (threadIdx.x < ns) {  // one thread per tile loads its region and payload offset
@@ -209,6 +204,35 @@ __global__ void __launch_bounds__(kThreads) k_release(const Geom g, const CallAr
             }
         }
         __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_release(const Geom g, const CallArgs a) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ SegInfo si;
+    const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row;
+    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const uint32_t sg = item % g.seg_per_row;
+        const uint32_t fr = item / g.seg_per_row;
+        release_item(g, a, fr / g.GR, (int)(fr % g.GR), (int)sg, dyn, si);
+    }
+}
+
+// Batch: items = (tile row, segment) of every image, image i owning [base[2], base[2] + GR * seg_per_row).
+__global__ void __launch_bounds__(kThreads) k_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ SegInfo si;
+    __shared__ BatchShared bs;
+    int cur = -1;
+    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int i = batch_find(tab, n_img, item, 2);
+        if (i != cur) {
+            batch_load(tab, i, bs);
+            cur = i;
+        }
+        const uint32_t local = item - tab[i].base[2];
+        const int spr = bs.g.seg_per_row;
+        release_item(bs.g, bs.a, 0u, (int)(local / spr), (int)(local % spr), dyn, si);
     }
 }
 
@@ -598,6 +622,15 @@ cudaError_t launch_release(const Geom &g, const CallArgs &a, cudaStream_t s) {
     prof_begin("k_release", s);
     k_release<<<grid, kThreads, smem, s>>>(g, a);
     prof_end("k_release", s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items, size_t smem, cudaStream_t s) {
+    cudaFuncSetAttribute(k_batch_release, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = grid_for(k_batch_release, smem, items);
+    prof_begin("k_batch_release", s);
+    k_batch_release<<<grid, kThreads, smem, s>>>(tab, n_img, items);
+    prof_end("k_batch_release", s);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,132 @@
+"""Ragged batches (dp_pix_batch_*): every image's record is byte-identical to what dp_pix_release writes for
+that image alone (same kernels, same keyed noise) and agrees with the oracle; reconstructions equal the
+oracle's; the CUDA-graph replay and every autotuned segment width give the same bytes."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2511_04261_b300 as P
+from paper_2511_04261_b300 import synth
+from tests.gpu_util import compare_records, gpu_release
+
+pytestmark = pytest.mark.gpu
+
+KW = dict(C=3, grids=[6, 20], eps=[0.5, 1.5], R=255.0, m=32.0, seed=3)
+
+
+def _portraits(sizes, seed):
+    rng = np.random.default_rng(seed)
+    imgs, mattes = [], []
+    for (M, N) in sizes:
+        img, alpha = synth.portrait(rng, M, N)
+        imgs.append(img)
+        mattes.append(alpha)
+    return imgs, mattes
+
+
+def _run_batch(sizes, imgs, srcs, source, dtype=O.DT_F32, outs=True, out_type=P.OUT_U8, use_graph=True,
+               autotune=False, pitch_extra=0):
+    bp = P.BatchPlan(sizes, source=source, dtype=dtype, **KW)
+    frames = []
+    for im in imgs:
+        if pitch_extra:
+            M, N, C = im.shape
+            buf = torch.zeros((M, N * C + pitch_extra), dtype=torch.uint8, device="cuda")
+            buf[:, : N * C] = torch.from_numpy(im.reshape(M, N * C)).cuda()
+            frames.append(buf[:, : N * C])
+        else:
+            frames.append(torch.from_numpy(np.ascontiguousarray(im)).cuda())
+    src_t = [torch.from_numpy(np.ascontiguousarray(s)).cuda() if s is not None else None for s in srcs]
+    recs = bp.alloc_records()
+    ws = bp.alloc_workspace()
+    dt = torch.uint8 if out_type == P.OUT_U8 else torch.float32
+    o = [torch.full((M, N, 3), 7, dtype=dt, device="cuda") for (M, N) in sizes] if outs else None
+    bp.bind(frames, src_t, recs, ws, outs=o, out_type=out_type, stream_ids=[5 + i for i in range(len(sizes))],
+            frame_idx=[100 + i for i in range(len(sizes))])
+    if autotune:
+        bp.autotune(reps=1)
+    bp.run(use_graph=use_graph)
+    if use_graph:
+        bp.run(use_graph=True)  # a replay gives the same bytes
+    torch.cuda.synchronize()
+    assert P.dp_pix_status() == 0
+    got = [P.dp_pix_store(r) for r in recs]
+    return bp, got, [t.cpu().numpy() for t in o] if outs else None
+
+
+def _check_against_single_and_oracle(sizes, imgs, srcs, source, got, outs, dtype=O.DT_F32, out_type=P.OUT_U8,
+                                     oracle_every=1):
+    for i, (M, N) in enumerate(sizes):
+        kw = dict(M=M, N=N, source=source, dtype=dtype, stream_id=5 + i, **KW)
+        _, _, single = gpu_release(imgs[i], srcs[i], frame_idx0=100 + i, **kw)
+        assert got[i] == single[0], i
+        if i % oracle_every == 0:
+            rec, means, sums, etas = O.release(imgs[i], srcs[i], frame_idx=100 + i, **kw)
+            compare_records(got[i], rec, means, sums, etas, dtype)
+        if outs is not None:
+            exp = O.reconstruct(np.frombuffer(got[i], np.uint8), 0 if out_type == P.OUT_U8 else 1)
+            assert np.array_equal(outs[i], exp), i
+
+
+@pytest.mark.parametrize("out_type", [P.OUT_U8, P.OUT_F32])
+def test_batch_matte_matches_single_release_and_oracle(out_type):
+    sizes = [(130, 250), (61, 61), (600, 413), (59, 700), (240, 120), (333, 333)]
+    imgs, mattes = _portraits(sizes, 11)
+    bp, got, outs = _run_batch(sizes, imgs, mattes, O.SRC_MATTE, out_type=out_type)
+    _check_against_single_and_oracle(sizes, imgs, mattes, O.SRC_MATTE, got, outs, out_type=out_type)
+
+
+@pytest.mark.parametrize("dtype", [O.DT_U8, O.DT_SUM])
+def test_batch_mask_and_labels(dtype):
+    sizes = [(200, 180), (64, 300), (121, 65)]
+    rng = np.random.default_rng(5)
+    imgs = [rng.integers(0, 256, size=(M, N, 3), dtype=np.uint8) for (M, N) in sizes]
+    masks = [(rng.random((M, N)) < 0.6).astype(np.uint8) for (M, N) in sizes]
+    _, got, outs = _run_batch(sizes, imgs, masks, O.SRC_MASK, dtype=dtype)
+    _check_against_single_and_oracle(sizes, imgs, masks, O.SRC_MASK, got, outs, dtype=dtype)
+    labels = [rng.integers(0, 2, size=(-(-M // 60), -(-N // 60)), dtype=np.uint8) for (M, N) in sizes]
+    _, got, outs = _run_batch(sizes, imgs, labels, O.SRC_TILE_LABELS, dtype=dtype, use_graph=False)
+    _check_against_single_and_oracle(sizes, imgs, labels, O.SRC_TILE_LABELS, got, outs, dtype=dtype)
+
+
+def test_batch_autotune_and_strided_frames_keep_the_bytes():
+    sizes = [(300, 500), (90, 800), (61, 120), (180, 180)]
+    imgs, mattes = _portraits(sizes, 12)
+    _, base, base_out = _run_batch(sizes, imgs, mattes, O.SRC_MATTE, use_graph=False)
+    bp, tuned, tuned_out = _run_batch(sizes, imgs, mattes, O.SRC_MATTE, autotune=True, pitch_extra=13)
+    assert 1 <= bp.seg_tiles() <= 16
+    assert tuned == base
+    for a, b in zip(tuned_out, base_out):
+        assert np.array_equal(a, b)
+
+
+def test_batch_without_outputs_and_rebinding():
+    sizes = [(120, 200), (64, 64)]
+    imgs, mattes = _portraits(sizes, 13)
+    _, got, _ = _run_batch(sizes, imgs, mattes, O.SRC_MATTE, outs=False)
+    _check_against_single_and_oracle(sizes, imgs, mattes, O.SRC_MATTE, got, None)
+
+
+def test_batch_rejects_bad_arguments():
+    with pytest.raises(P.DppixError):
+        P.BatchPlan([(100, 100)], source=P.SRC_VARIANCE, grids=[8, 16], eps=[1, 1])
+    bp = P.BatchPlan([(100, 100)], source=P.SRC_MATTE_F32, **KW)
+    fr = torch.zeros((100, 100, 3), dtype=torch.uint8, device="cuda")
+    matte = torch.zeros((100, 100), dtype=torch.float32, device="cuda")
+    recs = bp.alloc_records()
+    with pytest.raises(P.DppixError):  # workspace too small
+        bp.bind([fr], [matte], recs, torch.empty(16, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(P.DppixError):  # matte missing
+        bp.bind([fr], [None], recs, bp.alloc_workspace())
+
+
+def test_batch_config3_shapes_sampled():
+    """Images drawn from the ragged-batch size distribution (sides 512..4096), released and rebuilt in one
+    batch; every record equals its single-image release and a sample is checked against the oracle."""
+    sizes = synth.portrait_batch_shapes(seed=1003, n=256)[:12]
+    imgs, mattes = _portraits(sizes, 1003)
+    _, got, outs = _run_batch(sizes, imgs, mattes, O.SRC_MATTE)
+    _check_against_single_and_oracle(sizes, imgs, mattes, O.SRC_MATTE, got, outs, oracle_every=4)
