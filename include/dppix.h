@@ -238,7 +238,8 @@ DPPIX_API int dp_pix_batch_bind(dp_pix_batch_t b, const dp_pix_batch_image *imgs
                                 uint64_t ws_bytes, void *cuda_stream);
 
 /* Releases every bound image (and reconstructs those with an output), asynchronously on cuda_stream.
- * use_graph != 0: the first call on a stream captures the launches into a CUDA graph, later calls replay it.
+ * use_graph != 0: the first call captures the launches into a CUDA graph (on a private stream), and every
+ * call launches that graph on cuda_stream.
  * Device-side problems (a bad label) arrive through dp_pix_status().  Errors: INVALID_ARG (not bound), CUDA. */
 DPPIX_API int dp_pix_batch_run(dp_pix_batch_t b, int use_graph, void *cuda_stream);
 

@@ -34,9 +34,10 @@ struct dp_pix_batch_s {
     int out_type = DP_PIX_OUT_U8, out_align = 16, any_out = 0;
     uint32_t items_cls = 0, items_rel = 0, items_rec = 0, max_gc = 0, max_tiles = 0;
     size_t rel_smem = 0;
-    // graph
+    // graph (captured on a private stream -- capture is not possible on the legacy default stream -- and
+    // launched on the caller's)
     cudaGraphExec_t exec = nullptr;
-    cudaStream_t exec_stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
@@ -59,7 +60,6 @@ uint64_t a256(uint64_t x) { return (x + 255ull) & ~255ull; }
 void drop_graph(dp_pix_batch_s *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
-    b->exec_stream = nullptr;
 }
 
 // Release staging bytes for S tiles per segment (as the single-image plan computes them).
@@ -216,6 +216,7 @@ int dp_pix_batch_plan(const dp_pix_desc *common, const int32_t *M, const int32_t
 int dp_pix_batch_destroy(dp_pix_batch_t b) {
     if (!b) return DP_PIX_OK;
     drop_graph(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
     return DP_PIX_OK;
 }
@@ -256,13 +257,19 @@ int dp_pix_batch_run(dp_pix_batch_t b, int use_graph, void *cuda_stream) {
         const cudaError_t e = launch_all(b, s);
         return e == cudaSuccess ? DP_PIX_OK : cfail(e, "batch launch");
     }
-    if (!b->exec || b->exec_stream != s) {
-        drop_graph(b);
+    if (!b->exec) {
+        if (!b->cap_stream) {
+            const cudaError_t ce = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+            if (ce != cudaSuccess) {
+                b->cap_stream = nullptr;
+                return cfail(ce, "batch capture stream");
+            }
+        }
         cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cfail(e, "batch graph capture");
-        const cudaError_t le = launch_all(b, s);
-        e = cudaStreamEndCapture(s, &graph);
+        const cudaError_t le = launch_all(b, b->cap_stream);
+        e = cudaStreamEndCapture(b->cap_stream, &graph);
         if (le != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
             return cfail(le, "batch launch (capture)");
@@ -274,7 +281,6 @@ int dp_pix_batch_run(dp_pix_batch_t b, int use_graph, void *cuda_stream) {
             b->exec = nullptr;
             return cfail(e, "batch graph instantiate");
         }
-        b->exec_stream = s;
     }
     prof_begin("batch_graph", s);
     const cudaError_t e = cudaGraphLaunch(b->exec, s);
