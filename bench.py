@@ -579,6 +579,169 @@ def run_soft(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------------------
+# workload "batch": a ragged batch of 256 portraits (sides 512..4096), f32 alpha matte -> 2 regions
+# ------------------------------------------------------------------------------------------------------
+BATCH = dict(n=256, grids=[6, 20], eps=[0.5, 1.5], R=255.0, m=32.0, seed=3)
+BATCH_METRIC = ("megapixels/sec released + reconstructed, ragged batch of 256 portraits with alpha mattes (1 B300); "
+                "% HBM roofline")
+
+
+def run_batch(args):
+    import torch
+    import paper_2511_04261_b300 as P
+    from paper_2511_04261_b300 import build, synth
+    build.build()
+    world, rank, _ = dist_setup(args.gpus)
+    n = BATCH["n"]
+    sizes = synth.portrait_batch_shapes(seed=1003 + rank, n=n)
+    frames, mattes = [], []
+    for i, (M_, N_) in enumerate(sizes):
+        im, al = synth.portrait_device(1003000 + 1000 * rank + i, M_, N_)
+        frames.append(im)
+        mattes.append(al)
+    px = sum(M_ * N_ for M_, N_ in sizes)
+    kw = dict(C=3, grids=BATCH["grids"], eps=BATCH["eps"], R=BATCH["R"], m=BATCH["m"], seed=BATCH["seed"])
+    bp = P.BatchPlan(sizes, source=P.SRC_MATTE_F32, dtype=P.REC_F32, **kw)
+    recs = bp.alloc_records()
+    ws = bp.alloc_workspace()
+    outs = [torch.empty((M_, N_, 3), dtype=torch.uint8, device="cuda") for M_, N_ in sizes]
+    sids = [rank] * n
+    bp.bind(frames, mattes, recs, ws, outs=outs, stream_ids=sids, frame_idx=list(range(n)))
+    seg = bp.autotune(reps=2)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        bp.run(use_graph=True)
+    torch.cuda.synchronize()
+    P.dp_pix_status()
+    sampler = ClockSampler(torch.cuda.current_device())
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        bp.run(use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms_max = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    value = world * px / 1e6 / (ms_max / 1e3)
+    # per-kernel durations: the same launches without the graph (the library times each launch)
+    P.prof_reset()
+    P.prof_enable(True)
+    for _ in range(3):
+        bp.run(use_graph=False)
+    torch.cuda.synchronize()
+    prof = P.prof_read()
+    P.prof_enable(False)
+    P.dp_pix_status()
+    # algorithmic bytes per launch
+    hdrs = [P.record_header(bytes(r[:512].cpu().numpy())) for r in recs]
+    payload = sum(h["total_bytes"] - h["payload_offset"] for h in hdrs)
+    ntiles = sum(h["GR"] * h["GC"] for h in hdrs)
+    algo = {"k_batch_classify": 4 * px + ntiles, "k_batch_finalize": ntiles * 9 + n * 512,
+            "k_batch_release": 3 * px + payload + 5 * ntiles, "k_batch_reconstruct_u8": 3 * px + payload + ntiles}
+    hbm, peak_kind = measured_peaks()
+    dom_name, (dom_launches, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    per_launch_ms = dom_ms / max(1, dom_launches)
+    achieved = algo[dom_name] / (per_launch_ms / 1e3) / 1e9 if dom_name in algo else None
+    tot = sum(v[1] for v in prof.values())
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm if achieved else None, "traffic": None,
+                "algorithmic_bytes_per_launch": algo.get(dom_name), "avg_launch_ms": per_launch_ms,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else
+                "fallback 6.4 TB/s",
+                "kernels": {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / max(1e-9, tot),
+                                "algorithmic_GBps": algo[k] / (v[1] / max(1, v[0]) / 1e3) / 1e9 if k in algo else None}
+                            for k, v in prof.items()}}
+    # the plain per-frame path on the same images: one plan per size, dp_pix_release + dp_pix_reconstruct each
+    plans = [P.Plan(M=M_, N=N_, source=P.SRC_MATTE_F32, dtype=P.REC_F32, **kw) for M_, N_ in sizes]
+    pws = [p.alloc_workspace(1) for p in plans]
+    precs = [p.alloc_records(1) for p in plans]
+
+    def per_image():
+        for i, p in enumerate(plans):
+            p.release(frames[i], mattes[i], stream_id=rank, frame_idx0=i, records=precs[i], ws=pws[i])
+            P.dp_pix_reconstruct(precs[i], sizes[i][0], sizes[i][1], 3, P.OUT_U8, out=outs[i])
+
+    per_image()
+    torch.cuda.synchronize()
+    reps = 3
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(reps):
+        per_image()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    per_ms = a0.elapsed_time(a1) / reps
+    # end to end: pinned host images and mattes in, records out, every step
+    e2e = None
+    if not args.no_e2e:
+        hf = [f.cpu().pin_memory() for f in frames]
+        hm = [m_.cpu().pin_memory() for m_ in mattes]
+        hr = [torch.empty(r.numel(), dtype=torch.uint8).pin_memory() for r in recs]
+
+        def e2e_step():
+            for i in range(n):
+                frames[i].copy_(hf[i], non_blocking=True)
+                mattes[i].copy_(hm[i], non_blocking=True)
+            bp.run(use_graph=True)
+            for i in range(n):
+                hr[i].copy_(recs[i], non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        t0 = time.perf_counter()
+        n_e2e = 2
+        for _ in range(n_e2e):
+            e2e_step()
+        e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / n_e2e, world)
+        e2e = {"value": world * px / 1e6 / (e2e_ms / 1e3), "unit": "Mpx/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": 7 * px, "d2h_bytes_per_step": sum(r.numel() for r in recs),
+               "path": "pinned host images + mattes -> device; dp_pix_batch_run (graph); record buffers -> host"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        t0, done, dpx = time.perf_counter(), 0, 0
+        order = sorted(range(n), key=lambda i: sizes[i][0] * sizes[i][1])
+        for i in order:
+            img, mt = frames[i].cpu().numpy(), mattes[i].cpu().numpy()
+            rec, *_ = O.release(img, mt, M=sizes[i][0], N=sizes[i][1], source=O.SRC_MATTE, dtype=O.DT_F32,
+                                stream_id=rank, frame_idx=i, **kw)
+            O.reconstruct(rec, 0)
+            done += 1
+            dpx += sizes[i][0] * sizes[i][1]
+            if time.perf_counter() - t0 > args.cpu_budget:
+                break
+        dt = time.perf_counter() - t0
+        cpu = {"value": dpx / 1e6 / dt, "unit": "Mpx/s", "cores": 1, "kind": "oracle",
+               "sample": "%d smallest images of the batch, %.1f Mpx (oracle release + reconstruct, 1 thread, %.1f s)"
+                         % (done, dpx / 1e6, dt)}
+    if rank == 0:
+        line = {"metric": BATCH_METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+                "config": {"workload": "batch256_portraits_512to4096_matte_b6_b20", "images": n,
+                           "megapixels": px / 1e6, "grids": BATCH["grids"], "eps": BATCH["eps"], "m": BATCH["m"],
+                           "T": 60, "region_source": "f32 alpha matte >= 0.5", "record": "f32 means + u8 tile map",
+                           "step": "dp_pix_batch_run: classify + finalize + release + reconstruct, CUDA graph",
+                           "seg_tiles_autotuned": seg,
+                           "l2": "inputs larger than L2 (%.0f MB read per step)" % (7 * px / 1e6),
+                           "generator": "synth.portrait_device seeds 1003000+i (torch Philox on the GPU)",
+                           "parallelism": "1 GPU" if world == 1 else "replicas"},
+                "per_image_path": {"ms_per_step": per_ms, "value": world * px / 1e6 / (per_ms / 1e3), "unit": "Mpx/s",
+                                   "path": "256 x (dp_pix_release + dp_pix_reconstruct), one plan per image size"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": args.steps * sum(1 for k in prof if k.startswith("k_batch"))}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -593,9 +756,9 @@ def main():
     ap.add_argument("--fused-threads", type=int, default=None, help="DP_PIX_TUNE_FUSED_THREADS (default: the plan's)")
     ap.add_argument("--path", choices=["fused", "two-call"], default="fused",
                     help="fused: dp_pix_release_reconstruct; two-call: dp_pix_release then dp_pix_reconstruct")
-    ap.add_argument("--workload", choices=["clip", "soft"], default="clip",
+    ap.add_argument("--workload", choices=["clip", "soft", "batch"], default="clip",
                     help="clip: the 64-frame 1080p release + reconstruction (the benchmark); soft: the differentiable "
-                         "layer on a 32 x 3 x 1024 x 1024 batch")
+                         "layer on a 32 x 3 x 1024 x 1024 batch; batch: 256 ragged portraits with mattes")
     args = ap.parse_args()
     set_frames(args.frames)
     if args.warmup < 3:
@@ -604,6 +767,8 @@ def main():
         return run_reference(args)
     if args.workload == "soft":
         return run_soft(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

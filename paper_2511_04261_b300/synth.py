@@ -15,7 +15,7 @@ from scipy.special import ndtr
 
 __all__ = [
     "gradient_background", "rect_frame", "moving_rect_clip", "portrait", "portrait_batch_shapes",
-    "soft_batch", "camera_pool", "random_frame",
+    "soft_batch", "camera_pool", "random_frame", "portrait_device",
 ]
 
 
@@ -146,3 +146,37 @@ def random_frame(seed: int, M: int, N: int, C: int = 3, pitch: int | None = None
         return rng.integers(0, 256, size=(M, N, C), dtype=np.uint8)
     buf = rng.integers(0, 256, size=(M, pitch), dtype=np.uint8)
     return buf
+
+
+def portrait_device(seed: int, H: int, W: int, C: int = 3, device="cuda"):
+    """The portrait generator's distribution drawn on the GPU with torch (for the 256-image ragged batch,
+    whose 1.36 Gpx would take minutes in numpy): same background, subject, noise and matte recipe as
+    `portrait`, from torch's Philox generator seeded with `seed` (values differ from `portrait`'s).
+    Returns (image u8 [H, W, C], alpha f32 [H, W]) on `device`."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+
+    def u(lo, hi, n=1):
+        return lo + (hi - lo) * torch.rand(n, generator=gen, device=device, dtype=torch.float64)
+
+    a, g, h = u(30, 120, C), u(-60, 90, C), u(-60, 90, C)
+    xs = torch.arange(W, device=device, dtype=torch.float64) / max(W - 1, 1)
+    ys = torch.arange(H, device=device, dtype=torch.float64) / max(H - 1, 1)
+    bg = (a[None, None, :] + g[None, None, :] * xs[None, :, None] + h[None, None, :] * ys[:, None, None]).float()
+    cy = H / 2 * (1 + float(u(-0.1, 0.1)))
+    cx = W / 2 * (1 + float(u(-0.1, 0.1)))
+    ay = float(u(0.2, 0.35)) * H
+    ax = float(u(0.2, 0.35)) * W
+    s = 0.01 * min(H, W)
+    yy = (torch.arange(H, device=device, dtype=torch.float64) + 0.5 - cy)[:, None]
+    xx = (torch.arange(W, device=device, dtype=torch.float64) + 0.5 - cx)[None, :]
+    rho = torch.sqrt((yy / ay) ** 2 + (xx / ax) ** 2)
+    grad = torch.sqrt((yy / ay**2) ** 2 + (xx / ax**2) ** 2) / torch.clamp(rho, min=1e-12)
+    dist = (1.0 - rho) / torch.clamp(grad, min=1e-12)
+    alpha = torch.special.ndtr(dist / s).float()
+    subject = 128.0 + 40.0 * torch.randn((H, W, C), generator=gen, device=device, dtype=torch.float32)
+    noise = 6.0 * torch.randn((H, W, C), generator=gen, device=device, dtype=torch.float32)
+    a3 = alpha[:, :, None]
+    img = a3 * subject + (1.0 - a3) * (bg + noise)
+    return torch.clamp(torch.round(img), 0, 255).to(torch.uint8), alpha
