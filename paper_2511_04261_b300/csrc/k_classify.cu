@@ -24,6 +24,7 @@ __device__ __forceinline__ void classify_row(const Geom &g, const CallArgs &a, i
     for (int x = threadIdx.x; x < Wp; x += blockDim.x) {
         const int sx = reflect_idx(x, g.N, g.pad_mode);
         uint32_t c = 0;
+#pragma unroll 8
         for (int j = 0; j < T; ++j) {
             const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
             const uint8_t *row = src + (int64_t)sy * a.src_pitch;
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_classify(const BatchEntry *t
 cudaError_t launch_batch_classify(const BatchEntry *tab, uint32_t n_img, uint32_t items, int max_gc, int matte,
                                   cudaStream_t s) {
     const size_t smem = (size_t)max_gc * 4;
-    const int per_sm = 4;
+    const int per_sm = 8;
     const int grid = (int)std::min<uint64_t>(items, (uint64_t)per_sm * sm_count());
     if (matte) {
         prof_begin("k_batch_classify", s);

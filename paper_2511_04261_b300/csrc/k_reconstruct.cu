@@ -4,11 +4,11 @@
 // Work item = (record, tile row, segment of tiles).  Every pixel of a cell takes the cell's stored value
 // (u8 output rounds half to even); rows and columns past M, N (the padding) are cropped.
 //
-// Fast path (records with the launch's channel count, 16-byte aligned output rows): the segment -- a whole
-// tile row when it fits -- has its cell values converted once into shared memory; each thread owns
-// 16-byte columns of the output rows, assembles its vector from the cells it covers, and stores the same
-// vector to every row of the current cell band before rebuilding it, so the write phase has no barrier
-// and every warp store is coalesced.
+// Fast path (records with the launch's channel count): the segment -- a whole tile row when it fits -- has
+// its cell values converted once into shared memory; each thread owns 16-byte columns of the output rows and
+// assembles its vector from the cells it covers.  With 16-byte aligned rows the same vector is stored to
+// every row of the current cell band before it is rebuilt; rows of any other alignment get their aligned
+// middle in 16-byte chunks built per row and their head and tail one element at a time.
 // Generic path (anything else): the CTA builds each distinct output row in shared memory and copies it out
 // with the widest aligned stores.
 #include <algorithm>
@@ -77,7 +77,7 @@ __device__ bool read_header(const dp_pix_record_header *h, uint64_t cap, int max
         return false;
     rg.fast = 0;
     const int trb = rg.T * rg.C * oes;  // bytes of one tile row of output
-    if (rg.C == fast_C && out_align == 16 && trb >= 16) {
+    if (rg.C == fast_C && (out_align == 16 || oes == 1 || out_align >= 4) && trb >= 16) {
         // S tiles per segment, S a multiple of s0 so that segment starts stay 16-byte aligned, and as many
         // tiles as the staging buffers take (a whole tile row of a 1080p frame)
         const int s0 = 16 / gcd_i(trb, 16);
@@ -145,8 +145,8 @@ __device__ void seg_tile_info(const uint8_t *rec, const RecGeom &rg, int ty, int
 
 template <int C, int kOutF32>
 __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i, int ty, int sg, uint8_t *obase,
-                          int64_t out_pitch, uint8_t *stage, uint32_t *colinfo, SegTiles &st, uint32_t *cnt_s,
-                          int32_t *status) {
+                          int64_t out_pitch, int out_align, uint8_t *stage, uint32_t *colinfo, SegTiles &st,
+                          uint32_t *cnt_s, int32_t *status) {
     constexpr int oes = kOutF32 ? 4 : 1;
     const int T = rg.T;
     const int tx0 = sg * rg.SR;
@@ -180,9 +180,13 @@ __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i,
     __syncthreads();
     // write phase: no barrier until the next item
     const int x0 = tx0 * T;
-    seg_write_rows<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T),
-                               obase + (int64_t)(ty * T) * out_pitch + (int64_t)x0 * C * oes, out_pitch, threadIdx.x,
-                               blockDim.x);
+    uint8_t *orow0 = obase + (int64_t)(ty * T) * out_pitch + (int64_t)x0 * C * oes;
+    if (out_align == 16)
+        seg_write_rows<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T), orow0,
+                                   out_pitch, threadIdx.x, blockDim.x);
+    else
+        seg_write_rows_any<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T),
+                                       orow0, out_pitch, threadIdx.x, blockDim.x);
     __syncthreads();
 }
 
@@ -296,7 +300,7 @@ __global__ void __launch_bounds__(kThreads)
             for (uint64_t k = k0; k < k1; ++k) {
                 const int ty = (int)(k / rg.nseg), sg = (int)(k - (uint64_t)ty * rg.nseg);
                 if (kFastC > 0 && rg.fast)
-                    fast_item<(kFastC > 0 ? kFastC : 1), kOutF32>(rec, rg, i, ty, sg, obase, out_pitch, stage, colinfo,
+                    fast_item<(kFastC > 0 ? kFastC : 1), kOutF32>(rec, rg, i, ty, sg, obase, out_pitch, out_align, stage, colinfo,
                                                                    st, cnt_s, status);
                 else
                     generic_item<kOutF32>(rec, rg, i, ty, sg, obase, out_pitch, out_align, rowpat, st, cnt_s, status);
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(kThreads)
         if (ty >= rg.GR) continue;
         for (int sg = 0; sg < rg.nseg; ++sg) {
             if (kFastC > 0 && rg.fast)
-                fast_item<(kFastC > 0 ? kFastC : 1), kOutF32>(rec, rg, (uint32_t)i, ty, sg, e.out, e.out_pitch, stage,
+                fast_item<(kFastC > 0 ? kFastC : 1), kOutF32>(rec, rg, (uint32_t)i, ty, sg, e.out, e.out_pitch, out_align, stage,
                                                                colinfo, st, cnt_s, status);
             else
                 generic_item<kOutF32>(rec, rg, (uint32_t)i, ty, sg, e.out, e.out_pitch, out_align, rowpat, st, cnt_s,
@@ -408,7 +412,7 @@ cudaError_t launch_rc(const uint8_t *records, int64_t record_stride, uint32_t n,
 
 cudaError_t launch_batch_reconstruct(const BatchEntry *tab, uint32_t n_img, uint32_t items, int out_type, int max_C,
                                      int out_align, int32_t *status, cudaStream_t s) {
-    const int fc = out_align == 16 ? max_C : 0;
+    const int fc = max_C;  // the fast path serves any row alignment (16-byte rows reuse vectors per band)
 #define DPPIX_BRC(F, FC) return launch_brc<F, FC>(tab, n_img, items, max_C, out_align, status, s)
     if (out_type == DP_PIX_OUT_F32) {
         switch (fc) {
@@ -432,7 +436,7 @@ cudaError_t launch_batch_reconstruct(const BatchEntry *tab, uint32_t n_img, uint
 cudaError_t launch_reconstruct(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out,
                                int64_t out_frame_stride, int64_t out_pitch, int out_type, int max_M, int max_N,
                                int max_C, int out_align, int32_t *status, cudaStream_t s) {
-    const int fc = out_align == 16 ? max_C : 0;
+    const int fc = max_C;  // the fast path serves any row alignment (16-byte rows reuse vectors per band)
 #define DPPIX_RC(F, FC) \
     return launch_rc<F, FC>(records, record_stride, n, out, out_frame_stride, out_pitch, max_M, max_N, max_C, out_align, \
                             status, s)

@@ -25,10 +25,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Stage rows ty*T .. ty*T+T-1 (mirrored past M) and pixel columns [x0, x0 + ns*T) (mirrored past N) of
@@ -50,14 +46,40 @@ __device__ void stage_segment(const Geom &g, const CallArgs &a, uint32_t f, int 
             cp_async16(raw + j * rs + 16 * v, fbase + (int64_t)sy * g.pitch + 16 * v);
         }
         done = nv << 4;
-    } else if (a.vec == 4) {
-        const int nv = vb >> 2;
+    } else {
+        // rows not 16-byte aligned: each staged 16-byte chunk is cut out of the two aligned 16-byte granules
+        // that hold it (funnel shifts), so the loads stay 16 bytes wide.  Every granule read holds at least one
+        // byte of the row, so no load leaves the frame's allocation.
+        const int nv = vb >> 4;
         for (int idx = tid; idx < T * nv; idx += nt) {
             const int j = idx / nv, v = idx - j * nv;
             const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
-            cp_async4(raw + j * rs + 4 * v, fbase + (int64_t)sy * g.pitch + 4 * v);
+            const uint8_t *row = fbase + (int64_t)sy * g.pitch;
+            const uintptr_t addr = reinterpret_cast<uintptr_t>(row) + 16u * (uint32_t)v;
+            const int o = (int)(addr & 15u);
+            const uint4 *ga = reinterpret_cast<const uint4 *>(addr - (uintptr_t)o);
+            uint4 out;
+            if (o == 0) {
+                out = __ldg(ga);
+            } else {
+                const uint4 x = __ldg(ga), y = __ldg(ga + 1);
+                const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+                const int q = o >> 2, sh = 8 * (o & 3);
+                uint32_t r[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    // words q+k and q+k+1 of the 32-byte window, selected without dynamic register indexing
+                    uint32_t lo = w[k], hi = w[k + 1];
+                    if (q == 1) { lo = w[k + 1]; hi = w[k + 2]; }
+                    if (q == 2) { lo = w[k + 2]; hi = w[k + 3]; }
+                    if (q == 3) { lo = w[k + 3]; hi = w[k + 4]; }
+                    r[k] = __funnelshift_r(lo, hi, sh);
+                }
+                out = make_uint4(r[0], r[1], r[2], r[3]);
+            }
+            *reinterpret_cast<uint4 *>(raw + j * rs + 16 * v) = out;
         }
-        done = nv << 2;
+        done = nv << 4;
     }
     const int tail = vb - done;
     if (tail > 0) {
