@@ -111,6 +111,14 @@ typedef struct dp_pix_sizes {
 
 /* The 512-byte record header, little-endian, at the start of every record (Table IV generalised).
  * The tile-row index, map and payload follow at the offsets it gives. */
+/* Noise key of one frame: the Philox counter of its cells carries stream_id (< 2^24) and frame_idx (Eq. 9
+ * draws are keyed by (seed, frame, region, cell)).  Used where one call releases frames of several streams. */
+typedef struct dp_pix_frame_key {
+    uint64_t frame_idx;
+    uint32_t stream_id;
+    uint32_t reserved;            /* 0 */
+} dp_pix_frame_key;
+
 typedef struct dp_pix_record_header {
     char magic[4];                /* "DPPX" */
     uint32_t version;             /* 1 */
@@ -182,6 +190,18 @@ DPPIX_API int dp_pix_release(dp_pix_plan_t plan, const void *d_frames, int64_t f
                    void *cuda_stream);
 
 /*
+ * dp_pix_release with a noise key per frame instead of (stream_id, frame_idx0 + i): frame i of the call is
+ * released with d_keys[i] (device array of n_frames keys), so frames of different streams share one call.
+ * Records are byte-identical to releasing each frame alone with its key.  A key whose stream_id is >= 2^24
+ * is reported through dp_pix_status() (DP_PIX_E_DEVICE) and its frame's record is undefined.  Other
+ * arguments and errors: as dp_pix_release.
+ */
+DPPIX_API int dp_pix_release_keyed(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
+                                   const void *d_region_src, int64_t src_pitch, int64_t src_frame_stride,
+                                   uint32_t n_frames, const dp_pix_frame_key *d_keys, void *d_records,
+                                   int64_t record_stride, void *d_ws, uint64_t ws_bytes, void *cuda_stream);
+
+/*
  * dp_pix_release followed by dp_pix_reconstruct of the same frames, in one call (Alg. 3 with its
  * restoring steps; Sec. VI-F).  Writes the same records and the same images as the two calls would.
  * When the images' rows are 16-byte aligned and the release uses variance classes with a common grid
@@ -248,6 +268,66 @@ DPPIX_API int dp_pix_batch_run(dp_pix_batch_t b, int use_graph, void *cuda_strea
  * the graph.  Synchronizes cuda_stream.  dp_pix_batch_tuning reports the width in use. */
 DPPIX_API int dp_pix_batch_autotune(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int reps, void *cuda_stream);
 DPPIX_API int dp_pix_batch_tuning(dp_pix_batch_t b, int *seg_tiles);
+
+/* ---- serving loop (no counterpart in the paper; its deployment motivation is many cameras) --------------- */
+/* A request loop for frames arriving from many cameras.  Frames are copied from host memory into device
+ * slots carved out of one caller-owned arena (the memory budget: a request is admitted when a slot of its
+ * camera's resolution is free), released in batches -- all admitted frames of one resolution in one keyed
+ * launch -- and their records copied back to host memory; up to n_streams batches are in flight at once, so
+ * requests that arrive while others are on the GPU join the next batch and its copies and kernels overlap
+ * the running ones.  Frame f of camera c is released with stream_id c and frame_idx f (its arrival rank at
+ * that camera), so each record is byte-identical to dp_pix_release of that frame alone.  A worker thread
+ * owned by the server issues every CUDA call after creation.  Region source: VARIANCE (no per-frame side
+ * input); other sources are UNSUPPORTED here. */
+typedef struct dp_pix_server_s *dp_pix_server_t;
+
+typedef struct dp_pix_server_result {
+    uint64_t ticket;
+    uint64_t frame_idx;           /* arrival rank of the frame at its camera */
+    uint64_t record_bytes;        /* header.total_bytes of the record now in the request's host buffer */
+    uint32_t camera;
+    int32_t status;               /* DP_PIX_OK or a DP_PIX_E_* code of the batch that carried the frame */
+    double queue_us;              /* submit -> admitted into a batch */
+    double latency_us;            /* submit -> record in host memory */
+} dp_pix_server_result;
+
+typedef struct dp_pix_server_stats {
+    uint64_t submitted, completed, batches, launches;
+    uint64_t frames_in_flight_max;  /* most frames on the device at once */
+    double mean_batch_frames;
+} dp_pix_server_stats;
+
+/* Device bytes one frame slot of camera c needs (frame + record + workspace + key), for sizing the arena, and
+ * the host record capacity every request of camera c must provide.  Host only. */
+DPPIX_API int dp_pix_server_sizes(const dp_pix_desc *common, int32_t M, int32_t N, uint64_t *slot_bytes,
+                                  uint64_t *record_bytes);
+
+/* Creates a server for n_cameras cameras of M[c] x N[c] (common: the region parameters as for dp_pix_plan;
+ * M, N, row_pitch ignored).  d_arena: arena_bytes of device memory, 256-byte aligned, owned by the caller
+ * and untouched by anyone else until dp_pix_server_destroy returns; it is split among the resolutions in
+ * proportion to their cameras' frame bytes.  n_streams: batches in flight (1..8).  Errors: as dp_pix_plan,
+ * UNSUPPORTED (source), BUFFER_TOO_SMALL (no slot for some resolution), CUDA. */
+DPPIX_API int dp_pix_server_create(const dp_pix_desc *common, const int32_t *M, const int32_t *N, uint32_t n_cameras,
+                                   uint32_t n_streams, void *d_arena, uint64_t arena_bytes, dp_pix_server_t *out);
+
+/* Queues frame `host_frame` (M*N*C bytes, rows dense; pinned memory copies asynchronously) of `camera`; its
+ * record will be written to host_record (record_cap >= dp_pix_server_sizes' record_bytes).  Both buffers
+ * must stay valid until the request's result has been returned by dp_pix_server_wait.  *ticket identifies
+ * the request.  Thread-safe.  Errors: INVALID_ARG (camera, buffer), BUFFER_TOO_SMALL (record_cap). */
+DPPIX_API int dp_pix_server_submit(dp_pix_server_t s, uint32_t camera, const void *host_frame, void *host_record,
+                                   uint64_t record_cap, uint64_t *ticket);
+
+/* Waits up to timeout_ms (< 0: forever; 0: poll) for request `ticket` and fills *res once (the result is then
+ * forgotten).  Returns DP_PIX_OK, DP_PIX_E_TIMEOUT (not done yet), or INVALID_ARG (unknown ticket).
+ * Thread-safe. */
+DPPIX_API int dp_pix_server_wait(dp_pix_server_t s, uint64_t ticket, int timeout_ms, dp_pix_server_result *res);
+
+DPPIX_API int dp_pix_server_stats_get(dp_pix_server_t s, dp_pix_server_stats *st);
+DPPIX_API int dp_pix_server_slots(dp_pix_server_t s, uint32_t camera, uint32_t *slots);
+
+/* Finishes the queued requests, stops the worker and frees the server's host state (the arena is the
+ * caller's).  NULL is allowed. */
+DPPIX_API int dp_pix_server_destroy(dp_pix_server_t s);
 
 /* ---- differentiable soft layer (a training pattern on top of the release; not in the paper) ------------ */
 /* y = w * P~_{b0}(x) + (1 - w) * P~_{b1}(x) on planar f32 images, where P~_b is the uniform release of

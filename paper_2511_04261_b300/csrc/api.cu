@@ -352,7 +352,7 @@ struct FusedOut {
 int release_impl(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride, const void *d_region_src,
                  int64_t src_pitch, int64_t src_frame_stride, uint32_t n_frames, uint32_t stream_id, uint64_t frame_idx0,
                  void *d_records, int64_t record_stride, void *d_ws, uint64_t ws_bytes, void *cuda_stream,
-                 FusedOut *fo) {
+                 FusedOut *fo, const dp_pix_frame_key *keys = nullptr) {
     if (!plan) return fail(DP_PIX_E_INVALID_ARG, "plan is NULL");
     const Geom &g = plan->g;
     if (n_frames == 0) return DP_PIX_OK;
@@ -392,6 +392,7 @@ int release_impl(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
     a.record_stride = record_stride;
     a.ws = static_cast<uint8_t *>(d_ws);
     a.status = status_word();
+    a.keys = keys;
     const uintptr_t base = (uintptr_t)d_frames;
     const int64_t fs = n_frames > 1 ? frame_stride : 0;
     const int64_t seg_bytes = (int64_t)g.seg_tiles * g.T * g.C;
@@ -443,6 +444,15 @@ int dp_pix_release(dp_pix_plan_t plan, const void *d_frames, int64_t frame_strid
     t_err[0] = 0;
     return release_impl(plan, d_frames, frame_stride, d_region_src, src_pitch, src_frame_stride, n_frames, stream_id,
                         frame_idx0, d_records, record_stride, d_ws, ws_bytes, cuda_stream, nullptr);
+}
+
+int dp_pix_release_keyed(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride, const void *d_region_src,
+                         int64_t src_pitch, int64_t src_frame_stride, uint32_t n_frames, const dp_pix_frame_key *d_keys,
+                         void *d_records, int64_t record_stride, void *d_ws, uint64_t ws_bytes, void *cuda_stream) {
+    t_err[0] = 0;
+    if (n_frames > 0 && !d_keys) return fail(DP_PIX_E_INVALID_ARG, "keys are required");
+    return release_impl(plan, d_frames, frame_stride, d_region_src, src_pitch, src_frame_stride, n_frames, 0, 0,
+                        d_records, record_stride, d_ws, ws_bytes, cuda_stream, nullptr, d_keys);
 }
 
 int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,

@@ -68,7 +68,16 @@ struct CallArgs {
     uint8_t *ws;
     int32_t vec;                      // widest safe global load for frame rows: 16, 4 or 1 bytes
     int32_t *status;                  // device status word
+    const dp_pix_frame_key *keys;     // per-frame (stream id, frame index), or NULL: stream_id, frame_idx0 + f
 };
+
+// Noise key of frame f of a call: its stream id and frame index.
+__device__ __forceinline__ uint32_t key_stream(const CallArgs &a, uint32_t f) {
+    return a.keys ? a.keys[f].stream_id : a.stream_id;
+}
+__device__ __forceinline__ uint64_t key_frame(const CallArgs &a, uint32_t f) {
+    return a.keys ? a.keys[f].frame_idx : a.frame_idx0 + f;
+}
 
 // One image of a ragged batch: its own geometry and call arguments, as a single-image release would get
 // them, plus where its work items start in each phase's flattened work list.

@@ -104,9 +104,10 @@ __device__ void finalize_frame(const Geom &g, const CallArgs &a, uint32_t f, con
         h.header_bytes = kHeaderBytes;
         h.flags = g.noise_free ? 1u : 0u;
         h.M = g.M; h.N = g.N; h.C = g.C; h.T = g.T; h.K = g.K; h.GR = g.GR; h.GC = g.GC;
-        h.pad_mode = g.pad_mode; h.record_dtype = g.dtype; h.region_source = g.source; h.stream_id = a.stream_id;
+        if (key_stream(a, f) >= (1u << 24)) raise_status(a.status, DP_PIX_E_DEVICE, 0x400u | (f & 0xFFu));
+        h.pad_mode = g.pad_mode; h.record_dtype = g.dtype; h.region_source = g.source; h.stream_id = key_stream(a, f);
         h.seed = g.seed;
-        h.frame_idx = a.frame_idx0 + f;
+        h.frame_idx = key_frame(a, f);
         h.value_range = g.R; h.m = g.m;
         h.total_bytes = off;
         h.map_offset = g.map_offset;

@@ -191,7 +191,8 @@ __device__ __forceinline__ void release_item(const Geom &g, const CallArgs &a, u
 
         // horizontal pass, noise, clip, store
         const int totalB = si.startB[ns];
-        const uint64_t frame = a.frame_idx0 + f;
+        const uint64_t frame = key_frame(a, f);
+        const uint32_t sid = key_stream(a, f);
         for (int it = threadIdx.x; it < totalB; it += blockDim.x) {
             int t = 0;
             while (t + 1 < ns && it >= si.startB[t + 1]) ++t;
@@ -208,7 +209,7 @@ __device__ __forceinline__ void release_item(const Geom &g, const CallArgs &a, u
             const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)((tx0 + t) * cs + cx);
             uint4 words = make_uint4(0, 0, 0, 0);
             if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
-                words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, a.stream_id, frame);
+                words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame);
             uint8_t *dst = rec + si.tileoff[t] + (uint64_t)cell * C * g.es;
 #pragma unroll
             for (int ch = 0; ch < 4; ++ch) {
@@ -362,11 +363,11 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats(const Geom g, const Cal
 // Noise, clip and store of one (cell, channel) set (Alg. 3 steps 9-10 and 15-17).
 // ov (optional) receives the value a reconstruction reads back from the stored element (Sec. VI-F).
 __device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint8_t *dst, const uint32_t *S, int r,
-                                          uint32_t cell_idx, uint64_t frame, float *ov = nullptr) {
+                                          uint32_t cell_idx, uint64_t frame, uint32_t sid, float *ov = nullptr) {
     const int C = g.C;
     uint4 words = make_uint4(0, 0, 0, 0);
     if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
-        words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, a.stream_id, frame);
+        words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame);
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
         if (ch >= C) break;
@@ -448,7 +449,8 @@ __global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs 
     const uint16_t *gimg = reinterpret_cast<const uint16_t *>(wsf + g.ws_gsum);
     const int C = g.C, gcs = g.T / g.g;
     const size_t rowvals = (size_t)g.gpitch;
-    const uint64_t frame = a.frame_idx0 + f;
+    const uint64_t frame = key_frame(a, f);
+    const uint32_t sid = key_stream(a, f);
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         int r = 0;
         while (r + 1 < g.K && e >= cstart[r + 1]) ++r;
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs 
             default: gblock_sum<4>(p0, rowvals, nb, S); break;
         }
         const uint32_t cell_idx = (ty * cs + cy) * (uint32_t)(g.GC * cs) + tx * cs + cx;
-        emit_cell(g, a, rec + roff[r] + (uint64_t)local * C * g.es, S, r, cell_idx, frame);
+        emit_cell(g, a, rec + roff[r] + (uint64_t)local * C * g.es, S, r, cell_idx, frame, sid);
     }
 }
 
@@ -572,7 +574,8 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
         __syncthreads();
         // ---- B: cells, region by region ----
         const int ncell = rcell[g.K];
-        const uint64_t frame = a.frame_idx0 + f;
+        const uint64_t frame = key_frame(a, f);
+        const uint32_t sid = key_stream(a, f);
         const uint16_t *gs16 = reinterpret_cast<const uint16_t *>(gseg);
         for (int e = threadIdx.x; e < ncell; e += kThr) {
             int r = 0;
@@ -589,7 +592,7 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
             gblock_sum<C>(gs16 + (size_t)(cy * nb) * gsv + (size_t)(t * gcs + cx * nb) * C, (size_t)gsv, nb, S);
             const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)(tx * cs + cx);
             float ov[4] = {0.f, 0.f, 0.f, 0.f};
-            emit_cell(g, a, rec + st.off[t] + (uint64_t)c * C * g.es, S, r, cell_idx, frame, ov);
+            emit_cell(g, a, rec + st.off[t] + (uint64_t)c * C * g.es, S, r, cell_idx, frame, sid, ov);
             const int si = st.base[t] + c;  // the stage keeps segment order for the row writer
             if (kOutF32) {
                 reinterpret_cast<float4 *>(stage)[si] = make_float4(ov[0], ov[1], ov[2], ov[3]);
