@@ -315,6 +315,8 @@ def run_ours(args):
         plan.tune(P.TUNE_FUSED_PX, args.fused_px)
     if args.fused_threads:
         plan.tune(P.TUNE_FUSED_THREADS, args.fused_threads)
+    if args.split:
+        plan.tune(P.TUNE_SPLIT, args.split)
     frames = torch.from_numpy(clip).to(dev)
     records = plan.alloc_records(F, device=dev)
     ws = plan.alloc_workspace(F, device=dev)
@@ -353,7 +355,8 @@ def run_ours(args):
     P.prof_enable(False)
     P.dp_pix_status()
     ms = e0.elapsed_time(e1) / args.steps
-    args.tuning = {"fused_px": plan.tuning(P.TUNE_FUSED_PX), "fused_threads": plan.tuning(P.TUNE_FUSED_THREADS)}
+    args.tuning = {"fused_px": plan.tuning(P.TUNE_FUSED_PX), "fused_threads": plan.tuning(P.TUNE_FUSED_THREADS),
+                   "split": plan.tuning(P.TUNE_SPLIT)}
     ms_max = max_over_ranks(ms, world)
     value = whole_job_mpx_per_s(world, ms_max)
     launches = sum(v[0] for v in prof.values())
@@ -913,6 +916,7 @@ def main():
     ap.add_argument("--frames", type=int, default=64, help="frames per step (64 = the benchmark workload)")
     ap.add_argument("--fused-px", type=int, default=None, help="DP_PIX_TUNE_FUSED_PX (default: the plan's)")
     ap.add_argument("--fused-threads", type=int, default=None, help="DP_PIX_TUNE_FUSED_THREADS (default: the plan's)")
+    ap.add_argument("--split", type=int, default=None, help="DP_PIX_TUNE_SPLIT (default: the plan's)")
     ap.add_argument("--path", choices=["fused", "two-call"], default="fused",
                     help="fused: dp_pix_release_reconstruct; two-call: dp_pix_release then dp_pix_reconstruct")
     ap.add_argument("--workload", choices=["clip", "soft", "batch", "serve"], default="clip",

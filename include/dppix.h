@@ -156,10 +156,14 @@ DPPIX_API int dp_pix_plan_destroy(dp_pix_plan_t plan);
  *   DP_PIX_TUNE_FUSED_PX       pixel columns per work item of the fused release + reconstruction,
  *                              64..2048 (default 1024; rounded down to whole, aligned tiles)
  *   DP_PIX_TUNE_FUSED_THREADS  threads per block of that kernel, 128 or 256 (default 128)
+ *   DP_PIX_TUNE_SPLIT          dp_pix_release_reconstruct runs its frames in this many chunks on the
+ *                              library's side streams, forked from and joined to the caller's stream with
+ *                              events, 1..8 (default 1: everything on the caller's stream)
  * dp_pix_plan_tune returns INVALID_ARG for an unknown knob or a value out of range; dp_pix_plan_tuning
  * writes the current value to *value. */
 #define DP_PIX_TUNE_FUSED_PX 1
 #define DP_PIX_TUNE_FUSED_THREADS 2
+#define DP_PIX_TUNE_SPLIT 4
 DPPIX_API int dp_pix_plan_tune(dp_pix_plan_t plan, int knob, int value);
 DPPIX_API int dp_pix_plan_tuning(dp_pix_plan_t plan, int knob, int *value);
 

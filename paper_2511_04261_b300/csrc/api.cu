@@ -116,6 +116,21 @@ uint64_t plan_ws_per_frame(const dp_pix_plan_s *plan) { return plan ? plan->g.ws
 
 int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
+// Non-blocking side streams of the current device (created once, kept for the process).
+cudaStream_t *side_streams(int n) {
+    static std::mutex mu;
+    static cudaStream_t streams[64][8] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || n < 1 || n > 8) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    for (int i = 0; i < n; ++i)
+        if (!streams[dev][i] && cudaStreamCreateWithFlags(&streams[dev][i], cudaStreamNonBlocking) != cudaSuccess) {
+            streams[dev][i] = nullptr;
+            return nullptr;
+        }
+    return streams[dev];
+}
+
 int32_t *status_word() {
     static int32_t *cached[64] = {nullptr};
     int dev = 0;
@@ -233,6 +248,7 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     g.ws_per_frame = off;
     g.fused_px = 1024;
     g.fused_threads = 128;
+    g.split = 1;
     // staged segment: S tiles of one tile row, S*T*C a multiple of 16 when possible
     int s0 = 16 / (int)gcd64(TC, 16);
     int S = s0 * (int)((384 + (int64_t)s0 * TC - 1) / ((int64_t)s0 * TC));
@@ -322,6 +338,10 @@ int dp_pix_plan_tune(dp_pix_plan_t plan, int knob, int value) {
             if (value != 128 && value != 256) return fail(DP_PIX_E_INVALID_ARG, "fused threads must be 128 or 256");
             plan->g.fused_threads = value;
             return DP_PIX_OK;
+        case DP_PIX_TUNE_SPLIT:
+            if (value < 1 || value > 8) return fail(DP_PIX_E_INVALID_ARG, "split must be 1..8");
+            plan->g.split = value;
+            return DP_PIX_OK;
         default:
             return fail(DP_PIX_E_INVALID_ARG, "unknown knob %d", knob);
     }
@@ -333,6 +353,7 @@ int dp_pix_plan_tuning(dp_pix_plan_t plan, int knob, int *value) {
     switch (knob) {
         case DP_PIX_TUNE_FUSED_PX: *value = plan->g.fused_px; return DP_PIX_OK;
         case DP_PIX_TUNE_FUSED_THREADS: *value = plan->g.fused_threads; return DP_PIX_OK;
+        case DP_PIX_TUNE_SPLIT: *value = plan->g.split; return DP_PIX_OK;
         default: return fail(DP_PIX_E_INVALID_ARG, "unknown knob %d", knob);
     }
 }
@@ -476,12 +497,50 @@ int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frames, int64_t
     while (align > 1 &&
            ((uintptr_t)d_out % align || out_pitch % align || (n_frames > 1 && out_frame_stride % align)))
         align >>= 1;
-    FusedOut fo{static_cast<uint8_t *>(d_out), n_frames > 1 ? out_frame_stride : 0, out_pitch, out_type, align, false};
-    int rc = release_impl(plan, d_frames, frame_stride, d_region_src, src_pitch, src_frame_stride, n_frames, stream_id,
-                          frame_idx0, d_records, record_stride, d_ws, ws_bytes, cuda_stream, &fo);
-    if (rc || fo.fused) return rc;
-    return dp_pix_reconstruct(d_records, record_stride, n_frames, d_out, out_frame_stride, out_pitch, out_type, g.M,
-                              g.N, g.C, cuda_stream);
+    auto run = [&](uint32_t f0, uint32_t nf, cudaStream_t st) -> int {
+        const uint8_t *fr = static_cast<const uint8_t *>(d_frames) + (uint64_t)f0 * (uint64_t)frame_stride;
+        const uint8_t *src = d_region_src ? static_cast<const uint8_t *>(d_region_src) + (uint64_t)f0 * src_frame_stride
+                                          : nullptr;
+        uint8_t *rec = static_cast<uint8_t *>(d_records) + (uint64_t)f0 * (uint64_t)record_stride;
+        uint8_t *ws = static_cast<uint8_t *>(d_ws) + (uint64_t)f0 * g.ws_per_frame;
+        uint8_t *out = static_cast<uint8_t *>(d_out) + (uint64_t)f0 * (uint64_t)out_frame_stride;
+        const uint64_t wsb = ws_bytes >= (uint64_t)f0 * g.ws_per_frame ? ws_bytes - (uint64_t)f0 * g.ws_per_frame : 0;
+        FusedOut fo{out, nf > 1 ? out_frame_stride : 0, out_pitch, out_type, align, false};
+        int rc = release_impl(plan, fr, frame_stride, src, src_pitch, src_frame_stride, nf, stream_id, frame_idx0 + f0,
+                              rec, record_stride, ws, wsb, st, &fo);
+        if (rc || fo.fused) return rc;
+        return dp_pix_reconstruct(rec, record_stride, nf, out, out_frame_stride, out_pitch, out_type, g.M, g.N, g.C, st);
+    };
+    cudaStream_t caller = static_cast<cudaStream_t>(cuda_stream);
+    const int split = g.split;
+    if (split <= 1 || n_frames < 2u * (uint32_t)split) return run(0, n_frames, caller);
+    // frames in `split` chunks on the library's side streams, so that one chunk's latency-bound steps (the
+    // frame-wide rank) overlap another chunk's bandwidth-bound ones; forked from and joined to the caller's
+    // stream with events
+    cudaStream_t *side = side_streams(split);
+    if (!side) return fail(DP_PIX_E_CUDA, "side streams unavailable");
+    cudaEvent_t fork = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, caller);
+    if (e != cudaSuccess) return cuda_fail(e, "split fork");
+    int rc = DP_PIX_OK;
+    for (int i = 0; i < split && rc == DP_PIX_OK; ++i) {
+        const uint32_t f0 = (uint32_t)((uint64_t)n_frames * i / split), f1 = (uint32_t)((uint64_t)n_frames * (i + 1) / split);
+        e = cudaStreamWaitEvent(side[i], fork, 0);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "split wait");
+            break;
+        }
+        rc = run(f0, f1 - f0, side[i]);
+        cudaEvent_t join = nullptr;
+        e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(join, side[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, join, 0);
+        if (join) cudaEventDestroy(join);
+        if (e != cudaSuccess && rc == DP_PIX_OK) rc = cuda_fail(e, "split join");
+    }
+    cudaEventDestroy(fork);
+    return rc;
 }
 
 int dp_pix_store(const void *d_record, void *dst, uint64_t cap, uint64_t *written, int dst_is_host,

@@ -52,6 +52,7 @@ struct Geom {
     int32_t seg_rowstride;            // bytes per staged row (multiple of 16)
     int32_t vbands;                   // max bands of a staged tile = T / b_min (or T / g for stats)
     int32_t fused_px, fused_threads;  // launch shape of the fused release + reconstruction (tunable)
+    int32_t split;                    // frame chunks of a fused call run on side streams (tunable)
 };
 
 // Per-call arguments of a release.
@@ -221,6 +222,7 @@ void prof_begin(const char *name, cudaStream_t s);
 void prof_end(const char *name, cudaStream_t s);
 int sm_count();
 int32_t *status_word();  // device address of the status word on the current device (nullptr on failure)
+cudaStream_t *side_streams(int n);  // n (<= 8) non-blocking streams of the current device, or nullptr
 }  // namespace dppix
 struct dp_pix_plan_s;
 namespace dppix {

@@ -117,7 +117,11 @@ def test_plan_tuning_knobs():
     assert plan.tuning(P.TUNE_FUSED_PX) == 1024 and plan.tuning(P.TUNE_FUSED_THREADS) == 128
     plan.tune(P.TUNE_FUSED_PX, 512).tune(P.TUNE_FUSED_THREADS, 256)
     assert plan.tuning(P.TUNE_FUSED_PX) == 512 and plan.tuning(P.TUNE_FUSED_THREADS) == 256
-    for knob, bad in [(P.TUNE_FUSED_PX, 63), (P.TUNE_FUSED_PX, 4096), (P.TUNE_FUSED_THREADS, 192), (99, 1)]:
+    assert plan.tuning(P.TUNE_SPLIT) == 1
+    plan.tune(P.TUNE_SPLIT, 4)
+    assert plan.tuning(P.TUNE_SPLIT) == 4
+    for knob, bad in [(P.TUNE_FUSED_PX, 63), (P.TUNE_FUSED_PX, 4096), (P.TUNE_FUSED_THREADS, 192),
+                      (P.TUNE_SPLIT, 0), (P.TUNE_SPLIT, 9), (99, 1)]:
         with pytest.raises(P.DppixError) as e:
             plan.tune(knob, bad)
         assert e.value.code == _lib.E_INVALID_ARG

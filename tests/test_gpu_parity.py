@@ -404,8 +404,9 @@ def test_release_reconstruct_config2_sampled():
 
 @pytest.mark.parametrize("ot", [P.OUT_U8, P.OUT_F32])
 def test_release_reconstruct_launch_shapes_do_not_change_results(ot):
-    """Every fused launch shape (pixel columns per item, threads per block) gives the same bytes."""
-    F, M, N = 3, 200, 352
+    """Every fused launch shape (pixel columns per item, threads per block, frame chunks on side streams)
+    gives the same bytes."""
+    F, M, N = 8, 200, 352
     rng = np.random.default_rng(17)
     imgs = rng.integers(0, 256, size=(F, M, N, 3), dtype=np.uint8)
     imgs[:, :, : N // 2] //= 16
@@ -413,9 +414,10 @@ def test_release_reconstruct_launch_shapes_do_not_change_results(ot):
               seed=23, m=16)
     t = torch.from_numpy(imgs).cuda()
     base = None
-    for px in (64, 96, 512, 2048):
-        for thr in (128, 256):
-            plan = P.Plan(**kw).tune(P.TUNE_FUSED_PX, px).tune(P.TUNE_FUSED_THREADS, thr)
+    for px, thr, split in [(64, 128, 1), (96, 256, 2), (512, 128, 4), (512, 256, 1), (1024, 128, 3),
+                           (2048, 256, 4), (2048, 128, 1)]:
+        if True:
+            plan = P.Plan(**kw).tune(P.TUNE_FUSED_PX, px).tune(P.TUNE_FUSED_THREADS, thr).tune(P.TUNE_SPLIT, split)
             recs, img = plan.release_reconstruct(t, out_type=ot)
             torch.cuda.synchronize()
             assert P.dp_pix_status() == 0
@@ -426,5 +428,5 @@ def test_release_reconstruct_launch_shapes_do_not_change_results(ot):
                     exp = O.reconstruct(np.frombuffer(got[0][i], np.uint8), 0 if ot == P.OUT_U8 else 1)
                     assert np.array_equal(got[1][i], exp)
             else:
-                assert got[0] == base[0], (px, thr)
-                assert np.array_equal(got[1], base[1]), (px, thr)
+                assert got[0] == base[0], (px, thr, split)
+                assert np.array_equal(got[1], base[1]), (px, thr, split)
