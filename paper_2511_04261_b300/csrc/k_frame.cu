@@ -224,43 +224,23 @@ __global__ void __launch_bounds__(kFrameThreads) k_rank(const Geom g, const Call
     const int Q = g.K - 1;
     const uint64_t *keys = reinterpret_cast<const uint64_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_keys);
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) vals[i] = (keys[i] << g.idx_bits) | (uint64_t)i;
-    __shared__ unsigned long long diff_s;
-    if (threadIdx.x == 0) diff_s = 0ull;
-    __syncthreads();
-    // bits above the highest one in which the values differ are common to all of them: no pass looks at them
-    {
-        const uint64_t v0 = vals[0];
-        unsigned long long d = 0ull;
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) d |= vals[i] ^ v0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) d |= __shfl_xor_sync(0xffffffffu, d, off);
-        if ((threadIdx.x & 31) == 0 && d) atomicOr(&diff_s, d);
-    }
-    __syncthreads();
-    const int sig = diff_s ? 64 - __clzll((long long)diff_s) : 1;  // significant low bits
-    const int passes = Q > 0 ? (sig + 7) / 8 : 0;
     if ((int)threadIdx.x < Q) {
-        prefix[threadIdx.x] = 8 * passes >= 64 ? 0ull : vals[0] >> (8 * passes);
+        prefix[threadIdx.x] = 0ull;
         target[threadIdx.x] = (uint32_t)(((uint64_t)(threadIdx.x + 1) * n + g.K - 1) / g.K);  // 0-based rank
     }
     __syncthreads();
+    const int passes = Q > 0 ? (g.val_bits + 7) / 8 : 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t n_up = (n + blockDim.x - 1) / blockDim.x * blockDim.x;  // whole warps for the matching below
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * (passes - 1 - pass);
         for (int i = threadIdx.x; i < Q * 256; i += blockDim.x) hist[i >> 8][i & 255] = 0u;
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < n_up; i += blockDim.x) {
-            const bool valid = i < n;
-            const uint64_t v = valid ? vals[i] : 0ull;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint64_t v = vals[i];
             const uint64_t hi = shift + 8 >= 64 ? 0ull : v >> (shift + 8);
             const uint32_t d = (uint32_t)(v >> shift) & 255u;
-            for (int q = 0; q < Q; ++q) {
-                // lanes with the same digit add their count once (the leading digits are shared by most values)
-                const bool want = valid && hi == prefix[q];
-                const unsigned peers = __match_any_sync(0xffffffffu, want ? d : 0xFFFFFFFFu);
-                if (want && lane == __ffs(peers) - 1) atomicAdd(&hist[q][d], (uint32_t)__popc(peers));
-            }
+            for (int q = 0; q < Q; ++q)
+                if (hi == prefix[q]) atomicAdd(&hist[q][d], 1u);
         }
         __syncthreads();
         if (warp < Q) {  // warp q finds the digit bucket that holds its target rank
