@@ -134,22 +134,6 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
-// Two independent Philox4x32-10 blocks under one key, round by round, so that the two dependency chains
-// interleave (each result equals philox4x32_10 of its counter).
-__device__ __forceinline__ void philox4x32_10_x2(uint4 &c, uint4 &d, uint2 k) {
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        const uint32_t mo0 = 0xD2511F53u * d.x, ni0 = __umulhi(0xD2511F53u, d.x);
-        const uint32_t mo1 = 0xCD9E8D57u * d.z, ni1 = __umulhi(0xCD9E8D57u, d.z);
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-        d = make_uint4(ni1 ^ d.y ^ k.x, mo1, ni0 ^ d.w ^ k.y, mo0);
-        k.x += 0x9E3779B9u;
-        k.y += 0xBB67AE85u;
-    }
-}
-
 __device__ __forceinline__ uint32_t word_of(const uint4 &w, int i) {
     return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w));
 }

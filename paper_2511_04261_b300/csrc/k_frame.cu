@@ -82,9 +82,6 @@ __device__ void finalize_frame(const Geom &g, const CallArgs &a, uint32_t f, con
 #pragma unroll
         for (int q = 0; q < kMaxK; ++q) cnt[q] += (r == (uint32_t)q);
     }
-    // the header is zeroed by the block (the scan's barriers order it before thread 0 fills it in)
-    for (int i = threadIdx.x; i < (int)(sizeof(dp_pix_record_header) / 4); i += blockDim.x)
-        reinterpret_cast<uint32_t *>(&sm.hdr)[i] = 0u;
     block_excl_scan_k(cnt, excl, total, sm.warp_tot);
 
     uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
@@ -101,6 +98,7 @@ __device__ void finalize_frame(const Geom &g, const CallArgs &a, uint32_t f, con
             off = align16_u64(off + (uint64_t)total[r] * sm.tile_bytes[r]);
         }
         dp_pix_record_header &h = sm.hdr;
+        memset(&h, 0, sizeof(h));
         h.magic[0] = 'D'; h.magic[1] = 'P'; h.magic[2] = 'P'; h.magic[3] = 'X';
         h.version = 1;
         h.header_bytes = kHeaderBytes;
@@ -214,58 +212,44 @@ __global__ void __launch_bounds__(kFrameThreads) k_batch_finalize(const BatchEnt
 // K - 1 class boundaries matter: the tile of rank ceil(q n / K) starts class q.  Each boundary value is
 // found exactly by a radix select over the unique packed values key << idx_bits | index (8-bit digits from
 // the top); a tile's class is then the number of boundaries not above its value.
-__global__ void __launch_bounds__(kFrameThreads) k_rank(const Geom g, const CallArgs a, int rb) {
+__global__ void __launch_bounds__(kFrameThreads) k_rank(const Geom g, const CallArgs a) {
     extern __shared__ __align__(16) uint8_t dyn[];
     FinalizeSmem &sm = *reinterpret_cast<FinalizeSmem *>(dyn);
     const uint32_t f = blockIdx.x, n = g.ntiles;
     uint64_t *vals = reinterpret_cast<uint64_t *>(dyn + sizeof(FinalizeSmem));
     uint8_t *map_s = reinterpret_cast<uint8_t *>(vals + n);
-    const int nb = 1 << rb;  // digit buckets
-    uint32_t *hist = reinterpret_cast<uint32_t *>(map_s + ((n + 15) & ~15u));  // [Q][nb]
+    __shared__ uint32_t hist[kMaxK - 1][256];
     __shared__ uint64_t prefix[kMaxK - 1];
     __shared__ uint32_t target[kMaxK - 1];
-    __shared__ unsigned long long diff_s;
     const int Q = g.K - 1;
     const uint64_t *keys = reinterpret_cast<const uint64_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_keys);
-    const uint64_t k0 = (keys[0] << g.idx_bits);
-    unsigned long long d = 0ull;
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint64_t v = (keys[i] << g.idx_bits) | (uint64_t)i;
-        vals[i] = v;
-        d |= v ^ k0;
-    }
-    // bits above the highest one in which the values differ are shared by all of them: no pass reads them
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) d |= __shfl_xor_sync(0xffffffffu, d, off);
-    if (threadIdx.x == 0) diff_s = 0ull;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0 && d) atomicOr(&diff_s, d);
-    __syncthreads();
-    const int sig = diff_s ? 64 - __clzll((long long)diff_s) : 1;
-    const int passes = Q > 0 ? (sig + rb - 1) / rb : 0;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) vals[i] = (keys[i] << g.idx_bits) | (uint64_t)i;
     if ((int)threadIdx.x < Q) {
-        prefix[threadIdx.x] = rb * passes >= 64 ? 0ull : k0 >> (rb * passes);
+        prefix[threadIdx.x] = 0ull;
         target[threadIdx.x] = (uint32_t)(((uint64_t)(threadIdx.x + 1) * n + g.K - 1) / g.K);  // 0-based rank
     }
     __syncthreads();
+    const int passes = Q > 0 ? (g.val_bits + 7) / 8 : 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int per_lane = nb >> 5;
     for (int pass = 0; pass < passes; ++pass) {
-        const int shift = rb * (passes - 1 - pass);
-        for (int i = threadIdx.x; i < Q * nb; i += blockDim.x) hist[i] = 0u;
+        const int shift = 8 * (passes - 1 - pass);
+        for (int i = threadIdx.x; i < Q * 256; i += blockDim.x) hist[i >> 8][i & 255] = 0u;
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
             const uint64_t v = vals[i];
-            const uint64_t hi = shift + rb >= 64 ? 0ull : v >> (shift + rb);
-            const uint32_t dg = (uint32_t)(v >> shift) & (uint32_t)(nb - 1);
+            const uint64_t hi = shift + 8 >= 64 ? 0ull : v >> (shift + 8);
+            const uint32_t d = (uint32_t)(v >> shift) & 255u;
             for (int q = 0; q < Q; ++q)
-                if (hi == prefix[q]) atomicAdd(&hist[q * nb + dg], 1u);
+                if (hi == prefix[q]) atomicAdd(&hist[q][d], 1u);
         }
         __syncthreads();
         if (warp < Q) {  // warp q finds the digit bucket that holds its target rank
-            const uint32_t *h = hist + warp * nb + lane * per_lane;
-            uint32_t sum = 0;
-            for (int j = 0; j < per_lane; ++j) sum += h[j];
+            uint32_t c[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                c[j] = hist[warp][8 * lane + j];
+                sum += c[j];
+            }
             uint32_t incl = sum;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
@@ -276,8 +260,8 @@ __global__ void __launch_bounds__(kFrameThreads) k_rank(const Geom g, const Call
             if (excl <= t && t < incl) {
                 uint32_t acc = excl;
                 int j = 0;
-                while (j < per_lane - 1 && acc + h[j] <= t) acc += h[j++];
-                prefix[warp] = (prefix[warp] << rb) | (uint64_t)(lane * per_lane + j);
+                while (j < 7 && acc + c[j] <= t) acc += c[j++];
+                prefix[warp] = (prefix[warp] << 8) | (uint64_t)(8 * lane + j);
                 target[warp] = t - acc;
             }
         }
@@ -333,15 +317,10 @@ cudaError_t launch_batch_finalize(const BatchEntry *tab, uint32_t n_img, uint32_
 }
 
 cudaError_t launch_rank(const Geom &g, const CallArgs &a, cudaStream_t s) {
-    // 8-bit digits: wider digits cut passes but their histogram zeroing and scans cost more (measured:
-    // 11-bit digits took 45.6 us per 64-frame launch against 20.6 us)
-    const size_t base = sizeof(FinalizeSmem) + (size_t)g.ntiles * 8 + (((size_t)g.ntiles + 15) & ~(size_t)15);
-    const size_t q = (size_t)(g.K > 1 ? g.K - 1 : 1);
-    const int rb = 8;
-    const size_t smem = base + q * 4 * ((size_t)1 << rb);
+    const size_t smem = sizeof(FinalizeSmem) + (size_t)g.ntiles * 8 + g.ntiles;
     cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prof_begin("k_rank", s);
-    k_rank<<<a.n_frames, kFrameThreads, smem, s>>>(g, a, rb);
+    k_rank<<<a.n_frames, kFrameThreads, smem, s>>>(g, a);
     prof_end("k_rank", s);
     return cudaGetLastError();
 }

@@ -360,12 +360,14 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats(const Geom g, const Cal
     }
 }
 
-// Noise, clip and store of one cell's channels from its Philox words (Alg. 3 steps 9-10 and 15-17; the
-// words are ignored for sums and noise-free plans).  ov (optional) receives the value a reconstruction reads
-// back from the stored element (Sec. VI-F).
-__device__ __forceinline__ void emit_words(const Geom &g, uint8_t *dst, const uint32_t *S, int r, const uint4 &words,
-                                           float *ov) {
+// Noise, clip and store of one (cell, channel) set (Alg. 3 steps 9-10 and 15-17).
+// ov (optional) receives the value a reconstruction reads back from the stored element (Sec. VI-F).
+__device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint8_t *dst, const uint32_t *S, int r,
+                                          uint32_t cell_idx, uint64_t frame, uint32_t sid, float *ov = nullptr) {
     const int C = g.C;
+    uint4 words = make_uint4(0, 0, 0, 0);
+    if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
+        words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame);
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
         if (ch >= C) break;
@@ -385,15 +387,6 @@ __device__ __forceinline__ void emit_words(const Geom &g, uint8_t *dst, const ui
             }
         }
     }
-}
-
-// emit_words with the cell's own draw: counter (cell index, region | stream << 8, frame).
-__device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint8_t *dst, const uint32_t *S, int r,
-                                          uint32_t cell_idx, uint64_t frame, uint32_t sid, float *ov = nullptr) {
-    uint4 words = make_uint4(0, 0, 0, 0);
-    if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
-        words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame);
-    emit_words(g, dst, S, r, words, ov);
 }
 
 // Sum of an nb x nb block of g-cells (C u16 channel sums each; rows rowvals values apart) into S[0..C).
@@ -584,13 +577,7 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
         const uint64_t frame = key_frame(a, f);
         const uint32_t sid = key_stream(a, f);
         const uint16_t *gs16 = reinterpret_cast<const uint16_t *>(gseg);
-        // two cells per thread and step: their Philox chains run interleaved (philox4x32_10_x2)
-        struct Cell {
-            int r, t, c;
-            uint32_t idx;
-            uint32_t S[4];
-        };
-        auto prep = [&](int e, Cell &q) {
+        for (int e = threadIdx.x; e < ncell; e += kThr) {
             int r = 0;
             while (r + 1 < g.K && e >= rcell[r + 1]) ++r;
             const int cs = rcs[r], local = e - rcell[r];
@@ -601,17 +588,12 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
             const int t = rlist[rtile[r] + k];
             const int cy = p2 ? c >> lcs : c / cs, cx = c - cy * cs;
             const int tx = tx0 + t, nb = st.b[t] / g.g;
-            q.S[0] = q.S[1] = q.S[2] = q.S[3] = 0u;
-            gblock_sum<C>(gs16 + (size_t)(cy * nb) * gsv + (size_t)(t * gcs + cx * nb) * C, (size_t)gsv, nb, q.S);
-            q.r = r;
-            q.t = t;
-            q.c = c;
-            q.idx = (uint32_t)(ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)(tx * cs + cx);
-        };
-        auto finish = [&](const Cell &q, const uint4 &words) {
+            uint32_t S[4] = {0u, 0u, 0u, 0u};
+            gblock_sum<C>(gs16 + (size_t)(cy * nb) * gsv + (size_t)(t * gcs + cx * nb) * C, (size_t)gsv, nb, S);
+            const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)(tx * cs + cx);
             float ov[4] = {0.f, 0.f, 0.f, 0.f};
-            emit_words(g, rec + st.off[q.t] + (uint64_t)q.c * C * g.es, q.S, q.r, words, ov);
-            const int si = st.base[q.t] + q.c;  // the stage keeps segment order for the row writer
+            emit_cell(g, a, rec + st.off[t] + (uint64_t)c * C * g.es, S, r, cell_idx, frame, sid, ov);
+            const int si = st.base[t] + c;  // the stage keeps segment order for the row writer
             if (kOutF32) {
                 reinterpret_cast<float4 *>(stage)[si] = make_float4(ov[0], ov[1], ov[2], ov[3]);
             } else {
@@ -620,20 +602,6 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
                 for (int ch = 0; ch < C; ++ch) pk |= to_u8(ov[ch]) << (8 * ch);
                 reinterpret_cast<uint32_t *>(stage)[si] = pk;
             }
-        };
-        const bool draw = !g.noise_free && g.dtype != DP_PIX_REC_SUM_U32;
-        const uint2 key = make_uint2((uint32_t)g.seed, (uint32_t)(g.seed >> 32));
-        for (int e = threadIdx.x; e < ncell; e += 2 * kThr) {
-            const bool two = e + kThr < ncell;
-            Cell q0, q1;
-            prep(e, q0);
-            if (two) prep(e + kThr, q1);
-            else q1 = q0;
-            uint4 w0 = make_uint4(q0.idx, (uint32_t)q0.r | (sid << 8), (uint32_t)frame, (uint32_t)(frame >> 32));
-            uint4 w1 = make_uint4(q1.idx, (uint32_t)q1.r | (sid << 8), (uint32_t)frame, (uint32_t)(frame >> 32));
-            if (draw) philox4x32_10_x2(w0, w1, key);
-            finish(q0, w0);
-            if (two) finish(q1, w1);
         }
         __syncthreads();
         // ---- C: output rows ----
