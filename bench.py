@@ -230,11 +230,11 @@ def algorithmic_bytes(plan, payload_bytes):
     }
 
 
-def traffic_from_profile(kernel):
+def traffic_from_profile(kernel, workload=None):
     """dram bytes per launch from the committed ncu summary of this kernel on this workload, if the kernel
     source has not changed since the capture (the summary records the source's sha256)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, WORKLOAD))
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload or WORKLOAD))
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -525,7 +525,8 @@ def run_soft(args):
     achieved = algo[dom_name] / (per_launch_ms / 1e3) / 1e9
     tot = sum(v[1] for v in prof.values())
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "algorithmic_bytes_per_launch": algo[dom_name],
+                "frac": achieved / hbm, "traffic": traffic_from_profile(dom_name, workload),
+                "algorithmic_bytes_per_launch": algo[dom_name],
                 "avg_launch_ms": per_launch_ms,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else
                 "fallback 6.4 TB/s",
@@ -652,7 +653,8 @@ def run_batch(args):
     achieved = algo[dom_name] / (per_launch_ms / 1e3) / 1e9 if dom_name in algo else None
     tot = sum(v[1] for v in prof.values())
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm if achieved else None, "traffic": None,
+                "frac": achieved / hbm if achieved else None,
+                "traffic": traffic_from_profile(dom_name, "batch256_portraits_512to4096_matte_b6_b20"),
                 "algorithmic_bytes_per_launch": algo.get(dom_name), "avg_launch_ms": per_launch_ms,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else
                 "fallback 6.4 TB/s",
