@@ -21,7 +21,41 @@ __device__ __forceinline__ void classify_row(const Geom &g, const CallArgs &a, i
     __syncthreads();
     const uint8_t *src = a.src + (uint64_t)f * (uint64_t)a.src_frame_stride;
     const int Wp = g.GC * T;
-    for (int x = threadIdx.x; x < Wp; x += blockDim.x) {
+    int x_first = 0;  // first column left to the per-column loop below
+    if (kMatte) {
+        // in-image columns in groups of 4, read as 16-byte granules (rows are 4-byte aligned, so a group spans
+        // at most two granules, the second loaded only when it holds wanted bytes); the 4 per-column counts
+        // are kept in registers over the tile row's T rows
+        const int ngrp = (g.N + 3) >> 2;
+        for (int q = threadIdx.x; q < ngrp; q += blockDim.x) {
+            const int c0 = 4 * q, cnt = min(4, g.N - c0);
+            uint32_t c[4] = {0u, 0u, 0u, 0u};
+#pragma unroll 4
+            for (int j = 0; j < T; ++j) {
+                const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
+                const uintptr_t addr = reinterpret_cast<uintptr_t>(src + (int64_t)sy * a.src_pitch) + 16u * (uint32_t)q;
+                const int o = (int)(addr & 15u);
+                const uint4 *ga = reinterpret_cast<const uint4 *>(addr - (uintptr_t)o);
+                const uint4 x0 = __ldg(ga);
+                const uint4 x1 = o + 4 * cnt > 16 ? __ldg(ga + 1) : make_uint4(0u, 0u, 0u, 0u);
+                const uint32_t w[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                const int qw = o >> 2;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    uint32_t v = w[k];
+                    if (qw == 1) v = w[k + 1];
+                    if (qw == 2) v = w[k + 2];
+                    if (qw == 3) v = w[k + 3];
+                    c[k] += (k < cnt && !(__uint_as_float(v) >= g.matte_thr)) ? 1u : 0u;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < cnt) atomicAdd(&cnt_s[(c0 + k) / T], c[k]);
+        }
+        x_first = g.N;
+    }
+    for (int x = x_first + threadIdx.x; x < Wp; x += blockDim.x) {
         const int sx = reflect_idx(x, g.N, g.pad_mode);
         uint32_t c = 0;
 #pragma unroll 8

@@ -47,37 +47,40 @@ __device__ void stage_segment(const Geom &g, const CallArgs &a, uint32_t f, int 
         }
         done = nv << 4;
     } else {
-        // rows not 16-byte aligned: each staged 16-byte chunk is cut out of the two aligned 16-byte granules
-        // that hold it (funnel shifts), so the loads stay 16 bytes wide.  Every granule read holds at least one
-        // byte of the row, so no load leaves the frame's allocation.
+        // rows not 16-byte aligned: each thread takes 4 consecutive staged chunks of a row, loads the 5 aligned
+        // 16-byte granules that hold them (all loads in flight together) and cuts the chunks out with funnel
+        // shifts.  Every granule read holds at least one byte of the row, so no load leaves the allocation.
         const int nv = vb >> 4;
-        for (int idx = tid; idx < T * nv; idx += nt) {
-            const int j = idx / nv, v = idx - j * nv;
+        const int ng = (nv + 3) >> 2;
+        for (int idx = tid; idx < T * ng; idx += nt) {
+            const int j = idx / ng, v0 = 4 * (idx - j * ng);
+            const int cnt = min(4, nv - v0);
             const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
-            const uint8_t *row = fbase + (int64_t)sy * g.pitch;
-            const uintptr_t addr = reinterpret_cast<uintptr_t>(row) + 16u * (uint32_t)v;
+            const uintptr_t addr = reinterpret_cast<uintptr_t>(fbase + (int64_t)sy * g.pitch) + 16u * (uint32_t)v0;
             const int o = (int)(addr & 15u);
             const uint4 *ga = reinterpret_cast<const uint4 *>(addr - (uintptr_t)o);
-            uint4 out;
-            if (o == 0) {
-                out = __ldg(ga);
-            } else {
-                const uint4 x = __ldg(ga), y = __ldg(ga + 1);
-                const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-                const int q = o >> 2, sh = 8 * (o & 3);
+            uint4 x[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+                x[q] = (q < cnt || (q == cnt && o != 0)) ? __ldg(ga + q) : make_uint4(0u, 0u, 0u, 0u);
+            const int qw = o >> 2, sh = 8 * (o & 3);
+            uint4 *dst = reinterpret_cast<uint4 *>(raw + j * rs + 16 * v0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q >= cnt) break;
+                const uint32_t w[8] = {x[q].x, x[q].y, x[q].z, x[q].w, x[q + 1].x, x[q + 1].y, x[q + 1].z, x[q + 1].w};
                 uint32_t r[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    // words q+k and q+k+1 of the 32-byte window, selected without dynamic register indexing
+                    // words qw+k and qw+k+1 of the 32-byte window, selected without dynamic register indexing
                     uint32_t lo = w[k], hi = w[k + 1];
-                    if (q == 1) { lo = w[k + 1]; hi = w[k + 2]; }
-                    if (q == 2) { lo = w[k + 2]; hi = w[k + 3]; }
-                    if (q == 3) { lo = w[k + 3]; hi = w[k + 4]; }
+                    if (qw == 1) { lo = w[k + 1]; hi = w[k + 2]; }
+                    if (qw == 2) { lo = w[k + 2]; hi = w[k + 3]; }
+                    if (qw == 3) { lo = w[k + 3]; hi = w[k + 4]; }
                     r[k] = __funnelshift_r(lo, hi, sh);
                 }
-                out = make_uint4(r[0], r[1], r[2], r[3]);
+                dst[q] = make_uint4(r[0], r[1], r[2], r[3]);
             }
-            *reinterpret_cast<uint4 *>(raw + j * rs + 16 * v) = out;
         }
         done = nv << 4;
     }
