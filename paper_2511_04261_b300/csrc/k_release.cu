@@ -47,14 +47,16 @@ __device__ void stage_segment(const Geom &g, const CallArgs &a, uint32_t f, int 
         }
         done = nv << 4;
     } else {
-        // rows not 16-byte aligned: each thread takes 4 consecutive staged chunks of a row, loads the 5 aligned
-        // 16-byte granules that hold them (all loads in flight together) and cuts the chunks out with funnel
-        // shifts.  Every granule read holds at least one byte of the row, so no load leaves the allocation.
-        const int nv = vb >> 4;
-        const int ng = (nv + 3) >> 2;
+        // rows not 16-byte aligned: each thread takes 4 consecutive staged chunks of a row (the last one may be
+        // partial), loads the aligned 16-byte granules that hold them (all in flight together) and cuts the
+        // chunks out with funnel shifts.  Only granules holding a byte of the row are read, so no load leaves
+        // the allocation.
+        const int nvt = (vb + 15) >> 4, tb = vb & 15;
+        const int ng = (nvt + 3) >> 2;
         for (int idx = tid; idx < T * ng; idx += nt) {
             const int j = idx / ng, v0 = 4 * (idx - j * ng);
-            const int cnt = min(4, nv - v0);
+            const int cnt = min(4, nvt - v0);
+            const int last_bytes = (v0 + cnt == nvt && tb) ? tb : 16;  // bytes of the group's last chunk
             const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
             const uintptr_t addr = reinterpret_cast<uintptr_t>(fbase + (int64_t)sy * g.pitch) + 16u * (uint32_t)v0;
             const int o = (int)(addr & 15u);
@@ -62,9 +64,9 @@ __device__ void stage_segment(const Geom &g, const CallArgs &a, uint32_t f, int 
             uint4 x[5];
 #pragma unroll
             for (int q = 0; q < 5; ++q)
-                x[q] = (q < cnt || (q == cnt && o != 0)) ? __ldg(ga + q) : make_uint4(0u, 0u, 0u, 0u);
+                x[q] = (q < cnt || (q == cnt && o + last_bytes > 16)) ? __ldg(ga + q) : make_uint4(0u, 0u, 0u, 0u);
             const int qw = o >> 2, sh = 8 * (o & 3);
-            uint4 *dst = reinterpret_cast<uint4 *>(raw + j * rs + 16 * v0);
+            uint8_t *dst = raw + j * rs + 16 * v0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (q >= cnt) break;
@@ -79,10 +81,14 @@ __device__ void stage_segment(const Geom &g, const CallArgs &a, uint32_t f, int 
                     if (qw == 3) { lo = w[k + 3]; hi = w[k + 4]; }
                     r[k] = __funnelshift_r(lo, hi, sh);
                 }
-                dst[q] = make_uint4(r[0], r[1], r[2], r[3]);
+                if (q < cnt - 1 || last_bytes == 16) {
+                    reinterpret_cast<uint4 *>(dst)[q] = make_uint4(r[0], r[1], r[2], r[3]);
+                } else {
+                    for (int bb = 0; bb < last_bytes; ++bb) dst[16 * q + bb] = (uint8_t)(r[bb >> 2] >> (8 * (bb & 3)));
+                }
             }
         }
-        done = nv << 4;
+        done = vb;
     }
     const int tail = vb - done;
     if (tail > 0) {
