@@ -7,8 +7,8 @@
 // Fast path (records with the launch's channel count): the segment -- a whole tile row when it fits -- has
 // its cell values converted once into shared memory; each thread owns 16-byte columns of the output rows and
 // assembles its vector from the cells it covers.  With 16-byte aligned rows the same vector is stored to
-// every row of the current cell band before it is rebuilt; rows of any other alignment copy each distinct
-// row, assembled once in shared memory, with aligned 16-byte stores cut out by funnel shifts.
+// every row of the current cell band before it is rebuilt; rows of any other alignment get their aligned
+// middle in 16-byte chunks built per row and their head and tail one element at a time.
 // Generic path (anything else): the CTA builds each distinct output row in shared memory and copies it out
 // with the widest aligned stores.
 #include <algorithm>
@@ -185,9 +185,8 @@ __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i,
         seg_write_rows<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T), orow0,
                                    out_pitch, threadIdx.x, blockDim.x);
     else
-        seg_write_rows_pat<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T),
-                                       orow0, out_pitch, reinterpret_cast<uint8_t *>(colinfo + kMaxSegPx),
-                                       threadIdx.x, blockDim.x);
+        seg_write_rows_any<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T),
+                                       orow0, out_pitch, threadIdx.x, blockDim.x);
     __syncthreads();
 }
 
@@ -268,7 +267,7 @@ template <int kOutF32, int kFastC>
 __global__ void __launch_bounds__(kThreads)
     k_reconstruct(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out, int64_t out_frame_stride,
                   int64_t out_pitch, int max_M, int max_N, int max_C, int out_align, int32_t *status) {
-    extern __shared__ __align__(16) uint8_t dyn[];  // fast path: stage[kStageBytes], colinfo[kMaxSegPx], row pattern
+    extern __shared__ __align__(16) uint8_t dyn[];  // fast path: stage[kStageBytes] then colinfo[kMaxSegPx]
     __shared__ __align__(16) uint8_t rowpat[kRowBytes];
     __shared__ __align__(16) dp_pix_record_header hdr_s;
     __shared__ RecGeom rg;
@@ -360,9 +359,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int kOutF32, int kFastC>
 cudaError_t launch_brc(const BatchEntry *tab, uint32_t n_img, uint32_t items, int max_C, int out_align,
                        int32_t *status, cudaStream_t s) {
-    // unaligned output rows: room for one row pattern of a segment after the column map
-    const size_t smem = kStageBytes + kMaxSegPx * 4 +
-                        (out_align < 16 ? (size_t)kMaxSegPx * max_C * (kOutF32 ? 4 : 1) + 32 : 0);
+    const size_t smem = kStageBytes + kMaxSegPx * 4;
     auto kern = k_batch_reconstruct<kOutF32, kFastC>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
@@ -396,9 +393,7 @@ template <int kOutF32, int kFastC>
 cudaError_t launch_rc(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out, int64_t out_frame_stride,
                       int64_t out_pitch, int max_M, int max_N, int max_C, int out_align, int32_t *status,
                       cudaStream_t s) {
-    // unaligned output rows: room for one row pattern of a segment after the column map
-    const size_t smem = kStageBytes + kMaxSegPx * 4 +
-                        (out_align < 16 ? (size_t)kMaxSegPx * max_C * (kOutF32 ? 4 : 1) + 32 : 0);
+    const size_t smem = kStageBytes + kMaxSegPx * 4;
     auto kern = k_reconstruct<kOutF32, kFastC>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;

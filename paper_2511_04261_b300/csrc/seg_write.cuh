@@ -201,86 +201,78 @@ __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, cons
     }
 }
 
-// Rows of any alignment, the whole block: each distinct row of the segment -- rows [j, jn) in which no tile
-// enters a new cell band -- is assembled once in shared memory (pat: 16-byte chunks built from the staged
-// cells), then copied to each of its rows with aligned 16-byte stores cut out of the pattern by funnel shifts;
-// the bytes before a row's first 16-byte boundary and after its last one are copied one at a time.  pat holds
-// at least the row's bytes rounded up to 16, plus 16.  Barriers inside; every thread of the block must call.
+// Writes the jmax output rows of a segment whose rows may start at any byte alignment (f32 rows at 4-byte
+// alignment): per row, the aligned middle in 16-byte chunks, each assembled from the cells it covers for
+// that row (rows do not share vectors, their alignments differ), and the head and tail (< 16 bytes each)
+// one element at a time.
 template <int C, int kOutF32>
-__device__ void seg_write_rows_pat(const SegTiles &st, const uint32_t *colinfo, const uint8_t *stage, int ns, int T,
-                                   int vpx, int jmax, uint8_t *orow0, int64_t out_pitch, uint8_t *pat, int tid,
-                                   int nthr) {
+__device__ void seg_write_rows_any(const SegTiles &st, const uint32_t *colinfo, const uint8_t *stage, int ns, int T,
+                                   int vpx, int jmax, uint8_t *orow0, int64_t out_pitch, int tid, int nthr) {
     constexpr int oes = kOutF32 ? 4 : 1;
     constexpr int kElems = 16 / oes;
     constexpr int NPX = kOutF32 ? FastK<C>::NPXF : FastK<C>::NPX8;
     const int row_bytes = vpx * C * oes;
-    const int nch = (row_bytes + 15) >> 4;
     const int last_px = ns * T - 1;
-    const int per_row = (row_bytes >> 4) + 1;  // aligned chunks (<= row_bytes / 16) plus one head/tail unit
-    int j = 0;
-    while (j < jmax) {
-        int jn = jmax;
-        for (int t = 0; t < ns; ++t) jn = min(jn, (j / st.b[t] + 1) * st.b[t]);
-        for (int k = tid; k < nch; k += nthr) {
-            const int o = k << 4;
-            const int e0 = o / oes;
-            const int p = e0 % C;
-            const int l0 = e0 / C;
-            const int lastp = min((e0 + kElems - 1) / C, last_px);
-            const uint32_t cl = colinfo[lastp];
-            const int tA = colinfo[min(l0, last_px)] >> 16;
-            const int baseA = st.base[tA] + (j / st.b[tA]) * st.cs[tA];
-            const int tB = cl >> 16;
-            const int baseB = st.base[tB] + (j / st.b[tB]) * st.cs[tB];
-            uint4 vec;
-            if (kOutF32) {
-                float4 pv[NPX];
+    const int maxch = (row_bytes >> 4) + 1;
+    for (int w = tid; w < jmax * maxch; w += nthr) {
+        const int j = w / maxch, k = w - j * maxch;
+        uint8_t *row = orow0 + (int64_t)j * out_pitch;
+        const int h = min((int)((16u - (uint32_t)(reinterpret_cast<uintptr_t>(row) & 15u)) & 15u), row_bytes);
+        if (k >= ((row_bytes - h) >> 4)) continue;
+        const int o = h + 16 * k;
+        const int e0 = o / oes;
+        const int p = e0 % C;
+        const int l0 = e0 / C;
+        const int lastp = min((e0 + kElems - 1) / C, last_px);
+        const uint32_t cl = colinfo[lastp];
+        const int tA = colinfo[min(l0, last_px)] >> 16;
+        const int tB = cl >> 16;
+        const int baseA = st.base[tA] + (j / st.b[tA]) * st.cs[tA];
+        const int baseB = st.base[tB] + (j / st.b[tB]) * st.cs[tB];
+        uint4 vec;
+        if (kOutF32) {
+            float4 pv[NPX];
 #pragma unroll
-                for (int l = 0; l < NPX; ++l) {
-                    const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
-                    pv[l] = reinterpret_cast<const float4 *>(stage)[((int)(v >> 16) != tA ? baseB : baseA) + (int)(v & 0xFFFFu)];
-                }
-                vec = build_f32_phase<C>(p, pv);
-            } else {
-                uint32_t pv[NPX];
-#pragma unroll
-                for (int l = 0; l < NPX; ++l) {
-                    const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
-                    pv[l] = reinterpret_cast<const uint32_t *>(stage)[((int)(v >> 16) != tA ? baseB : baseA) + (int)(v & 0xFFFFu)];
-                }
-                vec = build_u8_phase<C>(p, pv);
+            for (int l = 0; l < NPX; ++l) {
+                const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
+                const int idx = ((int)(v >> 16) != tA ? baseB : baseA) + (int)(v & 0xFFFFu);
+                pv[l] = reinterpret_cast<const float4 *>(stage)[idx];
             }
-            *reinterpret_cast<uint4 *>(pat + o) = vec;
-        }
-        __syncthreads();
-        for (int w = tid; w < (jn - j) * per_row; w += nthr) {
-            const int r = j + w / per_row, kk = w - (w / per_row) * per_row;
-            uint8_t *row = orow0 + (int64_t)r * out_pitch;
-            const int h = min((int)((16u - (uint32_t)(reinterpret_cast<uintptr_t>(row) & 15u)) & 15u), row_bytes);
-            const int nmid = (row_bytes - h) >> 4;
-            if (kk < nmid) {
-                // pattern bytes [h + 16 kk, +16): granules kk and kk+1 (h < 16), shifted by h bytes
-                const uint4 x = reinterpret_cast<const uint4 *>(pat)[kk];
-                const uint4 y = reinterpret_cast<const uint4 *>(pat)[kk + 1];
-                const uint32_t wv[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-                const int qw = h >> 2, sh = 8 * (h & 3);
-                uint32_t o4[4];
+            vec = build_f32_phase<C>(p, pv);
+        } else {
+            uint32_t pv[NPX];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    uint32_t lo = wv[k], hi = wv[k + 1];
-                    if (qw == 1) { lo = wv[k + 1]; hi = wv[k + 2]; }
-                    if (qw == 2) { lo = wv[k + 2]; hi = wv[k + 3]; }
-                    if (qw == 3) { lo = wv[k + 3]; hi = wv[k + 4]; }
-                    o4[k] = __funnelshift_r(lo, hi, sh);
-                }
-                *reinterpret_cast<uint4 *>(row + h + 16 * kk) = make_uint4(o4[0], o4[1], o4[2], o4[3]);
-            } else if (kk == nmid) {
-                for (int bb = 0; bb < h; ++bb) row[bb] = pat[bb];
-                for (int bb = h + 16 * nmid; bb < row_bytes; ++bb) row[bb] = pat[bb];
+            for (int l = 0; l < NPX; ++l) {
+                const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
+                const int idx = ((int)(v >> 16) != tA ? baseB : baseA) + (int)(v & 0xFFFFu);
+                pv[l] = reinterpret_cast<const uint32_t *>(stage)[idx];
             }
+            vec = build_u8_phase<C>(p, pv);
         }
-        __syncthreads();
-        j = jn;
+        *reinterpret_cast<uint4 *>(row + o) = vec;
+    }
+    // heads and tails: at most 2 * kElems - 2 elements per row
+    constexpr int kEdge = 2 * kElems;
+    for (int w = tid; w < jmax * kEdge; w += nthr) {
+        const int j = w / kEdge, i = w - j * kEdge;
+        uint8_t *row = orow0 + (int64_t)j * out_pitch;
+        const int h = min((int)((16u - (uint32_t)(reinterpret_cast<uintptr_t>(row) & 15u)) & 15u), row_bytes);
+        const int tail0 = h + (((row_bytes - h) >> 4) << 4);
+        const int nh = h / oes, nt = (row_bytes - tail0) / oes;
+        int e;
+        if (i < nh) e = i;
+        else if (i - nh < nt) e = tail0 / oes + (i - nh);
+        else continue;
+        const int px = e / C, ch = e - px * C;
+        const uint32_t v = colinfo[px];
+        const int t = (int)(v >> 16);
+        const int idx = st.base[t] + (j / st.b[t]) * st.cs[t] + (int)(v & 0xFFFFu);
+        if (kOutF32) {
+            const float4 f = reinterpret_cast<const float4 *>(stage)[idx];
+            reinterpret_cast<float *>(row)[e] = ch == 0 ? f.x : (ch == 1 ? f.y : (ch == 2 ? f.z : f.w));
+        } else {
+            row[e] = (uint8_t)(reinterpret_cast<const uint32_t *>(stage)[idx] >> (8 * ch));
+        }
     }
 }
 
