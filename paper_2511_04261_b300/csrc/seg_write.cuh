@@ -118,50 +118,44 @@ __device__ __forceinline__ void seg_prefix_colinfo(SegTiles &st, int ns, int T, 
     }
 }
 
+// Subtracts n from k until k < n; returns how many times.
+__device__ __forceinline__ int wrap_count(int &k, int n) {
+    int c = 0;
+    while (k >= n) {
+        k -= n;
+        ++c;
+    }
+    return c;
+}
+
 // Writes the jmax output rows of a segment whose first output byte is orow0 (16-byte aligned) and
 // whose rows hold vpx pixels; stage holds the segment's cell values (packed u8 or float4).  Threads
-// tid = 0..nthr-1 of the group (whole warps) share the work.
-//
-// Work is dealt to warps as tasks (row group, phase, 32 consecutive chunks of that phase): a 16-byte chunk k
-// starts at element 16k / oes, whose channel ("phase") is k mod 3 for C = 3 and 0 otherwise, so every lane of a
-// warp builds its vector with the same compile-time byte selectors.  A lane then walks its chunk down the
-// rows of the group, rebuilding the vector only when one of its (at most two) tiles enters a new cell band.
+// tid = 0..nthr-1 of the group share the work.
 template <int C, int kOutF32>
 __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, const uint8_t *stage, int ns, int T, int vpx,
                                int jmax, uint8_t *orow0, int64_t out_pitch, int tid, int nthr) {
     constexpr int oes = kOutF32 ? 4 : 1;
-    constexpr int NP = C == 3 ? 3 : 1;  // phases of 16-byte chunks
-    constexpr int kElems = 16 / oes;
-    constexpr int NPX = kOutF32 ? FastK<C>::NPXF : FastK<C>::NPX8;
+    // write phase: thread = (16-byte column chunk, group of rows); no barrier until the next item
     const int row_bytes = vpx * C * oes;
     const int nch = (row_bytes + 15) >> 4;
-    const int last_px = ns * T - 1;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-    // chunk blocks of 32 per phase, and row groups so that each warp gets a few tasks
-    int blocks = 0;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) blocks += ((nch - p + NP - 1) / NP + 31) >> 5;
-    int RG = (3 * nwarps + blocks - 1) / blocks;
+    int RG = (2 * nthr + nch - 1) / nch;  // about two (chunk, row group) units per thread
     RG = RG < 1 ? 1 : (RG > jmax ? jmax : RG);
     const int rpg = (jmax + RG - 1) / RG;
-    const int tasks = blocks * RG;
-    for (int task = warp; task < tasks; task += nwarps) {
-        const int grp = task / blocks;
-        int bi = task - grp * blocks, p = 0;
-#pragma unroll
-        for (int q = 0; q < NP - 1; ++q) {
-            const int bq = ((nch - p + NP - 1) / NP + 31) >> 5;
-            if (bi >= bq) {
-                bi -= bq;
-                ++p;
-            }
-        }
-        const int k = NP * (32 * bi + lane) + p;
+    const int last_px = ns * T - 1;
+    constexpr int kElems = 16 / oes;
+    constexpr int NPX = kOutF32 ? FastK<C>::NPXF : FastK<C>::NPX8;
+    // units (chunk k, row group grp), w = grp * nch + k; consecutive threads take consecutive chunks so that warp
+    // stores are contiguous, and (k, grp) follow w without a division per unit
+    int k = tid % nch, grp = tid / nch;
+    for (int w = tid; w < nch * RG; w += nthr, k += nthr, grp += wrap_count(k, nch)) {
         const int j0 = grp * rpg, j1 = min(jmax, j0 + rpg);
-        if (k >= nch || j0 >= j1) continue;
+        if (j0 >= j1) continue;
         const int o = k << 4;
-        const int e0 = o / oes;
-        const int l0 = e0 / C;
+        const int e0 = o / oes;  // first output element of the chunk
+        const int p = e0 % C;
+        const int l0 = e0 / C;   // first pixel column
+        // the chunk's real pixels lie in at most two tiles (a tile row has >= 16 bytes); trailing entries past
+        // them are never used by the vector builder and are pointed at the last real pixel
         const int lastp = min((e0 + kElems - 1) / C, last_px);
         const uint32_t cl = colinfo[lastp];
         const int tA = colinfo[min(l0, last_px)] >> 16;
@@ -175,46 +169,46 @@ __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, cons
             inB[l] = (int)(v >> 16) != tA;
         }
         const int bA = st.b[tA], bB = st.b[tB], csA = st.cs[tA], csB = st.cs[tB];
-        const int sA = (bA & (bA - 1)) == 0 ? __ffs(bA) - 1 : -1, sB = (bB & (bB - 1)) == 0 ? __ffs(bB) - 1 : -1;
-        int cyA = sA >= 0 ? j0 >> sA : j0 / bA, cyB = sB >= 0 ? j0 >> sB : j0 / bB;
-        int nextA = (cyA + 1) * bA, nextB = (cyB + 1) * bB;
-        const int b0A = st.base[tA], b0B = st.base[tB];
-        auto build = [&]() -> uint4 {
-            const int baseA = b0A + cyA * csA, baseB = b0B + cyB * csB;
+        const bool full = o + 16 <= row_bytes;
+        // cell bands followed incrementally: band of row j, and the row where it ends
+        int bandA = (bA & (bA - 1)) == 0 ? j0 >> (__ffs(bA) - 1) : j0 / bA;
+        int bandB = (bB & (bB - 1)) == 0 ? j0 >> (__ffs(bB) - 1) : j0 / bB;
+        int endA = (bandA + 1) * bA, endB = (bandB + 1) * bB;
+        int j = j0;
+        while (j < j1) {
+            const int jn = min(j1, min(endA, endB));
+            const int baseA = st.base[tA] + bandA * csA, baseB = st.base[tB] + bandB * csB;
+            uint4 vec;
             if (kOutF32) {
                 float4 pv[NPX];
 #pragma unroll
                 for (int l = 0; l < NPX; ++l) pv[l] = reinterpret_cast<const float4 *>(stage)[(inB[l] ? baseB : baseA) + cc[l]];
-                return build_f32_phase<C>(p, pv);
+                vec = build_f32_phase<C>(p, pv);
             } else {
                 uint32_t pv[NPX];
 #pragma unroll
                 for (int l = 0; l < NPX; ++l) pv[l] = reinterpret_cast<const uint32_t *>(stage)[(inB[l] ? baseB : baseA) + cc[l]];
-                return build_u8_phase<C>(p, pv);
+                vec = build_u8_phase<C>(p, pv);
             }
-        };
-        uint4 vec = build();
-        const bool full = o + 16 <= row_bytes;
-        uint8_t *dst = orow0 + (int64_t)j0 * out_pitch + o;
-        for (int j = j0; j < j1; ++j, dst += out_pitch) {
-            if (j == nextA || j == nextB) {
-                if (j == nextA) {
-                    ++cyA;
-                    nextA += bA;
+            uint8_t *dst = orow0 + (int64_t)j * out_pitch + o;
+            for (int rr = j; rr < jn; ++rr, dst += out_pitch) {
+                if (full) {
+                    *reinterpret_cast<uint4 *>(dst) = vec;
+                } else {
+                    for (int i = 0; o + i < row_bytes; ++i) {
+                        const uint32_t wv = i < 4 ? vec.x : (i < 8 ? vec.y : (i < 12 ? vec.z : vec.w));
+                        dst[i] = (uint8_t)(wv >> (8 * (i & 3)));
+                    }
                 }
-                if (j == nextB) {
-                    ++cyB;
-                    nextB += bB;
-                }
-                vec = build();
             }
-            if (full) {
-                *reinterpret_cast<uint4 *>(dst) = vec;
-            } else {
-                for (int i = 0; o + i < row_bytes; ++i) {
-                    const uint32_t wv = i < 4 ? vec.x : (i < 8 ? vec.y : (i < 12 ? vec.z : vec.w));
-                    dst[i] = (uint8_t)(wv >> (8 * (i & 3)));
-                }
+            j = jn;
+            if (j == endA) {
+                ++bandA;
+                endA += bA;
+            }
+            if (j == endB) {
+                ++bandB;
+                endB += bB;
             }
         }
     }
