@@ -116,6 +116,33 @@ uint64_t plan_ws_per_frame(const dp_pix_plan_s *plan) { return plan ? plan->g.ws
 
 int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
+// Blocks of `kernel` resident per SM at `threads` threads and `smem` dynamic bytes, on the current device.
+// The first call for a kernel on a device also raises its dynamic shared-memory limit to the device's opt-in
+// maximum, so launches never need to set it again; results are cached (these queries cost microseconds of
+// host time per launch otherwise).
+int launch_prep(const void *kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int, size_t>, int> occ;
+    static std::map<std::pair<const void *, int>, bool> raised;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(kernel, dev, threads, smem);
+    auto it = occ.find(key);
+    if (it != occ.end()) return it->second;
+    if (!raised[std::make_pair(kernel, dev)]) {
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (optin > 0) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        raised[std::make_pair(kernel, dev)] = true;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    occ[key] = per_sm;
+    return per_sm;
+}
+
 // Non-blocking side streams of the current device (created once, kept for the process).
 cudaStream_t *side_streams(int n) {
     static std::mutex mu;

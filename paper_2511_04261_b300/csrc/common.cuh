@@ -223,6 +223,7 @@ void prof_end(const char *name, cudaStream_t s);
 int sm_count();
 int32_t *status_word();  // device address of the status word on the current device (nullptr on failure)
 cudaStream_t *side_streams(int n);  // n (<= 8) non-blocking streams of the current device, or nullptr
+int launch_prep(const void *kernel, int threads, size_t smem);  // blocks per SM (cached); raises the smem limit
 }  // namespace dppix
 struct dp_pix_plan_s;
 namespace dppix {

@@ -282,11 +282,7 @@ __global__ void __launch_bounds__(kFrameThreads) k_rank(const Geom g, const Call
 
 cudaError_t launch_finalize_labels(const Geom &g, const CallArgs &a, cudaStream_t s) {
     const size_t smem = sizeof(FinalizeSmem) + g.ntiles;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr_set = true;
-    }
+    launch_prep(reinterpret_cast<const void *>(k_finalize), kFrameThreads, smem);
     prof_begin("k_finalize", s);
     k_finalize<<<a.n_frames, kFrameThreads, smem, s>>>(g, a, 1);
     prof_end("k_finalize", s);
@@ -295,11 +291,7 @@ cudaError_t launch_finalize_labels(const Geom &g, const CallArgs &a, cudaStream_
 
 cudaError_t launch_finalize_map(const Geom &g, const CallArgs &a, cudaStream_t s) {
     const size_t smem = sizeof(FinalizeSmem) + g.ntiles;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr_set = true;
-    }
+    launch_prep(reinterpret_cast<const void *>(k_finalize), kFrameThreads, smem);
     prof_begin("k_finalize", s);
     k_finalize<<<a.n_frames, kFrameThreads, smem, s>>>(g, a, 0);
     prof_end("k_finalize", s);
@@ -308,7 +300,7 @@ cudaError_t launch_finalize_map(const Geom &g, const CallArgs &a, cudaStream_t s
 
 cudaError_t launch_batch_finalize(const BatchEntry *tab, uint32_t n_img, uint32_t max_tiles, cudaStream_t s) {
     const size_t smem = sizeof(FinalizeSmem) + max_tiles;
-    cudaFuncSetAttribute(k_batch_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    launch_prep(reinterpret_cast<const void *>(k_batch_finalize), kFrameThreads, smem);
     const int grid = (int)std::min<uint32_t>(n_img, (uint32_t)sm_count());
     prof_begin("k_batch_finalize", s);
     k_batch_finalize<<<grid, kFrameThreads, smem, s>>>(tab, n_img);
@@ -318,7 +310,7 @@ cudaError_t launch_batch_finalize(const BatchEntry *tab, uint32_t n_img, uint32_
 
 cudaError_t launch_rank(const Geom &g, const CallArgs &a, cudaStream_t s) {
     const size_t smem = sizeof(FinalizeSmem) + (size_t)g.ntiles * 8 + g.ntiles;
-    cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    launch_prep(reinterpret_cast<const void *>(k_rank), kFrameThreads, smem);
     prof_begin("k_rank", s);
     k_rank<<<a.n_frames, kFrameThreads, smem, s>>>(g, a);
     prof_end("k_rank", s);

@@ -361,10 +361,7 @@ cudaError_t launch_brc(const BatchEntry *tab, uint32_t n_img, uint32_t items, in
                        int32_t *status, cudaStream_t s) {
     const size_t smem = kStageBytes + kMaxSegPx * 4;
     auto kern = k_batch_reconstruct<kOutF32, kFastC>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-    if (per_sm < 1) per_sm = 1;
+    const int per_sm = launch_prep(reinterpret_cast<const void *>(kern), kThreads, smem);
     const int grid = (int)std::min<uint64_t>(items, (uint64_t)per_sm * sm_count());
     const char *name = kOutF32 ? "k_batch_reconstruct_f32" : "k_batch_reconstruct_u8";
     prof_begin(name, s);
@@ -395,10 +392,7 @@ cudaError_t launch_rc(const uint8_t *records, int64_t record_stride, uint32_t n,
                       cudaStream_t s) {
     const size_t smem = kStageBytes + kMaxSegPx * 4;
     auto kern = k_reconstruct<kOutF32, kFastC>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-    if (per_sm < 1) per_sm = 1;
+    const int per_sm = launch_prep(reinterpret_cast<const void *>(kern), kThreads, smem);
     const int grid = per_sm * sm_count();
     const char *name = kOutF32 ? "k_reconstruct_f32" : "k_reconstruct_u8";
     prof_begin(name, s);

@@ -489,9 +489,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs 
 
 template <typename K>
 int grid_for(K kernel, size_t smem, uint32_t items) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
+    const int per_sm = launch_prep(reinterpret_cast<const void *>(kernel), kThreads, smem);
     const uint64_t cap = (uint64_t)per_sm * (uint64_t)sm_count();
     return (int)(items < cap ? items : cap);
 }
@@ -627,11 +625,9 @@ template <int C, int kOutF32, int kThr>
 cudaError_t launch_er(const Geom &g, const CallArgs &a, uint8_t *out, int64_t ofs, int64_t op, const FusedShape &fs,
                       cudaStream_t s) {
     auto kern = k_emit_recon<C, kOutF32, kThr>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, fs.smem);
+
     const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)((g.GC + fs.seg - 1) / fs.seg);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThr, fs.smem) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
+    const int per_sm = launch_prep(reinterpret_cast<const void *>(kern), kThr, fs.smem);
     const uint64_t cap = (uint64_t)per_sm * (uint64_t)sm_count();
     const int grid = (int)(items < cap ? items : cap);
     const char *name = kOutF32 ? "k_emit_recon_f32" : "k_emit_recon_u8";
@@ -650,7 +646,6 @@ size_t seg_smem(const Geom &g, int bands_per_tile) {
 
 cudaError_t launch_release(const Geom &g, const CallArgs &a, cudaStream_t s) {
     const size_t smem = seg_smem(g, g.vbands);
-    cudaFuncSetAttribute(k_release, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row;
     const int grid = grid_for(k_release, smem, items);
     prof_begin("k_release", s);
@@ -660,7 +655,6 @@ cudaError_t launch_release(const Geom &g, const CallArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items, size_t smem, cudaStream_t s) {
-    cudaFuncSetAttribute(k_batch_release, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = grid_for(k_batch_release, smem, items);
     prof_begin("k_batch_release", s);
     k_batch_release<<<grid, kThreads, smem, s>>>(tab, n_img, items);
@@ -674,14 +668,12 @@ cudaError_t launch_tile_stats(const Geom &g, const CallArgs &a, cudaStream_t s) 
     if (fe != cudaErrorNotSupported) return fe;
     if (g.var_onepass) {
         const size_t smem = seg_smem(g, g.T / g.g);
-        cudaFuncSetAttribute(k_tile_stats<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         const int grid = grid_for(k_tile_stats<true>, smem, items);
         prof_begin("k_tile_stats_gsum", s);
         k_tile_stats<true><<<grid, kThreads, smem, s>>>(g, a);
         prof_end("k_tile_stats_gsum", s);
     } else {
         const size_t smem = seg_smem(g, 0);
-        cudaFuncSetAttribute(k_tile_stats<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         const int grid = grid_for(k_tile_stats<false>, smem, items);
         prof_begin("k_tile_stats", s);
         k_tile_stats<false><<<grid, kThreads, smem, s>>>(g, a);

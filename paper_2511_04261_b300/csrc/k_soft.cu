@@ -383,9 +383,7 @@ bool soft_fast(const SoftGeom &sg, const void *const *ptrs, int nptr, int *js) {
 }
 
 int soft_grid(const void *kern, int threads, uint64_t work) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
+    const int per_sm = launch_prep(kern, threads, 0);
     const uint64_t cap = (uint64_t)per_sm * (uint64_t)sm_count();
     const uint64_t want = (work + threads - 1) / threads;
     return (int)std::max<uint64_t>(1, std::min(cap, want));
