@@ -131,9 +131,13 @@ int launch_prep(const void *kernel, int threads, size_t smem) {
     auto it = occ.find(key);
     if (it != occ.end()) return it->second;
     if (!raised[std::make_pair(kernel, dev)]) {
+        // the dynamic limit is the opt-in maximum less the kernel's static shared memory
         int optin = 0;
+        cudaFuncAttributes fa{};
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (optin > 0) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (optin > 0 && cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && optin > (int)fa.sharedSizeBytes)
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+        cudaGetLastError();  // a refused attribute surfaces at the launch, not here
         raised[std::make_pair(kernel, dev)] = true;
     }
     int per_sm = 0;
