@@ -426,6 +426,32 @@ __device__ __forceinline__ void gblock_sum(const uint16_t *p0, size_t rowvals, i
     }
 }
 
+// gblock_sum for a compile-time block width NB (g-cells per side): fully unrolled loads and adds.
+template <int C, int NB>
+__device__ __forceinline__ void gblock_sum_n(const uint16_t *p0, size_t rowvals, uint32_t *S) {
+#pragma unroll
+    for (int yy = 0; yy < NB; ++yy) {
+        const uint16_t *p = p0 + (size_t)yy * rowvals;
+#pragma unroll
+        for (int xx = 0; xx < NB; ++xx)
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) S[ch] += p[xx * C + ch];
+    }
+}
+
+// Block sum dispatched on the block width: unrolled for 1, 2, 4 and 8 g-cells, the generic loop otherwise.
+// (Work items hand a warp cells of one grid size, so the branch is uniform across the warp.)
+template <int C>
+__device__ __forceinline__ void gblock_sum_any(const uint16_t *p0, size_t rowvals, int nb, uint32_t *S) {
+    switch (nb) {
+        case 1: gblock_sum_n<C, 1>(p0, rowvals, S); break;
+        case 2: gblock_sum_n<C, 2>(p0, rowvals, S); break;
+        case 4: gblock_sum_n<C, 4>(p0, rowvals, S); break;
+        case 8: gblock_sum_n<C, 8>(p0, rowvals, S); break;
+        default: gblock_sum<C>(p0, rowvals, nb, S); break;
+    }
+}
+
 // ------------------------------------------------------------------------------------------------------
 // k_emit: walks each record's payload in order, one thread per cell.  Element e of the payload lies in the
 // region whose cumulative cell count passes e; the region-ordered tile list gives its tile, and the cell
@@ -477,10 +503,10 @@ __global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs 
         const uint16_t *p0 = gimg + ((size_t)(ty * gcs + cy * nb)) * rowvals + ((size_t)tx * gcs + (size_t)cx * nb) * C;
         uint32_t S[4] = {0u, 0u, 0u, 0u};
         switch (C) {
-            case 1: gblock_sum<1>(p0, rowvals, nb, S); break;
-            case 2: gblock_sum<2>(p0, rowvals, nb, S); break;
-            case 3: gblock_sum<3>(p0, rowvals, nb, S); break;
-            default: gblock_sum<4>(p0, rowvals, nb, S); break;
+            case 1: gblock_sum_any<1>(p0, rowvals, nb, S); break;
+            case 2: gblock_sum_any<2>(p0, rowvals, nb, S); break;
+            case 3: gblock_sum_any<3>(p0, rowvals, nb, S); break;
+            default: gblock_sum_any<4>(p0, rowvals, nb, S); break;
         }
         const uint32_t cell_idx = (ty * cs + cy) * (uint32_t)(g.GC * cs) + tx * cs + cx;
         emit_cell(g, a, rec + roff[r] + (uint64_t)local * C * g.es, S, r, cell_idx, frame, sid);
@@ -516,7 +542,7 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
     extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ SegTiles st;
     __shared__ uint8_t rlist[kSegMaxTiles];
-    __shared__ int32_t rtile[kMaxK], rcell[kMaxK + 1], rcs[kMaxK];
+    __shared__ int32_t rtile[kMaxK], rcell[kMaxK + 1], rcs[kMaxK], rnb[kMaxK];
     constexpr int oes = kOutF32 ? 4 : 1;
     uint8_t *gseg = dyn;
     uint8_t *stage = dyn + fs.stage_off;
@@ -572,6 +598,7 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
                     rtile[r] = tb;
                     rcell[r] = cb;
                     rcs[r] = cs;
+                    rnb[r] = g.grid[r] / g.g;
                 }
                 tb += n;
                 cb += n * cs * cs;
@@ -594,9 +621,9 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
             const int c = local - k * cs * cs;
             const int t = rlist[rtile[r] + k];
             const int cy = p2 ? c >> lcs : c / cs, cx = c - cy * cs;
-            const int tx = tx0 + t, nb = st.b[t] / g.g;
+            const int tx = tx0 + t, nb = rnb[r];
             uint32_t S[4] = {0u, 0u, 0u, 0u};
-            gblock_sum<C>(gs16 + (size_t)(cy * nb) * gsv + (size_t)(t * gcs + cx * nb) * C, (size_t)gsv, nb, S);
+            gblock_sum_any<C>(gs16 + (size_t)(cy * nb) * gsv + (size_t)(t * gcs + cx * nb) * C, (size_t)gsv, nb, S);
             const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)(tx * cs + cx);
             float ov[4] = {0.f, 0.f, 0.f, 0.f};
             emit_cell(g, a, rec + st.off[t] + (uint64_t)c * C * g.es, S, r, cell_idx, frame, sid, ov);
