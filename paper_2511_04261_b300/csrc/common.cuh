@@ -147,28 +147,38 @@ __device__ __forceinline__ uint4 cell_noise_words(uint64_t seed, uint32_t cell_i
 }
 
 // Laplace(0, sigma) by the inverse CDF at u = (x + 1/2) / 2^32 (Eq. 9).  With k = x (lower half) or
-// k = 2^32-1-x (upper half, sign flipped), ln(2u) or ln(2(1-u)) is ln t, t = (k + 1/2) / 2^31.  Both halves
-// use one log1pf call so that a warp whose lanes fall in different halves runs it once:
-//  - t < 1/2: t = 2^e * m with m in [1, 2) read from the float's exponent and mantissa, so
-//    ln t = e ln 2 + log1p(m - 1) with m - 1 exact;
-//  - t >= 1/2: ln t = log1p(-(j + 1/2) / 2^31) with the exact integer j = 2^31-1-k, so nothing cancels
-//    near t = 1.
+// k = 2^32-1-x (upper half, sign flipped), ln(2u) or ln(2(1-u)) is ln t, t = (k + 1/2) / 2^31 in (0, 1).
+// ln t is evaluated without a library call and without a branch, so that the lanes of a warp never split:
+//  - t < 1/sqrt(2): t = 2^e m with m in [1/sqrt(2), sqrt(2)) taken from the float's exponent and mantissa,
+//    and y = m - 1 (exact);
+//  - t >= 1/sqrt(2): e = 0 and y = -(j + 1/2) / 2^31 with the exact integer j = 2^31-1-k, so nothing cancels
+//    near t = 1;
+// then ln(1 + y) = 2 atanh(s), s = y / (2 + y), |s| <= 0.172, from the odd series of atanh
+// (Abramowitz & Stegun 4.5.64 with 4.1.27) truncated after s^11 (relative truncation error < 3e-9).
 __device__ __forceinline__ float laplace_from_word(uint32_t x, float sigma) {
     const bool upper = (x >> 31) != 0u;
-    const uint32_t k = upper ? ~x : x;
-    float arg, off;
-    if (k < (1u << 30)) {
-        const float t = (__uint2float_rn(k) + 0.5f) * 0x1p-31f;  // a normal float in [2^-32, 1/2)
-        const int bits = __float_as_int(t);
-        const int e = ((bits >> 23) & 0xFF) - 127;
-        arg = __int_as_float((bits & 0x007FFFFF) | 0x3F800000) - 1.0f;
-        off = (float)e * 0.693147180559945309f;
-    } else {
-        const uint32_t j = 0x7FFFFFFFu - k;
-        arg = -(__uint2float_rn(j) + 0.5f) * 0x1p-31f;
-        off = 0.0f;
-    }
-    const float lnt = off + log1pf(arg);
+    const uint32_t k = upper ? ~x : x;                         // [0, 2^31)
+    const bool low = k <= 1518500249u;                          // t < 1/sqrt(2)
+    // lower branch: t as a normal float in [2^-32, 0.7071), split into 2^e * m
+    const float t = (__uint2float_rn(k) + 0.5f) * 0x1p-31f;
+    const int bits = __float_as_int(t);
+    int e = ((bits >> 23) & 0xFF) - 127;
+    float m = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);  // [1, 2)
+    const bool big = m > 1.41421356f;
+    m = big ? 0.5f * m : m;
+    e = big ? e + 1 : e;
+    // upper branch: y from the exact distance to 1
+    const uint32_t j = 0x7FFFFFFFu - k;
+    const float y = low ? m - 1.0f : -(__uint2float_rn(j) + 0.5f) * 0x1p-31f;
+    const float ef = low ? (float)e : 0.0f;
+    const float sr = __fdividef(y, 2.0f + y);
+    const float z = sr * sr;
+    float poly = fmaf(z, 1.0f / 11.0f, 1.0f / 9.0f);
+    poly = fmaf(z, poly, 1.0f / 7.0f);
+    poly = fmaf(z, poly, 1.0f / 5.0f);
+    poly = fmaf(z, poly, 1.0f / 3.0f);
+    const float l1p = 2.0f * fmaf(sr * z, poly, sr);          // ln(1 + y)
+    const float lnt = fmaf(ef, 0.693147180559945309f, l1p);
     return upper ? -sigma * lnt : sigma * lnt;
 }
 
