@@ -185,7 +185,11 @@ __device__ __forceinline__ float laplace_from_word(uint32_t x, float sigma) {
 // Clipped noisy mean (Sec. IV-D; Alg. 2 steps 6-9): v = min(max(S / b^2 + eta, 0), R).
 __device__ __forceinline__ float noisy_mean(uint32_t S, float b2, float inv_b2, float eta, float R) {
     // a power-of-two b^2 has an exact reciprocal, and then the product is the correctly rounded quotient
-    const float mu = inv_b2 != 0.0f ? __fmul_rn(__uint2float_rn(S), inv_b2) : __fdiv_rn(__uint2float_rn(S), b2);
+    float mu;
+    if (inv_b2 != 0.0f)
+        mu = __fmul_rn(__uint2float_rn(S), inv_b2);
+    else
+        mu = __fdiv_rn(__uint2float_rn(S), b2);
     const float v = __fadd_rn(mu, eta);
     return fminf(fmaxf(v, 0.0f), R);
 }

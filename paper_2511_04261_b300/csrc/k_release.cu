@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
     extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ SegTiles st;
     __shared__ uint8_t rlist[kSegMaxTiles];
-    __shared__ int32_t rtile[kMaxK], rcell[kMaxK + 1], rcs[kMaxK], rnb[kMaxK];
+    __shared__ int32_t rtile[kMaxK], rcell[kMaxK + 1], rcs[kMaxK], rnb[kMaxK], rlcs[kMaxK];
     constexpr int oes = kOutF32 ? 4 : 1;
     uint8_t *gseg = dyn;
     uint8_t *stage = dyn + fs.stage_off;
@@ -599,6 +599,7 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
                     rcell[r] = cb;
                     rcs[r] = cs;
                     rnb[r] = g.grid[r] / g.g;
+                    rlcs[r] = (cs & (cs - 1)) == 0 ? __ffs(cs) - 1 : -1;
                 }
                 tb += n;
                 cb += n * cs * cs;
@@ -614,13 +615,20 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
         for (int e = threadIdx.x; e < ncell; e += kThr) {
             int r = 0;
             while (r + 1 < g.K && e >= rcell[r + 1]) ++r;
-            const int cs = rcs[r], local = e - rcell[r];
-            const bool p2 = (cs & (cs - 1)) == 0;
-            const int lcs = __ffs(cs) - 1;
-            const int k = p2 ? local >> (2 * lcs) : local / (cs * cs);
-            const int c = local - k * cs * cs;
+            const int cs = rcs[r], local = e - rcell[r], lcs = rlcs[r];
+            int k, c, cy, cx;
+            if (lcs >= 0) {  // power-of-two cells per tile side: shifts and masks (uniform across the warp)
+                k = local >> (2 * lcs);
+                c = local & ((1 << (2 * lcs)) - 1);
+                cy = c >> lcs;
+                cx = c & (cs - 1);
+            } else {
+                k = local / (cs * cs);
+                c = local - k * cs * cs;
+                cy = c / cs;
+                cx = c - cy * cs;
+            }
             const int t = rlist[rtile[r] + k];
-            const int cy = p2 ? c >> lcs : c / cs, cx = c - cy * cs;
             const int tx = tx0 + t, nb = rnb[r];
             uint32_t S[4] = {0u, 0u, 0u, 0u};
             gblock_sum_any<C>(gs16 + (size_t)(cy * nb) * gsv + (size_t)(t * gcs + cx * nb) * C, (size_t)gsv, nb, S);
