@@ -170,45 +170,47 @@ __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, cons
         }
         const int bA = st.b[tA], bB = st.b[tB], csA = st.cs[tA], csB = st.cs[tB];
         const bool full = o + 16 <= row_bytes;
-        // cell bands followed incrementally: band of row j, and the row where it ends
+        // cell bands followed incrementally: band of row j, and the row where it ends.  Every lane walks the
+        // same rows (the store loop never diverges); a lane rebuilds its vector only where its band changes.
         int bandA = (bA & (bA - 1)) == 0 ? j0 >> (__ffs(bA) - 1) : j0 / bA;
         int bandB = (bB & (bB - 1)) == 0 ? j0 >> (__ffs(bB) - 1) : j0 / bB;
         int endA = (bandA + 1) * bA, endB = (bandB + 1) * bB;
-        int j = j0;
-        while (j < j1) {
-            const int jn = min(j1, min(endA, endB));
-            const int baseA = st.base[tA] + bandA * csA, baseB = st.base[tB] + bandB * csB;
-            uint4 vec;
+        const int b0A = st.base[tA], b0B = st.base[tB];
+        auto build = [&]() -> uint4 {
+            const int baseA = b0A + bandA * csA, baseB = b0B + bandB * csB;
             if (kOutF32) {
                 float4 pv[NPX];
 #pragma unroll
                 for (int l = 0; l < NPX; ++l) pv[l] = reinterpret_cast<const float4 *>(stage)[(inB[l] ? baseB : baseA) + cc[l]];
-                vec = build_f32_phase<C>(p, pv);
+                return build_f32_phase<C>(p, pv);
             } else {
                 uint32_t pv[NPX];
 #pragma unroll
                 for (int l = 0; l < NPX; ++l) pv[l] = reinterpret_cast<const uint32_t *>(stage)[(inB[l] ? baseB : baseA) + cc[l]];
-                vec = build_u8_phase<C>(p, pv);
+                return build_u8_phase<C>(p, pv);
             }
-            uint8_t *dst = orow0 + (int64_t)j * out_pitch + o;
-            for (int rr = j; rr < jn; ++rr, dst += out_pitch) {
-                if (full) {
-                    *reinterpret_cast<uint4 *>(dst) = vec;
-                } else {
-                    for (int i = 0; o + i < row_bytes; ++i) {
-                        const uint32_t wv = i < 4 ? vec.x : (i < 8 ? vec.y : (i < 12 ? vec.z : vec.w));
-                        dst[i] = (uint8_t)(wv >> (8 * (i & 3)));
-                    }
+        };
+        uint4 vec = build();
+        uint8_t *dst = orow0 + (int64_t)j0 * out_pitch + o;
+        for (int j = j0; j < j1; ++j, dst += out_pitch) {
+            if (j == endA || j == endB) {
+                if (j == endA) {
+                    ++bandA;
+                    endA += bA;
                 }
+                if (j == endB) {
+                    ++bandB;
+                    endB += bB;
+                }
+                vec = build();
             }
-            j = jn;
-            if (j == endA) {
-                ++bandA;
-                endA += bA;
-            }
-            if (j == endB) {
-                ++bandB;
-                endB += bB;
+            if (full) {
+                *reinterpret_cast<uint4 *>(dst) = vec;
+            } else {
+                for (int i = 0; o + i < row_bytes; ++i) {
+                    const uint32_t wv = i < 4 ? vec.x : (i < 8 ? vec.y : (i < 12 ? vec.z : vec.w));
+                    dst[i] = (uint8_t)(wv >> (8 * (i & 3)));
+                }
             }
         }
     }
