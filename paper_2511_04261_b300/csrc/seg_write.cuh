@@ -73,8 +73,25 @@ __device__ __forceinline__ uint4 build_f32(const float4 *pv) {
     return make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]), __float_as_uint(o[3]));
 }
 
+// C = 3 with a runtime phase and no branch: word k of the chunk draws on pixels a and a + 1 with
+// a = (p + 4k) / 3, which for p in {0, 1, 2} takes at most two values per word, so each word is one byte
+// permute of two selected pixels with a selected selector (neighbouring lanes have different phases).
+__device__ __forceinline__ uint4 build_u8_c3(int p, const uint32_t *pv) {
+    constexpr uint32_t s00 = word_sel<3>(0), s01 = word_sel<3>(1), s02 = word_sel<3>(2);
+    constexpr uint32_t s10 = word_sel<3>(4), s11 = word_sel<3>(5), s12 = word_sel<3>(6);
+    constexpr uint32_t s20 = word_sel<3>(8), s21 = word_sel<3>(9), s22 = word_sel<3>(10);
+    constexpr uint32_t s30 = word_sel<3>(12), s31 = word_sel<3>(13), s32 = word_sel<3>(14);
+    const bool p0 = p == 0, p1 = p == 1;
+    const uint32_t w0 = __byte_perm(pv[0], pv[1], p0 ? s00 : (p1 ? s01 : s02));
+    const uint32_t w1 = p == 2 ? __byte_perm(pv[2], pv[3], s12) : __byte_perm(pv[1], pv[2], p0 ? s10 : s11);
+    const uint32_t w2 = p0 ? __byte_perm(pv[2], pv[3], s20) : __byte_perm(pv[3], pv[4], p1 ? s21 : s22);
+    const uint32_t w3 = __byte_perm(pv[4], pv[5], p0 ? s30 : (p1 ? s31 : s32));
+    return make_uint4(w0, w1, w2, w3);
+}
+
 template <int C>
 __device__ __forceinline__ uint4 build_u8_phase(int p, const uint32_t *pv) {
+    if (C == 3) return build_u8_c3(p, pv);
     if (p == 0) return build_u8<C, 0>(pv);
     if (C > 1 && p == 1) return build_u8<C, (C > 1 ? 1 : 0)>(pv);
     if (C > 2 && p == 2) return build_u8<C, (C > 2 ? 2 : 0)>(pv);
