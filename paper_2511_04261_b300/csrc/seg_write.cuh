@@ -155,7 +155,7 @@ __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, cons
     // write phase: thread = (16-byte column chunk, group of rows); no barrier until the next item
     const int row_bytes = vpx * C * oes;
     const int nch = (row_bytes + 15) >> 4;
-    int RG = (2 * nthr + nch - 1) / nch;  // about two (chunk, row group) units per thread
+    int RG = (nthr + nch - 1) / nch;  // about one (chunk, row group) unit per thread: long row runs per set-up
     RG = RG < 1 ? 1 : (RG > jmax ? jmax : RG);
     const int rpg = (jmax + RG - 1) / RG;
     const int last_px = ns * T - 1;
@@ -209,7 +209,28 @@ __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, cons
         };
         uint4 vec = build();
         uint8_t *dst = orow0 + (int64_t)j0 * out_pitch + o;
-        for (int j = j0; j < j1; ++j, dst += out_pitch) {
+        int j = j0;
+        if (full && (bA & 3) == 0 && (bB & 3) == 0 && (j0 & 3) == 0) {
+            // bands of multiples of 4 rows: the band check once per 4 rows
+            for (; j + 4 <= j1; j += 4, dst += 4 * out_pitch) {
+                if (j == endA || j == endB) {
+                    if (j == endA) {
+                        ++bandA;
+                        endA += bA;
+                    }
+                    if (j == endB) {
+                        ++bandB;
+                        endB += bB;
+                    }
+                    vec = build();
+                }
+                *reinterpret_cast<uint4 *>(dst) = vec;
+                *reinterpret_cast<uint4 *>(dst + out_pitch) = vec;
+                *reinterpret_cast<uint4 *>(dst + 2 * out_pitch) = vec;
+                *reinterpret_cast<uint4 *>(dst + 3 * out_pitch) = vec;
+            }
+        }
+        for (; j < j1; ++j, dst += out_pitch) {
             if (j == endA || j == endB) {
                 if (j == endA) {
                     ++bandA;
