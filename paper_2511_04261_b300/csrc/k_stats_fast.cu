@@ -47,7 +47,7 @@ __device__ __forceinline__ uint4 ld_stream(const void *p) {
 }
 
 template <int C, int G>
-__global__ void __launch_bounds__(kThreads, 6) k_tile_stats_fast(const Geom g, const CallArgs a) {
+__global__ void __launch_bounds__(kThreads) k_tile_stats_fast(const Geom g, const CallArgs a) {
     using K = Chunk<C, G>;
     const int T = g.T;
     const int NQ = g.N * C / K::BYTES;   // chunks per image row (no column padding)
