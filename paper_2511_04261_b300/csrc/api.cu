@@ -257,7 +257,7 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
         if (g.idx_bits < 1) g.idx_bits = 1;
         const unsigned __int128 n = (unsigned __int128)TC * (unsigned __int128)T;
         const unsigned __int128 kmax = (n * 255u) * (n * 255u) / 4u + 1u;
-        if (bits_for(kmax) + g.idx_bits > 64) return fail(DP_PIX_E_UNSUPPORTED, "rank key does not fit 64 bits");
+        if (bits_for(kmax) + g.idx_bits > 63) return fail(DP_PIX_E_UNSUPPORTED, "rank key does not fit 63 bits");
         g.val_bits = bits_for(kmax) + g.idx_bits;
         g.var_onepass = (g.g >= 4 && g.g <= 16) ? 1 : 0;
     }

@@ -287,6 +287,42 @@ def test_reconstruct_rejects_malformed_record():
     assert not out.any()
 
 
+@pytest.mark.parametrize("M,N,grids", [
+    (32, 32, [32, 16, 8, 4]),      # one tile, four classes: three boundaries lie beyond the last rank
+    (32, 96, [32, 16, 8, 4]),      # three tiles
+    (200, 330, [32, 16, 8, 4]),    # 77 tiles
+    (720, 1280, [16, 8]),          # 3600 tiles
+    (1080, 1920, [16, 8]),         # 8160 tiles
+    (720, 1280, [8, 4]),           # 14400 tiles
+    (2160, 3840, [32, 16, 8, 4]),  # 4K frames: 8160 tiles of 32 x 32
+])
+def test_variance_classes_every_rank_path(M, N, grids):
+    """The tile -> class map (variance quantile classes: tiles ranked by (key, tile index), class
+    floor(K rank / n)) equals the oracle's.  Frames: the moving-rectangle clip; the same, flat in its upper
+    half (hundreds of tiles share the key 0); one random tile repeated over the frame (equal keys away from
+    the mirrored edges, so a boundary's histogram bin is full and the kernel sorts); uniform noise (keys
+    within a few per cent of each other)."""
+    T = math.lcm(*grids)
+    clip = np.concatenate([synth.moving_rect_clip(seed=M + N, frames=2, M=M, N=N)] * 2)
+    clip[1, : M // 2] = 17
+    rng = np.random.default_rng(M * N)
+    tile = rng.integers(0, 256, size=(T, T, 3), dtype=np.uint8)
+    clip[2] = np.tile(tile, (-(-M // T), -(-N // T), 1))[:M, :N]
+    clip[3] = rng.integers(0, 256, size=(M, N, 3), dtype=np.uint8)
+    kw = dict(M=M, N=N, C=3, grids=grids, eps=[1.0] * len(grids), source=O.SRC_VARIANCE, dtype=O.DT_F32, seed=3,
+              m=16)
+    plan = P.Plan(**kw)
+    recs_d = plan.release(torch.from_numpy(clip).cuda(), None)
+    torch.cuda.synchronize()
+    assert P.dp_pix_status() == 0
+    for i in range(len(clip)):
+        got = O.record_map(np.frombuffer(P.dp_pix_store(recs_d[i]), np.uint8))
+        exp = O.classify(clip[i], None, **kw)
+        assert np.array_equal(got, exp), (i, int((got != exp).sum()))
+        K, n = len(grids), exp.size  # class q holds the ranks r with floor(K r / n) = q
+        assert np.array_equal(np.bincount(exp.reshape(-1), minlength=K), np.bincount(K * np.arange(n) // n, minlength=K))
+
+
 # ------------------------------------------------------------------------------------------------------
 # Full-size workloads at the benchmark's launch configuration, sampled against the oracle
 # ------------------------------------------------------------------------------------------------------
