@@ -4,10 +4,12 @@ The library is plain CUDA C++ with a C ABI (include/dppix.h); it links the CUDA 
 has no torch dependency.  `build()` is idempotent: it rebuilds only when a source is newer than the
 library.
 """
+import concurrent.futures
 import glob
 import os
 import subprocess
 import sys
+import tempfile
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
@@ -30,15 +32,24 @@ def _stale():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles each source to an object in parallel (one nvcc per file), then links the shared library."""
     if not force and not _stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE, "-o", tmp, *sources()]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+             "-I", INCLUDE]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
+        flags.insert(0, "-Xptxas=-v")
+    with tempfile.TemporaryDirectory(prefix="dppix_build_") as tmpdir:
+        objs = [os.path.join(tmpdir, os.path.basename(src) + ".o") for src in sources()]
+        jobs = max(1, min(len(objs), os.cpu_count() or 1))
+        with concurrent.futures.ThreadPoolExecutor(max_workers=jobs) as pool:
+            futs = [pool.submit(subprocess.run, [nvcc, *flags, "-c", src, "-o", obj], check=True)
+                    for src, obj in zip(sources(), objs)]
+            for fut in futs:
+                fut.result()
+        tmp = LIB + ".tmp%d" % os.getpid()
+        subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
     return LIB
 
