@@ -9,13 +9,13 @@ import glob
 import os
 import subprocess
 import sys
-import tempfile
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libdppix.so")
+OBJDIR = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,7 +32,8 @@ def _stale():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compiles each source to an object in parallel (one nvcc per file), then links the shared library."""
+    """Compiles each stale source to an object under _build/ (one nvcc per file, in parallel), then links the
+    shared library.  An object is stale when it is older than its source, a header, or this file."""
     if not force and not _stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
@@ -40,16 +41,25 @@ def build(force: bool = False, verbose: bool = False) -> str:
              "-I", INCLUDE]
     if verbose:
         flags.insert(0, "-Xptxas=-v")
-    with tempfile.TemporaryDirectory(prefix="dppix_build_") as tmpdir:
-        objs = [os.path.join(tmpdir, os.path.basename(src) + ".o") for src in sources()]
-        jobs = max(1, min(len(objs), os.cpu_count() or 1))
-        with concurrent.futures.ThreadPoolExecutor(max_workers=jobs) as pool:
-            futs = [pool.submit(subprocess.run, [nvcc, *flags, "-c", src, "-o", obj], check=True)
-                    for src, obj in zip(sources(), objs)]
-            for fut in futs:
-                fut.result()
-        tmp = LIB + ".tmp%d" % os.getpid()
-        subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
+    os.makedirs(OBJDIR, exist_ok=True)
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__]
+    newest_header = max(os.path.getmtime(h) for h in headers)
+    objs, todo = [], []
+    for src in sources():
+        obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
+        objs.append(obj)
+        if force or verbose or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), newest_header):
+            todo.append((src, obj))
+    jobs = max(1, min(len(todo), os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=jobs) as pool:
+        futs = [pool.submit(subprocess.run, [nvcc, *flags, "-c", src, "-o", obj + ".tmp"], check=True)
+                for src, obj in todo]
+        for fut in futs:
+            fut.result()
+    for _, obj in todo:
+        os.replace(obj + ".tmp", obj)
+    tmp = LIB + ".tmp%d" % os.getpid()
+    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
     return LIB
 
