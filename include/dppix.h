@@ -155,7 +155,7 @@ DPPIX_API int dp_pix_plan_destroy(dp_pix_plan_t plan);
  * before the plan is shared; a call must not race with releases that use the plan.
  *   DP_PIX_TUNE_FUSED_PX       pixel columns per work item of the fused release + reconstruction,
  *                              64..2048 (default 1024; rounded down to whole, aligned tiles)
- *   DP_PIX_TUNE_FUSED_THREADS  threads per block of that kernel, 128 or 256 (default 128)
+ *   DP_PIX_TUNE_FUSED_THREADS  threads per block of that kernel, 96, 128, 192 or 256 (default 128)
  *   DP_PIX_TUNE_SPLIT          dp_pix_release_reconstruct runs its frames in this many chunks on the
  *                              library's side streams, forked from and joined to the caller's stream with
  *                              events, 1..8 (default 1: everything on the caller's stream)

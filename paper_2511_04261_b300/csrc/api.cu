@@ -366,7 +366,8 @@ int dp_pix_plan_tune(dp_pix_plan_t plan, int knob, int value) {
             plan->g.fused_px = value;
             return DP_PIX_OK;
         case DP_PIX_TUNE_FUSED_THREADS:
-            if (value != 128 && value != 256) return fail(DP_PIX_E_INVALID_ARG, "fused threads must be 128 or 256");
+            if (value != 96 && value != 128 && value != 192 && value != 256)
+                return fail(DP_PIX_E_INVALID_ARG, "fused threads must be 96, 128, 192 or 256");
             plan->g.fused_threads = value;
             return DP_PIX_OK;
         case DP_PIX_TUNE_SPLIT:

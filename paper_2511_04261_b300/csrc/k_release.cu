@@ -757,9 +757,13 @@ cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, in
     }
     if (seg < sm) return cudaErrorNotSupported;
     const int thr = g.fused_threads;
-#define DPPIX_ER(CC, F)                                                              \
-    return thr == 128 ? launch_er<CC, F, 128>(g, a, out, out_frame_stride, out_pitch, fs, s) \
-                      : launch_er<CC, F, 256>(g, a, out, out_frame_stride, out_pitch, fs, s)
+#define DPPIX_ER(CC, F)                                                                        \
+    switch (thr) {                                                                             \
+        case 96: return launch_er<CC, F, 96>(g, a, out, out_frame_stride, out_pitch, fs, s);   \
+        case 192: return launch_er<CC, F, 192>(g, a, out, out_frame_stride, out_pitch, fs, s); \
+        case 256: return launch_er<CC, F, 256>(g, a, out, out_frame_stride, out_pitch, fs, s); \
+        default: return launch_er<CC, F, 128>(g, a, out, out_frame_stride, out_pitch, fs, s);  \
+    }
     if (oes == 4) {
         switch (g.C) {
             case 1: DPPIX_ER(1, 1);

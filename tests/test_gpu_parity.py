@@ -451,7 +451,7 @@ def test_release_reconstruct_launch_shapes_do_not_change_results(ot):
     t = torch.from_numpy(imgs).cuda()
     base = None
     for px, thr, split in [(64, 128, 1), (96, 256, 2), (512, 128, 4), (512, 256, 1), (1024, 128, 3),
-                           (2048, 256, 4), (2048, 128, 1)]:
+                           (2048, 256, 4), (2048, 128, 1), (960, 192, 1), (640, 96, 2)]:
         if True:
             plan = P.Plan(**kw).tune(P.TUNE_FUSED_PX, px).tune(P.TUNE_FUSED_THREADS, thr).tune(P.TUNE_SPLIT, split)
             recs, img = plan.release_reconstruct(t, out_type=ot)
