@@ -122,15 +122,41 @@ __device__ __forceinline__ void batch_load(const BatchEntry *tab, int i, BatchSh
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64 multiplies with the
 // published multipliers, the key bumped by the published Weyl constants between rounds.
 // ---------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void philox_round(uint4 &c, uint2 &k) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+}
+
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 #pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-        k.x += 0x9E3779B9u;
-        k.y += 0xBB67AE85u;
-    }
+    for (int round = 0; round < 10; ++round) philox_round(c, k);
+    return c;
+}
+
+// Philox-4x32-10 for counters that differ only in their first word: philox_prep does the first round's
+// work on the other three words once, philox_finish completes one counter (same words as philox4x32_10).
+struct PhiloxPrep {
+    uint32_t x1, y1, zxor;  // round-1 outputs that do not depend on the first word; c3 ^ k.y
+    uint2 k1;               // the key after round 1
+};
+
+__device__ __forceinline__ PhiloxPrep philox_prep(uint32_t c1, uint32_t c2, uint32_t c3, uint2 k) {
+    PhiloxPrep p;
+    p.x1 = __umulhi(0xCD9E8D57u, c2) ^ c1 ^ k.x;
+    p.y1 = 0xCD9E8D57u * c2;
+    p.zxor = c3 ^ k.y;
+    p.k1 = make_uint2(k.x + 0x9E3779B9u, k.y + 0xBB67AE85u);
+    return p;
+}
+
+__device__ __forceinline__ uint4 philox_finish(const PhiloxPrep &p, uint32_t c0) {
+    uint4 c = make_uint4(p.x1, p.y1, __umulhi(0xD2511F53u, c0) ^ p.zxor, 0xD2511F53u * c0);
+    uint2 k = p.k1;
+#pragma unroll
+    for (int round = 1; round < 10; ++round) philox_round(c, k);
     return c;
 }
 
@@ -148,37 +174,29 @@ __device__ __forceinline__ uint4 cell_noise_words(uint64_t seed, uint32_t cell_i
 
 // Laplace(0, sigma) by the inverse CDF at u = (x + 1/2) / 2^32 (Eq. 9).  With k = x (lower half) or
 // k = 2^32-1-x (upper half, sign flipped), ln(2u) or ln(2(1-u)) is ln t, t = (k + 1/2) / 2^31 in (0, 1).
-// ln t is evaluated without a library call and without a branch, so that the lanes of a warp never split:
-//  - t < 1/sqrt(2): t = 2^e m with m in [1/sqrt(2), sqrt(2)) taken from the float's exponent and mantissa,
-//    and y = m - 1 (exact);
-//  - t >= 1/sqrt(2): e = 0 and y = -(j + 1/2) / 2^31 with the exact integer j = 2^31-1-k, so nothing cancels
-//    near t = 1;
-// then ln(1 + y) = 2 atanh(s), s = y / (2 + y), |s| <= 0.172, from the odd series of atanh
-// (Abramowitz & Stegun 4.5.64 with 4.1.27) truncated after s^11 (relative truncation error < 3e-9).
+// ln t is evaluated without a branch, so that the lanes of a warp never split; both halves are computed
+// and one is selected:
+//  - t < 1/sqrt(2): ln 2 * __log2f(t).  |ln t| > 0.34 there, so the intrinsic's documented error (absolute
+//    2^-22 on [1/2, 2], 2 ulp elsewhere) stays a relative error below 1e-6;
+//  - t >= 1/sqrt(2): y = t - 1 = -(j + 1/2) / 2^31 from the exact integer j = 2^31-1-k, so nothing cancels
+//    near t = 1, and ln(1 + y) = 2 atanh(s), s = y / (2 + y), |s| <= 0.172, from the odd series of atanh
+//    (Abramowitz & Stegun 4.5.64 with 4.1.27) truncated after s^11 (relative truncation error < 3e-9).
 __device__ __forceinline__ float laplace_from_word(uint32_t x, float sigma) {
     const bool upper = (x >> 31) != 0u;
-    const uint32_t k = upper ? ~x : x;                         // [0, 2^31)
-    const bool low = k <= 1518500249u;                          // t < 1/sqrt(2)
-    // lower branch: t as a normal float in [2^-32, 0.7071), split into 2^e * m
-    const float t = (__uint2float_rn(k) + 0.5f) * 0x1p-31f;
-    const int bits = __float_as_int(t);
-    int e = ((bits >> 23) & 0xFF) - 127;
-    float m = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);  // [1, 2)
-    const bool big = m > 1.41421356f;
-    m = big ? 0.5f * m : m;
-    e = big ? e + 1 : e;
-    // upper branch: y from the exact distance to 1
+    const uint32_t k = upper ? ~x : x;    // [0, 2^31)
+    const bool low = k <= 1518500249u;     // t < 1/sqrt(2)
+    const float t = fmaf(__uint2float_rn(k), 0x1p-31f, 0x1p-32f);
+    const float ln_low = 0.693147180559945309f * __log2f(t);
     const uint32_t j = 0x7FFFFFFFu - k;
-    const float y = low ? m - 1.0f : -(__uint2float_rn(j) + 0.5f) * 0x1p-31f;
-    const float ef = low ? (float)e : 0.0f;
+    const float y = -fmaf(__uint2float_rn(j), 0x1p-31f, 0x1p-32f);
     const float sr = __fdividef(y, 2.0f + y);
     const float z = sr * sr;
     float poly = fmaf(z, 1.0f / 11.0f, 1.0f / 9.0f);
     poly = fmaf(z, poly, 1.0f / 7.0f);
     poly = fmaf(z, poly, 1.0f / 5.0f);
     poly = fmaf(z, poly, 1.0f / 3.0f);
-    const float l1p = 2.0f * fmaf(sr * z, poly, sr);          // ln(1 + y)
-    const float lnt = fmaf(ef, 0.693147180559945309f, l1p);
+    const float ln_high = 2.0f * fmaf(sr * z, poly, sr);  // ln(1 + y)
+    const float lnt = low ? ln_low : ln_high;
     return upper ? -sigma * lnt : sigma * lnt;
 }
 

@@ -369,23 +369,20 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats(const Geom g, const Cal
     }
 }
 
-// Noise, clip and store of one (cell, channel) set (Alg. 3 steps 9-10 and 15-17).
-// ov (optional) receives the value a reconstruction reads back from the stored element (Sec. VI-F).
-__device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint8_t *dst, const uint32_t *S, int r,
-                                          uint32_t cell_idx, uint64_t frame, uint32_t sid, float *ov = nullptr) {
-    const int C = g.C;
-    uint4 words = make_uint4(0, 0, 0, 0);
-    if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
-        words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame);
+// Noise, clip and store of one cell's C channels (Alg. 3 steps 9-10 and 15-17) from its Philox words;
+// sigma, b^2 and 1/b^2 (0 when not exact) of its region.  ov (optional) receives the value a
+// reconstruction reads back from the stored element (Sec. VI-F).
+__device__ __forceinline__ void emit_values(const Geom &g, int C, uint8_t *dst, const uint32_t *S, uint4 words,
+                                            float sigma, float b2, float inv_b2, float *ov) {
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
         if (ch >= C) break;
         if (g.dtype == DP_PIX_REC_SUM_U32) {
             reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
-            if (ov) ov[ch] = __fdiv_rn(__uint2float_rn(S[ch]), g.b2_f[r]);
+            if (ov) ov[ch] = __fdiv_rn(__uint2float_rn(S[ch]), b2);
         } else {
-            const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), g.sigma_f[r]);
-            const float v = noisy_mean(S[ch], g.b2_f[r], g.inv_b2_f[r], eta, g.R_f);
+            const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), sigma);
+            const float v = noisy_mean(S[ch], b2, inv_b2, eta, g.R_f);
             if (g.dtype == DP_PIX_REC_F32) {
                 reinterpret_cast<float *>(dst)[ch] = v;
                 if (ov) ov[ch] = v;
@@ -396,6 +393,14 @@ __device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint
             }
         }
     }
+}
+
+__device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint8_t *dst, const uint32_t *S, int r,
+                                          uint32_t cell_idx, uint64_t frame, uint32_t sid, float *ov = nullptr) {
+    uint4 words = make_uint4(0, 0, 0, 0);
+    if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
+        words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame);
+    emit_values(g, g.C, dst, S, words, g.sigma_f[r], g.b2_f[r], g.inv_b2_f[r], ov);
 }
 
 // Sum of an nb x nb block of g-cells (C u16 channel sums each; rows rowvals values apart) into S[0..C).
@@ -608,41 +613,52 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
         }
         __syncthreads();
         // ---- B: cells, region by region ----
-        const int ncell = rcell[g.K];
         const uint64_t frame = key_frame(a, f);
         const uint32_t sid = key_stream(a, f);
+        const bool noisy = !g.noise_free && g.dtype != DP_PIX_REC_SUM_U32;
         const uint16_t *gs16 = reinterpret_cast<const uint16_t *>(gseg);
-        for (int e = threadIdx.x; e < ncell; e += kThr) {
-            int r = 0;
-            while (r + 1 < g.K && e >= rcell[r + 1]) ++r;
-            const int cs = rcs[r], local = e - rcell[r], lcs = rlcs[r];
-            int k, c, cy, cx;
-            if (lcs >= 0) {  // power-of-two cells per tile side: shifts and masks (uniform across the warp)
-                k = local >> (2 * lcs);
-                c = local & ((1 << (2 * lcs)) - 1);
-                cy = c >> lcs;
-                cx = c & (cs - 1);
-            } else {
-                k = local / (cs * cs);
-                c = local - k * cs * cs;
-                cy = c / cs;
-                cx = c - cy * cs;
-            }
-            const int t = rlist[rtile[r] + k];
-            const int tx = tx0 + t, nb = rnb[r];
-            uint32_t S[4] = {0u, 0u, 0u, 0u};
-            gblock_sum_any<C>(gs16 + (size_t)(cy * nb) * gsv + (size_t)(t * gcs + cx * nb) * C, (size_t)gsv, nb, S);
-            const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)(tx * cs + cx);
-            float ov[4] = {0.f, 0.f, 0.f, 0.f};
-            emit_cell(g, a, rec + st.off[t] + (uint64_t)c * C * g.es, S, r, cell_idx, frame, sid, ov);
-            const int si = st.base[t] + c;  // the stage keeps segment order for the row writer
-            if (kOutF32) {
-                reinterpret_cast<float4 *>(stage)[si] = make_float4(ov[0], ov[1], ov[2], ov[3]);
-            } else {
-                uint32_t pk = 0;
+        for (int r = 0; r < g.K; ++r) {
+            const int e0 = rcell[r], e1 = rcell[r + 1];
+            if (e0 >= e1) continue;
+            const int cs = rcs[r], lcs = rlcs[r], nb = rnb[r], tb = rtile[r];
+            const uint32_t crow = (uint32_t)(g.GC * cs);  // cells per row of the frame's padded b_r-grid
+            const float sigma = g.sigma_f[r], b2 = g.b2_f[r], inv_b2 = g.inv_b2_f[r];
+            const PhiloxPrep pp = philox_prep((uint32_t)r | (sid << 8), (uint32_t)frame, (uint32_t)(frame >> 32),
+                                              make_uint2((uint32_t)g.seed, (uint32_t)(g.seed >> 32)));
+            // the item's cells go round robin over the threads (cell e to thread e mod kThr) across regions,
+            // so that a region's few large cells do not all land on the first warp
+            int e = e0 + (int)(((uint32_t)threadIdx.x + (uint32_t)kThr - (uint32_t)e0 % (uint32_t)kThr) % (uint32_t)kThr);
+            for (; e < e1; e += kThr) {
+                const int local = e - e0;
+                int k, c, cy, cx;
+                if (lcs >= 0) {  // power-of-two cells per tile side: shifts and masks (uniform across the warp)
+                    k = local >> (2 * lcs);
+                    c = local & ((1 << (2 * lcs)) - 1);
+                    cy = c >> lcs;
+                    cx = c & (cs - 1);
+                } else {
+                    k = local / (cs * cs);
+                    c = local - k * cs * cs;
+                    cy = c / cs;
+                    cx = c - cy * cs;
+                }
+                const int t = rlist[tb + k];
+                const int tx = tx0 + t;
+                uint32_t S[4] = {0u, 0u, 0u, 0u};
+                gblock_sum_any<C>(gs16 + (size_t)(cy * nb) * gsv + (size_t)(t * gcs + cx * nb) * C, (size_t)gsv, nb, S);
+                const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * crow + (uint32_t)(tx * cs + cx);
+                float ov[4] = {0.f, 0.f, 0.f, 0.f};
+                const uint4 words = noisy ? philox_finish(pp, cell_idx) : make_uint4(0, 0, 0, 0);
+                emit_values(g, C, rec + st.off[t] + (uint64_t)c * C * g.es, S, words, sigma, b2, inv_b2, ov);
+                const int si = st.base[t] + c;  // the stage keeps segment order for the row writer
+                if (kOutF32) {
+                    reinterpret_cast<float4 *>(stage)[si] = make_float4(ov[0], ov[1], ov[2], ov[3]);
+                } else {
+                    uint32_t pk = 0;
 #pragma unroll
-                for (int ch = 0; ch < C; ++ch) pk |= to_u8(ov[ch]) << (8 * ch);
-                reinterpret_cast<uint32_t *>(stage)[si] = pk;
+                    for (int ch = 0; ch < C; ++ch) pk |= to_u8(ov[ch]) << (8 * ch);
+                    reinterpret_cast<uint32_t *>(stage)[si] = pk;
+                }
             }
         }
         __syncthreads();
