@@ -24,7 +24,7 @@ def _labels(rng, M, N, grids):
 # ------------------------------------------------------------------------------------------------------
 def test_philox_words_bit_exact_and_laplace():
     rng = np.random.default_rng(1)
-    n = 4096
+    n = 16384
     ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64)
     ctr[:4] = [[0, 0, 0, 0], [2**32 - 1] * 4, [1, 0, 0, 0], [0, 0, 0, 1]]
     seed = 0x1234567890ABCDEF
