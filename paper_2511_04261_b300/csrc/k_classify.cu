@@ -30,7 +30,7 @@ __device__ __forceinline__ void classify_row(const Geom &g, const CallArgs &a, i
         for (int q = threadIdx.x; q < ngrp; q += blockDim.x) {
             const int c0 = 4 * q, cnt = min(4, g.N - c0);
             uint32_t c[4] = {0u, 0u, 0u, 0u};
-#pragma unroll 4
+#pragma unroll 8
             for (int j = 0; j < T; ++j) {
                 const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
                 const uintptr_t addr = reinterpret_cast<uintptr_t>(src + (int64_t)sy * a.src_pitch) + 16u * (uint32_t)q;
@@ -105,17 +105,18 @@ __global__ void __launch_bounds__(kThreads) k_batch_classify(const BatchEntry *t
 cudaError_t launch_batch_classify(const BatchEntry *tab, uint32_t n_img, uint32_t items, int max_gc, int matte,
                                   cudaStream_t s) {
     const size_t smem = (size_t)max_gc * 4;
-    const int per_sm = 8;
+    // one wave of resident CTAs looping over the items (a second, partial wave would run its CTAs' whole
+    // shares on an otherwise idle GPU)
+    const void *kern = matte ? reinterpret_cast<const void *>(k_batch_classify<true>)
+                             : reinterpret_cast<const void *>(k_batch_classify<false>);
+    const int per_sm = launch_prep(kern, kThreads, smem);
     const int grid = (int)std::min<uint64_t>(items, (uint64_t)per_sm * sm_count());
-    if (matte) {
-        prof_begin("k_batch_classify", s);
+    prof_begin("k_batch_classify", s);
+    if (matte)
         k_batch_classify<true><<<grid, kThreads, smem, s>>>(tab, n_img, items);
-        prof_end("k_batch_classify", s);
-    } else {
-        prof_begin("k_batch_classify", s);
+    else
         k_batch_classify<false><<<grid, kThreads, smem, s>>>(tab, n_img, items);
-        prof_end("k_batch_classify", s);
-    }
+    prof_end("k_batch_classify", s);
     return cudaGetLastError();
 }
 

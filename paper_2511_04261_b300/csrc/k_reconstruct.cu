@@ -20,9 +20,17 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kRowBytes = 2048;     // generic path: shared-memory row pattern
-constexpr int kStageBytes = 32768;  // fast path: staged cell values of one segment
+constexpr int kStageBytes = 24576;  // fast path: staged cell values of one segment
 constexpr int kMaxSegPx = kSegMaxPx;
 constexpr int kMaxSegTiles = kSegMaxTiles;
+// Bytes of one row-pattern buffer of the u8 writer for rows of any alignment (C channels).
+__host__ __device__ constexpr int pat_stride(int C) { return 16 * (kMaxSegPx * C / 16 + 1); }
+
+// Dynamic shared memory of the fast path: stage | colinfo | two row patterns (u8 rows of any alignment).
+__host__ __device__ constexpr size_t fast_smem(int out_f32, int fast_c, int out_align) {
+    return (size_t)kStageBytes + kMaxSegPx * 4 +
+           (!out_f32 && fast_c > 0 && out_align != 16 ? 2 * (size_t)pat_stride(fast_c) : 0);
+}
 
 struct RecGeom {
     int32_t ok, fast;
@@ -145,14 +153,15 @@ __device__ void seg_tile_info(const uint8_t *rec, const RecGeom &rg, int ty, int
 
 template <int C, int kOutF32>
 __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i, int ty, int sg, uint8_t *obase,
-                          int64_t out_pitch, int out_align, uint8_t *stage, uint32_t *colinfo, SegTiles &st,
-                          uint32_t *cnt_s, int32_t *status) {
+                          int64_t out_pitch, int out_align, uint8_t *stage, uint32_t *colinfo, uint8_t *pat,
+                          SegTiles &st, uint32_t *cnt_s, int32_t *status) {
     constexpr int oes = kOutF32 ? 4 : 1;
     const int T = rg.T;
     const int tx0 = sg * rg.SR;
     const int ns = min(rg.SR, rg.GC - tx0);
     seg_tile_info(rec, rg, ty, tx0, ns, rec_i, status, st, cnt_s);
     seg_prefix_colinfo(st, ns, T, colinfo, threadIdx.x, blockDim.x);
+    if (!kOutF32 && out_align != 16) seg_row_groups(st, ns, T, threadIdx.x);
     __syncthreads();
     // cell values of the segment, converted once
     const int ncell = st.base[ns];
@@ -184,6 +193,9 @@ __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i,
     if (out_align == 16)
         seg_write_rows<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T), orow0,
                                    out_pitch, threadIdx.x, blockDim.x);
+    else if (!kOutF32)
+        seg_write_rows_pat<C>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T), orow0,
+                              out_pitch, pat, pat_stride(C), threadIdx.x, blockDim.x);
     else
         seg_write_rows_any<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T),
                                        orow0, out_pitch, threadIdx.x, blockDim.x);
@@ -267,7 +279,7 @@ template <int kOutF32, int kFastC>
 __global__ void __launch_bounds__(kThreads)
     k_reconstruct(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out, int64_t out_frame_stride,
                   int64_t out_pitch, int max_M, int max_N, int max_C, int out_align, int32_t *status) {
-    extern __shared__ __align__(16) uint8_t dyn[];  // fast path: stage[kStageBytes] then colinfo[kMaxSegPx]
+    extern __shared__ __align__(16) uint8_t dyn[];  // fast path: stage | colinfo | two row patterns
     __shared__ __align__(16) uint8_t rowpat[kRowBytes];
     __shared__ __align__(16) dp_pix_record_header hdr_s;
     __shared__ RecGeom rg;
@@ -276,6 +288,7 @@ __global__ void __launch_bounds__(kThreads)
     constexpr int oes = kOutF32 ? 4 : 1;
     uint8_t *stage = dyn;
     uint32_t *colinfo = reinterpret_cast<uint32_t *>(dyn + kStageBytes);
+    uint8_t *pat = dyn + kStageBytes + kMaxSegPx * 4;
     const uint32_t G = gridDim.x;
     const uint32_t per_rec = n <= G ? G / n : 1u;  // CTAs per record
     const uint32_t slots = n <= G ? n : G;         // records handled concurrently
@@ -301,7 +314,7 @@ __global__ void __launch_bounds__(kThreads)
                 const int ty = (int)(k / rg.nseg), sg = (int)(k - (uint64_t)ty * rg.nseg);
                 if (kFastC > 0 && rg.fast)
                     fast_item<(kFastC > 0 ? kFastC : 1), kOutF32>(rec, rg, i, ty, sg, obase, out_pitch, out_align, stage, colinfo,
-                                                                   st, cnt_s, status);
+                                                                   pat, st, cnt_s, status);
                 else
                     generic_item<kOutF32>(rec, rg, i, ty, sg, obase, out_pitch, out_align, rowpat, st, cnt_s, status);
             }
@@ -325,6 +338,7 @@ __global__ void __launch_bounds__(kThreads)
     constexpr int oes = kOutF32 ? 4 : 1;
     uint8_t *stage = dyn;
     uint32_t *colinfo = reinterpret_cast<uint32_t *>(dyn + kStageBytes);
+    uint8_t *pat = dyn + kStageBytes + kMaxSegPx * 4;
     int cur = -1;
     for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
         const int i = batch_find(tab, n_img, item, 3);
@@ -348,7 +362,7 @@ __global__ void __launch_bounds__(kThreads)
         for (int sg = 0; sg < rg.nseg; ++sg) {
             if (kFastC > 0 && rg.fast)
                 fast_item<(kFastC > 0 ? kFastC : 1), kOutF32>(rec, rg, (uint32_t)i, ty, sg, e.out, e.out_pitch, out_align, stage,
-                                                               colinfo, st, cnt_s, status);
+                                                               colinfo, pat, st, cnt_s, status);
             else
                 generic_item<kOutF32>(rec, rg, (uint32_t)i, ty, sg, e.out, e.out_pitch, out_align, rowpat, st, cnt_s,
                                       status);
@@ -359,7 +373,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int kOutF32, int kFastC>
 cudaError_t launch_brc(const BatchEntry *tab, uint32_t n_img, uint32_t items, int max_C, int out_align,
                        int32_t *status, cudaStream_t s) {
-    const size_t smem = kStageBytes + kMaxSegPx * 4;
+    const size_t smem = fast_smem(kOutF32, kFastC, out_align);
     auto kern = k_batch_reconstruct<kOutF32, kFastC>;
     const int per_sm = launch_prep(reinterpret_cast<const void *>(kern), kThreads, smem);
     const int grid = (int)std::min<uint64_t>(items, (uint64_t)per_sm * sm_count());
@@ -390,7 +404,7 @@ template <int kOutF32, int kFastC>
 cudaError_t launch_rc(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out, int64_t out_frame_stride,
                       int64_t out_pitch, int max_M, int max_N, int max_C, int out_align, int32_t *status,
                       cudaStream_t s) {
-    const size_t smem = kStageBytes + kMaxSegPx * 4;
+    const size_t smem = fast_smem(kOutF32, kFastC, out_align);
     auto kern = k_reconstruct<kOutF32, kFastC>;
     const int per_sm = launch_prep(reinterpret_cast<const void *>(kern), kThreads, smem);
     const int grid = per_sm * sm_count();

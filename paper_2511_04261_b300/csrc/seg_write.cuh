@@ -19,6 +19,8 @@ __device__ __forceinline__ uint32_t to_u8(float v) { return __float2uint_rn(fmin
 struct SegTiles {
     int32_t reg[kSegMaxTiles], b[kSegMaxTiles], cs[kSegMaxTiles], base[kSegMaxTiles + 1];
     uint64_t off[kSegMaxTiles];
+    uint32_t rowgrp[2][kMaxT / 32];  // row-group starts of the pattern writer, one mask per warp of tiles
+    int32_t gbase[2][kSegMaxTiles];  // pattern writer: first staged cell of each tile's band in a row group
 };
 
 // ---- vector assembly ----------------------------------------------------------------------------------
@@ -326,6 +328,121 @@ __device__ void seg_write_rows_any(const SegTiles &st, const uint32_t *colinfo, 
         } else {
             row[e] = (uint8_t)(reinterpret_cast<const uint32_t *>(stage)[idx] >> (8 * ch));
         }
+    }
+}
+
+// ---- rows of any alignment, u8 output, through row patterns --------------------------------------------
+// The rows of a segment fall into groups inside which every tile stays in one cell band: a group starts at
+// row j when j is a multiple of some tile's grid.  Each group's output row is built once in shared memory
+// and then stored to each row of the group with 16-byte stores at that row's own byte alignment (the pattern
+// read as a 32-byte window and funnel-shifted), the head and tail bytes one at a time.
+
+// Marks the group starts of the segment's rows (bit j of rowgrp[w][j / 32], w = the warp of tiles 0..31 or
+// 32..63).  Threads 0..63 of the group take part; the caller's next barrier publishes the masks.
+__device__ __forceinline__ void seg_row_groups(SegTiles &st, int ns, int T, int tid) {
+    if (tid < 64) {
+        uint32_t m[kMaxT / 32] = {0u, 0u, 0u, 0u};
+        if (tid < ns) {
+            const int b = st.b[tid];
+            for (int j = 0; j < T; j += b) m[j >> 5] |= 1u << (j & 31);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int q = 0; q < kMaxT / 32; ++q) m[q] |= __shfl_xor_sync(0xffffffffu, m[q], off);
+        if ((tid & 31) == 0)
+#pragma unroll
+            for (int q = 0; q < kMaxT / 32; ++q) st.rowgrp[tid >> 5][q] = m[q];
+    }
+}
+
+// First group start after row j, or jmax.
+__device__ __forceinline__ int seg_next_group(const SegTiles &st, int j, int jmax) {
+    for (int q = (j + 1) >> 5; q < kMaxT / 32; ++q) {
+        uint32_t m = st.rowgrp[0][q] | st.rowgrp[1][q];
+        if (q == ((j + 1) >> 5)) m &= ~0u << ((j + 1) & 31);
+        if (m != 0u) return min(jmax, 32 * q + __ffs(m) - 1);
+    }
+    return jmax;
+}
+
+// Band base of tile t for the row group starting at row j, into the buffer that the group after the current
+// one (which reads buffer buf) reads.
+__device__ __forceinline__ void st_gbase_next(SegTiles &st, int buf, int t, int j) {
+    st.gbase[buf ^ 1][t] = st.base[t] + (j / st.b[t]) * st.cs[t];
+}
+
+// Bytes h .. h + 15 of the 32 bytes lo:hi (h in 0..15).
+__device__ __forceinline__ uint4 window16(const uint4 &lo, const uint4 &hi, int h) {
+    const int sh = (h & 3) * 8;
+    switch (h >> 2) {
+        case 0: return make_uint4(__funnelshift_r(lo.x, lo.y, sh), __funnelshift_r(lo.y, lo.z, sh),
+                                  __funnelshift_r(lo.z, lo.w, sh), __funnelshift_r(lo.w, hi.x, sh));
+        case 1: return make_uint4(__funnelshift_r(lo.y, lo.z, sh), __funnelshift_r(lo.z, lo.w, sh),
+                                  __funnelshift_r(lo.w, hi.x, sh), __funnelshift_r(hi.x, hi.y, sh));
+        case 2: return make_uint4(__funnelshift_r(lo.z, lo.w, sh), __funnelshift_r(lo.w, hi.x, sh),
+                                  __funnelshift_r(hi.x, hi.y, sh), __funnelshift_r(hi.y, hi.z, sh));
+        default: return make_uint4(__funnelshift_r(lo.w, hi.x, sh), __funnelshift_r(hi.x, hi.y, sh),
+                                   __funnelshift_r(hi.y, hi.z, sh), __funnelshift_r(hi.z, hi.w, sh));
+    }
+}
+
+// Writes the jmax u8 output rows (vpx pixels each, first output byte orow0, any alignment) of a segment whose
+// cell values are staged (packed u8) and whose row groups seg_row_groups marked.  pat: two pattern buffers,
+// pat_stride bytes apart, each of at least 16 * (ceil(vpx C / 16) + 1) bytes (16-byte aligned).  Threads
+// tid = 0..nthr-1 of the group share the work; one barrier per row group.
+template <int C>
+__device__ void seg_write_rows_pat(SegTiles &st, const uint32_t *colinfo, const uint8_t *stage, int ns, int T,
+                                   int vpx, int jmax, uint8_t *orow0, int64_t out_pitch, uint8_t *pat, int pat_stride,
+                                   int tid, int nthr) {
+    constexpr int NPX = FastK<C>::NPX8;
+    const int row_bytes = vpx * C;
+    const int nch = (row_bytes + 15) >> 4;
+    const int last_px = ns * T - 1;
+    const uint32_t *stage32 = reinterpret_cast<const uint32_t *>(stage);
+    int buf = 0;
+    for (int ja = 0; ja < jmax;) {
+        const int jb = seg_next_group(st, ja, jmax);
+        uint8_t *P = pat + buf * pat_stride;
+        // each tile's band base for the next group, published by this group's barrier (the first group's
+        // bands are the tiles' first ones)
+        if (tid < ns && jb < jmax) st_gbase_next(st, buf, tid, jb);
+        const int32_t *gb = ja == 0 ? st.base : st.gbase[buf];
+        // the group's row (the band of row ja in every tile), one 16-byte chunk per thread step
+        for (int k = tid; k < nch; k += nthr) {
+            const int e0 = k << 4;
+            const int p = e0 % C, l0 = e0 / C;
+            const int lastp = min((e0 + 15) / C, last_px);
+            const uint32_t cl = colinfo[lastp];
+            const int tA = colinfo[min(l0, last_px)] >> 16, tB = cl >> 16;
+            const int baseA = gb[tA], baseB = gb[tB];
+            uint32_t pv[NPX];
+#pragma unroll
+            for (int l = 0; l < NPX; ++l) {
+                const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
+                pv[l] = stage32[((int)(v >> 16) != tA ? baseB : baseA) + (int)(v & 0xFFFFu)];
+            }
+            *reinterpret_cast<uint4 *>(P + 16 * k) = build_u8_phase<C>(p, pv);
+        }
+        __syncthreads();
+        // rows ja .. jb-1: unit k < nch of a row is its k-th aligned 16-byte chunk, unit nch its head and tail
+        const int U = nch + 1;
+        int jr = tid / U, k = tid - jr * U;
+        for (int w = tid; w < (jb - ja) * U; w += nthr, k += nthr, jr += wrap_count(k, U)) {
+            uint8_t *row = orow0 + (int64_t)(ja + jr) * out_pitch;
+            const int h = min((int)((16u - (uint32_t)(reinterpret_cast<uintptr_t>(row) & 15u)) & 15u), row_bytes);
+            const int nfull = (row_bytes - h) >> 4;
+            if (k < nfull) {
+                const uint4 lo = *reinterpret_cast<const uint4 *>(P + 16 * k);
+                const uint4 hi = *reinterpret_cast<const uint4 *>(P + 16 * k + 16);
+                *reinterpret_cast<uint4 *>(row + h + 16 * k) = window16(lo, hi, h);
+            } else if (k == nch) {
+                for (int i = 0; i < h; ++i) row[i] = P[i];
+                for (int i = h + 16 * nfull; i < row_bytes; ++i) row[i] = P[i];
+            }
+        }
+        buf ^= 1;  // the next group builds into the other buffer; the barrier above already ordered this one
+        ja = jb;
     }
 }
 
