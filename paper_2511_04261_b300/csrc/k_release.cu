@@ -798,8 +798,10 @@ cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, in
 }
 
 cudaError_t launch_emit(const Geom &g, const CallArgs &a, cudaStream_t s) {
-    // enough resident threads per frame to cover the GPU a few times over, looping over the cells
-    int per_frame = (8 * sm_count() + (int)a.n_frames - 1) / (int)a.n_frames;
+    // one wave of resident CTAs shared out over the frames, looping over the cells (a partial second wave
+    // would leave its CTAs' whole shares to the end)
+    const int per_sm = launch_prep(reinterpret_cast<const void *>(k_emit), kThreads, 0);
+    int per_frame = std::max(1, per_sm * sm_count() / (int)a.n_frames);
     int maxcells = 1;
     for (int r = 0; r < g.K; ++r) maxcells = std::max(maxcells, g.cells_side[r] * g.cells_side[r]);
     const int need = (int)(((uint64_t)g.ntiles * maxcells + kThreads - 1) / kThreads);
