@@ -496,6 +496,148 @@ def soft_oracle_time(x, w, g, budget_s):
     return done, time.perf_counter() - t0
 
 
+# ------------------------------------------------------------------------------------------------------
+# workload "uniform": Alg. 2 (one region, uniform grid b) on grayscale frames of the paper's two shapes, with a
+# sweep of b over 2..20 (the paper's timing figure and table, Sec. VII); the headline is 768 x 576 at b = 16
+# ------------------------------------------------------------------------------------------------------
+UNIFORM = dict(shapes=[(576, 768), (1080, 1920)], bs=list(range(2, 21)), eps=0.5, m=16.0, seed=5, frames=64)
+UNIFORM_METRIC = "ms per grayscale frame, uniform DP pixelization (Alg. 2: release + reconstruction), 768 x 576, b = 16"
+# the paper's average GPU time per frame at b = 16, eps 0.5, m 16 (RTX A5500 laptop GPU, CuPy; Table 4)
+UNIFORM_PAPER_MS = {(576, 768): 0.9, (1080, 1920): 2.1}
+
+
+def uniform_oracle_time(clip, b, budget_s):
+    """Oracle release + reconstruction of whole frames until the budget is used (at least one)."""
+    import numpy as np
+    import oracle as O
+    M, N = clip.shape[1], clip.shape[2]
+    lab = np.zeros((-(-M // b), -(-N // b)), dtype=np.uint8)
+    kw = dict(M=M, N=N, C=1, grids=[b], eps=[UNIFORM["eps"]], m=UNIFORM["m"], seed=UNIFORM["seed"],
+              source=O.SRC_TILE_LABELS, dtype=O.DT_F32)
+    t0, done = time.perf_counter(), 0
+    while done < clip.shape[0]:
+        rec, _, _, _ = O.release(clip[done], lab, frame_idx=done, **kw)
+        O.reconstruct(rec, 0)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    return done, time.perf_counter() - t0
+
+
+def run_uniform(args):
+    import torch
+    import paper_2511_04261_b300 as P
+    from paper_2511_04261_b300 import build, synth
+    build.build()
+    world, rank, _ = dist_setup(args.gpus)
+    F = UNIFORM["frames"]
+    stream = torch.cuda.current_stream()
+    sweep, single, prof_head, clocks, head_ms, algo_head = {}, {}, None, None, None, None
+    for (M, N) in UNIFORM["shapes"]:
+        clip_h = synth.moving_rect_clip(seed=1005 + rank, frames=F, M=M, N=N, C=1)
+        frames = torch.from_numpy(clip_h).cuda()
+        key = "%dx%d" % (N, M)
+        sweep[key] = {}
+        for b in UNIFORM["bs"]:
+            try:
+                plan = P.Plan(M=M, N=N, C=1, grids=[b], eps=[UNIFORM["eps"]], m=UNIFORM["m"], seed=UNIFORM["seed"],
+                              source=P.SRC_TILE_LABELS, dtype=P.REC_F32)
+            except P.DppixError as e:  # e.g. more tiles per frame than the plan takes (1080p at b = 2, 3)
+                sweep[key][b] = "unsupported: %s" % e
+                continue
+            lab = torch.zeros((F, -(-M // b), -(-N // b)), dtype=torch.uint8, device="cuda")
+            recs, ws = plan.alloc_records(F), plan.alloc_workspace(F)
+            out = torch.empty((F, M, N, 1), dtype=torch.uint8, device="cuda")
+
+            def call(nf=F):
+                plan.release_reconstruct(frames[:nf], lab[:nf], records=recs[:nf], out=out[:nf], ws=ws, stream_id=rank)
+
+            head = (M, N) == (576, 768) and b == 16
+            reps = args.steps if head else 10
+            for _ in range(max(3, args.warmup)):
+                call()
+            torch.cuda.synchronize()
+            if head:
+                sampler = ClockSampler(torch.cuda.current_device())
+                barrier(world)
+                torch.cuda.synchronize()
+                P.prof_reset()
+                P.prof_enable(True)
+                sampler.start()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_frame = max_over_ranks(e0.elapsed_time(e1) / reps / F, world)
+            sweep[key][b] = ms_frame
+            if head:
+                barrier(world)
+                clocks = sampler.stop()
+                prof_head = P.prof_read()
+                P.prof_enable(False)
+                head_ms = ms_frame
+                hdr = P.record_header(bytes(recs[0][:512].cpu().numpy()))
+                payload = hdr["total_bytes"] - hdr["payload_offset"]
+                tiles = hdr["GR"] * hdr["GC"]
+                algo_head = {"k_release": F * (M * N + payload + 5 * tiles),
+                             "k_reconstruct_u8": F * (M * N + payload + tiles), "k_finalize": F * (9 * tiles + 512)}
+            if b == 16:  # one frame per call, issued from Python each time (the paper's loop over frames)
+                ts = []
+                for _ in range(30):
+                    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a0.record(stream)
+                    call(1)
+                    a1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(a0.elapsed_time(a1))
+                ts.sort()
+                single[key] = {"p50_ms": ts[len(ts) // 2], "p99_ms": ts[min(len(ts) - 1, int(0.99 * len(ts)))],
+                               "paper_ms": UNIFORM_PAPER_MS[(M, N)]}
+    hbm, peak_kind = measured_peaks()
+    dom_name, (dom_launches, dom_ms) = max(prof_head.items(), key=lambda kv: kv[1][1])
+    per_launch_ms = dom_ms / max(1, dom_launches)
+    achieved = algo_head[dom_name] / (per_launch_ms / 1e3) / 1e9 if dom_name in algo_head else None
+    tot = sum(v[1] for v in prof_head.values())
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm if achieved else None,
+                "traffic": traffic_from_profile(dom_name, "uniform64_768x576_gray_b16"),
+                "algorithmic_bytes_per_launch": algo_head.get(dom_name), "avg_launch_ms": per_launch_ms,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else
+                "fallback 6.4 TB/s",
+                "kernels": {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / max(1e-9, tot),
+                                "algorithmic_GBps": algo_head[k] / (v[1] / max(1, v[0]) / 1e3) / 1e9
+                                if k in algo_head else None} for k, v in prof_head.items()}}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        clip_h = synth.moving_rect_clip(seed=1005, frames=64, M=576, N=768, C=1)
+        done, dt = uniform_oracle_time(clip_h, 16, args.cpu_budget)
+        cpu = {"value": 1e3 * dt / done, "unit": "ms/frame", "cores": 1, "kind": "oracle",
+               "sample": "%d frames of 768 x 576 at b = 16 (oracle release + reconstruct, 1 thread, %.1f s)" % (done, dt)}
+    if rank == 0:
+        line = {"metric": UNIFORM_METRIC, "value": head_ms, "unit": "ms/frame", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head_ms * F, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": head_ms / UNIFORM_PAPER_MS[(576, 768)], "dtype": "u8",
+                "data": "synthetic",
+                "config": {"workload": "uniform64_768x576_gray_b16", "frames_per_call": F, "M": 576, "N": 768, "C": 1,
+                           "grids": [16], "eps": [UNIFORM["eps"]], "m": UNIFORM["m"],
+                           "region_source": "one region (tile labels all 0)",
+                           "step": "dp_pix_release_reconstruct of 64 frames (release + reconstruction)",
+                           "stands_in_for": "PETS09-S2L1 (768 x 576) and Venice-2 (1920 x 1080) grayscale sequences",
+                           "generator_seed": 1005, "parallelism": "1 GPU" if world == 1 else "replicas",
+                           "l2": "64 frames (28 MB in, 28 MB out) per call: inside L2 at 768 x 576"},
+                "sweep_ms_per_frame": sweep, "single_frame": single,
+                "paper_ms_per_frame_b16": {"%dx%d" % (n, m): v for (m, n), v in UNIFORM_PAPER_MS.items()},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": None, "clocks": clocks,
+                "gpu_launches": sum(v[0] for v in prof_head.values())}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def run_soft(args):
     import torch
     import paper_2511_04261_b300 as P
@@ -937,15 +1079,18 @@ def main():
     ap.add_argument("--split", type=int, default=None, help="DP_PIX_TUNE_SPLIT (default: the plan's)")
     ap.add_argument("--path", choices=["fused", "two-call"], default="fused",
                     help="fused: dp_pix_release_reconstruct; two-call: dp_pix_release then dp_pix_reconstruct")
-    ap.add_argument("--workload", choices=["clip", "soft", "batch", "serve"], default="clip",
+    ap.add_argument("--workload", choices=["clip", "soft", "batch", "serve", "uniform"], default="clip",
                     help="clip: the 64-frame 1080p release + reconstruction (the benchmark); soft: the differentiable "
-                         "layer on a 32 x 3 x 1024 x 1024 batch; batch: 256 ragged portraits with mattes")
+                         "layer on a 32 x 3 x 1024 x 1024 batch; batch: 256 ragged portraits with mattes; serve: 16 "
+                         "camera streams; uniform: Alg. 2 on grayscale 768 x 576 and 1920 x 1080 frames, b = 2..20")
     args = ap.parse_args()
     set_frames(args.frames)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "uniform":
+        return run_uniform(args)
     if args.workload == "soft":
         return run_soft(args)
     if args.workload == "batch":

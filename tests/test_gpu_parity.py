@@ -323,6 +323,42 @@ def test_variance_classes_every_rank_path(M, N, grids):
         assert np.array_equal(np.bincount(exp.reshape(-1), minlength=K), np.bincount(K * np.arange(n) // n, minlength=K))
 
 
+@pytest.mark.parametrize("b", list(range(2, 21)))
+def test_uniform_grayscale_every_grid(b):
+    """Alg. 2 (one region, uniform grid b) on grayscale frames of 70 x 101 pixels, every b of the paper's
+    timing sweep (Sec. VII, 2..20): records and reconstructions equal the oracle's (ragged edges mirrored)."""
+    F, M, N = 2, 70, 101
+    clip = synth.moving_rect_clip(seed=40 + b, frames=F, M=M, N=N, C=1)
+    lab = np.zeros((F, -(-M // b), -(-N // b)), dtype=np.uint8)
+    kw = dict(M=M, N=N, C=1, grids=[b], eps=[0.5], m=16, source=O.SRC_TILE_LABELS, dtype=O.DT_F32, seed=11)
+    plan, recs_d, recs = gpu_release(clip, lab, **kw)
+    outs = P.dp_pix_reconstruct(recs_d, M, N, 1).cpu().numpy()
+    for i in range(F):
+        rec, means, sums, etas = O.release(clip[i], lab[i], frame_idx=i, **kw)
+        compare_records(recs[i], rec, means, sums, etas, O.DT_F32)
+        assert np.array_equal(outs[i], O.reconstruct(np.frombuffer(recs[i], np.uint8), 0))
+
+
+@pytest.mark.parametrize("b", [10, 14, 16])
+def test_uniform_grayscale_768x576(b):
+    """The paper's PETS shape (768 x 576 grayscale, eps 0.5, m 16) at b = 16 and at the two grids that leave
+    a padded edge (10, 14): one release + reconstruction call, every record element and pixel checked."""
+    F, M, N = 3, 576, 768
+    clip = synth.moving_rect_clip(seed=700 + b, frames=F, M=M, N=N, C=1)
+    lab = np.zeros((F, -(-M // b), -(-N // b)), dtype=np.uint8)
+    kw = dict(M=M, N=N, C=1, grids=[b], eps=[0.5], m=16, source=O.SRC_TILE_LABELS, dtype=O.DT_F32, seed=12)
+    plan = P.Plan(**kw)
+    recs_d, outs = plan.release_reconstruct(torch.from_numpy(clip).cuda(), torch.from_numpy(lab).cuda())
+    torch.cuda.synchronize()
+    assert P.dp_pix_status() == 0
+    outs = outs.cpu().numpy()
+    for i in range(F):
+        got = P.dp_pix_store(recs_d[i])
+        rec, means, sums, etas = O.release(clip[i], lab[i], frame_idx=i, **kw)
+        compare_records(got, rec, means, sums, etas, O.DT_F32)
+        assert np.array_equal(outs[i], O.reconstruct(np.frombuffer(got, np.uint8), 0))
+
+
 # ------------------------------------------------------------------------------------------------------
 # Full-size workloads at the benchmark's launch configuration, sampled against the oracle
 # ------------------------------------------------------------------------------------------------------
