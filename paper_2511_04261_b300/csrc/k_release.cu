@@ -759,7 +759,11 @@ cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, in
     int csmax = 1;
     for (int r = 0; r < g.K; ++r) csmax = std::max(csmax, g.cells_side[r]);
     const int vb = oes == 4 ? 16 : 4;
-    const int px = g.fused_px;
+    int px = g.fused_px;
+    // few frames (a single frame, a small batch): smaller items until the launch covers the SMs -- each item's
+    // chain of load, cells and rows is shorter as well
+    while (px > 256 && (uint64_t)a.n_frames * g.GR * (uint64_t)((g.GC * g.T + px - 1) / px) < (uint64_t)sm_count())
+        px >>= 1;
     int seg = std::max(1, std::min(kSegMaxTiles, std::min(px, kSegMaxPx) / g.T) / sm) * sm;
     FusedShape fs{};
     for (; seg >= sm; seg -= sm) {

@@ -7,7 +7,9 @@
 //  - the tile's sum of squares (dp4a of a word with itself) and sum, reduced over the tile's threads by
 //    shuffles into the exact rank key n*Q - S^2.
 // The g-cell sums go to a "g-image" (rows of g-cells, C u16 each) so that neighbouring threads store
-// neighbouring bytes (rows gpitch values apart).  Used when the frame needs no column padding and rows are 16-byte aligned; the
+// neighbouring bytes (rows gpitch values apart).  With few frames the T/g bands of a tile row are split over
+// 2^bs_log2 threads (the tile's column threads and band threads are adjacent lanes, so the key is still
+// reduced by shuffles), so that a single frame fills the GPU.  Used when the frame needs no column padding and rows are 16-byte aligned; the
 // staged kernel in k_release.cu covers everything else.
 #include "common.cuh"
 
@@ -46,26 +48,50 @@ __device__ __forceinline__ uint4 ld_stream(const void *p) {
     return v;
 }
 
-template <int C, int G>
-__global__ void __launch_bounds__(kThreads) k_tile_stats_fast(const Geom g, const CallArgs a) {
+template <int C, int G, bool kSplit>
+__global__ void __launch_bounds__(kThreads) k_tile_stats_fast(const Geom g, const CallArgs a, int bs_log2) {
     using K = Chunk<C, G>;
     const int T = g.T;
     const int NQ = g.N * C / K::BYTES;   // chunks per image row (no column padding)
-    const int CPT = T * C / K::BYTES;    // chunks per tile, a power of two <= 32
-    const uint64_t total = (uint64_t)a.n_frames * (uint64_t)g.GR * (uint64_t)NQ;
-    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = gid < total;
-    const uint64_t id = valid ? gid : total - 1;  // idle lanes shadow a valid one for the shuffles
-    const int q = (int)(id % NQ);
-    const uint64_t fr = id / NQ;
-    const int ty = (int)(fr % g.GR);
-    const uint32_t f = (uint32_t)(fr / g.GR);
+    const int CPT = T * C / K::BYTES;    // chunks per tile, a power of two; CPT << bs_log2 <= 32
+    if (!kSplit) bs_log2 = 0;
+    bool valid;
+    int q, ty, split = 0;
+    uint32_t f;
+    if (kSplit) {
+        // lane order: chunk of the tile (CPT), then band split (2^bs_log2), then tile column, tile row, frame;
+        // the launcher keeps these launches below 2^31 threads
+        const int lcpt = __ffs(CPT) - 1;
+        const uint32_t total = ((uint32_t)a.n_frames * (uint32_t)g.GR * (uint32_t)NQ) << bs_log2;
+        const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+        valid = gid < total;
+        const uint32_t id = valid ? gid : total - 1u;  // idle lanes shadow a valid one (whole idle lane groups)
+        const uint32_t id2 = id >> lcpt;
+        split = (int)(id2 & ((1u << bs_log2) - 1u));
+        const uint32_t id3 = id2 >> bs_log2;
+        const uint32_t NT = (uint32_t)(NQ >> lcpt);  // tiles per tile row
+        const uint32_t fr = id3 / NT;
+        q = (int)(id3 - fr * NT) * CPT + (int)(id & (uint32_t)(CPT - 1));
+        f = fr / (uint32_t)g.GR;
+        ty = (int)(fr - f * (uint32_t)g.GR);
+    } else {
+        const uint64_t total = (uint64_t)a.n_frames * (uint64_t)g.GR * (uint64_t)NQ;
+        const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        valid = gid < total;
+        const uint64_t id = valid ? gid : total - 1;  // idle lanes shadow a valid one for the shuffles
+        q = (int)(id % NQ);
+        const uint64_t fr = id / NQ;
+        ty = (int)(fr % g.GR);
+        f = (uint32_t)(fr / g.GR);
+    }
+    const int cq = q & (CPT - 1);
     const uint8_t *fbase = a.frames + (uint64_t)f * (uint64_t)a.frame_stride + (uint64_t)q * K::BYTES;
     uint16_t *gimg = reinterpret_cast<uint16_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_gsum);
     const int GP = g.gpitch;
     const int bands = T / G;
+    const int bpt = bands >> bs_log2;    // bands of this thread
     uint32_t Ssum = 0, Qsum = 0;
-    for (int band = 0; band < bands; ++band) {
+    for (int band = split * bpt; band < (split + 1) * bpt; ++band) {
         uint32_t acc[K::NG][C];
 #pragma unroll
         for (int c = 0; c < K::NG; ++c)
@@ -112,13 +138,13 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats_fast(const Geom g, cons
 #pragma unroll
             for (int ch = 0; ch < C; ++ch) Ssum += acc[c][ch];
     }
-    // tile totals over the CPT consecutive lanes of the tile
+    // tile totals over the tile's CPT << bs_log2 consecutive lanes
     unsigned long long Q64 = Qsum;
-    for (int off = CPT >> 1; off > 0; off >>= 1) {
+    for (int off = (CPT << bs_log2) >> 1; off > 0; off >>= 1) {
         Ssum += __shfl_xor_sync(0xffffffffu, Ssum, off);
         Q64 += __shfl_xor_sync(0xffffffffu, Q64, off);
     }
-    if (valid && (q % CPT) == 0) {
+    if (valid && cq == 0 && split == 0) {
         const uint32_t tile = (uint32_t)ty * g.GC + (uint32_t)(q / CPT);
         const unsigned long long n = (unsigned long long)T * T * C;
         uint64_t *keys = reinterpret_cast<uint64_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_keys);
@@ -129,10 +155,21 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats_fast(const Geom g, cons
 template <int C, int G>
 cudaError_t launch_fast(const Geom &g, const CallArgs &a, cudaStream_t s) {
     using K = Chunk<C, G>;
-    const uint64_t total = (uint64_t)a.n_frames * g.GR * (uint64_t)(g.N * C / K::BYTES);
+    const uint64_t base = (uint64_t)a.n_frames * g.GR * (uint64_t)(g.N * C / K::BYTES);
+    // split the bands of a tile row over more threads until the launch covers every SM with a few blocks
+    // (single frames, small batches); a power of two that divides the band count, lanes of one tile <= 32
+    const int bands = g.T / G, cpt = g.T * C / K::BYTES;
+    int bs_log2 = 0;
+    while ((base << bs_log2) < (uint64_t)sm_count() * 4 * kThreads && (bands >> bs_log2) % 2 == 0 &&
+           (cpt << (bs_log2 + 1)) <= 32)
+        ++bs_log2;
+    const uint64_t total = base << bs_log2;
     const uint64_t blocks = (total + kThreads - 1) / kThreads;
     prof_begin("k_tile_stats_gsum", s);
-    k_tile_stats_fast<C, G><<<(unsigned)blocks, kThreads, 0, s>>>(g, a);
+    if (bs_log2 > 0)  // only for small launches (below a few SM waves of threads)
+        k_tile_stats_fast<C, G, true><<<(unsigned)blocks, kThreads, 0, s>>>(g, a, bs_log2);
+    else
+        k_tile_stats_fast<C, G, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, a, 0);
     prof_end("k_tile_stats_gsum", s);
     return cudaGetLastError();
 }
