@@ -556,6 +556,22 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
     const int gsv = fs.gseg_bytes >> 1;  // u16 values per shared g-image row
     const uint32_t nseg = (uint32_t)((g.GC + seg - 1) / seg);
     const uint32_t items = a.n_frames * (uint32_t)g.GR * nseg;
+    // the g-cells of an item's segment (T/g rows of ns*T/g g-cells) are copied into gseg with cp.async; the
+    // copies for the next item are issued as soon as this item's cells are done, so that they arrive while
+    // its rows are written
+    auto fetch_gseg = [&](uint32_t it) {
+        const uint32_t fr_ = it / nseg;
+        const int ty_ = (int)(fr_ % g.GR), tx0_ = (int)(it % nseg) * seg;
+        const int ns_ = min(seg, g.GC - tx0_);
+        const uint8_t *wsf_ = a.ws + (uint64_t)(fr_ / g.GR) * g.ws_per_frame;
+        const int nvec = (ns_ * gcs * C * 2 + 15) >> 4;  // 16-byte chunks per row (the row pitch covers the last)
+        const uint8_t *src0 = wsf_ + g.ws_gsum + ((size_t)ty_ * gcs * g.gpitch + (size_t)tx0_ * gcs * C) * 2;
+        for (int i = threadIdx.x; i < gcs * nvec; i += kThr) {
+            const int row = i / nvec, v = i - row * nvec;
+            cp_async16(gseg + row * fs.gseg_bytes + v * 16, src0 + (size_t)row * g.gpitch * 2 + 16 * v);
+        }
+    };
+    if (blockIdx.x < items) fetch_gseg(blockIdx.x);
     for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
         const uint32_t sg = item % nseg, fr = item / nseg;
         const int ty = (int)(fr % g.GR);
@@ -564,7 +580,7 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
         const int ns = min(seg, g.GC - tx0);
         uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
         const uint8_t *wsf = a.ws + (uint64_t)f * g.ws_per_frame;
-        // ---- A: tile table and g-cells of the segment ----
+        // ---- A: tile table; the g-cells were fetched ahead ----
         if ((int)threadIdx.x < ns) {
             const int t = threadIdx.x;
             const uint32_t tile = (uint32_t)ty * g.GC + tx0 + t;
@@ -575,15 +591,7 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
             st.cs[t] = g.cells_side[r];
             st.off[t] = reinterpret_cast<const uint32_t *>(wsf + g.ws_tileoff)[tile];
         }
-        {
-            const int nvec = (ns * gcs * C * 2 + 15) >> 4;  // 16-byte chunks per row (the row pitch covers the last)
-            const uint8_t *src0 = wsf + g.ws_gsum + ((size_t)ty * gcs * g.gpitch + (size_t)tx0 * gcs * C) * 2;
-            for (int i = threadIdx.x; i < gcs * nvec; i += kThr) {
-                const int row = i / nvec, v = i - row * nvec;
-                const uint4 x = __ldcs(reinterpret_cast<const uint4 *>(src0 + (size_t)row * g.gpitch * 2) + v);
-                *reinterpret_cast<uint4 *>(gseg + row * fs.gseg_bytes + v * 16) = x;
-            }
-        }
+        cp_async_wait_all();  // this thread's copies of the item's g-cells; the barrier publishes everyone's
         __syncthreads();
         seg_prefix_colinfo(st, ns, T, colinfo, threadIdx.x, kThr);  // warp 0 and all threads
         if (threadIdx.x >= 32 && threadIdx.x < 64) {
@@ -662,6 +670,7 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
             }
         }
         __syncthreads();
+        if (item + gridDim.x < items) fetch_gseg(item + gridDim.x);  // gseg is free once the cells are done
         // ---- C: output rows ----
         const int x0 = tx0 * T;
         seg_write_rows<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, g.N - x0), min(T, g.M - ty * T),
