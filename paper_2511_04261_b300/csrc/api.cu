@@ -242,6 +242,19 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
         const uint64_t c = (uint64_t)g.cells_side[r] * g.cells_side[r];
         maxcells = c > maxcells ? c : maxcells;
     }
+    g.rel_pmax = 1;
+    for (int r = 0; r < d->K; ++r) {
+        const int P = rel_parts(g.grid[r], d->C);
+        if (P > g.rel_pmax) g.rel_pmax = P;
+    }
+    for (int r = 0; r < d->K; ++r) {
+        const int P = rel_parts(g.grid[r], d->C);
+        int lp = 0;
+        while ((1 << lp) < P) ++lp;
+        g.rel_lp[r] = lp;
+        const int units = g.cells_side[r] * g.cells_side[r] * P;
+        g.rel_units[r] = (units + g.rel_pmax - 1) / g.rel_pmax * g.rel_pmax;
+    }
     g.b_min = bmin;
     g.g = (int)gg;
     g.rowidx_offset = kHeaderBytes;

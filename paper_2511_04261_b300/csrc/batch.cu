@@ -62,12 +62,8 @@ void drop_graph(dp_pix_batch_s *b) {
     b->exec = nullptr;
 }
 
-// Release staging bytes for S tiles per segment (as the single-image plan computes them).
-size_t seg_smem_for(const Geom &g, int S) {
-    const int TC = g.T * g.C;
-    const int rs = (S * TC + 15) / 16 * 16;
-    return (size_t)g.T * rs + (size_t)S * g.vbands * TC * 2;
-}
+// Release staging bytes for S tiles per segment (two buffers of T staged rows).
+size_t seg_smem_for(const Geom &g, int S) { return release_smem(g.T, g.C, S); }
 
 void apply_seg(Geom &g, int S) {
     g.seg_tiles = S;
@@ -163,7 +159,7 @@ cudaError_t launch_all(dp_pix_batch_s *b, cudaStream_t s) {
     if (g0.source == DP_PIX_SRC_MASK_U8 || g0.source == DP_PIX_SRC_MATTE_F32)
         e = launch_batch_classify(tab, b->n, b->items_cls, (int)b->max_gc, g0.source == DP_PIX_SRC_MATTE_F32, s);
     if (e == cudaSuccess) e = launch_batch_finalize(tab, b->n, b->max_tiles, s);
-    if (e == cudaSuccess) e = launch_batch_release(tab, b->n, b->items_rel, b->rel_smem, s);
+    if (e == cudaSuccess) e = launch_batch_release(tab, b->n, b->items_rel, g0.T, g0.C, g0.seg_tiles, s);
     if (e == cudaSuccess && b->any_out)
         e = launch_batch_reconstruct(tab, b->n, b->items_rec, b->out_type, g0.C, b->out_align, status_word(), s);
     return e;

@@ -53,7 +53,21 @@ struct Geom {
     int32_t vbands;                   // max bands of a staged tile = T / b_min (or T / g for stats)
     int32_t fused_px, fused_threads;  // launch shape of the fused release + reconstruction (tunable)
     int32_t split;                    // frame chunks of a fused call run on side streams (tunable)
+    // release work units (k_release): a b_r x b_r cell is summed by 2^rel_lp[r] adjacent lanes (row parts);
+    // a tile of region r is rel_units[r] units, a multiple of rel_pmax (the largest part count)
+    int32_t rel_lp[kMaxK];
+    int32_t rel_units[kMaxK];
+    int32_t rel_pmax;
 };
+
+// Row parts of one b x b cell of C-channel u8 samples in the release: the smallest power of two P (at most
+// min(b, 32)) that keeps ceil(b/P) * b * C bytes per part within a budget, so that work units are similar.
+constexpr int kRelPartBytes = 384;
+__host__ __device__ inline int rel_parts(int b, int C) {
+    int P = 1;
+    while (2 * P <= b && P < 32 && ((b + P - 1) / P) * b * C > kRelPartBytes) P *= 2;
+    return P;
+}
 
 // Per-call arguments of a release.
 struct CallArgs {
@@ -243,7 +257,9 @@ cudaError_t launch_reconstruct(const uint8_t *records, int64_t record_stride, ui
 cudaError_t launch_batch_classify(const BatchEntry *tab, uint32_t n_img, uint32_t items, int max_gc, int matte,
                                   cudaStream_t s);
 cudaError_t launch_batch_finalize(const BatchEntry *tab, uint32_t n_img, uint32_t max_tiles, cudaStream_t s);
-cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items, int T, int C, int S,
+                                 cudaStream_t s);
+size_t release_smem(int T, int C, int S);  // dynamic shared memory of the release kernels for S-tile segments
 cudaError_t launch_batch_reconstruct(const BatchEntry *tab, uint32_t n_img, uint32_t items, int out_type, int max_C,
                                      int out_align, int32_t *status, cudaStream_t s);
 cudaError_t launch_debug_noise(uint64_t seed, const uint32_t *ctr, uint64_t n, uint32_t *words, float *eta,

@@ -1,17 +1,16 @@
 // k_release.cu -- the streaming kernels of the release path.
 //
-// All three kernels work on "segments": one tile row (T image rows) times `seg_tiles` consecutive tiles of
-// one frame.  A segment is staged into shared memory once (16-byte cp.async when rows are aligned), with
-// the mirror padding of the last tile row/column resolved by index while staging (Alg. 2 step 4, Alg. 3
-// step 3; the padded image is never materialised).  Then, from shared memory:
-//  - column sums over the rows of each cell band, four byte lanes at a time in 16-bit SIMD lanes
-//    (vertical pass), and per-(cell, channel) sums over the band's columns (horizontal pass): exact u32
-//    cell sums of the b_r x b_r cells (Eq. 2; Alg. 2 step 6; Alg. 3 steps 8 and 14);
-//  - k_release: Laplace noise from the in-register Philox, clip, write the record payload (Alg. 3 steps
-//    9-10 and 15-17);
+// The kernels work on "segments": one tile row (T image rows) times `seg_tiles` consecutive tiles of one
+// frame, with the mirror padding of the last tile row/column resolved by index (Alg. 2 step 4, Alg. 3
+// step 3; the padded image is never materialised).
+//  - k_release / k_batch_release: exact u32 sums of each tile's b_r x b_r cells (Eq. 2; Alg. 2 step 6;
+//    Alg. 3 steps 8 and 14) from the staged segment, Laplace noise from the in-register Philox, clip, the
+//    record payload (Alg. 3 steps 9-10 and 15-17);
 //  - k_tile_stats: per-tile S, Q for the variance classes and, when the grids share a divisor g >= 4, the
-//    g x g cell sums from which any b_r-cell sum is later assembled (image read once);
-//  - k_emit: g-cell sums -> b_r-cell sums -> noise -> record.
+//    g x g cell sums from which any b_r-cell sum is later assembled (image read once): column sums over
+//    each band's rows in 16-bit SIMD lanes, then per-(cell, channel) sums over the band's columns;
+//  - k_emit: g-cell sums -> b_r-cell sums -> noise -> record;
+//  - k_emit_recon: k_emit and the reconstruction fused.
 #include <algorithm>
 
 #include "seg_write.cuh"
@@ -113,159 +112,397 @@ __device__ void stage_segment(const Geom &g, const CallArgs &a, uint32_t f, int 
     __syncthreads();
 }
 
-// Vertical pass of one (tile, band, word column): sums `rows` staged rows of 4 bytes in 16-bit lanes and
-// stores the 4 column sums as u16 into vdst[0..3].
-__device__ __forceinline__ void band_word_sums(const uint8_t *raw, int rs, int row0, int rows, int byte0,
-                                               uint32_t *vdst) {
-    const uint32_t *src = reinterpret_cast<const uint32_t *>(raw + row0 * rs + byte0);
-    const int step = rs >> 2;
-    uint32_t lo = 0, hi = 0;
-    for (int i = 0; i < rows; ++i) {
-        const uint32_t w = src[i * step];
-        lo += __byte_perm(w, 0u, 0x4240);  // bytes 0, 2 -> 16-bit lanes
-        hi += __byte_perm(w, 0u, 0x4341);  // bytes 1, 3
+// Noise, clip and store of one cell's C channels (Alg. 3 steps 9-10 and 15-17) from its Philox words;
+// sigma, b^2 and 1/b^2 (0 when not exact) of its region.  ov (optional) receives the value a
+// reconstruction reads back from the stored element (Sec. VI-F).
+__device__ __forceinline__ void emit_values(const Geom &g, int C, uint8_t *dst, const uint32_t *S, uint4 words,
+                                            float sigma, float b2, float inv_b2, float *ov) {
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+        if (ch >= C) break;
+        if (g.dtype == DP_PIX_REC_SUM_U32) {
+            reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
+            if (ov) ov[ch] = __fdiv_rn(__uint2float_rn(S[ch]), b2);
+        } else {
+            const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), sigma);
+            const float v = noisy_mean(S[ch], b2, inv_b2, eta, g.R_f);
+            if (g.dtype == DP_PIX_REC_F32) {
+                reinterpret_cast<float *>(dst)[ch] = v;
+                if (ov) ov[ch] = v;
+            } else {
+                const uint32_t q = __float2uint_rn(v);
+                dst[ch] = (uint8_t)q;
+                if (ov) ov[ch] = (float)q;
+            }
+        }
     }
-    vdst[0] = __byte_perm(lo, hi, 0x5410);  // (col 0, col 1)
-    vdst[1] = __byte_perm(lo, hi, 0x7632);  // (col 2, col 3)
 }
 
-struct SegInfo {
-    int32_t b[16];
-    int32_t cs[16];
-    int32_t region[16];
-    uint32_t tileoff[16];
-    int32_t startA[17];
-    int32_t startB[17];
+__device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint8_t *dst, const uint32_t *S, int r,
+                                          uint32_t cell_idx, uint64_t frame, uint32_t sid, float *ov = nullptr) {
+    uint4 words = make_uint4(0, 0, 0, 0);
+    if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
+        words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame);
+    emit_values(g, g.C, dst, S, words, g.sigma_f[r], g.b2_f[r], g.inv_b2_f[r], ov);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// k_release / k_batch_release: staged segment -> exact cell sums of each tile's own grid -> noise -> clip
+// -> record (Alg. 3 steps 8-10 and 14-17).
+//
+// Staging: every row of an item is copied as the aligned 16-byte granules that hold its bytes (cp.async,
+// whatever the row's alignment), and the row's offset inside its first granule is kept; consumers realign
+// words with a funnel shift.  The item's map bytes and payload offsets come with the same asynchronous
+// copies, so preparing an item waits on nothing.  Items are double-buffered: the next item's copies are in
+// flight while the current one is summed.  Each CTA takes a contiguous range of items.  Work units are
+// (tile, cell, row part): a b_r x b_r cell is split into 2^rel_lp[r] row parts when its bytes exceed a
+// budget, so that units do similar work; the parts of a cell sit on adjacent, aligned lanes and add their
+// partial sums with shuffles.  A row part's sums use dp4a with compile-time channel masks on realigned words.
+// ------------------------------------------------------------------------------------------------------
+constexpr int kRelSegMax = 16;   // tiles per staged segment
+
+struct RelItem {
+    int32_t ns, tx0, xv, padb, ty, mapoff;
+    uint32_t f;
+    uint32_t mapw[6];                // aligned words holding the segment's map bytes (from byte mapoff)
+    uint32_t tileoff[kRelSegMax];    // payload offsets of the segment's tiles
+    int32_t rowbase[kMaxT];          // staged byte of each row's first pixel (row * stride + granule offset)
 };
 
-// ------------------------------------------------------------------------------------------------------
-// k_release: staged segment -> exact cell sums of each tile's own grid -> noise -> clip -> record.
-// ------------------------------------------------------------------------------------------------------
-// One work item: segment sg of tile row ty of frame f.  Shared memory: raw (T staged rows) | V (band sums).
-__device__ __forceinline__ void release_item(const Geom &g, const CallArgs &a, uint32_t f, int ty, int sg, uint8_t *dyn,
-                                             SegInfo &si) {
-    const int T = g.T, C = g.C, TC = T * C, rs = g.seg_rowstride;
-    uint8_t *raw = dyn;
-    uint16_t *V = reinterpret_cast<uint16_t *>(dyn + (size_t)T * rs);
-    const bool word_path = (TC & 3) == 0;
-    {
-        const int tx0 = sg * g.seg_tiles;
-        const int ns = min(g.seg_tiles, g.GC - tx0);
-        uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
-        if (threadIdx.x < ns) {  // one thread per tile loads its region and payload offset
-            const int t = threadIdx.x;
-            int r = rec[g.map_offset + (uint64_t)ty * g.GC + tx0 + t];
-            if (r >= g.K) r = 0;
-            si.region[t] = r;
-            si.tileoff[t] =
-                reinterpret_cast<const uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff)[ty * g.GC + tx0 + t];
-        }
-        stage_segment(g, a, f, ty, tx0, ns, raw);  // ends with a barrier (also covers si)
-        if (threadIdx.x == 0) {
-            int sa = 0, sb = 0;
-            for (int t = 0; t < ns; ++t) {
-                const int b = g.grid[si.region[t]];
-                si.b[t] = b;
-                si.cs[t] = T / b;
-                si.startA[t] = sa;
-                si.startB[t] = sb;
-                sa += (T / b) * (word_path ? (TC >> 2) : TC);
-                sb += (T / b) * (T / b);
-            }
-            si.startA[ns] = sa;
-            si.startB[ns] = sb;
-        }
-        __syncthreads();
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-        // vertical pass
-        const int totalA = si.startA[ns];
-        for (int it = threadIdx.x; it < totalA; it += blockDim.x) {
-            int t = 0;
-            while (t + 1 < ns && it >= si.startA[t + 1]) ++t;
-            const int rem = it - si.startA[t];
-            const int b = si.b[t];
-            if (word_path) {
-                const int wcs = TC >> 2;
-                const int band = rem / wcs, wc = rem - band * wcs;
-                uint32_t *vdst = reinterpret_cast<uint32_t *>(V + ((size_t)(t * g.vbands + band) * TC)) + 2 * wc;
-                band_word_sums(raw, rs, band * b, b, t * TC + 4 * wc, vdst);
-            } else {
-                const int band = rem / TC, k = rem - band * TC;
-                uint32_t s = 0;
-                for (int i = 0; i < b; ++i) s += raw[(band * b + i) * rs + t * TC + k];
-                V[(size_t)(t * g.vbands + band) * TC + k] = (uint16_t)s;
-            }
-        }
-        __syncthreads();
+// Bulk (TMA) copies into shared memory completing on an mbarrier, and the mbarrier operations they need.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// Waits for the phase of the given parity to complete; gives up (false) after a bounded number of tries
+// (try_wait itself blocks for a bounded time), so that a copy that never lands cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(smem_u32(bar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-        // horizontal pass, noise, clip, store
-        const int totalB = si.startB[ns];
-        const uint64_t frame = key_frame(a, f);
-        const uint32_t sid = key_stream(a, f);
-        for (int it = threadIdx.x; it < totalB; it += blockDim.x) {
-            int t = 0;
-            while (t + 1 < ns && it >= si.startB[t + 1]) ++t;
-            const int cell = it - si.startB[t];
-            const int cs = si.cs[t], b = si.b[t], r = si.region[t];
-            const int cy = cell / cs, cx = cell - cy * cs;
-            const uint16_t *vrow = V + (size_t)(t * g.vbands + cy) * TC + cx * b * C;
-            uint32_t S[4] = {0u, 0u, 0u, 0u};
-            for (int i = 0; i < b; ++i) {
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch)
-                    if (ch < C) S[ch] += vrow[i * C + ch];
-            }
-            const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)((tx0 + t) * cs + cx);
-            uint4 words = make_uint4(0, 0, 0, 0);
-            if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
-                words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame);
-            uint8_t *dst = rec + si.tileoff[t] + (uint64_t)cell * C * g.es;
-#pragma unroll
-            for (int ch = 0; ch < 4; ++ch) {
-                if (ch >= C) break;
-                if (g.dtype == DP_PIX_REC_SUM_U32) {
-                    reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
-                } else {
-                    const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), g.sigma_f[r]);
-                    const float v = noisy_mean(S[ch], g.b2_f[r], g.inv_b2_f[r], eta, g.R_f);
-                    if (g.dtype == DP_PIX_REC_F32)
-                        reinterpret_cast<float *>(dst)[ch] = v;
-                    else
-                        dst[ch] = (uint8_t)__float2uint_rn(v);
-                }
-            }
+// Bytes per staged row of an item of S tiles: room for the 15-byte granule offset and the word reads
+// that run up to 7 bytes past a row's last byte.
+__host__ __device__ __forceinline__ int rel_rowstride(int S, int T, int C) { return (S * T * C + 15) / 16 * 16 + 32; }
+
+// x / d for 0 <= x < 2^14, 1 <= d <= 128 from an approximate reciprocal: the product is at most one short.
+__device__ __forceinline__ int udiv_small(int x, int d, float inv) {
+    int q = __float2int_rz(__int2float_rn(x) * inv);
+    if (x - q * d >= d) ++q;
+    return q;
+}
+
+// Prepares item (f, ty, sg) into `it` and issues the copies of its map bytes, payload offsets and rows
+// (whole block; no barrier: the caller's barrier after cp.async.wait publishes `it`).
+__device__ __forceinline__ void rel_prepare(const Geom &g, const CallArgs &a, uint32_t f, int ty, int sg, RelItem &it,
+                                            uint8_t *raw, uint64_t *bar) {
+    const int T = g.T, C = g.C, S = g.seg_tiles;
+    const int rs = rel_rowstride(S, T, C);
+    const int tx0 = sg * S;
+    const int ns = min(S, g.GC - tx0);
+    const int x0 = tx0 * T;
+    const int xv = min(ns * T, g.N - x0);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uintptr_t msrc = reinterpret_cast<uintptr_t>(a.records + (uint64_t)f * (uint64_t)a.record_stride + g.map_offset +
+                                                       (uint64_t)ty * g.GC + tx0);
+    const int mo = (int)(msrc & 3u);
+    if (tid == 0) {
+        it.ns = ns;
+        it.tx0 = tx0;
+        it.xv = xv;
+        it.padb = (ns * T - xv) * C;
+        it.ty = ty;
+        it.mapoff = mo;
+        it.f = f;
+    }
+    if (tid < ((mo + ns + 3) >> 2)) cp_async4(&it.mapw[tid], reinterpret_cast<const void *>(msrc - mo + 4u * tid));
+    if (tid >= 32 && tid < 32 + ns) {
+        const uint32_t *toff = reinterpret_cast<const uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff);
+        cp_async4(&it.tileoff[tid - 32], toff + ty * g.GC + tx0 + (tid - 32));
+    }
+    // rows: thread j issues one bulk copy of row j (the aligned 16-byte granules that hold its bytes); each
+    // warp announces its rows' bytes to the mbarrier first
+    const uint8_t *fbase = a.frames + (uint64_t)f * (uint64_t)a.frame_stride + (int64_t)x0 * C;
+    const int vb = xv * C;
+    for (int j0 = warp * 32; j0 < T; j0 += blockDim.x) {
+        const int j = j0 + lane;
+        uint32_t bytes = 0;
+        const uint8_t *ga = nullptr;
+        if (j < T) {
+            const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
+            const uintptr_t addr = reinterpret_cast<uintptr_t>(fbase + (int64_t)sy * g.pitch);
+            const int o = (int)(addr & 15u);
+            ga = reinterpret_cast<const uint8_t *>(addr - (uintptr_t)o);
+            bytes = 16u * (uint32_t)((o + vb + 15) >> 4);
+            it.rowbase[j] = j * rs + o;
         }
-        __syncthreads();
+        const uint32_t wsum = __reduce_add_sync(0xffffffffu, bytes);
+        if (lane == 0) mbar_expect_tx(bar, wsum);
+        __syncwarp();
+        if (j < T) bulk_g2s(raw + j * rs, ga, bytes, bar);
     }
 }
 
+// dp4a mask of channel ch for a word whose first byte is byte 4k of a cell row (C interleaved channels).
+template <int C>
+__device__ __forceinline__ constexpr uint32_t chan_mask(int k, int ch) {
+    return C == 1 ? 0x01010101u
+         : C == 2 ? (ch == 0 ? 0x00010001u : 0x01000100u)
+         : C == 4 ? (1u << (8 * ch))
+         : /* C == 3: byte i of word k is channel (4k + i) mod 3 */
+           ((((4 * k + 0) % 3 == ch) ? 0x00000001u : 0u) | (((4 * k + 1) % 3 == ch) ? 0x00000100u : 0u) |
+            (((4 * k + 2) % 3 == ch) ? 0x00010000u : 0u) | (((4 * k + 3) % 3 == ch) ? 0x01000000u : 0u));
+}
+
+template <int C, int KP>
+__device__ __forceinline__ void acc_word(uint32_t w, uint32_t *S) {
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) S[ch] = __dp4a(w, chan_mask<C>(KP, ch), S[ch]);
+}
+
+// Channel sums of `nbytes` bytes starting at staged byte rowbase[j] + L0, over rows j in [r0, r1).
+template <int C>
+__device__ __forceinline__ void rows_sum(const uint8_t *raw, const int32_t *rowbase, int r0, int r1, int L0,
+                                         int nbytes, uint32_t *S) {
+    constexpr int PER = (C == 3) ? 3 : 1;  // words per mask period
+    const int nw = (nbytes + 3) >> 2;
+    const int nfull = nbytes >> 2;
+    const uint32_t tail = (nbytes & 3) ? (1u << (8 * (nbytes & 3))) - 1u : 0xFFFFFFFFu;
+    for (int j = r0; j < r1; ++j) {
+        const int addr = rowbase[j] + L0;
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(raw + (addr & ~3));
+        const uint32_t sh = 8u * (uint32_t)(addr & 3);
+        uint32_t lo = w[0];
+        int k = 0;
+        for (; k + PER <= nfull; k += PER) {
+#pragma unroll
+            for (int kk = 0; kk < PER; ++kk) {
+                const uint32_t hi = w[k + kk + 1];
+                const uint32_t x = __funnelshift_r(lo, hi, sh);
+                lo = hi;
+                if (kk == 0) acc_word<C, 0>(x, S);
+                if (kk == 1) acc_word<C, 1>(x, S);
+                if (kk == 2) acc_word<C, 2>(x, S);
+            }
+        }
+        // the rest: fewer than PER full words and the partial word, in mask order
+#pragma unroll
+        for (int kk = 0; kk < PER + 1; ++kk) {
+            if (k + kk >= nw) break;
+            const uint32_t hi = w[k + kk + 1];
+            uint32_t x = __funnelshift_r(lo, hi, sh);
+            lo = hi;
+            if (k + kk == nw - 1) x &= tail;
+            if (kk % PER == 0) acc_word<C, 0>(x, S);
+            if (kk % PER == 1) acc_word<C, 1>(x, S);
+            if (kk % PER == 2) acc_word<C, 2>(x, S);
+        }
+    }
+}
+
+// Sums, noise and record of the staged item `it` (whole block).
+template <int C>
+__device__ __forceinline__ void rel_compute(const Geom &g, const CallArgs &a, const RelItem &it, uint8_t *raw) {
+    const int T = g.T;
+    if (it.padb > 0) {
+        // mirrored columns past the right edge, copied next to the row's last in-image byte
+        const uint8_t *fb0 = a.frames + (uint64_t)it.f * (uint64_t)a.frame_stride;
+        const int x0 = it.tx0 * T, pb = it.padb;
+        for (int idx = threadIdx.x; idx < T * pb; idx += blockDim.x) {
+            const int j = idx / pb, k = idx - j * pb;
+            const int px = it.xv + k / C, ch = k - (k / C) * C;
+            const int sy = reflect_idx(it.ty * T + j, g.M, g.pad_mode);
+            const int sx = reflect_idx(x0 + px, g.N, g.pad_mode);
+            raw[it.rowbase[j] + it.xv * C + k] = fb0[(int64_t)sy * g.pitch + (int64_t)sx * C + ch];
+        }
+        fence_proxy_async();  // these generic writes precede the bulk copies that later refill the buffer
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int ns = it.ns, pmax = g.rel_pmax;
+    const uint8_t *mapb = reinterpret_cast<const uint8_t *>(it.mapw) + it.mapoff;
+    int total = 0;
+    for (int t = 0; t < ns; ++t) {
+        int r = mapb[t];
+        if (r >= g.K) r = 0;
+        total += g.rel_units[r];
+    }
+    uint8_t *rec = a.records + (uint64_t)it.f * (uint64_t)a.record_stride;
+    const uint64_t frame = key_frame(a, it.f);
+    const uint32_t sid = key_stream(a, it.f);
+    for (int u = threadIdx.x; u - lane < total; u += blockDim.x) {
+        uint32_t S[4] = {0u, 0u, 0u, 0u};
+        int t = 0, r = 0, lp = 0, cell = 0, part = 0;
+        bool valid = false;
+        if (u < total) {
+            int start = 0;
+            for (;; ++t) {
+                r = mapb[t];
+                if (r >= g.K) r = 0;
+                const int cnt = g.rel_units[r];
+                if (u < start + cnt || t + 1 == ns) break;
+                start += cnt;
+            }
+            const int lu = u - start;
+            const int cs = g.cells_side[r], b = g.grid[r];
+            lp = g.rel_lp[r];
+            part = lu & ((1 << lp) - 1);
+            cell = lu >> lp;
+            if (cell < cs * cs) {
+                valid = true;
+                const int cy = udiv_small(cell, cs, __fdividef(1.0f, (float)cs)), cx = cell - cy * cs;
+                const int rpp = (b + (1 << lp) - 1) >> lp;
+                const int r0 = cy * b + part * rpp;
+                const int r1 = min(r0 + rpp, (cy + 1) * b);
+                rows_sum<C>(raw, it.rowbase, r0, r1, (t * T + cx * b) * C, b * C, S);
+            } else {
+                lp = 0;
+            }
+        }
+        // the 2^lp lanes of a cell are adjacent and aligned: butterfly over the offsets below 2^lp
+        for (int o = 1; o < pmax; o <<= 1) {
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) {
+                const uint32_t v = __shfl_xor_sync(0xffffffffu, S[ch], o);
+                if (o < (1 << lp)) S[ch] += v;
+            }
+        }
+        if (valid && part == 0) {
+            const int cs = g.cells_side[r];
+            const int cy = udiv_small(cell, cs, __fdividef(1.0f, (float)cs)), cx = cell - cy * cs;
+            const uint32_t cell_idx =
+                (uint32_t)(it.ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)((it.tx0 + t) * cs + cx);
+            emit_cell(g, a, rec + it.tileoff[t] + (uint64_t)cell * C * g.es, S, r, cell_idx, frame, sid);
+        }
+    }
+}
+
+// Items [i0, i1) of a CTA: contiguous, equal shares.
+__device__ __forceinline__ void rel_range(uint32_t items, uint32_t &i0, uint32_t &i1) {
+    const uint32_t per = (items + gridDim.x - 1) / gridDim.x;
+    i0 = min(items, blockIdx.x * per);
+    i1 = min(items, i0 + per);
+}
+
+// The double-buffered item loop of both release kernels: prepare(item, nb) stages an item into buffer nb
+// (rows by bulk copies completing on bars[nb], its tables by cp.async), compute(nb) consumes buffer nb.
+// The mbarrier of a buffer completes one phase per item: thread 0 arrives once every warp has announced
+// the item's bytes.  A wait that gives up raises DP_PIX_E_TIMEOUT and ends the CTA.
+template <class Prep, class Comp>
+__device__ __forceinline__ void rel_loop(uint32_t i0, uint32_t i1, uint64_t *bars, int32_t *status, Prep prepare,
+                                         Comp compute) {
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int buf = 0;
+    uint32_t ph0 = 0, ph1 = 0;
+    if (i0 < i1) prepare(i0, 0);
+    cp_async_commit();
+    __syncthreads();
+    if (threadIdx.x == 0 && i0 < i1) mbar_arrive(&bars[0]);
+    for (uint32_t item = i0; item < i1; ++item) {
+        const bool next = item + 1 < i1;
+        if (next) prepare(item + 1, buf ^ 1);
+        cp_async_commit();
+        cp_async_wait_1();
+        const bool ok = mbar_wait(&bars[buf], buf ? ph1 : ph0);
+        const int fail = __syncthreads_or(!ok);
+        if (threadIdx.x == 0 && next) mbar_arrive(&bars[buf ^ 1]);
+        if (fail) {
+            if (threadIdx.x == 0) raise_status(status, DP_PIX_E_TIMEOUT, 0x500u);
+            if (next) (void)mbar_wait(&bars[buf ^ 1], buf ? ph0 : ph1);  // the next item's copies, bounded
+            cp_async_wait_all();
+            return;
+        }
+        if (buf) ph1 ^= 1u; else ph0 ^= 1u;
+        compute(buf);
+        __syncthreads();
+        buf ^= 1;
+    }
+    cp_async_wait_all();
+}
+
+template <int C>
 __global__ void __launch_bounds__(kThreads) k_release(const Geom g, const CallArgs a) {
     extern __shared__ __align__(16) uint8_t dyn[];
-    __shared__ SegInfo si;
-    const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row;
-    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
+    __shared__ RelItem it[2];
+    __shared__ uint64_t bars[2];
+    const int buf_bytes = g.T * rel_rowstride(g.seg_tiles, g.T, C);
+    uint32_t i0, i1;
+    rel_range(a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row, i0, i1);
+    auto prepare = [&](uint32_t item, int nb) {
         const uint32_t sg = item % g.seg_per_row;
         const uint32_t fr = item / g.seg_per_row;
-        release_item(g, a, fr / g.GR, (int)(fr % g.GR), (int)sg, dyn, si);
-    }
+        rel_prepare(g, a, fr / g.GR, (int)(fr % g.GR), (int)sg, it[nb], dyn + nb * buf_bytes, &bars[nb]);
+    };
+    auto compute = [&](int nb) { rel_compute<C>(g, a, it[nb], dyn + nb * buf_bytes); };
+    rel_loop(i0, i1, bars, a.status, prepare, compute);
 }
 
 // Batch: items = (tile row, segment) of every image, image i owning [base[2], base[2] + GR * seg_per_row).
-__global__ void __launch_bounds__(kThreads) k_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items) {
+template <int C>
+__global__ void __launch_bounds__(kThreads) k_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items,
+                                                            int buf_bytes) {
     extern __shared__ __align__(16) uint8_t dyn[];
-    __shared__ SegInfo si;
-    __shared__ BatchShared bs;
-    int cur = -1;
-    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const int i = batch_find(tab, n_img, item, 2);
-        if (i != cur) {
-            batch_load(tab, i, bs);
-            cur = i;
+    __shared__ RelItem it[2];
+    __shared__ BatchShared bs[2];
+    __shared__ uint64_t bars[2];
+    uint32_t i0, i1;
+    rel_range(items, i0, i1);
+    int cur0 = -1, cur1 = -1;        // image whose geometry bs[0], bs[1] hold
+    int img = -1;                    // image of the last prepared item, owning items [img_lo, img_hi)
+    uint32_t img_lo = 0, img_hi = 0;
+    auto prepare = [&](uint32_t item, int nb) {
+        if (img < 0 || item >= img_hi) {
+            int i = img < 0 ? batch_find(tab, n_img, item, 2) : img;
+            while (i + 1 < (int)n_img && tab[i + 1].base[2] <= item) ++i;
+            img = i;
+            img_lo = tab[i].base[2];
+            img_hi = i + 1 < (int)n_img ? tab[i + 1].base[2] : items;
         }
-        const uint32_t local = item - tab[i].base[2];
-        const int spr = bs.g.seg_per_row;
-        release_item(bs.g, bs.a, 0u, (int)(local / spr), (int)(local % spr), dyn, si);
-    }
+        int &cur = nb ? cur1 : cur0;
+        if (cur != img) {
+            batch_load(tab, img, bs[nb]);
+            cur = img;
+        }
+        const uint32_t local = item - img_lo;
+        const int spr = bs[nb].g.seg_per_row;
+        rel_prepare(bs[nb].g, bs[nb].a, 0u, (int)(local / spr), (int)(local % spr), it[nb], dyn + nb * buf_bytes,
+                    &bars[nb]);
+    };
+    auto compute = [&](int nb) { rel_compute<C>(bs[nb].g, bs[nb].a, it[nb], dyn + nb * buf_bytes); };
+    rel_loop(i0, i1, bars, tab[0].a.status, prepare, compute);
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -367,40 +604,6 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats(const Geom g, const Cal
         }
         __syncthreads();
     }
-}
-
-// Noise, clip and store of one cell's C channels (Alg. 3 steps 9-10 and 15-17) from its Philox words;
-// sigma, b^2 and 1/b^2 (0 when not exact) of its region.  ov (optional) receives the value a
-// reconstruction reads back from the stored element (Sec. VI-F).
-__device__ __forceinline__ void emit_values(const Geom &g, int C, uint8_t *dst, const uint32_t *S, uint4 words,
-                                            float sigma, float b2, float inv_b2, float *ov) {
-#pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
-        if (ch >= C) break;
-        if (g.dtype == DP_PIX_REC_SUM_U32) {
-            reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
-            if (ov) ov[ch] = __fdiv_rn(__uint2float_rn(S[ch]), b2);
-        } else {
-            const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), sigma);
-            const float v = noisy_mean(S[ch], b2, inv_b2, eta, g.R_f);
-            if (g.dtype == DP_PIX_REC_F32) {
-                reinterpret_cast<float *>(dst)[ch] = v;
-                if (ov) ov[ch] = v;
-            } else {
-                const uint32_t q = __float2uint_rn(v);
-                dst[ch] = (uint8_t)q;
-                if (ov) ov[ch] = (float)q;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint8_t *dst, const uint32_t *S, int r,
-                                          uint32_t cell_idx, uint64_t frame, uint32_t sid, float *ov = nullptr) {
-    uint4 words = make_uint4(0, 0, 0, 0);
-    if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
-        words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame);
-    emit_values(g, g.C, dst, S, words, g.sigma_f[r], g.b2_f[r], g.inv_b2_f[r], ov);
 }
 
 // Sum of an nb x nb block of g-cells (C u16 channel sums each; rows rowvals values apart) into S[0..C).
@@ -705,19 +908,35 @@ size_t seg_smem(const Geom &g, int bands_per_tile) {
 }  // namespace
 
 cudaError_t launch_release(const Geom &g, const CallArgs &a, cudaStream_t s) {
-    const size_t smem = seg_smem(g, g.vbands);
+    if (g.seg_tiles > kRelSegMax) return cudaErrorInvalidValue;
+    const int buf_bytes = g.T * rel_rowstride(g.seg_tiles, g.T, g.C);
+    const size_t smem = 2 * (size_t)buf_bytes;
     const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row;
-    const int grid = grid_for(k_release, smem, items);
     prof_begin("k_release", s);
-    k_release<<<grid, kThreads, smem, s>>>(g, a);
+    switch (g.C) {
+        case 1: k_release<1><<<grid_for(k_release<1>, smem, items), kThreads, smem, s>>>(g, a); break;
+        case 2: k_release<2><<<grid_for(k_release<2>, smem, items), kThreads, smem, s>>>(g, a); break;
+        case 3: k_release<3><<<grid_for(k_release<3>, smem, items), kThreads, smem, s>>>(g, a); break;
+        default: k_release<4><<<grid_for(k_release<4>, smem, items), kThreads, smem, s>>>(g, a); break;
+    }
     prof_end("k_release", s);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items, size_t smem, cudaStream_t s) {
-    const int grid = grid_for(k_batch_release, smem, items);
+size_t release_smem(int T, int C, int S) { return 2 * (size_t)T * (size_t)rel_rowstride(S, T, C); }
+
+cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items, int T, int C, int S,
+                                 cudaStream_t s) {
+    if (S > kRelSegMax) return cudaErrorInvalidValue;
+    const int buf_bytes = T * rel_rowstride(S, T, C);
+    const size_t smem = 2 * (size_t)buf_bytes;
     prof_begin("k_batch_release", s);
-    k_batch_release<<<grid, kThreads, smem, s>>>(tab, n_img, items);
+    switch (C) {
+        case 1: k_batch_release<1><<<grid_for(k_batch_release<1>, smem, items), kThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
+        case 2: k_batch_release<2><<<grid_for(k_batch_release<2>, smem, items), kThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
+        case 3: k_batch_release<3><<<grid_for(k_batch_release<3>, smem, items), kThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
+        default: k_batch_release<4><<<grid_for(k_batch_release<4>, smem, items), kThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
+    }
     prof_end("k_batch_release", s);
     return cudaGetLastError();
 }
