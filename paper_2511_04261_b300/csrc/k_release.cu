@@ -222,38 +222,42 @@ __device__ __forceinline__ int udiv_small(int x, int d, float inv) {
 
 // Prepares item (f, ty, sg) into `it` and issues the copies of its map bytes, payload offsets and rows
 // (whole block; no barrier: the caller's barrier after cp.async.wait publishes `it`).
-__device__ __forceinline__ void rel_prepare(const Geom &g, const CallArgs &a, uint32_t f, int ty, int sg, RelItem &it,
+__device__ __forceinline__ void rel_prepare(const Geom &g, const CallArgs &a, uint32_t f, uint32_t rowitem, RelItem &it,
                                             uint8_t *raw, uint64_t *bar) {
-    const int T = g.T, C = g.C, S = g.seg_tiles;
+    const int T = g.T;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (warp * 32 >= max(T, 64)) return;  // the copies need warps 0 and 1 and one thread per row
+    const int C = g.C, S = g.seg_tiles;
     const int rs = rel_rowstride(S, T, C);
-    const int tx0 = sg * S;
+    const int ty = (int)(rowitem / (uint32_t)g.seg_per_row);
+    const int tx0 = ((int)rowitem - ty * g.seg_per_row) * S;
     const int ns = min(S, g.GC - tx0);
     const int x0 = tx0 * T;
     const int xv = min(ns * T, g.N - x0);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uintptr_t msrc = reinterpret_cast<uintptr_t>(a.records + (uint64_t)f * (uint64_t)a.record_stride + g.map_offset +
-                                                       (uint64_t)ty * g.GC + tx0);
-    const int mo = (int)(msrc & 3u);
-    if (tid == 0) {
-        it.ns = ns;
-        it.tx0 = tx0;
-        it.xv = xv;
-        it.padb = (ns * T - xv) * C;
-        it.ty = ty;
-        it.mapoff = mo;
-        it.f = f;
-    }
-    if (tid < ((mo + ns + 3) >> 2)) cp_async4(&it.mapw[tid], reinterpret_cast<const void *>(msrc - mo + 4u * tid));
-    if (tid >= 32 && tid < 32 + ns) {
+    if (warp == 0) {
+        const uintptr_t msrc = reinterpret_cast<uintptr_t>(a.records + (uint64_t)f * (uint64_t)a.record_stride +
+                                                           g.map_offset + (uint64_t)ty * g.GC + tx0);
+        const int mo = (int)(msrc & 3u);
+        if (lane == 0) {
+            it.ns = ns;
+            it.tx0 = tx0;
+            it.xv = xv;
+            it.padb = (ns * T - xv) * C;
+            it.ty = ty;
+            it.mapoff = mo;
+            it.f = f;
+        }
+        if (lane < ((mo + ns + 3) >> 2)) cp_async4(&it.mapw[lane], reinterpret_cast<const void *>(msrc - mo + 4u * lane));
+    } else if (warp == 1 && lane < ns) {
         const uint32_t *toff = reinterpret_cast<const uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff);
-        cp_async4(&it.tileoff[tid - 32], toff + ty * g.GC + tx0 + (tid - 32));
+        cp_async4(&it.tileoff[lane], toff + ty * g.GC + tx0 + lane);
     }
     // rows: thread j issues one bulk copy of row j (the aligned 16-byte granules that hold its bytes); each
     // warp announces its rows' bytes to the mbarrier first
-    const uint8_t *fbase = a.frames + (uint64_t)f * (uint64_t)a.frame_stride + (int64_t)x0 * C;
-    const int vb = xv * C;
-    for (int j0 = warp * 32; j0 < T; j0 += blockDim.x) {
-        const int j = j0 + lane;
+    const int j = tid;
+    if (warp * 32 < T) {
+        const uint8_t *fbase = a.frames + (uint64_t)f * (uint64_t)a.frame_stride + (int64_t)x0 * C;
+        const int vb = xv * C;
         uint32_t bytes = 0;
         const uint8_t *ga = nullptr;
         if (j < T) {
@@ -400,7 +404,11 @@ __device__ __forceinline__ void rel_compute(const Geom &g, const CallArgs &a, co
             const int cy = udiv_small(cell, cs, __fdividef(1.0f, (float)cs)), cx = cell - cy * cs;
             const uint32_t cell_idx =
                 (uint32_t)(it.ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)((it.tx0 + t) * cs + cx);
-            emit_cell(g, a, rec + it.tileoff[t] + (uint64_t)cell * C * g.es, S, r, cell_idx, frame, sid);
+            uint4 words = make_uint4(0, 0, 0, 0);
+            if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
+                words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame);
+            emit_values(g, C, rec + it.tileoff[t] + (uint64_t)cell * C * g.es, S, words, g.sigma_f[r], g.b2_f[r],
+                        g.inv_b2_f[r], nullptr);
         }
     }
 }
@@ -461,10 +469,10 @@ __global__ void __launch_bounds__(kThreads) k_release(const Geom g, const CallAr
     const int buf_bytes = g.T * rel_rowstride(g.seg_tiles, g.T, C);
     uint32_t i0, i1;
     rel_range(a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row, i0, i1);
+    const uint32_t per_frame = (uint32_t)g.GR * (uint32_t)g.seg_per_row;
     auto prepare = [&](uint32_t item, int nb) {
-        const uint32_t sg = item % g.seg_per_row;
-        const uint32_t fr = item / g.seg_per_row;
-        rel_prepare(g, a, fr / g.GR, (int)(fr % g.GR), (int)sg, it[nb], dyn + nb * buf_bytes, &bars[nb]);
+        const uint32_t f = item / per_frame;
+        rel_prepare(g, a, f, item - f * per_frame, it[nb], dyn + nb * buf_bytes, &bars[nb]);
     };
     auto compute = [&](int nb) { rel_compute<C>(g, a, it[nb], dyn + nb * buf_bytes); };
     rel_loop(i0, i1, bars, a.status, prepare, compute);
@@ -496,10 +504,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_release(const BatchEntry *ta
             batch_load(tab, img, bs[nb]);
             cur = img;
         }
-        const uint32_t local = item - img_lo;
-        const int spr = bs[nb].g.seg_per_row;
-        rel_prepare(bs[nb].g, bs[nb].a, 0u, (int)(local / spr), (int)(local % spr), it[nb], dyn + nb * buf_bytes,
-                    &bars[nb]);
+        rel_prepare(bs[nb].g, bs[nb].a, 0u, item - img_lo, it[nb], dyn + nb * buf_bytes, &bars[nb]);
     };
     auto compute = [&](int nb) { rel_compute<C>(bs[nb].g, bs[nb].a, it[nb], dyn + nb * buf_bytes); };
     rel_loop(i0, i1, bars, tab[0].a.status, prepare, compute);
