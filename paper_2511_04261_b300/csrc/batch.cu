@@ -128,7 +128,10 @@ int build_table(dp_pix_batch_s *b, const dp_pix_batch_image *imgs, int out_type)
         e.base[1] = k;
         e.base[2] = rel;
         e.base[3] = rec;
-        cls += (uint32_t)g.GR;
+        {
+            const int cs = cls_seg_tiles(g.T, g.source == DP_PIX_SRC_MATTE_F32 ? 4 : 1);
+            cls += (uint32_t)g.GR * (uint32_t)((g.GC + cs - 1) / cs);
+        }
         rel += (uint32_t)g.GR * (uint32_t)g.seg_per_row;
         rec += (uint32_t)g.GR;
         b->max_gc = std::max<uint32_t>(b->max_gc, (uint32_t)g.GC);
@@ -157,7 +160,7 @@ cudaError_t launch_all(dp_pix_batch_s *b, cudaStream_t s) {
     const Geom &g0 = b->tab[0].g;
     cudaError_t e = cudaSuccess;
     if (g0.source == DP_PIX_SRC_MASK_U8 || g0.source == DP_PIX_SRC_MATTE_F32)
-        e = launch_batch_classify(tab, b->n, b->items_cls, (int)b->max_gc, g0.source == DP_PIX_SRC_MATTE_F32, s);
+        e = launch_batch_classify(tab, b->n, b->items_cls, g0.T, g0.source == DP_PIX_SRC_MATTE_F32, s);
     if (e == cudaSuccess) e = launch_batch_finalize(tab, b->n, b->max_tiles, s);
     if (e == cudaSuccess) e = launch_batch_release(tab, b->n, b->items_rel, g0.T, g0.C, g0.seg_tiles, s);
     if (e == cudaSuccess && b->any_out)

@@ -63,6 +63,13 @@ struct Geom {
 // Row parts of one b x b cell of C-channel u8 samples in the release: the smallest power of two P (at most
 // min(b, 32)) that keeps ceil(b/P) * b * C bytes per part within a budget, so that work units are similar.
 constexpr int kRelPartBytes = 384;
+
+// Tiles per classification item of a batch (source rows of at least 256 bytes, at most 16 tiles); es is the
+// source element size (1: u8 mask, 4: f32 matte).
+__host__ __device__ inline int cls_seg_tiles(int T, int es) {
+    const int S = (256 + T * es - 1) / (T * es);
+    return S < 1 ? 1 : (S > 16 ? 16 : S);
+}
 __host__ __device__ inline int rel_parts(int b, int C) {
     int P = 1;
     while (2 * P <= b && P < 32 && ((b + P - 1) / P) * b * C > kRelPartBytes) P *= 2;
@@ -254,7 +261,7 @@ cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, in
 cudaError_t launch_reconstruct(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out,
                                int64_t out_frame_stride, int64_t out_pitch, int out_type, int max_M, int max_N,
                                int max_C, int out_align, int32_t *status, cudaStream_t s);
-cudaError_t launch_batch_classify(const BatchEntry *tab, uint32_t n_img, uint32_t items, int max_gc, int matte,
+cudaError_t launch_batch_classify(const BatchEntry *tab, uint32_t n_img, uint32_t items, int T, int matte,
                                   cudaStream_t s);
 cudaError_t launch_batch_finalize(const BatchEntry *tab, uint32_t n_img, uint32_t max_tiles, cudaStream_t s);
 cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items, int T, int C, int S,

@@ -83,42 +83,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(const Geom g, const CallA
     classify_row<kMatte>(g, a, blockIdx.x, blockIdx.y, cnt_s);
 }
 
-// Batch: items = tile rows of every image (image i owns items [base_cls, base_cls + GR)).
-template <bool kMatte>
-__global__ void __launch_bounds__(kThreads) k_batch_classify(const BatchEntry *tab, uint32_t n_img, uint32_t items) {
-    extern __shared__ uint32_t cnt_s[];  // [max GC]
-    __shared__ BatchShared bs;
-    int cur = -1;
-    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const int i = batch_find(tab, n_img, item, 0);
-        if (i != cur) {
-            batch_load(tab, i, bs);
-            cur = i;
-        }
-        classify_row<kMatte>(bs.g, bs.a, (int)(item - tab[i].base[0]), 0u, cnt_s);
-        __syncthreads();  // cnt_s and bs are reused by the next item
-    }
-}
-
 }  // namespace
-
-cudaError_t launch_batch_classify(const BatchEntry *tab, uint32_t n_img, uint32_t items, int max_gc, int matte,
-                                  cudaStream_t s) {
-    const size_t smem = (size_t)max_gc * 4;
-    // one wave of resident CTAs looping over the items (a second, partial wave would run its CTAs' whole
-    // shares on an otherwise idle GPU)
-    const void *kern = matte ? reinterpret_cast<const void *>(k_batch_classify<true>)
-                             : reinterpret_cast<const void *>(k_batch_classify<false>);
-    const int per_sm = launch_prep(kern, kThreads, smem);
-    const int grid = (int)std::min<uint64_t>(items, (uint64_t)per_sm * sm_count());
-    prof_begin("k_batch_classify", s);
-    if (matte)
-        k_batch_classify<true><<<grid, kThreads, smem, s>>>(tab, n_img, items);
-    else
-        k_batch_classify<false><<<grid, kThreads, smem, s>>>(tab, n_img, items);
-    prof_end("k_batch_classify", s);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_classify(const Geom &g, const CallArgs &a, cudaStream_t s) {
     const dim3 grid(g.GR, a.n_frames);

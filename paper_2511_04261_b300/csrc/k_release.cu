@@ -220,6 +220,29 @@ __device__ __forceinline__ int udiv_small(int x, int d, float inv) {
     return q;
 }
 
+// Issues one bulk copy per row j < T of image rows ty*T + j (mirrored past M) of `base` (rows `pitch` bytes
+// apart), bytes [0, vb) of each, as the aligned 16-byte granules that hold them, into raw + j * rs;
+// rowbase[j] receives the staged position of byte 0.  Thread j copies row j: the warps with warp*32 < T
+// call this (whole warps).  Each warp announces its rows' bytes to the mbarrier before copying.
+__device__ __forceinline__ void stage_rows(const uint8_t *base, int64_t pitch, int M, int pad_mode, int ty, int T, int vb,
+                                           int rs, uint8_t *raw, int32_t *rowbase, uint64_t *bar) {
+    const int j = threadIdx.x, lane = threadIdx.x & 31;
+    uint32_t bytes = 0;
+    const uint8_t *ga = nullptr;
+    if (j < T) {
+        const int sy = reflect_idx(ty * T + j, M, pad_mode);
+        const uintptr_t addr = reinterpret_cast<uintptr_t>(base + (int64_t)sy * pitch);
+        const int o = (int)(addr & 15u);
+        ga = reinterpret_cast<const uint8_t *>(addr - (uintptr_t)o);
+        bytes = 16u * (uint32_t)((o + vb + 15) >> 4);
+        rowbase[j] = j * rs + o;
+    }
+    const uint32_t wsum = __reduce_add_sync(0xffffffffu, bytes);
+    if (lane == 0) mbar_expect_tx(bar, wsum);
+    __syncwarp();
+    if (j < T) bulk_g2s(raw + j * rs, ga, bytes, bar);
+}
+
 // Prepares item (f, ty, sg) into `it` and issues the copies of its map bytes, payload offsets and rows
 // (whole block; no barrier: the caller's barrier after cp.async.wait publishes `it`).
 __device__ __forceinline__ void rel_prepare(const Geom &g, const CallArgs &a, uint32_t f, uint32_t rowitem, RelItem &it,
@@ -252,27 +275,9 @@ __device__ __forceinline__ void rel_prepare(const Geom &g, const CallArgs &a, ui
         const uint32_t *toff = reinterpret_cast<const uint32_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_tileoff);
         cp_async4(&it.tileoff[lane], toff + ty * g.GC + tx0 + lane);
     }
-    // rows: thread j issues one bulk copy of row j (the aligned 16-byte granules that hold its bytes); each
-    // warp announces its rows' bytes to the mbarrier first
-    const int j = tid;
-    if (warp * 32 < T) {
-        const uint8_t *fbase = a.frames + (uint64_t)f * (uint64_t)a.frame_stride + (int64_t)x0 * C;
-        const int vb = xv * C;
-        uint32_t bytes = 0;
-        const uint8_t *ga = nullptr;
-        if (j < T) {
-            const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
-            const uintptr_t addr = reinterpret_cast<uintptr_t>(fbase + (int64_t)sy * g.pitch);
-            const int o = (int)(addr & 15u);
-            ga = reinterpret_cast<const uint8_t *>(addr - (uintptr_t)o);
-            bytes = 16u * (uint32_t)((o + vb + 15) >> 4);
-            it.rowbase[j] = j * rs + o;
-        }
-        const uint32_t wsum = __reduce_add_sync(0xffffffffu, bytes);
-        if (lane == 0) mbar_expect_tx(bar, wsum);
-        __syncwarp();
-        if (j < T) bulk_g2s(raw + j * rs, ga, bytes, bar);
-    }
+    if (warp * 32 < T)
+        stage_rows(a.frames + (uint64_t)f * (uint64_t)a.frame_stride + (int64_t)x0 * C, g.pitch, g.M, g.pad_mode, ty, T,
+                   xv * C, rs, raw, it.rowbase, bar);
 }
 
 // dp4a mask of channel ch for a word whose first byte is byte 4k of a cell row (C interleaved channels).
@@ -507,6 +512,123 @@ __global__ void __launch_bounds__(kThreads) k_batch_release(const BatchEntry *ta
         rel_prepare(bs[nb].g, bs[nb].a, 0u, item - img_lo, it[nb], dyn + nb * buf_bytes, &bars[nb]);
     };
     auto compute = [&](int nb) { rel_compute<C>(bs[nb].g, bs[nb].a, it[nb], dyn + nb * buf_bytes); };
+    rel_loop(i0, i1, bars, tab[0].a.status, prepare, compute);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// k_batch_classify: tile classification of every image of a batch from its u8 mask or f32 matte (Alg. 3
+// steps 5-6), over (image, tile row, segment of cls_seg_tiles tiles) items with the release's staging loop:
+// each item's T source rows arrive by bulk copies, then one thread per (column, row half) counts the simple
+// samples of its column (mask: nonzero; matte: alpha < thr), mirrored columns past the right edge taken
+// from their staged source column.  A tile is simple (region 0) iff 2 * #simple > T^2, a tie going to
+// complex (region 1).
+// ------------------------------------------------------------------------------------------------------
+struct ClsItem {
+    int32_t ns, tx0, xv, ty;
+    uint32_t cnt[kRelSegMax];
+    int32_t rowbase[kMaxT];
+};
+
+template <bool kMatte>
+__device__ __forceinline__ void cls_compute(const Geom &g, const CallArgs &a, const ClsItem &it, uint8_t *raw,
+                                            uint32_t *cnt_s) {
+    constexpr int es = kMatte ? 4 : 1;
+    const int T = g.T, ns = it.ns, ncols = ns * T;
+    const int x0 = it.tx0 * T;
+    const int rsplit = max(1, (int)blockDim.x / ncols);
+    const int rows_per = (T + rsplit - 1) / rsplit;
+    for (int u = threadIdx.x; u < ncols * rsplit; u += blockDim.x) {
+        const int part = u / ncols, c = u - part * ncols;
+        const int j0 = part * rows_per, j1 = min(T, j0 + rows_per);
+        const int x = x0 + c;
+        int sc = c;  // staged column of the sample
+        bool global = false;
+        if (c >= it.xv) {
+            const int sx = reflect_idx(x, g.N, g.pad_mode);
+            sc = sx - x0;
+            global = sc < 0;
+        }
+        uint32_t n = 0;
+        if (!global) {
+#pragma unroll 4
+            for (int j = j0; j < j1; ++j) {
+                const uint8_t *p = raw + it.rowbase[j] + sc * es;
+                if (kMatte)
+                    n += !(*reinterpret_cast<const float *>(p) >= g.matte_thr) ? 1u : 0u;
+                else
+                    n += *p != 0 ? 1u : 0u;
+            }
+        } else {
+            const int sx = reflect_idx(x, g.N, g.pad_mode);
+            for (int j = j0; j < j1; ++j) {
+                const int sy = reflect_idx(it.ty * T + j, g.M, g.pad_mode);
+                const uint8_t *p = a.src + (int64_t)sy * a.src_pitch + (int64_t)sx * es;
+                if (kMatte)
+                    n += !(*reinterpret_cast<const float *>(p) >= g.matte_thr) ? 1u : 0u;
+                else
+                    n += *p != 0 ? 1u : 0u;
+            }
+        }
+        atomicAdd(&cnt_s[c / T], n);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < ns) {
+        uint8_t *map = a.records + g.map_offset + (uint64_t)it.ty * g.GC + it.tx0;
+        map[threadIdx.x] = (2u * cnt_s[threadIdx.x] > (uint32_t)T * (uint32_t)T) ? 0 : 1;
+        cnt_s[threadIdx.x] = 0u;  // ready for the next item
+    }
+}
+
+template <bool kMatte>
+__global__ void __launch_bounds__(kThreads) k_batch_classify(const BatchEntry *tab, uint32_t n_img, uint32_t items,
+                                                             int buf_bytes) {
+    constexpr int es = kMatte ? 4 : 1;
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ ClsItem it[2];
+    __shared__ BatchShared bs[2];
+    __shared__ uint64_t bars[2];
+    __shared__ uint32_t cnt_s[kRelSegMax];
+    if (threadIdx.x < kRelSegMax) cnt_s[threadIdx.x] = 0u;
+    uint32_t i0, i1;
+    rel_range(items, i0, i1);
+    int cur0 = -1, cur1 = -1;
+    int img = -1;
+    uint32_t img_lo = 0, img_hi = 0;
+    auto prepare = [&](uint32_t item, int nb) {
+        if (img < 0 || item >= img_hi) {
+            int i = img < 0 ? batch_find(tab, n_img, item, 0) : img;
+            while (i + 1 < (int)n_img && tab[i + 1].base[0] <= item) ++i;
+            img = i;
+            img_lo = tab[i].base[0];
+            img_hi = i + 1 < (int)n_img ? tab[i + 1].base[0] : items;
+        }
+        int &cur = nb ? cur1 : cur0;
+        if (cur != img) {
+            batch_load(tab, img, bs[nb]);
+            cur = img;
+        }
+        const Geom &g = bs[nb].g;
+        const int T = g.T;
+        if ((int)(threadIdx.x & ~31u) >= T) return;  // whole warps: the rows' copies start with a warp reduction
+        const int S = cls_seg_tiles(T, es);
+        const int spr = (g.GC + S - 1) / S;
+        const uint32_t rowitem = item - img_lo;
+        const int ty = (int)(rowitem / (uint32_t)spr);
+        const int tx0 = ((int)rowitem - ty * spr) * S;
+        const int ns = min(S, g.GC - tx0);
+        const int x0 = tx0 * T;
+        const int xv = min(ns * T, g.N - x0);
+        ClsItem &c = it[nb];
+        if (threadIdx.x == 0) {
+            c.ns = ns;
+            c.tx0 = tx0;
+            c.xv = xv;
+            c.ty = ty;
+        }
+        stage_rows(bs[nb].a.src + (int64_t)x0 * es, bs[nb].a.src_pitch, g.M, g.pad_mode, ty, T, xv * es,
+                   rel_rowstride(S, T, es), dyn + nb * buf_bytes, c.rowbase, &bars[nb]);
+    };
+    auto compute = [&](int nb) { cls_compute<kMatte>(bs[nb].g, bs[nb].a, it[nb], dyn + nb * buf_bytes, cnt_s); };
     rel_loop(i0, i1, bars, tab[0].a.status, prepare, compute);
 }
 
@@ -943,6 +1065,23 @@ cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t
         default: k_batch_release<4><<<grid_for(k_batch_release<4>, smem, items), kThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
     }
     prof_end("k_batch_release", s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_classify(const BatchEntry *tab, uint32_t n_img, uint32_t items, int T, int matte,
+                                  cudaStream_t s) {
+    const int es = matte ? 4 : 1;
+    const int S = cls_seg_tiles(T, es);
+    const int buf_bytes = T * rel_rowstride(S, T, es);
+    const size_t smem = 2 * (size_t)buf_bytes;
+    prof_begin("k_batch_classify", s);
+    if (matte)
+        k_batch_classify<true><<<grid_for(k_batch_classify<true>, smem, items), kThreads, smem, s>>>(tab, n_img, items,
+                                                                                                      buf_bytes);
+    else
+        k_batch_classify<false><<<grid_for(k_batch_classify<false>, smem, items), kThreads, smem, s>>>(tab, n_img, items,
+                                                                                                        buf_bytes);
+    prof_end("k_batch_classify", s);
     return cudaGetLastError();
 }
 
