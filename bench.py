@@ -638,6 +638,130 @@ def run_uniform(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------------------
+# workload "utility": Sobel edge masks and the MSE / SSIM of a release (Sec. VI-A masks; Sec. VII-A, VII-B
+# utility measures) on 16 frames of the 1080p clip, plus the paper's three utility sweeps on a 768 x 576 frame
+# ------------------------------------------------------------------------------------------------------
+UTILITY = dict(frames=16, M=1080, N=1920, tau=(3 * 60) ** 2, sweep_b=list(range(2, 21)), sweep_m=[4, 8, 16, 32, 64, 128, 256],
+               sweep_eps=[0.1, 0.25, 0.5, 1.0, 1.5, 2.0], seed=6)
+UTILITY_METRIC = ("megapixels/sec through Sobel edge masks + MSE/SSIM of the release (1 B300); ALU roofline of the "
+                  "SSIM kernel")
+# integer operations per 7 x 7 window and channel: the five window sums slide by one row (2 rows x 7 taps x
+# 5 multiply-adds) and the window value is evaluated from them (~20 integer and float operations)
+SSIM_OPS_PER_WINDOW = 90
+# ALU peak: 148 SMs x 128 32-bit lanes x the maximum SM clock
+ALU_PEAK_TOPS = 148 * 128 * 2.032e9 / 1e12
+
+
+def run_utility(args):
+    import torch
+    import paper_2511_04261_b300 as P
+    from paper_2511_04261_b300 import build, synth
+    build.build()
+    world, rank, _ = dist_setup(args.gpus)
+    F, M, N = UTILITY["frames"], UTILITY["M"], UTILITY["N"]
+    x = torch.from_numpy(synth.moving_rect_clip(seed=1006 + rank, frames=F, M=M, N=N, C=3)).cuda()
+    plan = P.Plan(M=M, N=N, C=3, grids=GRIDS, eps=EPS, m=MVAR, seed=SEED, source=P.SRC_VARIANCE, dtype=P.REC_F32)
+    recs, ws = plan.alloc_records(F), plan.alloc_workspace(F)
+    y = torch.empty_like(x)
+    plan.release_reconstruct(x, None, records=recs, out=y, ws=ws, stream_id=rank)
+    masks = torch.empty((F, M, N), dtype=torch.uint8, device="cuda")
+    ubuf = torch.empty((F, 40), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        P.dp_pix_sobel_mask(x, UTILITY["tau"], out=masks)
+        P.dp_pix_utility(x, y, out=ubuf)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    value = world * F * M * N / 1e6 / (ms / 1e3)
+    P.prof_reset()
+    P.prof_enable(True)
+    for _ in range(5):
+        step()
+    torch.cuda.synchronize()
+    prof = P.prof_read()
+    P.prof_enable(False)
+    vals = P.utility_values(ubuf)
+    hbm, peak_kind = measured_peaks()
+    windows = F * (M - 6) * (N - 6) * 3
+    ssim_ms = prof["k_ssim"][1] / prof["k_ssim"][0]
+    ssim_tops = windows * SSIM_OPS_PER_WINDOW / (ssim_ms / 1e3) / 1e12
+    algo = {"k_sobel_mask": F * M * N * 4, "k_ssim": F * M * N * 6}
+    tot = sum(v[1] for v in prof.values())
+    roofline = {"bound": "alu", "kernel": "k_ssim", "achieved": ssim_tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                "frac": ssim_tops / ALU_PEAK_TOPS, "traffic": None,
+                "algorithmic_ops_per_launch": windows * SSIM_OPS_PER_WINDOW, "avg_launch_ms": ssim_ms,
+                "peak_source": "148 SMs x 128 int32 lanes x 2032 MHz (derived)",
+                "kernels": {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / max(1e-9, tot),
+                                "algorithmic_GBps": algo[k] / (v[1] / max(1, v[0]) / 1e3) / 1e9 if k in algo else None,
+                                "hbm_frac": algo[k] / (v[1] / max(1, v[0]) / 1e3) / 1e9 / hbm if k in algo else None}
+                            for k, v in prof.items()}}
+    # the paper's three sweeps (Sec. VII-A): b at eps 0.5, m 16; m at b 16, eps 0.5; eps at b 16, m 16 -- one
+    # 768 x 576 RGB frame, uniform grid (Alg. 2), MSE and SSIM of the reconstruction against the frame
+    f_h, _ = synth.rect_frame(seed=1001)
+    f = torch.from_numpy(f_h).cuda()
+
+    def util_of(b, m, eps):
+        pl = P.Plan(M=576, N=768, C=3, grids=[b], eps=[eps], m=m, seed=UTILITY["seed"], source=P.SRC_TILE_LABELS)
+        lab = torch.zeros((1, -(-576 // b), -(-768 // b)), dtype=torch.uint8, device="cuda")
+        out = torch.empty((1, 576, 768, 3), dtype=torch.uint8, device="cuda")
+        pl.release_reconstruct(f[None], lab, out=out)
+        v = P.utility_values(P.dp_pix_utility(f, out[0]))[0]
+        return {"mse": v["mse"], "ssim": v["ssim"]}
+
+    sweeps = {"b (eps 0.5, m 16)": {b: util_of(b, 16.0, 0.5) for b in UTILITY["sweep_b"]},
+              "m (b 16, eps 0.5)": {m: util_of(16, float(m), 0.5) for m in UTILITY["sweep_m"]},
+              "eps (b 16, m 16)": {e: util_of(16, 16.0, e) for e in UTILITY["sweep_eps"]}}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import utility as OU
+        xh, yh = x[0].cpu().numpy(), y[0].cpu().numpy()
+        t0 = time.perf_counter()
+        OU.sobel_mask(xh, UTILITY["tau"])
+        OU.mse(xh, yh)
+        crop = (64, 128)
+        OU.ssim(xh[:crop[0], :crop[1]], yh[:crop[0], :crop[1]])
+        dt = time.perf_counter() - t0
+        px = M * N  # the Sobel mask and MSE cover the frame; the SSIM sample is a 64 x 128 crop
+        cpu = {"value": (px / 1e6) / dt, "unit": "Mpx/s", "cores": 1, "kind": "oracle",
+               "sample": "one 1920 x 1080 frame: Sobel mask and MSE of the whole frame, SSIM of a 64 x 128 crop "
+                         "(oracle, numpy, 1 thread, %.2f s)" % dt}
+    if rank == 0:
+        line = {"metric": UTILITY_METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+                "config": {"workload": "utility16_1920x1080_rgb_sobel_mse_ssim", "frames": F, "M": M, "N": N, "C": 3,
+                           "sobel_tau": UTILITY["tau"], "ssim": "7x7 uniform windows, sample statistics, L 255",
+                           "step": "dp_pix_sobel_mask + dp_pix_utility (MSE, SSIM) of 16 frames against their release",
+                           "l2": "inputs larger than L2 (100 MB frames + 100 MB releases read per step)",
+                           "generator_seed": 1006, "parallelism": "1 GPU" if world == 1 else "replicas"},
+                "utility_of_step_frames": {"mse_mean": sum(v["mse"] for v in vals) / F,
+                                           "ssim_mean": sum(v["ssim"] for v in vals) / F},
+                "sweeps_768x576": sweeps, "roofline": roofline, "cpu_baseline": cpu, "e2e": None, "clocks": clocks,
+                "gpu_launches": args.steps * 3}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def run_soft(args):
     import torch
     import paper_2511_04261_b300 as P
@@ -1079,10 +1203,11 @@ def main():
     ap.add_argument("--split", type=int, default=None, help="DP_PIX_TUNE_SPLIT (default: the plan's)")
     ap.add_argument("--path", choices=["fused", "two-call"], default="fused",
                     help="fused: dp_pix_release_reconstruct; two-call: dp_pix_release then dp_pix_reconstruct")
-    ap.add_argument("--workload", choices=["clip", "soft", "batch", "serve", "uniform"], default="clip",
+    ap.add_argument("--workload", choices=["clip", "soft", "batch", "serve", "uniform", "utility"], default="clip",
                     help="clip: the 64-frame 1080p release + reconstruction (the benchmark); soft: the differentiable "
                          "layer on a 32 x 3 x 1024 x 1024 batch; batch: 256 ragged portraits with mattes; serve: 16 "
-                         "camera streams; uniform: Alg. 2 on grayscale 768 x 576 and 1920 x 1080 frames, b = 2..20")
+                         "camera streams; uniform: Alg. 2 on grayscale 768 x 576 and 1920 x 1080 frames, b = 2..20; "
+                         "utility: Sobel masks and MSE/SSIM of a release, with the paper's b / m / eps sweeps")
     args = ap.parse_args()
     set_frames(args.frames)
     if args.warmup < 3:
@@ -1091,6 +1216,8 @@ def main():
         return run_reference(args)
     if args.workload == "uniform":
         return run_uniform(args)
+    if args.workload == "utility":
+        return run_utility(args)
     if args.workload == "soft":
         return run_soft(args)
     if args.workload == "batch":

@@ -434,6 +434,48 @@ DPPIX_API int dp_pix_reconstruct(const void *d_records, int64_t record_stride, u
 DPPIX_API int dp_pix_debug_noise(uint64_t seed, const uint32_t *d_ctr, uint64_t n, uint32_t *d_words, float *d_eta,
                        float sigma, void *cuda_stream);
 
+/* ---- utility metrics and edge masks ------------------------------------------------------------------- */
+/*
+ * Edge-based simple/complex pixel mask (Sec. VI-A: region masks from an edge detector such as the Sobel
+ * operator).  For each pixel: I = sum of its C samples; Gx, Gy = the 3 x 3 Sobel responses of I (Gx: right
+ * column minus left column with row weights 1, 2, 1; Gy: bottom row minus top row with column weights
+ * 1, 2, 1), the frame mirrored at its four borders by pad_mode (DP_PIX_PAD_REFLECT: edge sample not
+ * repeated; DP_PIX_PAD_SYMMETRIC: repeated).  mask = 1 (simple) if Gx^2 + Gy^2 < tau, else 0 (complex):
+ * exact integers, so tau is a threshold on the squared gradient in channel-sum units.  The mask is the
+ * input of a DP_PIX_SRC_MASK_U8 release.
+ *   d_frames: n_frames frames of M x N x C u8, rows row_pitch bytes apart, frames frame_stride apart.
+ *   d_mask:   n_frames u8 masks of M x N, rows mask_pitch apart, frames mask_frame_stride apart.
+ * Caller-owned device buffers; asynchronous on cuda_stream.  Errors: INVALID_ARG (M or N < 2, C outside
+ * 1..4, bad pad_mode, pitches or strides too small, NULL), UNSUPPORTED (M or N > 2^24), CUDA.
+ */
+DPPIX_API int dp_pix_sobel_mask(const void *d_frames, int32_t M, int32_t N, int32_t C, int64_t row_pitch,
+                                int64_t frame_stride, uint32_t n_frames, int32_t pad_mode, uint32_t tau, void *d_mask,
+                                int64_t mask_pitch, int64_t mask_frame_stride, void *cuda_stream);
+
+/* Per-frame utility of a release (Sec. VII-A, VII-B: MSE and SSIM of the released frame against the
+ * original).  Written by dp_pix_utility in device memory. */
+typedef struct dp_pix_utility_t {
+    uint64_t sse;                 /* exact sum of squared sample differences */
+    uint64_t windows;             /* 7 x 7 windows per channel: (M - 6)(N - 6) */
+    double ssim_sum;              /* sum of the window SSIM values over windows and channels */
+    double mse;                   /* sse / (M N C) */
+    double ssim;                  /* ssim_sum / (windows C) */
+} dp_pix_utility_t;
+
+/*
+ * MSE and SSIM of n_frames image pairs (x: original, y: release), M x N x C u8.  SSIM is Wang et al.'s
+ * structural similarity (IEEE TIP 2004) with the defaults of the toolkit the paper used: every 7 x 7
+ * window inside the image, uniform weights, sample variances and covariance (1/48 normalisation),
+ * C1 = (0.01 * 255)^2, C2 = (0.03 * 255)^2, the mean over windows and channels.  Window sums are exact
+ * integers; each window's value is rounded once (fp32) and summed in fp64.
+ *   d_out: n_frames entries of dp_pix_utility_t (device memory, 8-byte aligned), zeroed by this call.
+ * Caller-owned device buffers; asynchronous on cuda_stream.  Errors: INVALID_ARG (M or N < 7, C outside
+ * 1..4, pitches or strides too small, NULL, misaligned d_out), UNSUPPORTED (M or N > 2^24), CUDA.
+ */
+DPPIX_API int dp_pix_utility(const void *d_x, const void *d_y, int32_t M, int32_t N, int32_t C, int64_t pitch_x,
+                             int64_t pitch_y, int64_t frame_stride_x, int64_t frame_stride_y, uint32_t n_frames,
+                             dp_pix_utility_t *d_out, void *cuda_stream);
+
 /* Synchronizes cuda_stream and returns DP_PIX_OK, or the first device-side error code recorded since the
  * last call (then clears it).  *detail (may be NULL) receives a kernel-specific detail word. */
 DPPIX_API int dp_pix_status(void *cuda_stream, uint32_t *detail);

@@ -14,5 +14,6 @@ from .api import (Plan, dp_pix_debug_noise, dp_pix_plan, dp_pix_reconstruct, dp_
 from .batch import BatchPlan
 from .serve import Server, dp_pix_release_keyed
 from .soft import SoftPixelize, SoftSpec, soft_backward, soft_forward, soft_pixelize
+from .utility import dp_pix_sobel_mask, dp_pix_utility, utility_values
 
 __version__ = "0.1.0"

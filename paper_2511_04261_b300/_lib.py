@@ -77,6 +77,11 @@ class Sizes(ct.Structure):
     ]
 
 
+class Utility(ct.Structure):
+    _fields_ = [("sse", ct.c_uint64), ("windows", ct.c_uint64), ("ssim_sum", ct.c_double), ("mse", ct.c_double),
+                ("ssim", ct.c_double)]
+
+
 class ProfEntry(ct.Structure):
     _fields_ = [("name", ct.c_char * 48), ("launches", ct.c_uint64), ("total_ms", ct.c_double)]
 
@@ -130,6 +135,8 @@ def lib():
     L.dp_pix_reconstruct.argtypes = [P, I64, U32, P, I64, I64, ct.c_int, I32, I32, I32, P]
     L.dp_pix_debug_noise.argtypes = [U64, P, U64, P, P, ct.c_float, P]
     L.dp_pix_status.argtypes = [P, ct.POINTER(U32)]
+    L.dp_pix_sobel_mask.argtypes = [P, I32, I32, I32, I64, I64, U32, I32, U32, P, I64, I64, P]
+    L.dp_pix_utility.argtypes = [P, P, I32, I32, I32, I64, I64, I64, I64, U32, P, P]
     L.dp_pix_last_error.restype = ct.c_char_p
     L.dp_pix_last_error.argtypes = []
     L.dp_pix_version.restype = ct.c_int
@@ -145,6 +152,7 @@ def lib():
                  "dp_pix_store_batch",
                  "dp_pix_reconstruct",
                  "dp_pix_debug_noise", "dp_pix_status", "dp_pix_prof_enable", "dp_pix_prof_read",
+                 "dp_pix_sobel_mask", "dp_pix_utility",
                  "dp_pix_prof_reset"):
         getattr(L, name).restype = ct.c_int
     _lib = L

@@ -1,0 +1,271 @@
+// k_utility.cu -- utility metrics of a release against its original (MSE, SSIM; Sec. VII-A, VII-B) and an
+// edge-based simple/complex pixel mask (the Sobel operator named for region masks in Sec. VI-A).
+//
+// - k_sobel_mask: one CTA per (frame, 32 rows, 256 columns): the channel-sum intensity of the block and a
+//   one-pixel mirrored border is staged in shared memory as u16, then each thread walks one column down the
+//   32 rows: Gx, Gy from the 3 x 3 Sobel taps in exact integers, mask = (Gx^2 + Gy^2 < tau) ? 1 : 0.
+// - k_ssim: one CTA per (frame, 32 window-centre rows, 128 window-centre columns); the 38 x 134-pixel
+//   input block of both images is staged in shared memory; each thread keeps, per channel, the five exact
+//   integer window sums (Sx, Sy, Sxx, Syy, Sxy) of its column's 7 x 7 window and slides it down the rows
+//   (adding the entering row's 7 taps, subtracting the leaving one's).  The window value is evaluated from
+//   the exact sums: with D = 49 Sxx - Sx^2 (and likewise), the 1/49^2 and 1/(49*48) factors of the means,
+//   variances and covariance cancel, so SSIM = (2 Sx Sy + c1)(2 Dxy + c2) / ((Sx^2 + Sy^2 + c1)(Dx + Dy + c2))
+//   with c1 = 49^2 C1 and c2 = 49*48 C2; only that last expression is rounded (fp32).  Window values are
+//   summed in fp64 per thread, then per block, then atomically per frame.  The exact u64 sum of squared
+//   sample differences comes from the same staged blocks, each block taking the pixels of its own window
+//   corners (the last block row and column also the image's last six rows and columns).
+// - k_utility_finalize: MSE = SSE / (M N C), SSIM = sum / ((M-6)(N-6) C).
+#include "common.cuh"
+
+namespace dppix {
+namespace {
+
+constexpr int kSobRows = 32, kSobCols = 256;
+constexpr int kSsimRows = 32, kSsimCols = 128, kWin = 7;
+
+// Mirror index on both sides for one-pixel borders and clamped overhangs (n >= 2).
+__device__ __forceinline__ int mirror2(int p, int n, int mode) {
+    if (p < 0) p = mode == DP_PIX_PAD_REFLECT ? -p : -p - 1;
+    if (p > n) p = n;
+    if (p == n) p = mode == DP_PIX_PAD_REFLECT ? n - 2 : n - 1;
+    return p;
+}
+
+template <int C>
+__global__ void __launch_bounds__(kSobCols) k_sobel_mask(const uint8_t *frames, int M, int N, int64_t pitch,
+                                                         int64_t fstride, int pad_mode, uint32_t tau, uint8_t *mask,
+                                                         int64_t mpitch, int64_t mfstride) {
+    __shared__ uint16_t I[kSobRows + 2][kSobCols + 2];
+    const int x0 = blockIdx.x * kSobCols, y0 = blockIdx.y * kSobRows;
+    const uint8_t *fb = frames + (int64_t)blockIdx.z * fstride;
+    constexpr int W = kSobCols + 2;
+    for (int idx = threadIdx.x; idx < (kSobRows + 2) * W; idx += blockDim.x) {
+        const int r = idx / W, c = idx - r * W;
+        const int y = mirror2(y0 - 1 + r, M, pad_mode), x = mirror2(x0 - 1 + c, N, pad_mode);
+        const uint8_t *p = fb + (int64_t)y * pitch + (int64_t)x * C;
+        uint32_t s = 0;
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch) s += __ldg(p + ch);
+        I[r][c] = (uint16_t)s;
+    }
+    __syncthreads();
+    const int c = threadIdx.x, x = x0 + c;
+    if (x >= N) return;
+    uint8_t *mb = mask + (int64_t)blockIdx.z * mfstride + x;
+    const int rows = min(kSobRows, M - y0);
+    for (int r = 0; r < rows; ++r) {
+        const int gx = ((int)I[r][c + 2] - (int)I[r][c]) + 2 * ((int)I[r + 1][c + 2] - (int)I[r + 1][c]) +
+                       ((int)I[r + 2][c + 2] - (int)I[r + 2][c]);
+        const int gy = ((int)I[r + 2][c] + 2 * (int)I[r + 2][c + 1] + (int)I[r + 2][c + 2]) -
+                       ((int)I[r][c] + 2 * (int)I[r][c + 1] + (int)I[r][c + 2]);
+        mb[(int64_t)(y0 + r) * mpitch] = ((uint32_t)(gx * gx + gy * gy) < tau) ? 1 : 0;
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Five exact sums of the 7 taps of staged row r, window columns [t, t + 7), channel ch.
+template <int C>
+__device__ __forceinline__ void row_taps(const uint8_t *xs, const uint8_t *ys, int rowbytes, int r, int t, int ch,
+                                         int &sx, int &sy, int &sxx, int &syy, int &sxy) {
+    const uint8_t *xp = xs + r * rowbytes + t * C + ch, *yp = ys + r * rowbytes + t * C + ch;
+    int a0 = 0, b0 = 0, aa = 0, bb = 0, ab = 0;
+#pragma unroll
+    for (int k = 0; k < kWin; ++k) {
+        const int a = xp[k * C], b = yp[k * C];
+        a0 += a;
+        b0 += b;
+        aa += a * a;
+        bb += b * b;
+        ab += a * b;
+    }
+    sx = a0;
+    sy = b0;
+    sxx = aa;
+    syy = bb;
+    sxy = ab;
+}
+
+template <int C>
+__global__ void __launch_bounds__(kSsimCols) k_ssim(const uint8_t *x, const uint8_t *y, int M, int N, int64_t px,
+                                                    int64_t py, int64_t fsx, int64_t fsy, float c1, float c2,
+                                                    dp_pix_utility_t *out) {
+    constexpr int SR = kSsimRows + kWin - 1, SC = kSsimCols + kWin - 1;
+    constexpr int RB = SC * C;  // staged bytes per row
+    __shared__ uint8_t xs[SR * RB], ys[SR * RB];
+    __shared__ double part[kSsimCols / 32];
+    const int f = blockIdx.z;
+    const int cy0 = blockIdx.y * kSsimRows, cx0 = blockIdx.x * kSsimCols;  // first window (top-left corner)
+    const int nwy = M - kWin + 1, nwx = N - kWin + 1;                      // windows per column / row
+    const int rows_in = min(SR, M - cy0), cols_in = min(SC, N - cx0);
+    const uint8_t *xb = x + (int64_t)f * fsx + (int64_t)cy0 * px + (int64_t)cx0 * C;
+    const uint8_t *yb = y + (int64_t)f * fsy + (int64_t)cy0 * py + (int64_t)cx0 * C;
+    const int nb = cols_in * C;
+    for (int idx = threadIdx.x; idx < rows_in * RB; idx += blockDim.x) {
+        const int r = idx / RB, k = idx - r * RB;
+        if (k < nb) {
+            xs[idx] = __ldg(xb + (int64_t)r * px + k);
+            ys[idx] = __ldg(yb + (int64_t)r * py + k);
+        }
+    }
+    __syncthreads();
+    // squared differences of the pixels this block owns: its 32 x 128 window corners, extended to the image's
+    // last row / column in the last block row / column (all of them staged)
+    {
+        const int ro = blockIdx.y + 1 == gridDim.y ? rows_in : kSsimRows;
+        const int co = (blockIdx.x + 1 == gridDim.x ? cols_in : kSsimCols) * C;
+        unsigned long long e = 0;
+        for (int r = 0; r < ro; ++r)
+            for (int k = threadIdx.x; k < co; k += blockDim.x) {
+                const int d = (int)xs[r * RB + k] - (int)ys[r * RB + k];
+                e += (unsigned long long)(d * d);
+            }
+        e = warp_sum_u64(e);
+        if ((threadIdx.x & 31) == 0 && e) atomicAdd(reinterpret_cast<unsigned long long *>(&out[f].sse), e);
+    }
+    const int t = threadIdx.x;
+    const int wx = cx0 + t;
+    const int nrows = min(kSsimRows, nwy - cy0);
+    double acc = 0.0;
+    if (wx < nwx) {
+#pragma unroll 1
+        for (int ch = 0; ch < C; ++ch) {
+            int Sx = 0, Sy = 0, Sxx = 0, Syy = 0, Sxy = 0;
+            for (int r = 0; r < kWin; ++r) {
+                int a, b, aa, bb, ab;
+                row_taps<C>(xs, ys, RB, r, t, ch, a, b, aa, bb, ab);
+                Sx += a;
+                Sy += b;
+                Sxx += aa;
+                Syy += bb;
+                Sxy += ab;
+            }
+            for (int i = 0; i < nrows; ++i) {
+                const long long dx = 49ll * Sxx - (long long)Sx * Sx;
+                const long long dy = 49ll * Syy - (long long)Sy * Sy;
+                const long long dxy = 49ll * Sxy - (long long)Sx * Sy;
+                const float num = (2.0f * (float)((long long)Sx * Sy) + c1) * (2.0f * (float)dxy + c2);
+                const float den = ((float)((long long)Sx * Sx + (long long)Sy * Sy) + c1) * ((float)(dx + dy) + c2);
+                acc += (double)__fdiv_rn(num, den);
+                if (i + 1 < nrows) {
+                    int a, b, aa, bb, ab;
+                    row_taps<C>(xs, ys, RB, i + kWin, t, ch, a, b, aa, bb, ab);
+                    Sx += a;
+                    Sy += b;
+                    Sxx += aa;
+                    Syy += bb;
+                    Sxy += ab;
+                    row_taps<C>(xs, ys, RB, i, t, ch, a, b, aa, bb, ab);
+                    Sx -= a;
+                    Sy -= b;
+                    Sxx -= aa;
+                    Syy -= bb;
+                    Sxy -= ab;
+                }
+            }
+        }
+    }
+    acc = warp_sum_f64(acc);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kSsimCols / 32; ++w) s += part[w];
+        atomicAdd(&out[f].ssim_sum, s);
+    }
+}
+
+__global__ void k_utility_finalize(dp_pix_utility_t *out, uint32_t n, int M, int N, int C) {
+    const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n) return;
+    const uint64_t w = (uint64_t)(M - kWin + 1) * (uint64_t)(N - kWin + 1);
+    out[f].windows = w;
+    out[f].mse = (double)out[f].sse / ((double)M * (double)N * (double)C);
+    out[f].ssim = out[f].ssim_sum / ((double)w * (double)C);
+}
+
+}  // namespace
+}  // namespace dppix
+
+using namespace dppix;
+
+extern "C" {
+
+int dp_pix_sobel_mask(const void *d_frames, int32_t M, int32_t N, int32_t C, int64_t row_pitch, int64_t frame_stride,
+                      uint32_t n_frames, int32_t pad_mode, uint32_t tau, void *d_mask, int64_t mask_pitch,
+                      int64_t mask_frame_stride, void *cuda_stream) {
+    if (!d_frames || !d_mask) return set_last_error(DP_PIX_E_INVALID_ARG, "null frame or mask pointer");
+    if (M < 2 || N < 2 || C < 1 || C > 4 || n_frames < 1 || n_frames > 65535)
+        return set_last_error(DP_PIX_E_INVALID_ARG, "need M, N >= 2, C in 1..4, 1 <= n_frames <= 65535");
+    if (M > (1 << 24) || N > (1 << 24)) return set_last_error(DP_PIX_E_UNSUPPORTED, "M or N too large");
+    if (pad_mode != DP_PIX_PAD_REFLECT && pad_mode != DP_PIX_PAD_SYMMETRIC)
+        return set_last_error(DP_PIX_E_INVALID_ARG, "pad_mode must be REFLECT or SYMMETRIC");
+    if (row_pitch < (int64_t)N * C || mask_pitch < N)
+        return set_last_error(DP_PIX_E_INVALID_ARG, "row_pitch < N*C or mask_pitch < N");
+    if (n_frames > 1 && (frame_stride < row_pitch * M || mask_frame_stride < mask_pitch * M))
+        return set_last_error(DP_PIX_E_INVALID_ARG, "frame strides smaller than a frame");
+    const int rc = cuda_device_ok();
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const dim3 grid((N + kSobCols - 1) / kSobCols, (M + kSobRows - 1) / kSobRows, n_frames);
+    const uint8_t *fr = static_cast<const uint8_t *>(d_frames);
+    uint8_t *mk = static_cast<uint8_t *>(d_mask);
+    prof_begin("k_sobel_mask", s);
+    switch (C) {
+        case 1: k_sobel_mask<1><<<grid, kSobCols, 0, s>>>(fr, M, N, row_pitch, frame_stride, pad_mode, tau, mk, mask_pitch, mask_frame_stride); break;
+        case 2: k_sobel_mask<2><<<grid, kSobCols, 0, s>>>(fr, M, N, row_pitch, frame_stride, pad_mode, tau, mk, mask_pitch, mask_frame_stride); break;
+        case 3: k_sobel_mask<3><<<grid, kSobCols, 0, s>>>(fr, M, N, row_pitch, frame_stride, pad_mode, tau, mk, mask_pitch, mask_frame_stride); break;
+        default: k_sobel_mask<4><<<grid, kSobCols, 0, s>>>(fr, M, N, row_pitch, frame_stride, pad_mode, tau, mk, mask_pitch, mask_frame_stride); break;
+    }
+    prof_end("k_sobel_mask", s);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DP_PIX_OK : set_last_error(DP_PIX_E_CUDA, cudaGetErrorString(e));
+}
+
+int dp_pix_utility(const void *d_x, const void *d_y, int32_t M, int32_t N, int32_t C, int64_t pitch_x, int64_t pitch_y,
+                   int64_t frame_stride_x, int64_t frame_stride_y, uint32_t n_frames, dp_pix_utility_t *d_out,
+                   void *cuda_stream) {
+    if (!d_x || !d_y || !d_out) return set_last_error(DP_PIX_E_INVALID_ARG, "null pointer");
+    if (M < kWin || N < kWin || C < 1 || C > 4 || n_frames < 1 || n_frames > 65535)
+        return set_last_error(DP_PIX_E_INVALID_ARG, "need M, N >= 7, C in 1..4, 1 <= n_frames <= 65535");
+    if (M > (1 << 24) || N > (1 << 24)) return set_last_error(DP_PIX_E_UNSUPPORTED, "M or N too large");
+    if (pitch_x < (int64_t)N * C || pitch_y < (int64_t)N * C)
+        return set_last_error(DP_PIX_E_INVALID_ARG, "row pitch < N*C");
+    if (n_frames > 1 && (frame_stride_x < pitch_x * M || frame_stride_y < pitch_y * M))
+        return set_last_error(DP_PIX_E_INVALID_ARG, "frame strides smaller than a frame");
+    if (reinterpret_cast<uintptr_t>(d_out) % 8) return set_last_error(DP_PIX_E_INVALID_ARG, "d_out not 8-byte aligned");
+    const int rc = cuda_device_ok();
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(dp_pix_utility_t) * n_frames, s);
+    if (e != cudaSuccess) return set_last_error(DP_PIX_E_CUDA, cudaGetErrorString(e));
+    const uint8_t *xp = static_cast<const uint8_t *>(d_x), *yp = static_cast<const uint8_t *>(d_y);
+    const float L = 255.0f;
+    const float c1 = (float)(49.0 * 49.0 * (0.01 * L) * (0.01 * L));
+    const float c2 = (float)(49.0 * 48.0 * (0.03 * L) * (0.03 * L));
+    const int nwy = M - kWin + 1, nwx = N - kWin + 1;
+    const dim3 grid((nwx + kSsimCols - 1) / kSsimCols, (nwy + kSsimRows - 1) / kSsimRows, n_frames);
+    prof_begin("k_ssim", s);
+    switch (C) {
+        case 1: k_ssim<1><<<grid, kSsimCols, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
+        case 2: k_ssim<2><<<grid, kSsimCols, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
+        case 3: k_ssim<3><<<grid, kSsimCols, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
+        default: k_ssim<4><<<grid, kSsimCols, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
+    }
+    prof_end("k_ssim", s);
+    k_utility_finalize<<<(n_frames + 127) / 128, 128, 0, s>>>(d_out, n_frames, M, N, C);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? DP_PIX_OK : set_last_error(DP_PIX_E_CUDA, cudaGetErrorString(e));
+}
+
+}  // extern "C"

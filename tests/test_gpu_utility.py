@@ -1,0 +1,95 @@
+"""Parity of the utility metrics and the Sobel edge mask (dp_pix_utility, dp_pix_sobel_mask) with the
+oracle: masks and squared-error sums bit-exact, SSIM within 1e-5 absolute (each window's value is rounded
+once in fp32 from exact integer sums; the oracle evaluates it in fp64)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2511_04261_b300 as P
+from oracle import utility as U
+from paper_2511_04261_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SSIM_TOL = 1e-5
+
+
+@pytest.mark.parametrize("M,N,C", [(70, 300, 3), (33, 257, 1), (40, 50, 4), (2, 2, 2), (97, 513, 3)])
+@pytest.mark.parametrize("mode", [P.PAD_REFLECT, P.PAD_SYMMETRIC])
+def test_sobel_mask_bit_exact(M, N, C, mode):
+    rng = np.random.default_rng(M * 1000 + N + C + 17 * mode)
+    frames = rng.integers(0, 256, size=(3, M, N, C), dtype=np.uint8)
+    frames[1] = frames[1] // 64 * 64  # flat patches and sharp steps
+    tau = int(rng.integers(0, 4 * (C * 255) ** 2))
+    got = P.dp_pix_sobel_mask(torch.from_numpy(frames).cuda(), tau, pad_mode=mode).cpu().numpy()
+    for i in range(3):
+        np.testing.assert_array_equal(got[i], U.sobel_mask(frames[i], tau, mode))
+
+
+def test_sobel_mask_strided_output_and_pets_frame():
+    f, _ = synth.rect_frame(seed=1001)
+    tau = (3 * 60) ** 2
+    out = torch.full((576, 800), 7, dtype=torch.uint8, device="cuda")
+    P.dp_pix_sobel_mask(torch.from_numpy(f).cuda(), tau, out=out[:, :768])
+    o = out.cpu().numpy()
+    np.testing.assert_array_equal(o[:, :768], U.sobel_mask(f, tau))
+    assert (o[:, 768:] == 7).all()  # nothing written past the mask's columns
+
+
+@pytest.mark.parametrize("M,N,C", [(7, 7, 1), (40, 150, 3), (45, 300, 1), (71, 140, 2), (39, 135, 4)])
+def test_utility_matches_oracle(M, N, C):
+    rng = np.random.default_rng(M + N + C)
+    x = rng.integers(0, 256, size=(2, M, N, C), dtype=np.uint8)
+    y = np.clip(x.astype(np.int64) + rng.integers(-30, 31, size=x.shape), 0, 255).astype(np.uint8)
+    y[1] = x[1] // 16 * 16  # a pixelization-like second pair
+    buf = P.dp_pix_utility(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    vals = P.utility_values(buf)
+    for i in range(2):
+        assert vals[i]["sse"] == U.sse(x[i], y[i])
+        assert vals[i]["mse"] == U.mse(x[i], y[i])
+        assert vals[i]["windows"] == (M - 6) * (N - 6)
+        assert abs(vals[i]["ssim"] - U.ssim(x[i], y[i])) <= SSIM_TOL
+
+
+def test_utility_identical_images_and_strided_inputs():
+    rng = np.random.default_rng(4)
+    big = torch.from_numpy(rng.integers(0, 256, size=(2, 50, 90, 3), dtype=np.uint8)).cuda()
+    x = big[:, 3:40, 5:80]  # row pitch and frame stride of the parent tensor
+    vals = P.utility_values(P.dp_pix_utility(x, x))
+    for v in vals:
+        assert v["sse"] == 0 and v["mse"] == 0.0
+        assert abs(v["ssim"] - 1.0) <= 1e-6
+
+
+def test_sobel_mask_drives_a_mask_release():
+    # the edge mask feeds a simple-mask release; the reconstruction's utility matches the oracle's metrics
+    f, _ = synth.rect_frame(seed=1001)
+    tau = (3 * 60) ** 2
+    ft = torch.from_numpy(f).cuda()
+    mask = P.dp_pix_sobel_mask(ft, tau)[0]
+    kw = dict(M=576, N=768, C=3, grids=[24, 8], eps=[1.0, 0.5], m=16.0, source=P.SRC_MASK_U8, seed=1)
+    plan = P.Plan(**kw)
+    recs = plan.release(ft[None], mask[None])
+    out = P.dp_pix_reconstruct(recs, 576, 768, 3)
+    torch.cuda.synchronize()
+    assert P.dp_pix_status() == 0
+    ora_rec = O.release(f, mask.cpu().numpy(), source=O.SRC_MASK, grids=[24, 8], eps=[1.0, 0.5], M=576, N=768, C=3,
+                        m=16.0, seed=1)[0]
+    np.testing.assert_array_equal(O.record_map(ora_rec), O.record_map(np.frombuffer(P.dp_pix_store(recs[0]), np.uint8)))
+    rec_img = out[0].cpu().numpy()
+    v = P.utility_values(P.dp_pix_utility(ft, out[0]))[0]
+    assert v["sse"] == U.sse(f, rec_img)
+    sub = P.utility_values(P.dp_pix_utility(ft[:96, :128], out[0][:96, :128]))[0]
+    assert abs(sub["ssim"] - U.ssim(f[:96, :128], rec_img[:96, :128])) <= SSIM_TOL
+
+
+def test_utility_and_sobel_reject_bad_arguments():
+    t = torch.zeros((6, 20, 3), dtype=torch.uint8, device="cuda")
+    with pytest.raises(P.DppixError):
+        P.dp_pix_utility(t, t)  # fewer than 7 rows
+    u = torch.zeros((1, 20, 3), dtype=torch.uint8, device="cuda")
+    with pytest.raises(P.DppixError):
+        P.dp_pix_sobel_mask(u, 10)  # one row
+    with pytest.raises(P.DppixError):
+        P.dp_pix_sobel_mask(torch.zeros((4, 4, 3), dtype=torch.uint8, device="cuda"), 10, pad_mode=5)
