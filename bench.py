@@ -762,6 +762,93 @@ def run_utility(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------------------
+# workload "storage": record sizes of the paper's storage study (Sec. VII-A: Alg. 2 over b; Sec. VII-B: Alg. 3
+# over the subgrid factor n) with u8 means, raw and deflated, against a PNG-like deflate of the released frame
+# ------------------------------------------------------------------------------------------------------
+STORAGE = dict(bs=[1, 2, 4, 8, 16, 32, 64], ns=[1, 2, 4, 8, 16, 32, 64], b_adaptive=64, eps=0.5, m_uniform=16.0,
+               m_adaptive=32.0, seed=7, portraits=4, portrait_hw=(1536, 1152))
+STORAGE_METRIC = "deflated u8 record bytes per 1920 x 1080 RGB frame at b = 16 (Alg. 2), against a PNG-like frame"
+
+
+def run_storage(args):
+    import torch
+    import paper_2511_04261_b300 as P
+    from paper_2511_04261_b300 import build, storage, synth
+    build.build()
+    world, rank, _ = dist_setup(args.gpus)
+    stream = torch.cuda.current_stream()
+    frames = {"768x576": synth.rect_frame(seed=1001)[0],
+              "1920x1080": synth.moving_rect_clip(seed=1002, frames=1, M=1080, N=1920, C=3)[0]}
+    uniform = {}
+    head = None
+    for key, f in frames.items():
+        M, N, C = f.shape
+        ft = torch.from_numpy(f).cuda()
+        uniform[key] = {"frame_bytes": f.nbytes, "png_like_frame_bytes": storage.png_like_bytes(f)}
+        for b in STORAGE["bs"]:
+            try:
+                plan = P.Plan(M=M, N=N, C=C, grids=[b], eps=[STORAGE["eps"]], m=STORAGE["m_uniform"],
+                              seed=STORAGE["seed"], source=P.SRC_TILE_LABELS, dtype=P.REC_U8)
+            except P.DppixError as e:
+                uniform[key][b] = "unsupported: %s" % e
+                continue
+            lab = torch.zeros((1, -(-M // b), -(-N // b)), dtype=torch.uint8, device="cuda")
+            recs, out = plan.release_reconstruct(ft[None], lab)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for _ in range(args.warmup):
+                plan.release_reconstruct(ft[None], lab, records=recs, out=out)
+            e0.record(stream)
+            for _ in range(args.steps):
+                plan.release_reconstruct(ft[None], lab, records=recs, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rec = P.dp_pix_store(recs[0])
+            t0 = time.perf_counter()
+            z = storage.deflate_record(rec)
+            t_defl = time.perf_counter() - t0
+            uniform[key][b] = {"record_bytes": len(rec), "deflated_record_bytes": len(z),
+                               "png_like_release_bytes": storage.png_like_bytes(out[0].cpu().numpy()),
+                               "release_reconstruct_ms": e0.elapsed_time(e1) / args.steps, "deflate_ms": 1e3 * t_defl}
+            if key == "1920x1080" and b == 16:
+                head = uniform[key][b]
+    # Alg. 3 over the subgrid factor n: portraits with mattes, background b = 64, foreground b / n
+    adaptive = {}
+    Hh, Ww = STORAGE["portrait_hw"]
+    ports = [synth.portrait(np.random.default_rng(2000 + i), Hh, Ww) for i in range(STORAGE["portraits"])]
+    for n in STORAGE["ns"]:
+        grids = [STORAGE["b_adaptive"], STORAGE["b_adaptive"] // n]
+        plan = P.Plan(M=Hh, N=Ww, C=3, grids=grids, eps=[STORAGE["eps"]] * 2, m=STORAGE["m_adaptive"],
+                      seed=STORAGE["seed"], source=P.SRC_MATTE_F32, dtype=P.REC_U8)
+        tot = {"record_bytes": 0, "deflated_record_bytes": 0, "png_like_release_bytes": 0}
+        for img, alpha in ports:
+            recs, out = plan.release_reconstruct(torch.from_numpy(img).cuda()[None], torch.from_numpy(alpha).cuda()[None])
+            rec = P.dp_pix_store(recs[0])
+            tot["record_bytes"] += len(rec)
+            tot["deflated_record_bytes"] += len(storage.deflate_record(rec))
+            tot["png_like_release_bytes"] += storage.png_like_bytes(out[0].cpu().numpy())
+        adaptive[n] = tot
+    if rank == 0:
+        line = {"metric": STORAGE_METRIC, "value": head["deflated_record_bytes"], "unit": "bytes", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["release_reconstruct_ms"],
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+                "config": {"workload": "storage_u8_records_uniform_b1to64_adaptive_n1to64", "eps": STORAGE["eps"],
+                           "m": {"uniform": STORAGE["m_uniform"], "adaptive": STORAGE["m_adaptive"]},
+                           "record": "u8 means + u8 tile map + header (dp_pix_store), deflated with zlib level 6",
+                           "png_like": "PNG up filter + deflate of the released frame (no chunk headers)",
+                           "adaptive": "%d portraits %dx%d, matte >= 0.5, grids [64, 64/n]" % (STORAGE["portraits"], Ww, Hh),
+                           "stands_in_for": "PETS09-S2L1 / Venice-2 frames and PPM-100 portraits",
+                           "parallelism": "1 GPU" if world == 1 else "replicas"},
+                "uniform": uniform, "adaptive_by_n": adaptive, "png_like_release_bytes_b16": head["png_like_release_bytes"],
+                "roofline": None, "cpu_baseline": None, "e2e": None,
+                "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def run_soft(args):
     import torch
     import paper_2511_04261_b300 as P
@@ -1203,11 +1290,13 @@ def main():
     ap.add_argument("--split", type=int, default=None, help="DP_PIX_TUNE_SPLIT (default: the plan's)")
     ap.add_argument("--path", choices=["fused", "two-call"], default="fused",
                     help="fused: dp_pix_release_reconstruct; two-call: dp_pix_release then dp_pix_reconstruct")
-    ap.add_argument("--workload", choices=["clip", "soft", "batch", "serve", "uniform", "utility"], default="clip",
+    ap.add_argument("--workload", choices=["clip", "soft", "batch", "serve", "uniform", "utility", "storage"],
+                    default="clip",
                     help="clip: the 64-frame 1080p release + reconstruction (the benchmark); soft: the differentiable "
                          "layer on a 32 x 3 x 1024 x 1024 batch; batch: 256 ragged portraits with mattes; serve: 16 "
                          "camera streams; uniform: Alg. 2 on grayscale 768 x 576 and 1920 x 1080 frames, b = 2..20; "
-                         "utility: Sobel masks and MSE/SSIM of a release, with the paper's b / m / eps sweeps")
+                         "utility: Sobel masks and MSE/SSIM of a release, with the paper's b / m / eps sweeps; storage: record "
+                         "sizes over b and n")
     args = ap.parse_args()
     set_frames(args.frames)
     if args.warmup < 3:
@@ -1218,6 +1307,8 @@ def main():
         return run_uniform(args)
     if args.workload == "utility":
         return run_utility(args)
+    if args.workload == "storage":
+        return run_storage(args)
     if args.workload == "soft":
         return run_soft(args)
     if args.workload == "batch":
