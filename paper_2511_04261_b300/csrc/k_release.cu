@@ -19,6 +19,7 @@ namespace dppix {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kRelThreads = 256;  // threads of the release kernels' item loop
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -467,7 +468,7 @@ __device__ __forceinline__ void rel_loop(uint32_t i0, uint32_t i1, uint64_t *bar
 }
 
 template <int C>
-__global__ void __launch_bounds__(kThreads) k_release(const Geom g, const CallArgs a) {
+__global__ void __launch_bounds__(kRelThreads) k_release(const Geom g, const CallArgs a) {
     extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ RelItem it[2];
     __shared__ uint64_t bars[2];
@@ -485,7 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_release(const Geom g, const CallAr
 
 // Batch: items = (tile row, segment) of every image, image i owning [base[2], base[2] + GR * seg_per_row).
 template <int C>
-__global__ void __launch_bounds__(kThreads) k_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items,
+__global__ void __launch_bounds__(kRelThreads) k_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items,
                                                             int buf_bytes) {
     extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ RelItem it[2];
@@ -849,8 +850,8 @@ __global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs 
 }
 
 template <typename K>
-int grid_for(K kernel, size_t smem, uint32_t items) {
-    const int per_sm = launch_prep(reinterpret_cast<const void *>(kernel), kThreads, smem);
+int grid_for(K kernel, size_t smem, uint32_t items, int threads = kThreads) {
+    const int per_sm = launch_prep(reinterpret_cast<const void *>(kernel), threads, smem);
     const uint64_t cap = (uint64_t)per_sm * (uint64_t)sm_count();
     return (int)(items < cap ? items : cap);
 }
@@ -1041,10 +1042,10 @@ cudaError_t launch_release(const Geom &g, const CallArgs &a, cudaStream_t s) {
     const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row;
     prof_begin("k_release", s);
     switch (g.C) {
-        case 1: k_release<1><<<grid_for(k_release<1>, smem, items), kThreads, smem, s>>>(g, a); break;
-        case 2: k_release<2><<<grid_for(k_release<2>, smem, items), kThreads, smem, s>>>(g, a); break;
-        case 3: k_release<3><<<grid_for(k_release<3>, smem, items), kThreads, smem, s>>>(g, a); break;
-        default: k_release<4><<<grid_for(k_release<4>, smem, items), kThreads, smem, s>>>(g, a); break;
+        case 1: k_release<1><<<grid_for(k_release<1>, smem, items, kRelThreads), kRelThreads, smem, s>>>(g, a); break;
+        case 2: k_release<2><<<grid_for(k_release<2>, smem, items, kRelThreads), kRelThreads, smem, s>>>(g, a); break;
+        case 3: k_release<3><<<grid_for(k_release<3>, smem, items, kRelThreads), kRelThreads, smem, s>>>(g, a); break;
+        default: k_release<4><<<grid_for(k_release<4>, smem, items, kRelThreads), kRelThreads, smem, s>>>(g, a); break;
     }
     prof_end("k_release", s);
     return cudaGetLastError();
@@ -1059,10 +1060,10 @@ cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t
     const size_t smem = 2 * (size_t)buf_bytes;
     prof_begin("k_batch_release", s);
     switch (C) {
-        case 1: k_batch_release<1><<<grid_for(k_batch_release<1>, smem, items), kThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
-        case 2: k_batch_release<2><<<grid_for(k_batch_release<2>, smem, items), kThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
-        case 3: k_batch_release<3><<<grid_for(k_batch_release<3>, smem, items), kThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
-        default: k_batch_release<4><<<grid_for(k_batch_release<4>, smem, items), kThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
+        case 1: k_batch_release<1><<<grid_for(k_batch_release<1>, smem, items, kRelThreads), kRelThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
+        case 2: k_batch_release<2><<<grid_for(k_batch_release<2>, smem, items, kRelThreads), kRelThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
+        case 3: k_batch_release<3><<<grid_for(k_batch_release<3>, smem, items, kRelThreads), kRelThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
+        default: k_batch_release<4><<<grid_for(k_batch_release<4>, smem, items, kRelThreads), kRelThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
     }
     prof_end("k_batch_release", s);
     return cudaGetLastError();
