@@ -158,7 +158,9 @@ int ora_geometry(const ora_desc *d, ora_geom *g)
     if (d->M < 1 || d->N < 1 || d->C < 1 || d->C > 4 || d->K < 1 || d->K > ORA_MAXK) return ORA_E_INVALID;
     if (d->pitch < (int64_t)d->N * d->C) return ORA_E_INVALID;
     if (!(d->R > 0) || !(d->m > 0)) return ORA_E_INVALID;
-    if (d->pad_mode != 0 && d->pad_mode != 1) return ORA_E_INVALID;
+    if (d->pad_mode < 0 || d->pad_mode > 2) return ORA_E_INVALID;
+    /* pad mode 2 (no padding, valid samples only) ranks no tile variances: tiles would hold unequal counts */
+    if (d->pad_mode == 2 && d->source == 3) return ORA_E_INVALID;
     if (d->dtype < 0 || d->dtype > 2) return ORA_E_INVALID;
     if (d->source < 0 || d->source > 3) return ORA_E_INVALID;
     if ((d->source == 1 || d->source == 2) && d->K != 2) return ORA_E_INVALID;
@@ -174,10 +176,10 @@ int ora_geometry(const ora_desc *d, ora_geom *g)
     g->GC = (int32_t)((d->N + T - 1) / T);
     g->PR = (int32_t)(g->GR * T - d->M);
     g->PC = (int32_t)(g->GC * T - d->N);
-    /* mirror padding must stay inside the image: reflect needs P <= n-1, symmetric P <= n */
+    /* mirror padding must stay inside the image: reflect needs P <= n-1, symmetric P <= n (mode 2 pads nothing) */
     int64_t lim_r = d->pad_mode == 0 ? d->M - 1 : d->M;
     int64_t lim_c = d->pad_mode == 0 ? d->N - 1 : d->N;
-    if (g->PR > lim_r || g->PC > lim_c) return ORA_E_PAD;
+    if (d->pad_mode != 2 && (g->PR > lim_r || g->PC > lim_c)) return ORA_E_PAD;
     for (int r = 0; r < d->K; ++r) {
         g->cells_side[r] = (int32_t)(T / d->b[r]);
         g->sigma[r] = d->R * d->m / ((double)d->b[r] * (double)d->b[r] * d->eps[r]);
@@ -256,8 +258,12 @@ int ora_classify(const ora_desc *d, const uint8_t *img, const void *src, int64_t
         for (int64_t ty = 0; ty < GR; ++ty)
             for (int64_t tx = 0; tx < GC; ++tx) {
                 int64_t simple = 0;
-                for (int64_t y = ty * T; y < (ty + 1) * T; ++y)
-                    for (int64_t x = tx * T; x < (tx + 1) * T; ++x) {
+                /* mode 2: only the tile's samples inside the frame count, and the mean is over them */
+                const int64_t y1 = d->pad_mode == 2 && (ty + 1) * T > d->M ? d->M : (ty + 1) * T;
+                const int64_t x1 = d->pad_mode == 2 && (tx + 1) * T > d->N ? d->N : (tx + 1) * T;
+                const int64_t nvalid = (y1 - ty * T) * (x1 - tx * T);
+                for (int64_t y = ty * T; y < y1; ++y)
+                    for (int64_t x = tx * T; x < x1; ++x) {
                         int64_t sy = ora_reflect(y, d->M, d->pad_mode);
                         int64_t sx = ora_reflect(x, d->N, d->pad_mode);
                         int is_simple;
@@ -269,7 +275,7 @@ int ora_classify(const ora_desc *d, const uint8_t *img, const void *src, int64_t
                         }
                         simple += is_simple;
                     }
-                map[ty * GC + tx] = (2 * simple > T * T) ? 0 : 1;
+                map[ty * GC + tx] = (2 * simple > nvalid) ? 0 : 1;
             }
         return ORA_OK;
     }
@@ -430,11 +436,33 @@ int ora_release(const ora_desc *d, const uint8_t *img, const void *src, int64_t 
                         uint32_t key[2] = {(uint32_t)d->seed, (uint32_t)(d->seed >> 32)};
                         uint32_t words[4];
                         ora_philox4x32_10(ctr, key, words);
+                        /* pad mode 2 (Alg. 1 semantics): an edge cell holds h x w samples inside the frame; its mean
+                         * is over them and its noise scale R m / (h w eps_r) (Eq. 11 with h w in place of b^2); a cell
+                         * wholly outside the frame holds no sample and stores 0 */
+                        int64_t h = b, w = b;
+                        if (d->pad_mode == 2) {
+                            h = d->M - gy * b;
+                            w = d->N - gx * b;
+                            h = h < 0 ? 0 : (h > b ? b : h);
+                            w = w < 0 ? 0 : (w > b ? b : w);
+                        }
+                        const int64_t n = h * w;
+                        const double sigma_c = d->R * d->m / ((double)n * d->eps[r]);
                         for (int ch = 0; ch < C; ++ch, ++e, ++k) {
-                            int64_t S = cell_sum(d, img, gy * b, gx * b, b, ch);
-                            double mu = (double)S * inv_b2;
-                            double eta = d->noise_free ? 0.0 : ora_laplace_from_word(words[ch], g.sigma[r]);
-                            double v = mu + eta;
+                            int64_t S;
+                            double mu, eta, v;
+                            if (d->pad_mode != 2) {
+                                S = cell_sum(d, img, gy * b, gx * b, b, ch);
+                                mu = (double)S * inv_b2;
+                                eta = d->noise_free ? 0.0 : ora_laplace_from_word(words[ch], g.sigma[r]);
+                            } else {
+                                S = 0;
+                                for (int64_t y = gy * b; y < gy * b + h; ++y)
+                                    for (int64_t x = gx * b; x < gx * b + w; ++x) S += img[y * d->pitch + x * C + ch];
+                                mu = n ? (double)S / (double)n : 0.0;
+                                eta = (d->noise_free || n == 0) ? 0.0 : ora_laplace_from_word(words[ch], sigma_c);
+                            }
+                            v = mu + eta;
                             if (v < 0.0) v = 0.0;
                             if (v > d->R) v = d->R;
                             uint8_t *dst = rec + roff[r] + e * (uint64_t)es;

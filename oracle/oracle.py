@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY: used by tests/, the package smoke check and the benchm
 
 A problem is described by keyword arguments (the same names the product binding uses, defined here
 independently):
-    M, N, C, grids (list of b_r), eps (list of eps_r), R=255, m=16, pad_mode=0 (reflect) | 1 (symmetric),
+    M, N, C, grids (list of b_r), eps (list of eps_r), R=255, m=16, pad_mode=0 (reflect) | 1 (symmetric) |
+    2 (no padding: edge cells use their valid samples only),
     source: 0 tile labels | 1 simple-mask u8 | 2 alpha matte f32 | 3 variance quantiles,
     matte_thr=0.5, dtype: 0 f32 | 1 u8 | 2 u32 sums, noise_free=False, stream_id=0, seed=0, frame_idx=0.
 """
@@ -17,6 +18,7 @@ from . import build as _build
 
 MAXK = 8
 SRC_TILE_LABELS, SRC_MASK, SRC_MATTE, SRC_VARIANCE = 0, 1, 2, 3
+PAD_REFLECT, PAD_SYMMETRIC, PAD_NONE = 0, 1, 2
 DT_F32, DT_U8, DT_SUM = 0, 1, 2
 
 
@@ -298,6 +300,7 @@ def soft_backward(x, w, g, **kw):
 
 
 __all__ = [
+    "PAD_REFLECT", "PAD_SYMMETRIC", "PAD_NONE",
     "OraError", "SRC_TILE_LABELS", "SRC_MASK", "SRC_MATTE", "SRC_VARIANCE", "DT_F32", "DT_U8", "DT_SUM",
     "philox4x32_10", "philox4x64_10", "laplace_from_word", "reflect", "geometry", "geometry_rc", "classify",
     "release", "record_info", "record_payload", "record_map", "reconstruct", "soft_forward", "soft_backward",
