@@ -55,6 +55,12 @@ extern "C" {
  * not repeated (numpy "reflect"); symmetric: it is (numpy "symmetric"). */
 #define DP_PIX_PAD_REFLECT 0
 #define DP_PIX_PAD_SYMMETRIC 1
+/* No padding, privacy-strict edges (Alg. 1's partial cells, Sec. IV-D): a cell crossing the frame's last
+ * row or column holds only its h x w samples inside the frame; its mean is S / (h w) and its noise scale
+ * R m / (h w eps_r), so that a sample weighs at most R m / (h w) in it (with mirroring a sample can appear
+ * twice in an edge cell).  A cell wholly outside the frame stores 0.  Mask and matte tiles are judged on
+ * their pixels inside the frame.  Not with DP_PIX_SRC_VARIANCE (UNSUPPORTED); no padding limit applies. */
+#define DP_PIX_PAD_NONE 2
 
 /* Where the tile -> region map comes from (Alg. 3 steps 5-6 and their generalisations).
  *  TILE_LABELS: caller passes u8 labels [G_R][G_C] (values < K), copied into the record.

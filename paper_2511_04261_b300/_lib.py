@@ -18,7 +18,7 @@ ERROR_NAMES = {
     -4: "DP_PIX_E_BUFFER_TOO_SMALL", -5: "DP_PIX_E_BAD_RECORD", -6: "DP_PIX_E_CUDA", -7: "DP_PIX_E_TIMEOUT",
     -8: "DP_PIX_E_DEVICE",
 }
-PAD_REFLECT, PAD_SYMMETRIC = 0, 1
+PAD_REFLECT, PAD_SYMMETRIC, PAD_NONE = 0, 1, 2
 SRC_TILE_LABELS, SRC_MASK_U8, SRC_MATTE_F32, SRC_VARIANCE = 0, 1, 2, 3
 REC_F32, REC_U8, REC_SUM_U32 = 0, 1, 2
 OUT_U8, OUT_F32 = 0, 1

@@ -184,8 +184,10 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     if (d->K < 1 || d->K > kMaxK) return fail(DP_PIX_E_INVALID_ARG, "K must be in 1..8");
     if (d->row_pitch < (int64_t)d->N * d->C) return fail(DP_PIX_E_INVALID_ARG, "row_pitch < N*C");
     if (!(d->value_range > 0) || !(d->m > 0)) return fail(DP_PIX_E_INVALID_ARG, "value_range and m must be > 0");
-    if (d->pad_mode != DP_PIX_PAD_REFLECT && d->pad_mode != DP_PIX_PAD_SYMMETRIC)
+    if (d->pad_mode != DP_PIX_PAD_REFLECT && d->pad_mode != DP_PIX_PAD_SYMMETRIC && d->pad_mode != DP_PIX_PAD_NONE)
         return fail(DP_PIX_E_INVALID_ARG, "bad pad_mode");
+    if (d->pad_mode == DP_PIX_PAD_NONE && d->region_source == DP_PIX_SRC_VARIANCE)
+        return fail(DP_PIX_E_UNSUPPORTED, "pad_mode NONE with variance classes (tiles of unequal sample counts)");
     if (d->region_source < 0 || d->region_source > 3) return fail(DP_PIX_E_INVALID_ARG, "bad region_source");
     if (d->record_dtype < 0 || d->record_dtype > 2) return fail(DP_PIX_E_INVALID_ARG, "bad record_dtype");
     if ((d->region_source == DP_PIX_SRC_MASK_U8 || d->region_source == DP_PIX_SRC_MATTE_F32) && d->K != 2)
@@ -212,7 +214,7 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     g.PC = (int)(g.GC * T - d->N);
     const int64_t lim_r = d->pad_mode == DP_PIX_PAD_REFLECT ? d->M - 1 : d->M;
     const int64_t lim_c = d->pad_mode == DP_PIX_PAD_REFLECT ? d->N - 1 : d->N;
-    if (g.PR > lim_r || g.PC > lim_c)
+    if (d->pad_mode != DP_PIX_PAD_NONE && (g.PR > lim_r || g.PC > lim_c))
         return fail(DP_PIX_E_PAD_TOO_LARGE, "padding (%d, %d) reaches past the image (%d x %d)", g.PR, g.PC, d->M, d->N);
     const uint64_t ntiles = (uint64_t)g.GR * (uint64_t)g.GC;
     if (ntiles > (uint64_t)kMaxFrameTiles) return fail(DP_PIX_E_UNSUPPORTED, "more than %d tiles per frame", kMaxFrameTiles);

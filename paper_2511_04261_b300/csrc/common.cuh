@@ -233,9 +233,11 @@ __device__ __forceinline__ float noisy_mean(uint32_t S, float b2, float inv_b2, 
     return fminf(fmaxf(v, 0.0f), R);
 }
 
-// Mirror padding by index: padded index p >= n maps back into [0, n) (Alg. 2 step 4).
+// Mirror padding by index: padded index p >= n maps back into [0, n) (Alg. 2 step 4).  Without padding
+// (DP_PIX_PAD_NONE) the sample past the edge is not used, and any index inside the frame is returned.
 __device__ __forceinline__ int reflect_idx(int p, int n, int pad_mode) {
     if (p < n) return p;
+    if (pad_mode == DP_PIX_PAD_NONE) return n - 1;
     return pad_mode == DP_PIX_PAD_REFLECT ? 2 * (n - 1) - p : 2 * n - 1 - p;
 }
 

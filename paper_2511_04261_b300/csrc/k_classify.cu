@@ -3,7 +3,7 @@
 // One CTA per (tile row, frame).  Each thread owns padded pixel columns, counts the simple samples of the
 // column over the tile row's T mirror-padded rows, and adds the count to its tile's counter.  A tile is
 // simple (region 0) iff 2 * #simple > T^2 -- the paper's mask mean > 1/2 on exact integers, a tie going
-// to complex (region 1).  MASK_U8: nonzero = simple.  MATTE_F32: a pixel is complex iff alpha >= thr.
+// to complex (region 1); without padding (DP_PIX_PAD_NONE) over the tile's pixels inside the frame.  MASK_U8: nonzero = simple.  MATTE_F32: a pixel is complex iff alpha >= thr.
 #include <algorithm>
 
 #include "common.cuh"
@@ -20,7 +20,9 @@ __device__ __forceinline__ void classify_row(const Geom &g, const CallArgs &a, i
     for (int i = threadIdx.x; i < g.GC; i += blockDim.x) cnt_s[i] = 0u;
     __syncthreads();
     const uint8_t *src = a.src + (uint64_t)f * (uint64_t)a.src_frame_stride;
-    const int Wp = g.GC * T;
+    const bool strict = g.pad_mode == DP_PIX_PAD_NONE;       // only samples inside the frame count
+    const int Wp = strict ? g.N : g.GC * T;
+    const int rows = strict ? min(T, g.M - ty * T) : T;
     int x_first = 0;  // first column left to the per-column loop below
     if (kMatte) {
         // in-image columns in groups of 4, read as 16-byte granules (rows are 4-byte aligned, so a group spans
@@ -31,7 +33,7 @@ __device__ __forceinline__ void classify_row(const Geom &g, const CallArgs &a, i
             const int c0 = 4 * q, cnt = min(4, g.N - c0);
             uint32_t c[4] = {0u, 0u, 0u, 0u};
 #pragma unroll 8
-            for (int j = 0; j < T; ++j) {
+            for (int j = 0; j < rows; ++j) {
                 const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
                 const uintptr_t addr = reinterpret_cast<uintptr_t>(src + (int64_t)sy * a.src_pitch) + 16u * (uint32_t)q;
                 const int o = (int)(addr & 15u);
@@ -59,7 +61,7 @@ __device__ __forceinline__ void classify_row(const Geom &g, const CallArgs &a, i
         const int sx = reflect_idx(x, g.N, g.pad_mode);
         uint32_t c = 0;
 #pragma unroll 8
-        for (int j = 0; j < T; ++j) {
+        for (int j = 0; j < rows; ++j) {
             const int sy = reflect_idx(ty * T + j, g.M, g.pad_mode);
             const uint8_t *row = src + (int64_t)sy * a.src_pitch;
             if (kMatte) {
@@ -73,8 +75,10 @@ __device__ __forceinline__ void classify_row(const Geom &g, const CallArgs &a, i
     }
     __syncthreads();
     uint8_t *map = a.records + (uint64_t)f * (uint64_t)a.record_stride + g.map_offset + (uint64_t)ty * g.GC;
-    const uint32_t half2 = (uint32_t)T * (uint32_t)T;
-    for (int tx = threadIdx.x; tx < g.GC; tx += blockDim.x) map[tx] = (2u * cnt_s[tx] > half2) ? 0 : 1;
+    for (int tx = threadIdx.x; tx < g.GC; tx += blockDim.x) {
+        const uint32_t n = (uint32_t)rows * (uint32_t)(strict ? min(T, g.N - tx * T) : T);  // samples counted
+        map[tx] = (2u * cnt_s[tx] > n) ? 0 : 1;
+    }
 }
 
 template <bool kMatte>

@@ -342,7 +342,9 @@ __device__ __forceinline__ void rows_sum(const uint8_t *raw, const int32_t *rowb
 template <int C>
 __device__ __forceinline__ void rel_compute(const Geom &g, const CallArgs &a, const RelItem &it, uint8_t *raw) {
     const int T = g.T;
-    if (it.padb > 0) {
+    const bool strict = g.pad_mode == DP_PIX_PAD_NONE;  // no padding: edge cells keep their samples in the frame
+    const int hv = strict ? min(T, g.M - it.ty * T) : T;  // rows of the item inside the frame
+    if (it.padb > 0 && !strict) {
         // mirrored columns past the right edge, copied next to the row's last in-image byte
         const uint8_t *fb0 = a.frames + (uint64_t)it.f * (uint64_t)a.frame_stride;
         const int x0 = it.tx0 * T, pb = it.padb;
@@ -391,8 +393,13 @@ __device__ __forceinline__ void rel_compute(const Geom &g, const CallArgs &a, co
                 const int cy = udiv_small(cell, cs, __fdividef(1.0f, (float)cs)), cx = cell - cy * cs;
                 const int rpp = (b + (1 << lp) - 1) >> lp;
                 const int r0 = cy * b + part * rpp;
-                const int r1 = min(r0 + rpp, (cy + 1) * b);
-                rows_sum<C>(raw, it.rowbase, r0, r1, (t * T + cx * b) * C, b * C, S);
+                int r1 = min(r0 + rpp, (cy + 1) * b);
+                int nbytes = b * C;
+                if (strict) {
+                    r1 = min(r1, hv);
+                    nbytes = max(0, min(b, g.N - (it.tx0 + t) * T - cx * b)) * C;
+                }
+                if (r0 < r1 && nbytes > 0) rows_sum<C>(raw, it.rowbase, r0, r1, (t * T + cx * b) * C, nbytes, S);
             } else {
                 lp = 0;
             }
@@ -410,11 +417,33 @@ __device__ __forceinline__ void rel_compute(const Geom &g, const CallArgs &a, co
             const int cy = udiv_small(cell, cs, __fdividef(1.0f, (float)cs)), cx = cell - cy * cs;
             const uint32_t cell_idx =
                 (uint32_t)(it.ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)((it.tx0 + t) * cs + cx);
-            uint4 words = make_uint4(0, 0, 0, 0);
-            if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
-                words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame);
-            emit_values(g, C, rec + it.tileoff[t] + (uint64_t)cell * C * g.es, S, words, g.sigma_f[r], g.b2_f[r],
-                        g.inv_b2_f[r], nullptr);
+            uint8_t *dst = rec + it.tileoff[t] + (uint64_t)cell * C * g.es;
+            float sigma = g.sigma_f[r], b2 = g.b2_f[r], ib2 = g.inv_b2_f[r];
+            int n = 1;
+            if (strict) {
+                // Alg. 1's partial cell: mean over its h x w samples in the frame, noise scale R m / (h w eps_r)
+                const int b = g.grid[r];
+                const int h = max(0, min(b, hv - cy * b));
+                const int w = max(0, min(b, g.N - (it.tx0 + t) * T - cx * b));
+                n = h * w;
+                if (n > 0 && n < b * b) {
+                    b2 = (float)n;
+                    ib2 = 0.0f;
+                    sigma = __fdiv_rn(g.sigma_f[r] * g.b2_f[r], (float)n);
+                }
+            }
+            if (n == 0) {  // wholly outside the frame: no sample, stored as 0
+#pragma unroll
+                for (int ch = 0; ch < C; ++ch) {
+                    if (g.es == 4) reinterpret_cast<uint32_t *>(dst)[ch] = 0u;
+                    else dst[ch] = 0;
+                }
+            } else {
+                uint4 words = make_uint4(0, 0, 0, 0);
+                if (!g.noise_free && g.dtype != DP_PIX_REC_SUM_U32)
+                    words = cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame);
+                emit_values(g, C, dst, S, words, sigma, b2, ib2, nullptr);
+            }
         }
     }
 }
@@ -536,11 +565,14 @@ __device__ __forceinline__ void cls_compute(const Geom &g, const CallArgs &a, co
     constexpr int es = kMatte ? 4 : 1;
     const int T = g.T, ns = it.ns, ncols = ns * T;
     const int x0 = it.tx0 * T;
+    const bool strict = g.pad_mode == DP_PIX_PAD_NONE;  // only the pixels inside the frame count
+    const int hv = strict ? min(T, g.M - it.ty * T) : T;
     const int rsplit = max(1, (int)blockDim.x / ncols);
     const int rows_per = (T + rsplit - 1) / rsplit;
     for (int u = threadIdx.x; u < ncols * rsplit; u += blockDim.x) {
         const int part = u / ncols, c = u - part * ncols;
-        const int j0 = part * rows_per, j1 = min(T, j0 + rows_per);
+        const int j0 = part * rows_per, j1 = min(hv, j0 + rows_per);
+        if (strict && c >= it.xv) continue;
         const int x = x0 + c;
         int sc = c;  // staged column of the sample
         bool global = false;
@@ -575,7 +607,8 @@ __device__ __forceinline__ void cls_compute(const Geom &g, const CallArgs &a, co
     __syncthreads();
     if ((int)threadIdx.x < ns) {
         uint8_t *map = a.records + g.map_offset + (uint64_t)it.ty * g.GC + it.tx0;
-        map[threadIdx.x] = (2u * cnt_s[threadIdx.x] > (uint32_t)T * (uint32_t)T) ? 0 : 1;
+        const int wv = strict ? min(T, g.N - (it.tx0 + (int)threadIdx.x) * T) : T;
+        map[threadIdx.x] = (2u * cnt_s[threadIdx.x] > (uint32_t)hv * (uint32_t)wv) ? 0 : 1;
         cnt_s[threadIdx.x] = 0u;  // ready for the next item
     }
 }
