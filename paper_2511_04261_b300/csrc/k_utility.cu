@@ -4,9 +4,10 @@
 // - k_sobel_mask: one CTA per (frame, 32 rows, 256 columns): the channel-sum intensity of the block and a
 //   one-pixel mirrored border is staged in shared memory as u16, then each thread walks one column down the
 //   32 rows: Gx, Gy from the 3 x 3 Sobel taps in exact integers, mask = (Gx^2 + Gy^2 < tau) ? 1 : 0.
-// - k_ssim: one CTA per (frame, 32 window-centre rows, 128 window-centre columns); the 38 x 134-pixel
+// - k_ssim: one CTA of 128 threads per (frame, 16 window rows, 256 window columns); the 22 x 262-pixel
 //   input block of both images is staged in shared memory; each thread keeps, per channel, the five exact
-//   integer window sums (Sx, Sy, Sxx, Syy, Sxy) of its column's 7 x 7 window and slides it down the rows
+//   integer window sums (Sx, Sy, Sxx, Syy, Sxy) of two adjacent columns' 7 x 7 windows (their six shared
+//   taps of a row summed once) and slides them down the rows
 //   (adding the entering row's 7 taps, subtracting the leaving one's).  The window value is evaluated from
 //   the exact sums: with D = 49 Sxx - Sx^2 (and likewise), the 1/49^2 and 1/(49*48) factors of the means,
 //   variances and covariance cancel, so SSIM = (2 Sx Sy + c1)(2 Dxy + c2) / ((Sx^2 + Sy^2 + c1)(Dx + Dy + c2))
@@ -21,7 +22,7 @@ namespace dppix {
 namespace {
 
 constexpr int kSobRows = 32, kSobCols = 256;
-constexpr int kSsimRows = 32, kSsimCols = 128, kWin = 7;
+constexpr int kSsimRows = 16, kSsimCols = 256, kSsimThreads = 128, kWin = 7;  // two window columns per thread
 
 // Mirror index on both sides for one-pixel borders and clamped overhangs (n >= 2).
 __device__ __forceinline__ int mirror2(int p, int n, int mode) {
@@ -74,36 +75,46 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
     return v;
 }
 
-// Five exact sums of the 7 taps of staged row r, window columns [t, t + 7), channel ch.
+// Five exact sums (x, y, x^2, y^2, xy) of staged row r over window columns t2 and t2 + 1 (taps t2 .. t2 + 6
+// and t2 + 1 .. t2 + 7, the six shared taps summed once), channel ch.
 template <int C>
-__device__ __forceinline__ void row_taps(const uint8_t *xs, const uint8_t *ys, int rowbytes, int r, int t, int ch,
-                                         int &sx, int &sy, int &sxx, int &syy, int &sxy) {
-    const uint8_t *xp = xs + r * rowbytes + t * C + ch, *yp = ys + r * rowbytes + t * C + ch;
-    int a0 = 0, b0 = 0, aa = 0, bb = 0, ab = 0;
+__device__ __forceinline__ void row_taps2(const uint8_t *xs, const uint8_t *ys, int rowbytes, int r, int t2, int ch,
+                                          int *s0, int *s1) {
+    const uint8_t *xp = xs + r * rowbytes + t2 * C + ch, *yp = ys + r * rowbytes + t2 * C + ch;
+    int sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
 #pragma unroll
-    for (int k = 0; k < kWin; ++k) {
+    for (int k = 1; k < kWin; ++k) {
         const int a = xp[k * C], b = yp[k * C];
-        a0 += a;
-        b0 += b;
-        aa += a * a;
-        bb += b * b;
-        ab += a * b;
+        sx += a;
+        sy += b;
+        sxx += a * a;
+        syy += b * b;
+        sxy += a * b;
     }
-    sx = a0;
-    sy = b0;
-    sxx = aa;
-    syy = bb;
-    sxy = ab;
+    const int a0 = xp[0], b0 = yp[0], a7 = xp[kWin * C], b7 = yp[kWin * C];
+    s0[0] = sx + a0, s0[1] = sy + b0, s0[2] = sxx + a0 * a0, s0[3] = syy + b0 * b0, s0[4] = sxy + a0 * b0;
+    s1[0] = sx + a7, s1[1] = sy + b7, s1[2] = sxx + a7 * a7, s1[3] = syy + b7 * b7, s1[4] = sxy + a7 * b7;
+}
+
+// SSIM of one 7 x 7 window from its exact sums (the 1/49^2 and 1/(49*48) factors cancel; see the header).
+__device__ __forceinline__ float ssim_of(const int *S, float c1, float c2) {
+    const long long sx = S[0], sy = S[1];
+    const long long dx = 49ll * S[2] - sx * sx;
+    const long long dy = 49ll * S[3] - sy * sy;
+    const long long dxy = 49ll * S[4] - sx * sy;
+    const float num = (2.0f * (float)(sx * sy) + c1) * (2.0f * (float)dxy + c2);
+    const float den = ((float)(sx * sx + sy * sy) + c1) * ((float)(dx + dy) + c2);
+    return __fdiv_rn(num, den);
 }
 
 template <int C>
-__global__ void __launch_bounds__(kSsimCols) k_ssim(const uint8_t *x, const uint8_t *y, int M, int N, int64_t px,
-                                                    int64_t py, int64_t fsx, int64_t fsy, float c1, float c2,
-                                                    dp_pix_utility_t *out) {
+__global__ void __launch_bounds__(kSsimThreads) k_ssim(const uint8_t *x, const uint8_t *y, int M, int N, int64_t px,
+                                                       int64_t py, int64_t fsx, int64_t fsy, float c1, float c2,
+                                                       dp_pix_utility_t *out) {
     constexpr int SR = kSsimRows + kWin - 1, SC = kSsimCols + kWin - 1;
     constexpr int RB = SC * C;  // staged bytes per row
     __shared__ uint8_t xs[SR * RB], ys[SR * RB];
-    __shared__ double part[kSsimCols / 32];
+    __shared__ double part[kSsimThreads / 32];
     const int f = blockIdx.z;
     const int cy0 = blockIdx.y * kSsimRows, cx0 = blockIdx.x * kSsimCols;  // first window (top-left corner)
     const int nwy = M - kWin + 1, nwx = N - kWin + 1;                      // windows per column / row
@@ -111,16 +122,14 @@ __global__ void __launch_bounds__(kSsimCols) k_ssim(const uint8_t *x, const uint
     const uint8_t *xb = x + (int64_t)f * fsx + (int64_t)cy0 * px + (int64_t)cx0 * C;
     const uint8_t *yb = y + (int64_t)f * fsy + (int64_t)cy0 * py + (int64_t)cx0 * C;
     const int nb = cols_in * C;
-    for (int idx = threadIdx.x; idx < rows_in * RB; idx += blockDim.x) {
-        const int r = idx / RB, k = idx - r * RB;
-        if (k < nb) {
-            xs[idx] = __ldg(xb + (int64_t)r * px + k);
-            ys[idx] = __ldg(yb + (int64_t)r * py + k);
+    for (int r = 0; r < rows_in; ++r)
+        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+            xs[r * RB + k] = __ldg(xb + (int64_t)r * px + k);
+            ys[r * RB + k] = __ldg(yb + (int64_t)r * py + k);
         }
-    }
     __syncthreads();
-    // squared differences of the pixels this block owns: its 32 x 128 window corners, extended to the image's
-    // last row / column in the last block row / column (all of them staged)
+    // squared differences of the pixels this block owns: its window corners, extended to the image's last
+    // rows / columns in the last block row / column (all of them staged)
     {
         const int ro = blockIdx.y + 1 == gridDim.y ? rows_in : kSsimRows;
         const int co = (blockIdx.x + 1 == gridDim.x ? cols_in : kSsimCols) * C;
@@ -133,44 +142,35 @@ __global__ void __launch_bounds__(kSsimCols) k_ssim(const uint8_t *x, const uint
         e = warp_sum_u64(e);
         if ((threadIdx.x & 31) == 0 && e) atomicAdd(reinterpret_cast<unsigned long long *>(&out[f].sse), e);
     }
-    const int t = threadIdx.x;
-    const int wx = cx0 + t;
+    const int t2 = 2 * threadIdx.x;
+    const bool v0 = cx0 + t2 < nwx, v1 = cx0 + t2 + 1 < nwx;
     const int nrows = min(kSsimRows, nwy - cy0);
     double acc = 0.0;
-    if (wx < nwx) {
+    if (v0) {
 #pragma unroll 1
         for (int ch = 0; ch < C; ++ch) {
-            int Sx = 0, Sy = 0, Sxx = 0, Syy = 0, Sxy = 0;
+            int V0[5] = {0, 0, 0, 0, 0}, V1[5] = {0, 0, 0, 0, 0};
             for (int r = 0; r < kWin; ++r) {
-                int a, b, aa, bb, ab;
-                row_taps<C>(xs, ys, RB, r, t, ch, a, b, aa, bb, ab);
-                Sx += a;
-                Sy += b;
-                Sxx += aa;
-                Syy += bb;
-                Sxy += ab;
+                int a[5], b[5];
+                row_taps2<C>(xs, ys, RB, r, t2, ch, a, b);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    V0[q] += a[q];
+                    V1[q] += b[q];
+                }
             }
             for (int i = 0; i < nrows; ++i) {
-                const long long dx = 49ll * Sxx - (long long)Sx * Sx;
-                const long long dy = 49ll * Syy - (long long)Sy * Sy;
-                const long long dxy = 49ll * Sxy - (long long)Sx * Sy;
-                const float num = (2.0f * (float)((long long)Sx * Sy) + c1) * (2.0f * (float)dxy + c2);
-                const float den = ((float)((long long)Sx * Sx + (long long)Sy * Sy) + c1) * ((float)(dx + dy) + c2);
-                acc += (double)__fdiv_rn(num, den);
+                acc += (double)ssim_of(V0, c1, c2);
+                if (v1) acc += (double)ssim_of(V1, c1, c2);
                 if (i + 1 < nrows) {
-                    int a, b, aa, bb, ab;
-                    row_taps<C>(xs, ys, RB, i + kWin, t, ch, a, b, aa, bb, ab);
-                    Sx += a;
-                    Sy += b;
-                    Sxx += aa;
-                    Syy += bb;
-                    Sxy += ab;
-                    row_taps<C>(xs, ys, RB, i, t, ch, a, b, aa, bb, ab);
-                    Sx -= a;
-                    Sy -= b;
-                    Sxx -= aa;
-                    Syy -= bb;
-                    Sxy -= ab;
+                    int a[5], b[5], c[5], d[5];
+                    row_taps2<C>(xs, ys, RB, i + kWin, t2, ch, a, b);
+                    row_taps2<C>(xs, ys, RB, i, t2, ch, c, d);
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) {
+                        V0[q] += a[q] - c[q];
+                        V1[q] += b[q] - d[q];
+                    }
                 }
             }
         }
@@ -179,9 +179,9 @@ __global__ void __launch_bounds__(kSsimCols) k_ssim(const uint8_t *x, const uint
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kSsimCols / 32; ++w) s += part[w];
-        atomicAdd(&out[f].ssim_sum, s);
+        double sum = 0.0;
+        for (int w = 0; w < kSsimThreads / 32; ++w) sum += part[w];
+        atomicAdd(&out[f].ssim_sum, sum);
     }
 }
 
@@ -257,10 +257,10 @@ int dp_pix_utility(const void *d_x, const void *d_y, int32_t M, int32_t N, int32
     const dim3 grid((nwx + kSsimCols - 1) / kSsimCols, (nwy + kSsimRows - 1) / kSsimRows, n_frames);
     prof_begin("k_ssim", s);
     switch (C) {
-        case 1: k_ssim<1><<<grid, kSsimCols, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
-        case 2: k_ssim<2><<<grid, kSsimCols, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
-        case 3: k_ssim<3><<<grid, kSsimCols, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
-        default: k_ssim<4><<<grid, kSsimCols, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
+        case 1: k_ssim<1><<<grid, kSsimThreads, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
+        case 2: k_ssim<2><<<grid, kSsimThreads, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
+        case 3: k_ssim<3><<<grid, kSsimThreads, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
+        default: k_ssim<4><<<grid, kSsimThreads, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
     }
     prof_end("k_ssim", s);
     k_utility_finalize<<<(n_frames + 127) / 128, 128, 0, s>>>(d_out, n_frames, M, N, C);
