@@ -11,8 +11,9 @@
 //   (adding the entering row's 7 taps, subtracting the leaving one's).  The window value is evaluated from
 //   the exact sums: with D = 49 Sxx - Sx^2 (and likewise), the 1/49^2 and 1/(49*48) factors of the means,
 //   variances and covariance cancel, so SSIM = (2 Sx Sy + c1)(2 Dxy + c2) / ((Sx^2 + Sy^2 + c1)(Dx + Dy + c2))
-//   with c1 = 49^2 C1 and c2 = 49*48 C2; only that last expression is rounded (fp32).  Window values are
-//   summed in fp64 per thread, then per block, then atomically per frame.  The exact u64 sum of squared
+//   with c1 = 49^2 C1 and c2 = 49*48 C2; only that last expression is rounded (fp32).  A thread's window
+//   values of one channel (at most 32) are summed in fp32, those partial sums in fp64 per thread, block and
+//   (atomically) frame.  The exact u64 sum of squared
 //   sample differences comes from the same staged blocks, each block taking the pixels of its own window
 //   corners (the last block row and column also the image's last six rows and columns).
 // - k_utility_finalize: MSE = SSE / (M N C), SSIM = sum / ((M-6)(N-6) C).
@@ -97,11 +98,13 @@ __device__ __forceinline__ void row_taps2(const uint8_t *xs, const uint8_t *ys, 
 }
 
 // SSIM of one 7 x 7 window from its exact sums (the 1/49^2 and 1/(49*48) factors cancel; see the header).
+// Every integer here fits in 32 bits (sums of 49 u8 samples: Sx <= 12495, 49 Sxx <= 1.6e8, Dx + Dy <=
+// 3.2e8), so nothing touches the FP64 pipe.
 __device__ __forceinline__ float ssim_of(const int *S, float c1, float c2) {
-    const long long sx = S[0], sy = S[1];
-    const long long dx = 49ll * S[2] - sx * sx;
-    const long long dy = 49ll * S[3] - sy * sy;
-    const long long dxy = 49ll * S[4] - sx * sy;
+    const int sx = S[0], sy = S[1];
+    const int dx = 49 * S[2] - sx * sx;
+    const int dy = 49 * S[3] - sy * sy;
+    const int dxy = 49 * S[4] - sx * sy;
     const float num = (2.0f * (float)(sx * sy) + c1) * (2.0f * (float)dxy + c2);
     const float den = ((float)(sx * sx + sy * sy) + c1) * ((float)(dx + dy) + c2);
     return __fdiv_rn(num, den);
@@ -159,9 +162,10 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const uint8_t *x, const u
                     V1[q] += b[q];
                 }
             }
+            float part_sum = 0.0f;  // at most 2 x 16 window values in [-1, 1] per channel
             for (int i = 0; i < nrows; ++i) {
-                acc += (double)ssim_of(V0, c1, c2);
-                if (v1) acc += (double)ssim_of(V1, c1, c2);
+                part_sum += ssim_of(V0, c1, c2);
+                if (v1) part_sum += ssim_of(V1, c1, c2);
                 if (i + 1 < nrows) {
                     int a[5], b[5], c[5], d[5];
                     row_taps2<C>(xs, ys, RB, i + kWin, t2, ch, a, b);
@@ -173,6 +177,7 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const uint8_t *x, const u
                     }
                 }
             }
+            acc += (double)part_sum;
         }
     }
     acc = warp_sum_f64(acc);
