@@ -155,7 +155,7 @@ __device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint
 // whatever the row's alignment), and the row's offset inside its first granule is kept; consumers realign
 // words with a funnel shift.  The item's map bytes and payload offsets come with the same asynchronous
 // copies, so preparing an item waits on nothing.  Items are double-buffered: the next item's copies are in
-// flight while the current one is summed.  Each CTA takes a contiguous range of items.  Work units are
+// flight while the current one is summed.  Each CTA takes chunks of consecutive items, dealt round-robin.  Work units are
 // (tile, cell, row part): a b_r x b_r cell is split into 2^rel_lp[r] row parts when its bytes exceed a
 // budget, so that units do similar work; the parts of a cell sit on adjacent, aligned lanes and add their
 // partial sums with shuffles.  A row part's sums use dp4a with compile-time channel masks on realigned words.
@@ -448,20 +448,36 @@ __device__ __forceinline__ void rel_compute(const Geom &g, const CallArgs &a, co
     }
 }
 
-// Items [i0, i1) of a CTA: contiguous, equal shares.
-__device__ __forceinline__ void rel_range(uint32_t items, uint32_t &i0, uint32_t &i1) {
-    const uint32_t per = (items + gridDim.x - 1) / gridDim.x;
-    i0 = min(items, blockIdx.x * per);
-    i1 = min(items, i0 + per);
-}
+// The items of a CTA: chunks of q consecutive items dealt round-robin over the CTAs, q = kRelChunk or, for
+// launches with fewer items, an equal share.  Each CTA's items increase, so an image changes at most once per
+// chunk, while concurrently running CTAs read neighbouring chunks (measured on the 256-portrait batch: release
+// 2.56 ms with one contiguous share per CTA, 2.22 / 2.21 / 2.18 ms with chunks of 8 / 16 / 32 items).
+constexpr uint32_t kRelChunk = 32;
+struct RelSeq {
+    uint32_t items, q;
+    __device__ __forceinline__ RelSeq(uint32_t n) : items(n) {
+        const uint32_t share = (n + gridDim.x - 1) / gridDim.x;
+        q = share < kRelChunk ? share : kRelChunk;
+        if (q == 0) q = 1;
+    }
+    __device__ __forceinline__ uint32_t first() const {
+        const uint64_t f = (uint64_t)blockIdx.x * q;
+        return f < items ? (uint32_t)f : items;
+    }
+    __device__ __forceinline__ uint32_t next(uint32_t item) const {
+        const uint64_t n = (item + 1) % q ? (uint64_t)item + 1 : (uint64_t)item + 1 + (uint64_t)(gridDim.x - 1) * q;
+        return n < items ? (uint32_t)n : items;
+    }
+};
 
 // The double-buffered item loop of both release kernels: prepare(item, nb) stages an item into buffer nb
 // (rows by bulk copies completing on bars[nb], its tables by cp.async), compute(nb) consumes buffer nb.
 // The mbarrier of a buffer completes one phase per item: thread 0 arrives once every warp has announced
 // the item's bytes.  A wait that gives up raises DP_PIX_E_TIMEOUT and ends the CTA.
 template <class Prep, class Comp>
-__device__ __forceinline__ void rel_loop(uint32_t i0, uint32_t i1, uint64_t *bars, int32_t *status, Prep prepare,
+__device__ __forceinline__ void rel_loop(const RelSeq &seq, uint64_t *bars, int32_t *status, Prep prepare,
                                          Comp compute) {
+    const uint32_t i0 = seq.first(), items = seq.items;
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -470,13 +486,14 @@ __device__ __forceinline__ void rel_loop(uint32_t i0, uint32_t i1, uint64_t *bar
     __syncthreads();
     int buf = 0;
     uint32_t ph0 = 0, ph1 = 0;
-    if (i0 < i1) prepare(i0, 0);
+    if (i0 < items) prepare(i0, 0);
     cp_async_commit();
     __syncthreads();
-    if (threadIdx.x == 0 && i0 < i1) mbar_arrive(&bars[0]);
-    for (uint32_t item = i0; item < i1; ++item) {
-        const bool next = item + 1 < i1;
-        if (next) prepare(item + 1, buf ^ 1);
+    if (threadIdx.x == 0 && i0 < items) mbar_arrive(&bars[0]);
+    for (uint32_t item = i0; item < items;) {
+        const uint32_t nitem = seq.next(item);
+        const bool next = nitem < items;
+        if (next) prepare(nitem, buf ^ 1);
         cp_async_commit();
         cp_async_wait_1();
         const bool ok = mbar_wait(&bars[buf], buf ? ph1 : ph0);
@@ -492,6 +509,7 @@ __device__ __forceinline__ void rel_loop(uint32_t i0, uint32_t i1, uint64_t *bar
         compute(buf);
         __syncthreads();
         buf ^= 1;
+        item = nitem;
     }
     cp_async_wait_all();
 }
@@ -502,15 +520,14 @@ __global__ void __launch_bounds__(kRelThreads) k_release(const Geom g, const Cal
     __shared__ RelItem it[2];
     __shared__ uint64_t bars[2];
     const int buf_bytes = g.T * rel_rowstride(g.seg_tiles, g.T, C);
-    uint32_t i0, i1;
-    rel_range(a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row, i0, i1);
+    const RelSeq seq(a.n_frames * (uint32_t)g.GR * (uint32_t)g.seg_per_row);
     const uint32_t per_frame = (uint32_t)g.GR * (uint32_t)g.seg_per_row;
     auto prepare = [&](uint32_t item, int nb) {
         const uint32_t f = item / per_frame;
         rel_prepare(g, a, f, item - f * per_frame, it[nb], dyn + nb * buf_bytes, &bars[nb]);
     };
     auto compute = [&](int nb) { rel_compute<C>(g, a, it[nb], dyn + nb * buf_bytes); };
-    rel_loop(i0, i1, bars, a.status, prepare, compute);
+    rel_loop(seq, bars, a.status, prepare, compute);
 }
 
 // Batch: items = (tile row, segment) of every image, image i owning [base[2], base[2] + GR * seg_per_row).
@@ -521,15 +538,13 @@ __global__ void __launch_bounds__(kRelThreads) k_batch_release(const BatchEntry 
     __shared__ RelItem it[2];
     __shared__ BatchShared bs[2];
     __shared__ uint64_t bars[2];
-    uint32_t i0, i1;
-    rel_range(items, i0, i1);
+    const RelSeq seq(items);
     int cur0 = -1, cur1 = -1;        // image whose geometry bs[0], bs[1] hold
     int img = -1;                    // image of the last prepared item, owning items [img_lo, img_hi)
     uint32_t img_lo = 0, img_hi = 0;
     auto prepare = [&](uint32_t item, int nb) {
-        if (img < 0 || item >= img_hi) {
-            int i = img < 0 ? batch_find(tab, n_img, item, 2) : img;
-            while (i + 1 < (int)n_img && tab[i + 1].base[2] <= item) ++i;
+        if (img < 0 || item >= img_hi) {  // items increase: the image changes at most once per chunk
+            const int i = batch_find(tab, n_img, item, 2);
             img = i;
             img_lo = tab[i].base[2];
             img_hi = i + 1 < (int)n_img ? tab[i + 1].base[2] : items;
@@ -542,7 +557,7 @@ __global__ void __launch_bounds__(kRelThreads) k_batch_release(const BatchEntry 
         rel_prepare(bs[nb].g, bs[nb].a, 0u, item - img_lo, it[nb], dyn + nb * buf_bytes, &bars[nb]);
     };
     auto compute = [&](int nb) { rel_compute<C>(bs[nb].g, bs[nb].a, it[nb], dyn + nb * buf_bytes); };
-    rel_loop(i0, i1, bars, tab[0].a.status, prepare, compute);
+    rel_loop(seq, bars, tab[0].a.status, prepare, compute);
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -623,15 +638,13 @@ __global__ void __launch_bounds__(kThreads) k_batch_classify(const BatchEntry *t
     __shared__ uint64_t bars[2];
     __shared__ uint32_t cnt_s[kRelSegMax];
     if (threadIdx.x < kRelSegMax) cnt_s[threadIdx.x] = 0u;
-    uint32_t i0, i1;
-    rel_range(items, i0, i1);
+    const RelSeq seq(items);
     int cur0 = -1, cur1 = -1;
     int img = -1;
     uint32_t img_lo = 0, img_hi = 0;
     auto prepare = [&](uint32_t item, int nb) {
-        if (img < 0 || item >= img_hi) {
-            int i = img < 0 ? batch_find(tab, n_img, item, 0) : img;
-            while (i + 1 < (int)n_img && tab[i + 1].base[0] <= item) ++i;
+        if (img < 0 || item >= img_hi) {  // items increase: the image changes at most once per chunk
+            const int i = batch_find(tab, n_img, item, 0);
             img = i;
             img_lo = tab[i].base[0];
             img_hi = i + 1 < (int)n_img ? tab[i + 1].base[0] : items;
@@ -663,7 +676,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_classify(const BatchEntry *t
                    rel_rowstride(S, T, es), dyn + nb * buf_bytes, c.rowbase, &bars[nb]);
     };
     auto compute = [&](int nb) { cls_compute<kMatte>(bs[nb].g, bs[nb].a, it[nb], dyn + nb * buf_bytes, cnt_s); };
-    rel_loop(i0, i1, bars, tab[0].a.status, prepare, compute);
+    rel_loop(seq, bars, tab[0].a.status, prepare, compute);
 }
 
 // ------------------------------------------------------------------------------------------------------
