@@ -325,6 +325,10 @@ __global__ void __launch_bounds__(kThreads)
 
 // Batch: one item per (image, tile row), image i owning [base[3], base[3] + GR); the record and the output of
 // each image come from the batch table, and its header is parsed when a CTA moves to a new image.
+// Tile rows per chunk: 1.  Images are in largest-first order and a tile row's work grows with the image width,
+// so single rows dealt round-robin balance the CTAs best (256-portrait batch: 1.71 ms, against 2.00 and 2.85 ms
+// with chunks of 4 and 16 rows).
+constexpr uint32_t kRecChunk = 1;
 template <int kOutF32, int kFastC>
 __global__ void __launch_bounds__(kThreads)
     k_batch_reconstruct(const BatchEntry *tab, uint32_t n_img, uint32_t items, int max_C, int out_align,
@@ -339,9 +343,18 @@ __global__ void __launch_bounds__(kThreads)
     uint8_t *stage = dyn;
     uint32_t *colinfo = reinterpret_cast<uint32_t *>(dyn + kStageBytes);
     uint8_t *pat = dyn + kStageBytes + kMaxSegPx * 4;
+    // chunks of q consecutive tile rows dealt round-robin; a CTA parses a header only when its image changes
+    const uint32_t share = (items + gridDim.x - 1) / gridDim.x;
+    const uint32_t q = share < kRecChunk ? (share ? share : 1u) : kRecChunk;
+    auto next_item = [&](uint32_t it) -> uint32_t {
+        const uint64_t n = (it + 1) % q ? (uint64_t)it + 1 : (uint64_t)it + 1 + (uint64_t)(gridDim.x - 1) * q;
+        return n < items ? (uint32_t)n : items;
+    };
     int cur = -1;
-    for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const int i = batch_find(tab, n_img, item, 3);
+    uint32_t lo = 0, hi = 0;  // items of image cur
+    for (uint32_t item = (uint64_t)blockIdx.x * q < items ? blockIdx.x * q : items; item < items;
+         item = next_item(item)) {
+        const int i = (cur >= 0 && item >= lo && item < hi) ? cur : batch_find(tab, n_img, item, 3);
         const BatchEntry &e = tab[i];
         const uint8_t *rec = e.a.records;
         if (i != cur) {
@@ -355,6 +368,8 @@ __global__ void __launch_bounds__(kThreads)
             }
             __syncthreads();
             cur = i;
+            lo = e.base[3];
+            hi = i + 1 < (int)n_img ? tab[i + 1].base[3] : items;
         }
         if (!rg.ok || e.out == nullptr) continue;
         const int ty = (int)(item - e.base[3]);
