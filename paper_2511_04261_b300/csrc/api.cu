@@ -244,19 +244,6 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
         const uint64_t c = (uint64_t)g.cells_side[r] * g.cells_side[r];
         maxcells = c > maxcells ? c : maxcells;
     }
-    g.rel_pmax = 1;
-    for (int r = 0; r < d->K; ++r) {
-        const int P = rel_parts(g.grid[r], d->C);
-        if (P > g.rel_pmax) g.rel_pmax = P;
-    }
-    for (int r = 0; r < d->K; ++r) {
-        const int P = rel_parts(g.grid[r], d->C);
-        int lp = 0;
-        while ((1 << lp) < P) ++lp;
-        g.rel_lp[r] = lp;
-        const int units = g.cells_side[r] * g.cells_side[r] * P;
-        g.rel_units[r] = (units + g.rel_pmax - 1) / g.rel_pmax * g.rel_pmax;
-    }
     g.b_min = bmin;
     g.g = (int)gg;
     g.rowidx_offset = kHeaderBytes;
@@ -310,7 +297,35 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     g.seg_per_row = (g.GC + S - 1) / S;
     g.seg_rowstride = (int)a16((uint64_t)S * TC);
     g.vbands = vb_rel;
+    set_release_units(g);
     return DP_PIX_OK;
+}
+
+}  // namespace
+
+int plan_geometry(const dp_pix_desc *d, Geom &g) { return make_geom(d, g); }
+
+// Release work units of each region for the plan's segment width (k_release): a cell's row parts follow the
+// byte budget of rel_parts, and are doubled further while an item of S tiles of the region would hold fewer
+// than kRelMinUnits units (large cells of few channels would otherwise leave most of a CTA idle).
+void set_release_units(Geom &g) {
+    const int S = g.seg_tiles > 0 ? g.seg_tiles : 1;
+    int P[kMaxK];
+    g.rel_pmax = 1;
+    for (int r = 0; r < g.K; ++r) {
+        const int b = g.grid[r], cs = g.cells_side[r];
+        int p = rel_parts(b, g.C);
+        while (S * cs * cs * p < kRelMinUnits && 2 * p <= b && p < 32) p *= 2;
+        P[r] = p;
+        if (p > g.rel_pmax) g.rel_pmax = p;
+    }
+    for (int r = 0; r < g.K; ++r) {
+        int lp = 0;
+        while ((1 << lp) < P[r]) ++lp;
+        g.rel_lp[r] = lp;
+        const int units = g.cells_side[r] * g.cells_side[r] * P[r];
+        g.rel_units[r] = (units + g.rel_pmax - 1) / g.rel_pmax * g.rel_pmax;
+    }
 }
 
 int check_cuda_device() {
@@ -320,9 +335,6 @@ int check_cuda_device() {
     return DP_PIX_OK;
 }
 
-}  // namespace
-
-int plan_geometry(const dp_pix_desc *d, Geom &g) { return make_geom(d, g); }
 int cuda_device_ok() { return check_cuda_device(); }
 
 namespace {

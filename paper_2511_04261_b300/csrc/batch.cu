@@ -69,6 +69,7 @@ void apply_seg(Geom &g, int S) {
     g.seg_tiles = S;
     g.seg_per_row = (g.GC + S - 1) / S;
     g.seg_rowstride = (S * g.T * g.C + 15) / 16 * 16;
+    set_release_units(g);
 }
 
 // Fills the work-order table (host) from the caller's images and the current segment width.

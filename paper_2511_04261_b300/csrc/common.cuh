@@ -63,6 +63,7 @@ struct Geom {
 // Row parts of one b x b cell of C-channel u8 samples in the release: the smallest power of two P (at most
 // min(b, 32)) that keeps ceil(b/P) * b * C bytes per part within a budget, so that work units are similar.
 constexpr int kRelPartBytes = 384;
+constexpr int kRelMinUnits = 64;  // work units an item of one region should at least hold
 
 // Tiles per classification item of a batch (source rows of at least 256 bytes, at most 16 tiles); es is the
 // source element size (1: u8 mask, 4: f32 matte).
@@ -287,6 +288,7 @@ namespace dppix {
 uint64_t plan_ws_per_frame(const dp_pix_plan_s *plan);  // workspace bytes per frame of a plan (0 for NULL)
 int set_last_error(int code, const char *msg);          // sets this thread's dp_pix_last_error(), returns code
 int plan_geometry(const dp_pix_desc *d, Geom &g);       // dp_pix_plan's validation and geometry (host)
+void set_release_units(Geom &g);                        // release work units for the plan's segment width
 int cuda_device_ok();                                   // DP_PIX_OK, or DP_PIX_E_CUDA with the message set
 
 }  // namespace dppix
