@@ -3,7 +3,8 @@
 //
 // - k_sobel_mask: one CTA per (frame, 32 rows, 256 columns): the channel-sum intensity of the block and a
 //   one-pixel mirrored border is staged in shared memory as u16, then each thread walks one column down the
-//   32 rows: Gx, Gy from the 3 x 3 Sobel taps in exact integers, mask = (Gx^2 + Gy^2 < tau) ? 1 : 0.
+//   32 rows with the 3 x 3 window in registers: Gx, Gy from the
+//   Sobel taps in exact integers, mask = (Gx^2 + Gy^2 < tau) ? 1 : 0.
 // - k_ssim: one CTA of 128 threads per (frame, 16 window rows, 256 window columns); the 22 x 262-pixel
 //   input block of both images is staged in shared memory; each thread keeps, per channel, the five exact
 //   integer window sums (Sx, Sy, Sxx, Syy, Sxy) of two adjacent columns' 7 x 7 windows (their six shared
@@ -55,12 +56,16 @@ __global__ void __launch_bounds__(kSobCols) k_sobel_mask(const uint8_t *frames, 
     if (x >= N) return;
     uint8_t *mb = mask + (int64_t)blockIdx.z * mfstride + x;
     const int rows = min(kSobRows, M - y0);
+    // the 3 x 3 window slides down the column: rows r, r + 1, r + 2 held in registers
+    int a0 = I[0][c], a1 = I[0][c + 1], a2 = I[0][c + 2];
+    int b0 = I[1][c], b1 = I[1][c + 1], b2 = I[1][c + 2];
     for (int r = 0; r < rows; ++r) {
-        const int gx = ((int)I[r][c + 2] - (int)I[r][c]) + 2 * ((int)I[r + 1][c + 2] - (int)I[r + 1][c]) +
-                       ((int)I[r + 2][c + 2] - (int)I[r + 2][c]);
-        const int gy = ((int)I[r + 2][c] + 2 * (int)I[r + 2][c + 1] + (int)I[r + 2][c + 2]) -
-                       ((int)I[r][c] + 2 * (int)I[r][c + 1] + (int)I[r][c + 2]);
+        const int c0 = I[r + 2][c], c1 = I[r + 2][c + 1], c2 = I[r + 2][c + 2];
+        const int gx = (a2 - a0) + 2 * (b2 - b0) + (c2 - c0);
+        const int gy = (c0 + 2 * c1 + c2) - (a0 + 2 * a1 + a2);
         mb[(int64_t)(y0 + r) * mpitch] = ((uint32_t)(gx * gx + gy * gy) < tau) ? 1 : 0;
+        a0 = b0, a1 = b1, a2 = b2;
+        b0 = c0, b1 = c1, b2 = c2;
     }
 }
 
