@@ -451,8 +451,9 @@ DPPIX_API int dp_pix_debug_noise(uint64_t seed, const uint32_t *d_ctr, uint64_t 
  * input of a DP_PIX_SRC_MASK_U8 release.
  *   d_frames: n_frames frames of M x N x C u8, rows row_pitch bytes apart, frames frame_stride apart.
  *   d_mask:   n_frames u8 masks of M x N, rows mask_pitch apart, frames mask_frame_stride apart.
- * Caller-owned device buffers; asynchronous on cuda_stream.  Errors: INVALID_ARG (M or N < 2, C outside
- * 1..4, bad pad_mode, pitches or strides too small, NULL), UNSUPPORTED (M or N > 2^24), CUDA.
+ * Caller-owned device buffers; asynchronous on cuda_stream; n_frames = 0 does nothing.  Errors: INVALID_ARG
+ * (M or N < 2, C outside 1..4, bad pad_mode, pitches or strides too small, NULL), UNSUPPORTED (M or N >
+ * 2^24), CUDA.
  */
 DPPIX_API int dp_pix_sobel_mask(const void *d_frames, int32_t M, int32_t N, int32_t C, int64_t row_pitch,
                                 int64_t frame_stride, uint32_t n_frames, int32_t pad_mode, uint32_t tau, void *d_mask,
@@ -475,8 +476,9 @@ typedef struct dp_pix_utility_t {
  * C1 = (0.01 * 255)^2, C2 = (0.03 * 255)^2, the mean over windows and channels.  Window sums are exact
  * integers; each window's value is rounded once (fp32) and summed in fp64.
  *   d_out: n_frames entries of dp_pix_utility_t (device memory, 8-byte aligned), zeroed by this call.
- * Caller-owned device buffers; asynchronous on cuda_stream.  Errors: INVALID_ARG (M or N < 7, C outside
- * 1..4, pitches or strides too small, NULL, misaligned d_out), UNSUPPORTED (M or N > 2^24), CUDA.
+ * Caller-owned device buffers; asynchronous on cuda_stream; n_frames = 0 does nothing.  Errors: INVALID_ARG
+ * (M or N < 7, C outside 1..4, pitches or strides too small, NULL, misaligned d_out), UNSUPPORTED (M or N >
+ * 2^24), CUDA.
  */
 DPPIX_API int dp_pix_utility(const void *d_x, const void *d_y, int32_t M, int32_t N, int32_t C, int64_t pitch_x,
                              int64_t pitch_y, int64_t frame_stride_x, int64_t frame_stride_y, uint32_t n_frames,

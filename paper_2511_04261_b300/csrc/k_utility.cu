@@ -214,9 +214,10 @@ extern "C" {
 int dp_pix_sobel_mask(const void *d_frames, int32_t M, int32_t N, int32_t C, int64_t row_pitch, int64_t frame_stride,
                       uint32_t n_frames, int32_t pad_mode, uint32_t tau, void *d_mask, int64_t mask_pitch,
                       int64_t mask_frame_stride, void *cuda_stream) {
+    if (n_frames == 0) return DP_PIX_OK;  // nothing to do
     if (!d_frames || !d_mask) return set_last_error(DP_PIX_E_INVALID_ARG, "null frame or mask pointer");
-    if (M < 2 || N < 2 || C < 1 || C > 4 || n_frames < 1 || n_frames > 65535)
-        return set_last_error(DP_PIX_E_INVALID_ARG, "need M, N >= 2, C in 1..4, 1 <= n_frames <= 65535");
+    if (M < 2 || N < 2 || C < 1 || C > 4 || n_frames > 65535)
+        return set_last_error(DP_PIX_E_INVALID_ARG, "need M, N >= 2, C in 1..4, n_frames <= 65535");
     if (M > (1 << 24) || N > (1 << 24)) return set_last_error(DP_PIX_E_UNSUPPORTED, "M or N too large");
     if (pad_mode != DP_PIX_PAD_REFLECT && pad_mode != DP_PIX_PAD_SYMMETRIC)
         return set_last_error(DP_PIX_E_INVALID_ARG, "pad_mode must be REFLECT or SYMMETRIC");
@@ -245,9 +246,10 @@ int dp_pix_sobel_mask(const void *d_frames, int32_t M, int32_t N, int32_t C, int
 int dp_pix_utility(const void *d_x, const void *d_y, int32_t M, int32_t N, int32_t C, int64_t pitch_x, int64_t pitch_y,
                    int64_t frame_stride_x, int64_t frame_stride_y, uint32_t n_frames, dp_pix_utility_t *d_out,
                    void *cuda_stream) {
+    if (n_frames == 0) return DP_PIX_OK;  // nothing to do
     if (!d_x || !d_y || !d_out) return set_last_error(DP_PIX_E_INVALID_ARG, "null pointer");
-    if (M < kWin || N < kWin || C < 1 || C > 4 || n_frames < 1 || n_frames > 65535)
-        return set_last_error(DP_PIX_E_INVALID_ARG, "need M, N >= 7, C in 1..4, 1 <= n_frames <= 65535");
+    if (M < kWin || N < kWin || C < 1 || C > 4 || n_frames > 65535)
+        return set_last_error(DP_PIX_E_INVALID_ARG, "need M, N >= 7, C in 1..4, n_frames <= 65535");
     if (M > (1 << 24) || N > (1 << 24)) return set_last_error(DP_PIX_E_UNSUPPORTED, "M or N too large");
     if (pitch_x < (int64_t)N * C || pitch_y < (int64_t)N * C)
         return set_last_error(DP_PIX_E_INVALID_ARG, "row pitch < N*C");

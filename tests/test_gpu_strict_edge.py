@@ -47,6 +47,19 @@ def test_strict_release_mask(M, N):
     compare_records(recs[0], rec, means, sums, etas, O.DT_F32)
 
 
+@pytest.mark.parametrize("dtype", [O.DT_F32, O.DT_U8])
+def test_strict_noise_free_is_valid_sample_block_mean(dtype):
+    rng = np.random.default_rng(40 + dtype)
+    M, N, grids = 45, 67, [8, 24]
+    img = rng.integers(0, 256, size=(M, N, 3), dtype=np.uint8)
+    lab = _labels(rng, M, N, grids)
+    kw = dict(M=M, N=N, C=3, grids=grids, eps=[1.0, 1.0], pad_mode=O.PAD_NONE, source=O.SRC_TILE_LABELS,
+              dtype=dtype, seed=5, m=16, noise_free=True)
+    _, recs_t, recs = gpu_release(img, lab, **kw)
+    rec, means, sums, etas = O.release(img, lab, **kw)
+    compare_records(recs[0], rec, means, sums, etas, dtype)
+
+
 def test_strict_release_matte():
     img, alpha = synth.portrait(np.random.default_rng(5), 181, 251)
     kw = dict(M=181, N=251, C=3, grids=[20, 6], eps=[1.5, 0.5], pad_mode=O.PAD_NONE, source=O.SRC_MATTE,

@@ -93,3 +93,10 @@ def test_utility_and_sobel_reject_bad_arguments():
         P.dp_pix_sobel_mask(u, 10)  # one row
     with pytest.raises(P.DppixError):
         P.dp_pix_sobel_mask(torch.zeros((4, 4, 3), dtype=torch.uint8, device="cuda"), 10, pad_mode=5)
+
+
+def test_empty_calls_do_nothing():
+    import ctypes as ct
+    from paper_2511_04261_b300 import _lib as L
+    assert L.lib().dp_pix_utility(None, None, 7, 7, 1, 7, 7, 49, 49, 0, None, None) == 0
+    assert L.lib().dp_pix_sobel_mask(None, 2, 2, 1, 2, 4, 0, 0, 1, None, 2, 4, None) == 0
