@@ -411,6 +411,28 @@ def run_ours(args):
                "direct_call": {"p50_ms": float(np.percentile(lat_direct, 50)),
                                "p99_ms": float(np.percentile(lat_direct, 99)),
                                "what": "the same call issued from Python each time (host submission included)"}}
+    # the plain region-adaptive release of one 768 x 576 RGB frame with its foreground mask (fg b 8 / eps 0.5,
+    # bg b 24 / eps 1, m 16, Philox seed 1), release + reconstruct, as one captured graph
+    f1, mask1 = synth.rect_frame(seed=1001)
+    f1d, m1d = torch.from_numpy(f1).to(dev)[None], torch.from_numpy(mask1).to(dev)[None]
+    plan1 = P.Plan(M=576, N=768, C=3, grids=[24, 8], eps=[1.0, 0.5], m=16.0, seed=1, source=P.SRC_MASK_U8,
+                   dtype=P.REC_F32)
+    r1, w1 = plan1.alloc_records(1, device=dev), plan1.alloc_workspace(1, device=dev)
+    o1 = torch.empty((1, 576, 768, 3), dtype=torch.uint8, device=dev)
+
+    def step1():
+        plan1.release_reconstruct(f1d, m1d, stream_id=rank, out_type=P.OUT_U8, records=r1, out=o1, ws=w1)
+
+    step1()
+    graph1 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph1):
+        step1()
+    torch.cuda.synchronize()
+    lat1 = timed(lambda i: graph1.replay())
+    latency["frame_768x576_mask"] = {
+        "p50_ms": float(np.percentile(lat1, 50)), "p99_ms": float(np.percentile(lat1, 99)),
+        "what": "one 768x576 RGB frame with its rectangle mask (fg b 8 eps 0.5, bg b 24 eps 1, m 16), release + "
+                "reconstruct, device-resident, CUDA-graph replay, 50 reps"}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
