@@ -149,7 +149,9 @@ __device__ __forceinline__ int wrap_count(int &k, int n) {
 
 // Writes the jmax output rows of a segment whose first output byte is orow0 (16-byte aligned) and
 // whose rows hold vpx pixels; stage holds the segment's cell values (packed u8 or float4).  Threads
-// tid = 0..nthr-1 of the group share the work.
+// tid = 0..nthr-1 of the group share the work.  The rows are stored with the streaming hint (st.global.cs):
+// nothing reads them back here, and their lines leave L2 while this issue-bound writer runs instead of being
+// written back during the next, bandwidth-bound pass (64-frame clip step: 205.1 -> 199.4 us).
 template <int C, int kOutF32>
 __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, const uint8_t *stage, int ns, int T, int vpx,
                                int jmax, uint8_t *orow0, int64_t out_pitch, int tid, int nthr) {
@@ -226,10 +228,10 @@ __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, cons
                     }
                     vec = build();
                 }
-                *reinterpret_cast<uint4 *>(dst) = vec;
-                *reinterpret_cast<uint4 *>(dst + out_pitch) = vec;
-                *reinterpret_cast<uint4 *>(dst + 2 * out_pitch) = vec;
-                *reinterpret_cast<uint4 *>(dst + 3 * out_pitch) = vec;
+                __stcs(reinterpret_cast<uint4 *>(dst), vec);
+                __stcs(reinterpret_cast<uint4 *>(dst + out_pitch), vec);
+                __stcs(reinterpret_cast<uint4 *>(dst + 2 * out_pitch), vec);
+                __stcs(reinterpret_cast<uint4 *>(dst + 3 * out_pitch), vec);
             }
         }
         for (; j < j1; ++j, dst += out_pitch) {
@@ -245,7 +247,7 @@ __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, cons
                 vec = build();
             }
             if (full) {
-                *reinterpret_cast<uint4 *>(dst) = vec;
+                __stcs(reinterpret_cast<uint4 *>(dst), vec);
             } else {
                 for (int i = 0; o + i < row_bytes; ++i) {
                     const uint32_t wv = i < 4 ? vec.x : (i < 8 ? vec.y : (i < 12 ? vec.z : vec.w));
