@@ -588,6 +588,7 @@ def run_uniform(args):
     F = UNIFORM["frames"]
     stream = torch.cuda.current_stream()
     sweep, single, prof_head, clocks, head_ms, algo_head = {}, {}, None, None, None, None
+    direct_ms_frame = None
     for (M, N) in UNIFORM["shapes"]:
         clip_h = synth.moving_rect_clip(seed=1005 + rank, frames=F, M=M, N=N, C=1)
         frames = torch.from_numpy(clip_h).cuda()
@@ -612,17 +613,22 @@ def run_uniform(args):
             for _ in range(max(3, args.warmup)):
                 call()
             torch.cuda.synchronize()
+            # the 64-frame call captured once and replayed (these small calls are otherwise bound by host-side
+            # launch work, which varies from box to box); the direct calls are timed beside it
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                call()
+            graph.replay()
+            torch.cuda.synchronize()
             if head:
                 sampler = ClockSampler(torch.cuda.current_device())
                 barrier(world)
                 torch.cuda.synchronize()
-                P.prof_reset()
-                P.prof_enable(True)
                 sampler.start()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(reps):
-                call()
+                graph.replay()
             e1.record(stream)
             torch.cuda.synchronize()
             ms_frame = max_over_ranks(e0.elapsed_time(e1) / reps / F, world)
@@ -630,6 +636,18 @@ def run_uniform(args):
             if head:
                 barrier(world)
                 clocks = sampler.stop()
+                e0.record(stream)
+                for _ in range(reps):
+                    call()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                direct_ms_frame = e0.elapsed_time(e1) / reps / F
+                # per-kernel durations: the library's own events around each launch, on direct calls
+                P.prof_reset()
+                P.prof_enable(True)
+                for _ in range(reps):
+                    call()
+                torch.cuda.synchronize()
                 prof_head = P.prof_read()
                 P.prof_enable(False)
                 head_ms = ms_frame
@@ -678,7 +696,9 @@ def run_uniform(args):
                 "config": {"workload": "uniform64_768x576_gray_b16", "frames_per_call": F, "M": 576, "N": 768, "C": 1,
                            "grids": [16], "eps": [UNIFORM["eps"]], "m": UNIFORM["m"],
                            "region_source": "one region (tile labels all 0)",
-                           "step": "dp_pix_release_reconstruct of 64 frames (release + reconstruction)",
+                           "step": "dp_pix_release_reconstruct of 64 frames (release + reconstruction), timed as a "
+                                   "CUDA-graph replay of the call",
+                           "direct_call_ms_per_frame": direct_ms_frame,
                            "stands_in_for": "PETS09-S2L1 (768 x 576) and Venice-2 (1920 x 1080) grayscale sequences",
                            "generator_seed": 1005, "parallelism": "1 GPU" if world == 1 else "replicas",
                            "l2": "64 frames (28 MB in, 28 MB out) per call: inside L2 at 768 x 576"},
