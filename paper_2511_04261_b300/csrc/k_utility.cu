@@ -5,10 +5,10 @@
 //   one-pixel mirrored border is staged in shared memory as u16, then each thread walks one column down the
 //   32 rows with the 3 x 3 window in registers: Gx, Gy from the
 //   Sobel taps in exact integers, mask = (Gx^2 + Gy^2 < tau) ? 1 : 0.
-// - k_ssim: one CTA of 128 threads per (frame, 16 window rows, 256 window columns); the 22 x 262-pixel
-//   input block of both images is staged in shared memory; each thread keeps, per channel, the five exact
-//   integer window sums (Sx, Sy, Sxx, Syy, Sxy) of two adjacent columns' 7 x 7 windows (their six shared
-//   taps of a row summed once) and slides them down the rows
+// - k_ssim: one CTA per (frame, 8 window rows, 512 window columns; 384 for C = 4); the 14 x 518-pixel input
+//   block of both images is staged in shared memory; each thread keeps, per channel, the five exact integer
+//   window sums (Sx, Sy, Sxx, Syy, Sxy) of four adjacent columns' 7 x 7 windows (a row's ten taps loaded
+//   once, the first window summed and the others slid by a tap) and slides them down the rows
 //   (adding the entering row's 7 taps, subtracting the leaving one's).  The window value is evaluated from
 //   the exact sums: with D = 49 Sxx - Sx^2 (and likewise), the 1/49^2 and 1/(49*48) factors of the means,
 //   variances and covariance cancel, so SSIM = (2 Sx Sy + c1)(2 Dxy + c2) / ((Sx^2 + Sy^2 + c1)(Dx + Dy + c2))
@@ -24,7 +24,11 @@ namespace dppix {
 namespace {
 
 constexpr int kSobRows = 32, kSobCols = 256;
-constexpr int kSsimRows = 16, kSsimCols = 256, kSsimThreads = 128, kWin = 7;  // two window columns per thread
+constexpr int kSsimRows = 8, kWin = 7;  // window rows per block; four window columns per thread
+template <int C> struct SsimShape {
+    static constexpr int COLS = C == 4 ? 384 : 512;  // window columns per block (staged block within 48 KB)
+    static constexpr int THREADS = COLS / 4;
+};
 
 // Mirror index on both sides for one-pixel borders and clamped overhangs (n >= 2).
 __device__ __forceinline__ int mirror2(int p, int n, int mode) {
@@ -81,25 +85,39 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
     return v;
 }
 
-// Five exact sums (x, y, x^2, y^2, xy) of staged row r over window columns t2 and t2 + 1 (taps t2 .. t2 + 6
-// and t2 + 1 .. t2 + 7, the six shared taps summed once), channel ch.
+// Five exact sums (x, y, x^2, y^2, xy) of staged row r over window columns t4 .. t4 + 3 (taps t4 + i ..
+// t4 + i + 6 for column i: the first window summed, the others slid by one tap), channel ch; S[i][q].
 template <int C>
-__device__ __forceinline__ void row_taps2(const uint8_t *xs, const uint8_t *ys, int rowbytes, int r, int t2, int ch,
-                                          int *s0, int *s1) {
-    const uint8_t *xp = xs + r * rowbytes + t2 * C + ch, *yp = ys + r * rowbytes + t2 * C + ch;
+__device__ __forceinline__ void row_taps4(const uint8_t *xs, const uint8_t *ys, int rowbytes, int r, int t4, int ch,
+                                          int (&S)[4][5]) {
+    const uint8_t *xp = xs + r * rowbytes + t4 * C + ch, *yp = ys + r * rowbytes + t4 * C + ch;
+    int a[kWin + 3], b[kWin + 3];
+#pragma unroll
+    for (int k = 0; k < kWin + 3; ++k) {
+        a[k] = xp[k * C];
+        b[k] = yp[k * C];
+    }
     int sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
 #pragma unroll
-    for (int k = 1; k < kWin; ++k) {
-        const int a = xp[k * C], b = yp[k * C];
-        sx += a;
-        sy += b;
-        sxx += a * a;
-        syy += b * b;
-        sxy += a * b;
+    for (int k = 0; k < kWin; ++k) {
+        sx += a[k];
+        sy += b[k];
+        sxx += a[k] * a[k];
+        syy += b[k] * b[k];
+        sxy += a[k] * b[k];
     }
-    const int a0 = xp[0], b0 = yp[0], a7 = xp[kWin * C], b7 = yp[kWin * C];
-    s0[0] = sx + a0, s0[1] = sy + b0, s0[2] = sxx + a0 * a0, s0[3] = syy + b0 * b0, s0[4] = sxy + a0 * b0;
-    s1[0] = sx + a7, s1[1] = sy + b7, s1[2] = sxx + a7 * a7, s1[3] = syy + b7 * b7, s1[4] = sxy + a7 * b7;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (i > 0) {
+            const int o = a[i - 1], n = a[i + kWin - 1], p = b[i - 1], m = b[i + kWin - 1];
+            sx += n - o;
+            sy += m - p;
+            sxx += n * n - o * o;
+            syy += m * m - p * p;
+            sxy += n * m - o * p;
+        }
+        S[i][0] = sx, S[i][1] = sy, S[i][2] = sxx, S[i][3] = syy, S[i][4] = sxy;
+    }
 }
 
 // SSIM of one 7 x 7 window from its exact sums (the 1/49^2 and 1/(49*48) factors cancel; see the header).
@@ -116,16 +134,17 @@ __device__ __forceinline__ float ssim_of(const int *S, float c1, float c2) {
 }
 
 template <int C>
-__global__ void __launch_bounds__(kSsimThreads) k_ssim(const uint8_t *x, const uint8_t *y, int M, int N, int64_t px,
-                                                       int64_t py, int64_t fsx, int64_t fsy, float c1, float c2,
-                                                       dp_pix_utility_t *out) {
-    constexpr int SR = kSsimRows + kWin - 1, SC = kSsimCols + kWin - 1;
+__global__ void __launch_bounds__(SsimShape<C>::THREADS) k_ssim(const uint8_t *x, const uint8_t *y, int M, int N,
+                                                              int64_t px, int64_t py, int64_t fsx, int64_t fsy, float c1,
+                                                              float c2, dp_pix_utility_t *out) {
+    constexpr int COLS = SsimShape<C>::COLS, NT = SsimShape<C>::THREADS;
+    constexpr int SR = kSsimRows + kWin - 1, SC = COLS + kWin - 1;
     constexpr int RB = SC * C;  // staged bytes per row
     __shared__ uint8_t xs[SR * RB], ys[SR * RB];
-    __shared__ double part[kSsimThreads / 32];
+    __shared__ double part[(NT + 31) / 32];
     const int f = blockIdx.z;
-    const int cy0 = blockIdx.y * kSsimRows, cx0 = blockIdx.x * kSsimCols;  // first window (top-left corner)
-    const int nwy = M - kWin + 1, nwx = N - kWin + 1;                      // windows per column / row
+    const int cy0 = blockIdx.y * kSsimRows, cx0 = blockIdx.x * COLS;  // first window (top-left corner)
+    const int nwy = M - kWin + 1, nwx = N - kWin + 1;                 // windows per column / row
     const int rows_in = min(SR, M - cy0), cols_in = min(SC, N - cx0);
     const uint8_t *xb = x + (int64_t)f * fsx + (int64_t)cy0 * px + (int64_t)cx0 * C;
     const uint8_t *yb = y + (int64_t)f * fsy + (int64_t)cy0 * py + (int64_t)cx0 * C;
@@ -140,7 +159,7 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const uint8_t *x, const u
     // rows / columns in the last block row / column (all of them staged)
     {
         const int ro = blockIdx.y + 1 == gridDim.y ? rows_in : kSsimRows;
-        const int co = (blockIdx.x + 1 == gridDim.x ? cols_in : kSsimCols) * C;
+        const int co = (blockIdx.x + 1 == gridDim.x ? cols_in : COLS) * C;
         unsigned long long e = 0;
         for (int r = 0; r < ro; ++r)
             for (int k = threadIdx.x; k < co; k += blockDim.x) {
@@ -150,36 +169,35 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const uint8_t *x, const u
         e = warp_sum_u64(e);
         if ((threadIdx.x & 31) == 0 && e) atomicAdd(reinterpret_cast<unsigned long long *>(&out[f].sse), e);
     }
-    const int t2 = 2 * threadIdx.x;
-    const bool v0 = cx0 + t2 < nwx, v1 = cx0 + t2 + 1 < nwx;
+    const int t4 = 4 * threadIdx.x;
+    const int nvalid = min(4, nwx - (cx0 + t4));  // window columns of this thread inside the image
     const int nrows = min(kSsimRows, nwy - cy0);
     double acc = 0.0;
-    if (v0) {
+    if (nvalid > 0) {
 #pragma unroll 1
         for (int ch = 0; ch < C; ++ch) {
-            int V0[5] = {0, 0, 0, 0, 0}, V1[5] = {0, 0, 0, 0, 0};
+            int V[4][5] = {};
             for (int r = 0; r < kWin; ++r) {
-                int a[5], b[5];
-                row_taps2<C>(xs, ys, RB, r, t2, ch, a, b);
+                int a[4][5];
+                row_taps4<C>(xs, ys, RB, r, t4, ch, a);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    V0[q] += a[q];
-                    V1[q] += b[q];
-                }
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) V[i][q] += a[i][q];
             }
-            float part_sum = 0.0f;  // at most 2 x 16 window values in [-1, 1] per channel
+            float part_sum = 0.0f;  // at most 4 x 8 window values in [-1, 1] per channel
             for (int i = 0; i < nrows; ++i) {
-                part_sum += ssim_of(V0, c1, c2);
-                if (v1) part_sum += ssim_of(V1, c1, c2);
-                if (i + 1 < nrows) {
-                    int a[5], b[5], c[5], d[5];
-                    row_taps2<C>(xs, ys, RB, i + kWin, t2, ch, a, b);
-                    row_taps2<C>(xs, ys, RB, i, t2, ch, c, d);
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) {
-                        V0[q] += a[q] - c[q];
-                        V1[q] += b[q] - d[q];
-                    }
+                for (int w = 0; w < 4; ++w)
+                    if (w < nvalid) part_sum += ssim_of(V[w], c1, c2);
+                if (i + 1 < nrows) {
+                    int a[4][5], d[4][5];
+                    row_taps4<C>(xs, ys, RB, i + kWin, t4, ch, a);
+                    row_taps4<C>(xs, ys, RB, i, t4, ch, d);
+#pragma unroll
+                    for (int w = 0; w < 4; ++w)
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) V[w][q] += a[w][q] - d[w][q];
                 }
             }
             acc += (double)part_sum;
@@ -190,7 +208,7 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const uint8_t *x, const u
     __syncthreads();
     if (threadIdx.x == 0) {
         double sum = 0.0;
-        for (int w = 0; w < kSsimThreads / 32; ++w) sum += part[w];
+        for (int w = 0; w < (NT + 31) / 32; ++w) sum += part[w];
         atomicAdd(&out[f].ssim_sum, sum);
     }
 }
@@ -266,14 +284,19 @@ int dp_pix_utility(const void *d_x, const void *d_y, int32_t M, int32_t N, int32
     const float c1 = (float)(49.0 * 49.0 * (0.01 * L) * (0.01 * L));
     const float c2 = (float)(49.0 * 48.0 * (0.03 * L) * (0.03 * L));
     const int nwy = M - kWin + 1, nwx = N - kWin + 1;
-    const dim3 grid((nwx + kSsimCols - 1) / kSsimCols, (nwy + kSsimRows - 1) / kSsimRows, n_frames);
+#define DPPIX_SSIM(CC)                                                                                            \
+    k_ssim<CC><<<dim3((nwx + SsimShape<CC>::COLS - 1) / SsimShape<CC>::COLS, (nwy + kSsimRows - 1) / kSsimRows,     \
+                      n_frames),                                                                                 \
+                 SsimShape<CC>::THREADS, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, \
+                                                 c2, d_out)
     prof_begin("k_ssim", s);
     switch (C) {
-        case 1: k_ssim<1><<<grid, kSsimThreads, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
-        case 2: k_ssim<2><<<grid, kSsimThreads, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
-        case 3: k_ssim<3><<<grid, kSsimThreads, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
-        default: k_ssim<4><<<grid, kSsimThreads, 0, s>>>(xp, yp, M, N, pitch_x, pitch_y, frame_stride_x, frame_stride_y, c1, c2, d_out); break;
+        case 1: DPPIX_SSIM(1); break;
+        case 2: DPPIX_SSIM(2); break;
+        case 3: DPPIX_SSIM(3); break;
+        default: DPPIX_SSIM(4); break;
     }
+#undef DPPIX_SSIM
     prof_end("k_ssim", s);
     k_utility_finalize<<<(n_frames + 127) / 128, 128, 0, s>>>(d_out, n_frames, M, N, C);
     e = cudaGetLastError();
