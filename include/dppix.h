@@ -58,7 +58,7 @@ extern "C" {
 /* No padding, privacy-strict edges (Alg. 1's partial cells, Sec. IV-D): a cell crossing the frame's last
  * row or column holds only its h x w samples inside the frame; its mean is S / (h w) and its noise scale
  * R m / (h w eps_r), so that a sample weighs at most R m / (h w) in it (with mirroring a sample can appear
- * twice in an edge cell).  A cell wholly outside the frame stores 0.  Mask and matte tiles are judged on
+ * twice in an edge cell).  A cell wholly outside the frame stores 0.  Mask and matte tiles are classified on
  * their pixels inside the frame.  Not with DP_PIX_SRC_VARIANCE (UNSUPPORTED); no padding limit applies. */
 #define DP_PIX_PAD_NONE 2
 

@@ -2,7 +2,7 @@
 
 Tolerance for fp32 noisy means (documented reading of the 2e-5 relative bar): the CUDA value v_g and the
 oracle's fp64 value v_o may differ by at most 2e-5 * max(|v_o|, |mu|, |eta|), i.e. relative to the largest
-operand of the final add, so cancellation cells (mu + eta near 0) are judged against the operands that
+operand of the final add, so cancellation cells (mu + eta near 0) are measured against the operands that
 produced them.  Integer results (maps, layouts, sums, u8 away from .5 ties) must match exactly.
 """
 import numpy as np

@@ -55,7 +55,7 @@ def test_edge_noise_scale_follows_valid_count():
     assert abs(np.mean(np.abs(z[edge])) - 1.0) < 0.1
 
 
-def test_mask_tiles_judged_on_valid_pixels():
+def test_mask_tiles_classified_on_valid_pixels():
     rng = np.random.default_rng(4)
     M, N, T = 50, 70, 24
     mask = (rng.random((M, N)) < 0.5).astype(np.uint8)
