@@ -46,14 +46,28 @@ __global__ void __launch_bounds__(kSobCols) k_sobel_mask(const uint8_t *frames, 
     const int x0 = blockIdx.x * kSobCols, y0 = blockIdx.y * kSobRows;
     const uint8_t *fb = frames + (int64_t)blockIdx.z * fstride;
     constexpr int W = kSobCols + 2;
-    for (int idx = threadIdx.x; idx < (kSobRows + 2) * W; idx += blockDim.x) {
-        const int r = idx / W, c = idx - r * W;
-        const int y = mirror2(y0 - 1 + r, M, pad_mode), x = mirror2(x0 - 1 + c, N, pad_mode);
-        const uint8_t *p = fb + (int64_t)y * pitch + (int64_t)x * C;
-        uint32_t s = 0;
+    // blocks whose staged rows and columns all lie inside the frame index directly (no mirroring)
+    const bool interior = x0 >= 1 && x0 - 1 + W <= N && y0 >= 1 && y0 - 1 + kSobRows + 2 <= M;
+    if (interior) {
+        const uint8_t *fb1 = fb + (int64_t)(y0 - 1) * pitch + (int64_t)(x0 - 1) * C;
+        for (int idx = threadIdx.x; idx < (kSobRows + 2) * W; idx += blockDim.x) {
+            const int r = idx / W, c = idx - r * W;
+            const uint8_t *p = fb1 + (int64_t)r * pitch + c * C;
+            uint32_t s = 0;
 #pragma unroll
-        for (int ch = 0; ch < C; ++ch) s += __ldg(p + ch);
-        I[r][c] = (uint16_t)s;
+            for (int ch = 0; ch < C; ++ch) s += __ldg(p + ch);
+            I[r][c] = (uint16_t)s;
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < (kSobRows + 2) * W; idx += blockDim.x) {
+            const int r = idx / W, c = idx - r * W;
+            const int y = mirror2(y0 - 1 + r, M, pad_mode), x = mirror2(x0 - 1 + c, N, pad_mode);
+            const uint8_t *p = fb + (int64_t)y * pitch + (int64_t)x * C;
+            uint32_t s = 0;
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) s += __ldg(p + ch);
+            I[r][c] = (uint16_t)s;
+        }
     }
     __syncthreads();
     const int c = threadIdx.x, x = x0 + c;
