@@ -6,17 +6,18 @@
 //   32 rows with the 3 x 3 window in registers: Gx, Gy from the
 //   Sobel taps in exact integers, mask = (Gx^2 + Gy^2 < tau) ? 1 : 0.
 // - k_ssim: one CTA per (frame, 8 window rows, 512 window columns; 384 for C = 4); the 14 x 518-pixel input
-//   block of both images is staged in shared memory; each thread keeps, per channel, the five exact integer
-//   window sums (Sx, Sy, Sxx, Syy, Sxy) of four adjacent columns' 7 x 7 windows (a row's ten taps loaded
-//   once, the first window summed and the others slid by a tap) and slides them down the rows
+//   block of both images is staged in shared memory as one plane per channel; each thread keeps, per channel,
+//   the five exact integer window sums (Sx, Sy, Sxx, Syy, Sxy) of four adjacent columns' 7 x 7 windows (a
+//   row's ten taps are three aligned words: the first window from dp4a, the others slid by a tap) and slides
+//   them down the rows
 //   (adding the entering row's 7 taps, subtracting the leaving one's).  The window value is evaluated from
 //   the exact sums: with D = 49 Sxx - Sx^2 (and likewise), the 1/49^2 and 1/(49*48) factors of the means,
 //   variances and covariance cancel, so SSIM = (2 Sx Sy + c1)(2 Dxy + c2) / ((Sx^2 + Sy^2 + c1)(Dx + Dy + c2))
 //   with c1 = 49^2 C1 and c2 = 49*48 C2; only that last expression is rounded (fp32).  A thread's window
 //   values of one channel (at most 32) are summed in fp32, those partial sums in fp64 per thread, block and
 //   (atomically) frame.  The exact u64 sum of squared
-//   sample differences comes from the same staged blocks, each block taking the pixels of its own window
-//   corners (the last block row and column also the image's last six rows and columns).
+//   sample differences is taken while staging, each block taking the pixels of its own window corners (the
+//   last block row and column also the image's last six rows and columns).
 // - k_utility_finalize: MSE = SSE / (M N C), SSIM = sum / ((M-6)(N-6) C).
 #include "common.cuh"
 
@@ -99,37 +100,33 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
     return v;
 }
 
-// Five exact sums (x, y, x^2, y^2, xy) of staged row r over window columns t4 .. t4 + 3 (taps t4 + i ..
-// t4 + i + 6 for column i: the first window summed, the others slid by one tap), channel ch; S[i][q].
-template <int C>
-__device__ __forceinline__ void row_taps4(const uint8_t *xs, const uint8_t *ys, int rowbytes, int r, int t4, int ch,
-                                          int (&S)[4][5]) {
-    const uint8_t *xp = xs + r * rowbytes + t4 * C + ch, *yp = ys + r * rowbytes + t4 * C + ch;
-    int a[kWin + 3], b[kWin + 3];
+// Five exact sums (x, y, x^2, y^2, xy) of one staged channel row over window columns t4 .. t4 + 3 (taps t4 + i
+// .. t4 + i + 6 for column i); S[i][q].  The row is a plane of one channel, so the ten taps are the first ten
+// bytes of three aligned words: the first window's sums are dp4a of whole words (the seventh tap's word masked
+// to three bytes), the others slide by one tap.
+__device__ __forceinline__ void row_taps4(const uint8_t *xrow, const uint8_t *yrow, int t4, int (&S)[4][5]) {
+    const uint32_t *wx = reinterpret_cast<const uint32_t *>(xrow + t4), *wy = reinterpret_cast<const uint32_t *>(yrow + t4);
+    const uint32_t x0 = wx[0], x1 = wx[1], x2 = wx[2], y0 = wy[0], y1 = wy[1], y2 = wy[2];
+    const uint32_t x1m = x1 & 0x00FFFFFFu, y1m = y1 & 0x00FFFFFFu;
+    int sx = (int)(__dp4a(x0, 0x01010101u, 0u) + __dp4a(x1m, 0x01010101u, 0u));
+    int sy = (int)(__dp4a(y0, 0x01010101u, 0u) + __dp4a(y1m, 0x01010101u, 0u));
+    int sxx = (int)(__dp4a(x0, x0, 0u) + __dp4a(x1m, x1m, 0u));
+    int syy = (int)(__dp4a(y0, y0, 0u) + __dp4a(y1m, y1m, 0u));
+    int sxy = (int)(__dp4a(x0, y0, 0u) + __dp4a(x1m, y1m, 0u));
+    S[0][0] = sx, S[0][1] = sy, S[0][2] = sxx, S[0][3] = syy, S[0][4] = sxy;
+    // leaving taps 0, 1, 2 (bytes 0-2 of word 0) and entering taps 7, 8, 9 (byte 3 of word 1, bytes 0-1 of word 2)
+    const int xo[3] = {(int)(x0 & 255u), (int)((x0 >> 8) & 255u), (int)((x0 >> 16) & 255u)};
+    const int yo[3] = {(int)(y0 & 255u), (int)((y0 >> 8) & 255u), (int)((y0 >> 16) & 255u)};
+    const int xn[3] = {(int)(x1 >> 24), (int)(x2 & 255u), (int)((x2 >> 8) & 255u)};
+    const int yn[3] = {(int)(y1 >> 24), (int)(y2 & 255u), (int)((y2 >> 8) & 255u)};
 #pragma unroll
-    for (int k = 0; k < kWin + 3; ++k) {
-        a[k] = xp[k * C];
-        b[k] = yp[k * C];
-    }
-    int sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
-#pragma unroll
-    for (int k = 0; k < kWin; ++k) {
-        sx += a[k];
-        sy += b[k];
-        sxx += a[k] * a[k];
-        syy += b[k] * b[k];
-        sxy += a[k] * b[k];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (i > 0) {
-            const int o = a[i - 1], n = a[i + kWin - 1], p = b[i - 1], m = b[i + kWin - 1];
-            sx += n - o;
-            sy += m - p;
-            sxx += n * n - o * o;
-            syy += m * m - p * p;
-            sxy += n * m - o * p;
-        }
+    for (int i = 1; i < 4; ++i) {
+        const int o = xo[i - 1], n = xn[i - 1], p = yo[i - 1], m = yn[i - 1];
+        sx += n - o;
+        sy += m - p;
+        sxx += n * n - o * o;
+        syy += m * m - p * p;
+        sxy += n * m - o * p;
         S[i][0] = sx, S[i][1] = sy, S[i][2] = sxx, S[i][3] = syy, S[i][4] = sxy;
     }
 }
@@ -153,8 +150,8 @@ __global__ void __launch_bounds__(SsimShape<C>::THREADS) k_ssim(const uint8_t *x
                                                               float c2, dp_pix_utility_t *out) {
     constexpr int COLS = SsimShape<C>::COLS, NT = SsimShape<C>::THREADS;
     constexpr int SR = kSsimRows + kWin - 1, SC = COLS + kWin - 1;
-    constexpr int RB = SC * C;  // staged bytes per row
-    __shared__ uint8_t xs[SR * RB], ys[SR * RB];
+    constexpr int SCP = (SC + 2 + 3) / 4 * 4;  // bytes per staged plane row: the last thread reads up to SC + 1
+    __shared__ __align__(16) uint8_t xs[C * SR * SCP], ys[C * SR * SCP];  // plane ch, row r at (ch SR + r) SCP
     __shared__ double part[(NT + 31) / 32];
     const int f = blockIdx.z;
     const int cy0 = blockIdx.y * kSsimRows, cx0 = blockIdx.x * COLS;  // first window (top-left corner)
@@ -163,26 +160,22 @@ __global__ void __launch_bounds__(SsimShape<C>::THREADS) k_ssim(const uint8_t *x
     const uint8_t *xb = x + (int64_t)f * fsx + (int64_t)cy0 * px + (int64_t)cx0 * C;
     const uint8_t *yb = y + (int64_t)f * fsy + (int64_t)cy0 * py + (int64_t)cx0 * C;
     const int nb = cols_in * C;
+    // staging into channel planes; the squared differences of the pixels this block owns (its window corners,
+    // extended to the image's last rows / columns in the last block row / column) are summed on the way
+    const int ro = blockIdx.y + 1 == gridDim.y ? rows_in : kSsimRows;
+    const int co = (blockIdx.x + 1 == gridDim.x ? cols_in : COLS) * C;
+    unsigned long long e = 0;
     for (int r = 0; r < rows_in; ++r)
         for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-            xs[r * RB + k] = __ldg(xb + (int64_t)r * px + k);
-            ys[r * RB + k] = __ldg(yb + (int64_t)r * py + k);
+            const int xv = __ldg(xb + (int64_t)r * px + k), yv = __ldg(yb + (int64_t)r * py + k);
+            const int pxl = k / C, ch = k - pxl * C;
+            xs[(ch * SR + r) * SCP + pxl] = (uint8_t)xv;
+            ys[(ch * SR + r) * SCP + pxl] = (uint8_t)yv;
+            if (r < ro && k < co) e += (unsigned long long)((xv - yv) * (xv - yv));
         }
+    e = warp_sum_u64(e);
+    if ((threadIdx.x & 31) == 0 && e) atomicAdd(reinterpret_cast<unsigned long long *>(&out[f].sse), e);
     __syncthreads();
-    // squared differences of the pixels this block owns: its window corners, extended to the image's last
-    // rows / columns in the last block row / column (all of them staged)
-    {
-        const int ro = blockIdx.y + 1 == gridDim.y ? rows_in : kSsimRows;
-        const int co = (blockIdx.x + 1 == gridDim.x ? cols_in : COLS) * C;
-        unsigned long long e = 0;
-        for (int r = 0; r < ro; ++r)
-            for (int k = threadIdx.x; k < co; k += blockDim.x) {
-                const int d = (int)xs[r * RB + k] - (int)ys[r * RB + k];
-                e += (unsigned long long)(d * d);
-            }
-        e = warp_sum_u64(e);
-        if ((threadIdx.x & 31) == 0 && e) atomicAdd(reinterpret_cast<unsigned long long *>(&out[f].sse), e);
-    }
     const int t4 = 4 * threadIdx.x;
     const int nvalid = min(4, nwx - (cx0 + t4));  // window columns of this thread inside the image
     const int nrows = min(kSsimRows, nwy - cy0);
@@ -193,7 +186,7 @@ __global__ void __launch_bounds__(SsimShape<C>::THREADS) k_ssim(const uint8_t *x
             int V[4][5] = {};
             for (int r = 0; r < kWin; ++r) {
                 int a[4][5];
-                row_taps4<C>(xs, ys, RB, r, t4, ch, a);
+                row_taps4(xs + (ch * SR + r) * SCP, ys + (ch * SR + r) * SCP, t4, a);
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -206,8 +199,8 @@ __global__ void __launch_bounds__(SsimShape<C>::THREADS) k_ssim(const uint8_t *x
                     if (w < nvalid) part_sum += ssim_of(V[w], c1, c2);
                 if (i + 1 < nrows) {
                     int a[4][5], d[4][5];
-                    row_taps4<C>(xs, ys, RB, i + kWin, t4, ch, a);
-                    row_taps4<C>(xs, ys, RB, i, t4, ch, d);
+                    row_taps4(xs + (ch * SR + i + kWin) * SCP, ys + (ch * SR + i + kWin) * SCP, t4, a);
+                    row_taps4(xs + (ch * SR + i) * SCP, ys + (ch * SR + i) * SCP, t4, d);
 #pragma unroll
                     for (int w = 0; w < 4; ++w)
 #pragma unroll
