@@ -43,7 +43,7 @@ def test_philox4x64_matches_numpy():
 
 
 def test_philox4x32_uniform_and_balanced():
-    # 4x32 shares the round/key-schedule macro pinned above; its own constants are checked statistically.
+    # 4x32 shares the round/key-schedule macro pinned above; its constants are pinned by the known-answer test below.
     words = []
     for i in range(30000):
         words.extend(O.philox4x32_10([i, 7, 3, 0], [0x12345678, 0x9ABCDEF0]))
@@ -57,6 +57,23 @@ def test_philox4x32_uniform_and_balanced():
     assert not np.array_equal(a, O.philox4x32_10([1, 0, 0, 0], [0, 0]))
     assert not np.array_equal(a, O.philox4x32_10([0, 0, 0, 0], [1, 0]))
     assert not np.array_equal(a, O.philox4x32_10([0, 0, 0, 1], [0, 0]))
+
+
+def test_philox4x32_known_answer_vectors():
+    """Philox4x32-10's multipliers (0xD2511F53, 0xCD9E8D57) and Weyl constants (0x9E3779B9, 0xBB67AE85)
+    are pinned by the published known-answer vectors of the generator (Salmon, Moraes, Dror, Shaw,
+    "Parallel random numbers: as easy as 1, 2, 3", SC'11; the Random123 distribution's kat_vectors file,
+    rows "philox4x32 10"): counter and key all zero, all ones, and the row built from the hex digits of pi.
+    A single mistyped constant changes every output word of every row."""
+    rows = [
+        ([0, 0, 0, 0], [0, 0], [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
+        ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2, [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
+        ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0],
+         [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
+    ]
+    for ctr, key, exp in rows:
+        got = O.philox4x32_10(ctr, key)
+        assert [int(w) for w in got] == exp, (ctr, key, ["%08x" % int(w) for w in got])
 
 
 # ------------------------------------------------------------------------------------------------------
@@ -351,6 +368,41 @@ def test_record_size_formula_and_layout():
         assert info["M"] == M and info["N"] == N and info["T"] == T and info["b"] == grids
         assert info["seed"] == 9 and info["frame_idx"] == 3 and info["stream_id"] == 2
         assert np.array_equal(O.record_map(rec), O.classify(img, mask, grids=grids, eps=eps, source=O.SRC_MASK))
+
+
+def test_u8_record_rounds_f32_mean_half_to_even():
+    """The u8 record (the paper stores uint8 noisy means, Sec. VII-A) holds the f32 mean rounded half to
+    even (numpy rint), neither truncated (numpy astype) nor rounded from the fp64 value."""
+    # noise-free, b = 2: a cell's mean is its sample sum / 4; sums 4k + 2 put it exactly on k + 1/2
+    M, N = 8, 16
+    ks = np.arange(M // 2 * N // 2) % 254
+    img = np.zeros((M, N, 1), dtype=np.uint8)
+    for i, k in enumerate(ks):
+        cy, cx = divmod(i, N // 2)
+        # samples k, k, k+1, k+1 sum to 4k + 2
+        img[2 * cy:2 * cy + 2, 2 * cx:2 * cx + 2, 0] = [[k, k + 1], [k + 1, k]]
+    labels = np.zeros((M // 2, N // 2), dtype=np.uint8)
+    rec, means, _, _ = O.release(img, labels, grids=[2], eps=[1.0], source=O.SRC_TILE_LABELS, dtype=O.DT_U8,
+                                 noise_free=True)
+    assert np.array_equal(means, ks + 0.5)
+    got = O.record_payload(rec)
+    assert np.array_equal(got, np.rint(np.float32(means)))
+    assert np.array_equal(got[ks % 2 == 0], ks[ks % 2 == 0])          # k + 1/2 -> k for even k
+    assert np.array_equal(got[ks % 2 == 1], ks[ks % 2 == 1] + 1)      # k + 1/2 -> k + 1 for odd k
+    # noisy release: the u8 payload is rint of the f32 payload of the same release, value by value
+    rng = np.random.default_rng(12)
+    img = rng.integers(0, 256, size=(70, 90, 3), dtype=np.uint8)
+    mask = rng.integers(0, 2, size=(70, 90), dtype=np.uint8)
+    kw = dict(grids=[24, 8], eps=[1.0, 0.5], source=O.SRC_MASK, seed=5, frame_idx=2)
+    rec32, means32, _, _ = O.release(img, mask, dtype=O.DT_F32, **kw)
+    rec8, means8, _, _ = O.release(img, mask, dtype=O.DT_U8, **kw)
+    assert np.array_equal(means32, means8)
+    f32 = O.record_payload(rec32)
+    assert np.array_equal(f32, np.float32(means32).astype(np.float64))
+    u8 = O.record_payload(rec8)
+    assert np.array_equal(u8, np.rint(np.float32(means32)))
+    frac = np.float32(means32) - np.floor(np.float32(means32))
+    assert np.any(frac > 0.5) and np.any((frac > 0) & (frac < 0.5))   # both rounding directions occur
 
 
 def test_reconstruct_broadcasts_record_values():
