@@ -11,8 +11,9 @@ dp_pix_reconstruct).  Inputs (398 MB per step) are larger than the 126 MB L2.
 
 Prints one JSON line.  `value` is whole-job Mpx/s (frames * M * N over all ranks / max-over-ranks time) with
 inputs resident in HBM; `e2e` is the same metric through the C ABI with host buffers (pinned host -> device
-copy of the frames, release, reconstruct, device -> host copy of the records, every step).  The reference
-arm is the CPU oracle (a deliberately plain program) on a bounded sample of the same workload.
+copy of the frames, release, reconstruct, device -> host copy of the pixelized frames and the records, every
+step).  The reference arm and `cpu_baseline` are the CPU oracle (a deliberately plain program) over the
+host's cores on a bounded sample of the same workload.
 """
 import argparse
 import json
@@ -212,20 +213,38 @@ def max_over_ranks(x, world):
 # algorithmic bytes per launch of each kernel on this workload
 # ------------------------------------------------------------------------------------------------------
 def algorithmic_bytes(plan, payload_bytes):
+    """The method's bytes per launch of each kernel (Sec. VI-F: frames in, records and pixelized frames out):
+    what any implementation of that kernel's share of the step must move.  The g-cell sums and rank keys that
+    the statistics pass hands to the fused kernel are an intermediate of this design, not the method's work;
+    they are counted in moved_bytes only."""
+    frame_bytes = F * M * N * C
+    ntiles = plan.GR * plan.GC
+    return {
+        # frames read once (the classification statistics and every cell sum come from this read)
+        "k_tile_stats_gsum": frame_bytes,
+        # record payload written
+        "k_emit": payload_bytes,
+        # frames written; record payload and maps read
+        "k_reconstruct_u8": frame_bytes + payload_bytes + F * ntiles,
+        # fused: record payload and pixelized frames written
+        "k_emit_recon_u8": frame_bytes + payload_bytes,
+        # map, offsets, index and header written
+        "k_rank": F * ntiles + F * (512 + plan.GR * 16),
+    }
+
+
+def moved_bytes(plan, payload_bytes):
+    """Bytes each kernel of this design moves per launch, intermediates included (g = 4 cell sums as u16 and
+    one u64 rank key per tile, u32 payload offsets)."""
     frame_bytes = F * M * N * C
     ntiles = plan.GR * plan.GC
     g = 4
     gsum_tile = ((plan.T // g) ** 2 * C + 7) // 8 * 8 * 2
     return {
-        # frames read once; g-cell sums and rank keys written
         "k_tile_stats_gsum": frame_bytes + F * ntiles * (gsum_tile + 8),
-        # g-cell sums and offsets read; record payload written
         "k_emit": F * ntiles * (gsum_tile + 4 + 1) + payload_bytes,
-        # frames written; record payload and maps read
         "k_reconstruct_u8": frame_bytes + payload_bytes + F * ntiles,
-        # fused: g-cell sums, offsets and map read; record payload and frames written
         "k_emit_recon_u8": frame_bytes + F * ntiles * (gsum_tile + 4 + 1) + payload_bytes,
-        # keys read; map, offsets, index and header written
         "k_rank": F * ntiles * (8 + 1 + 4) + F * (512 + plan.GR * 16),
     }
 
@@ -258,9 +277,18 @@ def traffic_from_profile(kernel, workload=None):
 # ------------------------------------------------------------------------------------------------------
 # the CPU oracle on a bounded sample (reference arm and cpu_baseline)
 # ------------------------------------------------------------------------------------------------------
-def oracle_time(clip, n_frames, budget_s=None):
+ORACLE_KW = None
+
+
+def _oracle_kw():
     import oracle as O
-    kw = dict(M=M, N=N, C=C, grids=GRIDS, eps=EPS, source=O.SRC_VARIANCE, dtype=O.DT_F32, seed=SEED, m=MVAR)
+    return dict(M=M, N=N, C=C, grids=GRIDS, eps=EPS, source=O.SRC_VARIANCE, dtype=O.DT_F32, seed=SEED, m=MVAR)
+
+
+def oracle_time(clip, n_frames, budget_s=None):
+    """The oracle on one host thread: release + reconstruction of up to n_frames frames."""
+    import oracle as O
+    kw = _oracle_kw()
     t0 = time.perf_counter()
     done = 0
     for i in range(n_frames):
@@ -273,27 +301,105 @@ def oracle_time(clip, n_frames, budget_s=None):
     return done, dt
 
 
+_POOL_STATE = {}
+
+
+def _pool_init(shm_name, shape):
+    from multiprocessing import shared_memory
+    import oracle as O
+    shm = shared_memory.SharedMemory(name=shm_name)
+    _POOL_STATE["shm"] = shm
+    _POOL_STATE["clip"] = np.ndarray(shape, dtype=np.uint8, buffer=shm.buf)
+    _POOL_STATE["kw"] = _oracle_kw()
+    O.oracle.lib()
+
+
+def _pool_frame(job):
+    import oracle as O
+    i, frame_idx = job
+    rec, *_ = O.release(_POOL_STATE["clip"][i], None, frame_idx=frame_idx, **_POOL_STATE["kw"])
+    O.reconstruct(rec, 0)
+    return 1
+
+
+class OraclePool:
+    """The oracle, unchanged, over every host core this process may use: one spawned worker process per core
+    (spawned, so no worker inherits a CUDA context), the clip shared with them through shared memory, one
+    frame per task."""
+
+    def __init__(self, clip):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        import oracle as O
+        O.oracle.lib()  # built once here, before the workers load it
+        self.cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        self.n = len(clip)
+        self.shm = shared_memory.SharedMemory(create=True, size=clip.nbytes)
+        np.ndarray(clip.shape, dtype=np.uint8, buffer=self.shm.buf)[:] = clip
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_pool_init,
+                                                 initargs=(self.shm.name, clip.shape))
+        self.pool.map(_pool_frame, [(i % self.n, i) for i in range(self.cores)])  # workers up and warm
+
+    def run(self, n_frames, frame_idx0=0):
+        """Seconds for n_frames frames (release + reconstruction each) over all workers."""
+        t0 = time.perf_counter()
+        done = sum(self.pool.map(_pool_frame, [(i % self.n, frame_idx0 + i) for i in range(n_frames)], chunksize=1))
+        return done, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        self.shm.close()
+        self.shm.unlink()
+
+
+def cpu_baseline_clip(clip, budget_s):
+    """The oracle timed on this host on a bounded sample of the clip: all cores (the value), one thread beside
+    it."""
+    pool = OraclePool(clip)
+    try:
+        n = max(pool.cores, F)
+        t_start = time.perf_counter()
+        done, dt = 0, 0.0
+        while time.perf_counter() - t_start < budget_s / 2 or done == 0:
+            d, t = pool.run(n, frame_idx0=done)
+            done, dt = done + d, dt + t
+    finally:
+        pool.close()
+    one, dt1 = oracle_time(clip, F, budget_s=budget_s / 2)
+    return {"value": done * M * N / 1e6 / dt, "unit": "Mpx/s", "cores": pool.cores, "kind": "oracle",
+            "sample": "%d frames of the clip over %d worker processes (oracle release + reconstruct, %.1f s); "
+                      "one thread: %d frames in %.1f s" % (done, pool.cores, dt, one, dt1),
+            "single_thread": {"value": one * M * N / 1e6 / dt1, "unit": "Mpx/s", "cores": 1}}
+
+
 def run_reference(args):
     world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
         return 0
     from paper_2511_04261_b300 import synth
-    per_step = 2
-    clip = synth.moving_rect_clip(seed=1002, frames=per_step, M=M, N=N)
-    for _ in range(args.warmup):
-        oracle_time(clip, per_step)
-    times = []
-    for _ in range(args.steps):
-        _, dt = oracle_time(clip, per_step)
-        times.append(dt)
+    clip = synth.moving_rect_clip(seed=1002, frames=F, M=M, N=N)
+    pool = OraclePool(clip)
+    per_step = min(F, max(2, pool.cores))
+    try:
+        for w in range(args.warmup):
+            pool.run(per_step, frame_idx0=w * per_step)
+        times = []
+        for k in range(args.steps):
+            _, dt = pool.run(per_step, frame_idx0=(args.warmup + k) * per_step)
+            times.append(dt)
+    finally:
+        pool.close()
     ms = 1e3 * sum(times) / len(times)
     value = per_step * M * N / 1e6 / (ms / 1e3)
-    sample = "%d of the %d frames per step (oracle release + reconstruct, 1 thread)" % (per_step, F)
+    sample = ("%d of the %d frames per step (oracle release + reconstruct over %d worker processes, one frame "
+              "each)" % (per_step, F, pool.cores))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": config({"reference": "CPU oracle (plain C, fp64), not a GPU program"}),
-            "cpu_baseline": {"value": value, "unit": "Mpx/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "Mpx/s", "cores": pool.cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "Mpx/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -340,8 +446,6 @@ def run_ours(args):
     sampler = ClockSampler(torch.cuda.current_device())
     barrier(world)
     torch.cuda.synchronize()
-    P.prof_reset()
-    P.prof_enable(True)
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -351,21 +455,30 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
+    P.dp_pix_status()
+    ms = e0.elapsed_time(e1) / args.steps
+    # per-kernel launch durations from a separate pass of the same steps with the library's events around
+    # each launch (kept out of the timed region above)
+    P.prof_reset()
+    P.prof_enable(True)
+    for k in range(args.steps):
+        step(frames, (args.warmup + args.steps + k) * F)
+    torch.cuda.synchronize()
     prof = P.prof_read()
     P.prof_enable(False)
     P.dp_pix_status()
-    ms = e0.elapsed_time(e1) / args.steps
+    launches = sum(v[0] for v in prof.values())  # the profiled pass runs as many steps as the timed region
     args.tuning = {"fused_px": plan.tuning(P.TUNE_FUSED_PX), "fused_threads": plan.tuning(P.TUNE_FUSED_THREADS),
                    "split": plan.tuning(P.TUNE_SPLIT)}
     ms_max = max_over_ranks(ms, world)
     value = whole_job_mpx_per_s(world, ms_max)
-    launches = sum(v[0] for v in prof.values())
 
     # ---- roofline of the dominant kernel (its own launch durations, from events on its stream) ----
     hbm, peak_kind = measured_peaks()
     hdrs = [P.record_header(P.dp_pix_store(records[i])) for i in range(F)]
     payload = sum(h["total_bytes"] - h["payload_offset"] for h in hdrs)
     algo = algorithmic_bytes(plan, payload)
+    moved = moved_bytes(plan, payload)
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     dom_name, (dom_launches, dom_ms) = dom[0], dom[1]
     per_launch_ms = dom_ms / max(1, dom_launches)
@@ -374,10 +487,21 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "traffic": traffic_from_profile(dom_name),
                 "algorithmic_bytes_per_launch": ab, "avg_launch_ms": per_launch_ms,
+                "moved_bytes_per_launch": moved.get(dom_name),
+                "moved_GBps": moved[dom_name] / (per_launch_ms / 1e3) / 1e9 if dom_name in moved else None,
+                "step_method_bytes": algo["k_tile_stats_gsum"] + algo["k_emit_recon_u8"],
+                "step_frac": (algo["k_tile_stats_gsum"] + algo["k_emit_recon_u8"]) / (ms_max / 1e3) / 1e9 / hbm,
+                "bytes_note": "achieved counts the method's bytes (payload and pixelized frames written); "
+                              "moved_bytes adds the g-cell sums and offsets read from the statistics pass; "
+                              "step_frac is the step's method bytes (frames read, records and frames written) "
+                              "over the step time",
+                "timing": "per-kernel durations from a separate profiled pass of %d steps; the timed region "
+                          "ran without library events" % args.steps,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else
                 "fallback 6.4 TB/s",
                 "kernels": {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / max(1e-9, sum(x[1] for x in prof.values())),
-                                "algorithmic_GBps": (algo[k] / (v[1] / max(1, v[0]) / 1e3) / 1e9) if k in algo and v[1] > 0 else None}
+                                "algorithmic_GBps": (algo[k] / (v[1] / max(1, v[0]) / 1e3) / 1e9) if k in algo and v[1] > 0 else None,
+                                "moved_GBps": (moved[k] / (v[1] / max(1, v[0]) / 1e3) / 1e9) if k in moved and v[1] > 0 else None}
                             for k, v in prof.items()}}
 
     # ---- single-frame latency (release + reconstruct of one device-resident frame) ----
@@ -438,22 +562,23 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, P, torch, plan, clip, frames, records, step, world)
+        e2e["records_only"] = run_e2e(args, P, torch, plan, clip, frames, records, step, world, frames_out=False)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        done, dt = oracle_time(clip, F, budget_s=args.cpu_budget)
-        cpu = {"value": done * M * N / 1e6 / dt, "unit": "Mpx/s", "cores": 1, "kind": "oracle",
-               "sample": "%d frames of the clip (oracle release + reconstruct, 1 thread, %.1f s)" % (done, dt)}
+        cpu = cpu_baseline_clip(clip, args.cpu_budget)
     return finish(args, rank, world, value, ms_max, roofline, cpu, e2e, clocks, launches, latency)
 
 
-def run_e2e(args, P, torch, plan, clip, frames, records, step, world):
+def run_e2e(args, P, torch, plan, clip, frames, records, step, world, frames_out=True):
     """End to end through the public calls with host buffers: every step copies its 64 pinned host frames in,
-    releases and reconstructs them, and copies the records out (dp_pix_store_batch).  Steps are pipelined on
-    three streams with two device buffer sets, as a streaming user would run them: step k+1's copy-in and
-    release overlap step k's copy-out (the host blocks in dp_pix_store_batch of step k meanwhile)."""
+    releases and reconstructs them, and copies both outputs out: the pixelized frames (into pinned host
+    memory) and the records (dp_pix_store_batch); frames_out=False copies the records only.  Steps are
+    pipelined on three streams with two device buffer sets, as a streaming user would run them: step k+1's
+    copy-in and release overlap step k's copy-out (the host blocks in dp_pix_store_batch of step k meanwhile)."""
     rank = int(os.environ.get("RANK", "0"))
     host_frames = torch.from_numpy(clip).pin_memory()
     host_recs = [torch.empty((F, plan.record_stride()), dtype=torch.uint8).pin_memory() for _ in range(2)]
+    host_out = [torch.empty((F, M, N, C), dtype=torch.uint8).pin_memory() for _ in range(2)] if frames_out else None
     dev = frames.device
     fbuf = [frames, torch.empty_like(frames)]
     rbuf = [records, plan.alloc_records(F, device=dev)]
@@ -482,7 +607,10 @@ def run_e2e(args, P, torch, plan, clip, frames, records, step, world):
     def collect(k):
         b = k % 2
         s_out.wait_event(done[b])
-        return P.dp_pix_store_batch(rbuf[b], host_recs[b], stream=s_out)
+        if frames_out:
+            with torch.cuda.stream(s_out):
+                host_out[b].copy_(obuf[b], non_blocking=True)
+        return P.dp_pix_store_batch(rbuf[b], host_recs[b], stream=s_out)  # returns once s_out has drained
 
     launch(0)
     collect(0)
@@ -497,11 +625,16 @@ def run_e2e(args, P, torch, plan, clip, frames, records, step, world):
         written = collect(k)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / e2e_steps, world)
+    if frames_out:
+        # the pixelized frames that came back are the ones the device computed
+        assert torch.equal(host_out[e2e_steps % 2][:2], obuf[e2e_steps % 2][:2].cpu())
     return {"value": world * F * M * N / 1e6 / (e2e_ms / 1e3), "unit": "Mpx/s", "ms_per_step": e2e_ms,
-            "h2d_bytes_per_step": F * M * N * C, "d2h_bytes_per_step": int(sum(written)) + F * 512,
-            "path": "pinned host frames -> device copy, %s, dp_pix_store_batch; steps pipelined on three streams with "
-                    "two device buffer sets" % ("dp_pix_release_reconstruct" if args.path == "fused" else
-                                                "dp_pix_release, dp_pix_reconstruct")}
+            "h2d_bytes_per_step": F * M * N * C,
+            "d2h_bytes_per_step": int(sum(written)) + F * 512 + (F * M * N * C if frames_out else 0),
+            "path": "pinned host frames -> device copy, %s, %sdp_pix_store_batch; steps pipelined on three streams "
+                    "with two device buffer sets" % ("dp_pix_release_reconstruct" if args.path == "fused" else
+                                                     "dp_pix_release, dp_pix_reconstruct",
+                                                     "pixelized frames -> pinned host copy, " if frames_out else "")}
 
 
 def finish(args, rank, world, value, ms_max, roofline, cpu, e2e, clocks, launches, latency):

@@ -116,6 +116,8 @@ uint64_t plan_ws_per_frame(const dp_pix_plan_s *plan) { return plan ? plan->g.ws
 
 int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
+void clear_last_error() { t_err[0] = 0; }
+
 // Blocks of `kernel` resident per SM at `threads` threads and `smem` dynamic bytes, on the current device.
 // The first call for a kernel on a device also raises its dynamic shared-memory limit to the device's opt-in
 // maximum, so launches never need to set it again; results are cached (these queries cost microseconds of
@@ -163,9 +165,11 @@ cudaStream_t *side_streams(int n) {
 }
 
 int32_t *status_word() {
+    static std::mutex mu;
     static int32_t *cached[64] = {nullptr};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);  // host threads making their first call on a device at once
     if (!cached[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_dppix_status) != cudaSuccess) return nullptr;

@@ -287,6 +287,7 @@ struct dp_pix_plan_s;
 namespace dppix {
 uint64_t plan_ws_per_frame(const dp_pix_plan_s *plan);  // workspace bytes per frame of a plan (0 for NULL)
 int set_last_error(int code, const char *msg);          // sets this thread's dp_pix_last_error(), returns code
+void clear_last_error();                               // empties this thread's dp_pix_last_error()
 int plan_geometry(const dp_pix_desc *d, Geom &g);       // dp_pix_plan's validation and geometry (host)
 void set_release_units(Geom &g);                        // release work units for the plan's segment width
 int cuda_device_ok();                                   // DP_PIX_OK, or DP_PIX_E_CUDA with the message set

@@ -53,6 +53,7 @@ extern "C" DPPIX_API int dp_pix_release_noalloc(dp_pix_plan_t plan, const void *
                                                 uint32_t n_frames, uint32_t stream_id, uint64_t frame_idx0,
                                                 void *d_records, int64_t record_stride, void *cuda_stream) {
     using namespace dppix;
+    clear_last_error();
     if (!plan) return set_last_error(DP_PIX_E_INVALID_ARG, "dp_pix_release_noalloc: plan is NULL");
     if (n_frames == 0) return DP_PIX_OK;
     const uint64_t need = (uint64_t)n_frames * plan_ws_per_frame(plan);
