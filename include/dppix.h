@@ -228,6 +228,19 @@ DPPIX_API int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frame
                                          int64_t record_stride, void *d_out, int64_t out_frame_stride, int64_t out_pitch,
                                          int out_type, void *d_ws, uint64_t ws_bytes, void *cuda_stream);
 
+/*
+ * dp_pix_release_reconstruct with a noise key per frame (as dp_pix_release_keyed): frame i is released
+ * with d_keys[i] and its image rebuilt from that record.  Records and images are byte-identical to
+ * dp_pix_release_reconstruct of each frame alone with its (stream_id, frame_idx).  Other arguments and
+ * errors: as dp_pix_release_reconstruct; INVALID_ARG when d_keys is NULL.
+ */
+DPPIX_API int dp_pix_release_reconstruct_keyed(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
+                                               const void *d_region_src, int64_t src_pitch, int64_t src_frame_stride,
+                                               uint32_t n_frames, const dp_pix_frame_key *d_keys, void *d_records,
+                                               int64_t record_stride, void *d_out, int64_t out_frame_stride,
+                                               int64_t out_pitch, int out_type, void *d_ws, uint64_t ws_bytes,
+                                               void *cuda_stream);
+
 /* ---- ragged batches (no counterpart in the paper, which releases one frame at a time) ----------------- */
 /* Many images of different sizes released with one set of region parameters.  Each image is released
  * exactly as dp_pix_release would release it alone with a plan for its size (same record bytes, same noise:
@@ -280,60 +293,78 @@ DPPIX_API int dp_pix_batch_autotune(dp_pix_batch_t b, const dp_pix_batch_image *
 DPPIX_API int dp_pix_batch_tuning(dp_pix_batch_t b, int *seg_tiles);
 
 /* ---- serving loop (no counterpart in the paper; its deployment motivation is many cameras) --------------- */
-/* A request loop for frames arriving from many cameras.  Frames are copied from host memory into device
- * slots carved out of one caller-owned arena (the memory budget: a request is admitted when a slot of its
- * camera's resolution is free), released in batches -- all admitted frames of one resolution in one keyed
- * launch -- and their records copied back to host memory; up to n_streams batches are in flight at once, so
- * requests that arrive while others are on the GPU join the next batch and its copies and kernels overlap
- * the running ones.  Frame f of camera c is released with stream_id c and frame_idx f (its arrival rank at
- * that camera), so each record is byte-identical to dp_pix_release of that frame alone.  A worker thread
- * owned by the server issues every CUDA call after creation.  Region source: VARIANCE (no per-frame side
+/* A request loop for frames arriving from many cameras.  Requests are queued from host memory by any
+ * thread; a worker thread owned by the server issues every CUDA call after creation.  Up to n_streams
+ * batches are in flight at once: whenever one is free, the worker admits the queued requests, oldest first,
+ * that the free part of the caller's arena holds (the memory budget), copies their frames in, releases all
+ * frames of one resolution in one keyed launch (with the reconstruction when a request asks for it), and
+ * copies the records (and images) back -- so requests that arrive while others are on the GPU join the
+ * next batch, and its copies and kernels overlap the running ones.
+ * Noise keys: frame f of camera c is released with stream_id c and frame_idx f, where f counts the
+ * camera's frames in submission order, starting from first_frame[c].  The counters live in device memory
+ * and are advanced on the device as batches are formed; each record is byte-identical to dp_pix_release
+ * of its frame alone with that key.  dp_pix_server_counters reads the counters back: creating the next
+ * server with them continues every camera's count, so a restarted server never draws one key twice (the
+ * parallel composition of Thm 1 needs independent noise).  Region source: VARIANCE (no per-frame side
  * input); other sources are UNSUPPORTED here. */
 typedef struct dp_pix_server_s *dp_pix_server_t;
 
 typedef struct dp_pix_server_result {
     uint64_t ticket;
-    uint64_t frame_idx;           /* arrival rank of the frame at its camera */
+    uint64_t frame_idx;           /* the frame's key index (from its record's header) */
     uint64_t record_bytes;        /* header.total_bytes of the record now in the request's host buffer */
     uint32_t camera;
     int32_t status;               /* DP_PIX_OK or a DP_PIX_E_* code of the batch that carried the frame */
     double queue_us;              /* submit -> admitted into a batch */
-    double latency_us;            /* submit -> record in host memory */
+    double latency_us;            /* submit -> results in host memory */
 } dp_pix_server_result;
 
 typedef struct dp_pix_server_stats {
     uint64_t submitted, completed, batches, launches;
     uint64_t frames_in_flight_max;  /* most frames on the device at once */
     double mean_batch_frames;
+    uint64_t arena_bytes_in_use_max; /* most arena bytes held by batches at once */
+    uint64_t arena_heap_bytes;       /* arena bytes available to batches (the arena minus counters and keys) */
 } dp_pix_server_stats;
 
-/* Device bytes one frame slot of camera c needs (frame + record + workspace + key), for sizing the arena, and
- * the host record capacity every request of camera c must provide.  Host only. */
+/* Device bytes one admitted frame of an M x N camera holds while its batch runs (frame + record +
+ * workspace), the host record capacity every request of that camera must provide, and the bytes a
+ * reconstruction adds.  Any pointer may be NULL.  Host only. */
 DPPIX_API int dp_pix_server_sizes(const dp_pix_desc *common, int32_t M, int32_t N, uint64_t *slot_bytes,
-                                  uint64_t *record_bytes);
+                                  uint64_t *record_bytes, uint64_t *recon_bytes);
 
 /* Creates a server for n_cameras cameras of M[c] x N[c] (common: the region parameters as for dp_pix_plan;
- * M, N, row_pitch ignored).  d_arena: arena_bytes of device memory, 256-byte aligned, owned by the caller
- * and untouched by anyone else until dp_pix_server_destroy returns; it is split among the resolutions in
- * proportion to their cameras' frame bytes.  n_streams: batches in flight (1..8).  Errors: as dp_pix_plan,
- * UNSUPPORTED (source), BUFFER_TOO_SMALL (no slot for some resolution), CUDA. */
+ * M, N, row_pitch ignored).  first_frame: n_cameras starting frame indices (the values dp_pix_server_counters
+ * returned for an earlier server with the same seed), or NULL for 0.  d_arena: arena_bytes of device memory,
+ * 256-byte aligned, owned by the caller and untouched by anyone else until dp_pix_server_destroy returns.
+ * Its first bytes hold the counters (8 per camera) and the key tables (4 KiB per stream); the rest is handed
+ * to batches.  n_streams: batches in flight (1..8).  Synchronizes the calling thread with the counter upload.
+ * Errors: as dp_pix_plan, UNSUPPORTED (source), BUFFER_TOO_SMALL (no room for one frame of the largest
+ * resolution with its reconstruction), CUDA. */
 DPPIX_API int dp_pix_server_create(const dp_pix_desc *common, const int32_t *M, const int32_t *N, uint32_t n_cameras,
-                                   uint32_t n_streams, void *d_arena, uint64_t arena_bytes, dp_pix_server_t *out);
+                                   const uint64_t *first_frame, uint32_t n_streams, void *d_arena,
+                                   uint64_t arena_bytes, dp_pix_server_t *out);
 
 /* Queues frame `host_frame` (M*N*C bytes, rows dense; pinned memory copies asynchronously) of `camera`; its
- * record will be written to host_record (record_cap >= dp_pix_server_sizes' record_bytes).  Both buffers
- * must stay valid until the request's result has been returned by dp_pix_server_wait.  *ticket identifies
- * the request.  Thread-safe.  Errors: INVALID_ARG (camera, buffer), BUFFER_TOO_SMALL (record_cap). */
+ * record will be written to host_record (record_cap >= dp_pix_server_sizes' record_bytes) and, when
+ * host_out is not NULL, its pixelized image (M*N*C u8, rows dense) to host_out.  Every buffer must stay
+ * valid until dp_pix_server_wait has returned the request's result.  *ticket identifies the request.
+ * Thread-safe; a camera's frames take consecutive indices in the order their submit calls return.
+ * Errors: INVALID_ARG (camera, buffer), BUFFER_TOO_SMALL (record_cap). */
 DPPIX_API int dp_pix_server_submit(dp_pix_server_t s, uint32_t camera, const void *host_frame, void *host_record,
-                                   uint64_t record_cap, uint64_t *ticket);
+                                   uint64_t record_cap, void *host_out, uint64_t *ticket);
 
 /* Waits up to timeout_ms (< 0: forever; 0: poll) for request `ticket` and fills *res once (the result is then
  * forgotten).  Returns DP_PIX_OK, DP_PIX_E_TIMEOUT (not done yet), or INVALID_ARG (unknown ticket).
  * Thread-safe. */
 DPPIX_API int dp_pix_server_wait(dp_pix_server_t s, uint64_t ticket, int timeout_ms, dp_pix_server_result *res);
 
+/* Waits until every submitted request has been released, then copies the first n cameras' next frame
+ * indices (device counters) to next_frame (host, n entries).  Requests submitted by other threads during
+ * the call may or may not be counted.  Errors: INVALID_ARG (n > cameras, NULL), CUDA. */
+DPPIX_API int dp_pix_server_counters(dp_pix_server_t s, uint64_t *next_frame, uint32_t n);
+
 DPPIX_API int dp_pix_server_stats_get(dp_pix_server_t s, dp_pix_server_stats *st);
-DPPIX_API int dp_pix_server_slots(dp_pix_server_t s, uint32_t camera, uint32_t *slots);
 
 /* Finishes the queued requests, stops the worker and frees the server's host state (the arena is the
  * caller's).  NULL is allowed. */

@@ -54,7 +54,8 @@ class ServerResult(ct.Structure):
 
 class ServerStats(ct.Structure):
     _fields_ = [("submitted", ct.c_uint64), ("completed", ct.c_uint64), ("batches", ct.c_uint64),
-                ("launches", ct.c_uint64), ("frames_in_flight_max", ct.c_uint64), ("mean_batch_frames", ct.c_double)]
+                ("launches", ct.c_uint64), ("frames_in_flight_max", ct.c_uint64), ("mean_batch_frames", ct.c_double),
+                ("arena_bytes_in_use_max", ct.c_uint64), ("arena_heap_bytes", ct.c_uint64)]
 
 
 class Desc(ct.Structure):
@@ -121,13 +122,15 @@ def lib():
     L.dp_pix_batch_autotune.argtypes = [P, ct.POINTER(BatchImage), ct.c_int, P]
     L.dp_pix_batch_tuning.argtypes = [P, ct.POINTER(ct.c_int)]
     L.dp_pix_release_keyed.argtypes = [P, P, I64, P, I64, I64, U32, P, P, I64, P, U64, P]
-    L.dp_pix_server_sizes.argtypes = [ct.POINTER(Desc), I32, I32, ct.POINTER(U64), ct.POINTER(U64)]
-    L.dp_pix_server_create.argtypes = [ct.POINTER(Desc), ct.POINTER(I32), ct.POINTER(I32), U32, U32, P, U64,
+    L.dp_pix_release_reconstruct_keyed.argtypes = [P, P, I64, P, I64, I64, U32, P, P, I64, P, I64, I64, ct.c_int,
+                                                   P, U64, P]
+    L.dp_pix_server_sizes.argtypes = [ct.POINTER(Desc), I32, I32, ct.POINTER(U64), ct.POINTER(U64), ct.POINTER(U64)]
+    L.dp_pix_server_create.argtypes = [ct.POINTER(Desc), ct.POINTER(I32), ct.POINTER(I32), U32, P, U32, P, U64,
                                        ct.POINTER(P)]
-    L.dp_pix_server_submit.argtypes = [P, U32, P, P, U64, ct.POINTER(U64)]
+    L.dp_pix_server_submit.argtypes = [P, U32, P, P, U64, P, ct.POINTER(U64)]
     L.dp_pix_server_wait.argtypes = [P, U64, ct.c_int, ct.POINTER(ServerResult)]
+    L.dp_pix_server_counters.argtypes = [P, P, U32]
     L.dp_pix_server_stats_get.argtypes = [P, ct.POINTER(ServerStats)]
-    L.dp_pix_server_slots.argtypes = [P, U32, ct.POINTER(U32)]
     L.dp_pix_server_destroy.argtypes = [P]
     L.dp_pix_release_noalloc.argtypes = [P, P, I64, P, I64, I64, U32, U32, U64, P, I64, P]
     L.dp_pix_store.argtypes = [P, P, U64, ct.POINTER(U64), ct.c_int, P]
@@ -148,7 +151,8 @@ def lib():
                  "dp_pix_soft_backward", "dp_pix_batch_plan", "dp_pix_batch_destroy", "dp_pix_batch_sizes",
                  "dp_pix_batch_bind", "dp_pix_batch_run", "dp_pix_batch_autotune", "dp_pix_batch_tuning",
                  "dp_pix_release_keyed", "dp_pix_server_sizes", "dp_pix_server_create", "dp_pix_server_submit",
-                 "dp_pix_server_wait", "dp_pix_server_stats_get", "dp_pix_server_slots", "dp_pix_server_destroy",
+                 "dp_pix_server_wait", "dp_pix_server_stats_get", "dp_pix_server_counters", "dp_pix_server_destroy",
+                 "dp_pix_release_reconstruct_keyed",
                  "dp_pix_store_batch",
                  "dp_pix_reconstruct",
                  "dp_pix_debug_noise", "dp_pix_status", "dp_pix_prof_enable", "dp_pix_prof_read",

@@ -539,12 +539,16 @@ int dp_pix_release_keyed(dp_pix_plan_t plan, const void *d_frames, int64_t frame
                         d_records, record_stride, d_ws, ws_bytes, cuda_stream, nullptr, d_keys);
 }
 
-int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
-                               const void *d_region_src, int64_t src_pitch, int64_t src_frame_stride,
-                               uint32_t n_frames, uint32_t stream_id, uint64_t frame_idx0, void *d_records,
-                               int64_t record_stride, void *d_out, int64_t out_frame_stride, int64_t out_pitch,
-                               int out_type, void *d_ws, uint64_t ws_bytes, void *cuda_stream) {
-    t_err[0] = 0;
+}  // extern "C"
+
+namespace {
+
+// dp_pix_release_reconstruct, keyed by (stream_id, frame_idx0 + i) or, when keys is set, by keys[i].
+int release_reconstruct_impl(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
+                             const void *d_region_src, int64_t src_pitch, int64_t src_frame_stride,
+                             uint32_t n_frames, uint32_t stream_id, uint64_t frame_idx0, const dp_pix_frame_key *keys,
+                             void *d_records, int64_t record_stride, void *d_out, int64_t out_frame_stride,
+                             int64_t out_pitch, int out_type, void *d_ws, uint64_t ws_bytes, void *cuda_stream) {
     if (!plan) return fail(DP_PIX_E_INVALID_ARG, "plan is NULL");
     if (n_frames == 0) return DP_PIX_OK;
     const Geom &g = plan->g;
@@ -570,7 +574,7 @@ int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frames, int64_t
         const uint64_t wsb = ws_bytes >= (uint64_t)f0 * g.ws_per_frame ? ws_bytes - (uint64_t)f0 * g.ws_per_frame : 0;
         FusedOut fo{out, nf > 1 ? out_frame_stride : 0, out_pitch, out_type, align, false};
         int rc = release_impl(plan, fr, frame_stride, src, src_pitch, src_frame_stride, nf, stream_id, frame_idx0 + f0,
-                              rec, record_stride, ws, wsb, st, &fo);
+                              rec, record_stride, ws, wsb, st, &fo, keys ? keys + f0 : nullptr);
         if (rc || fo.fused) return rc;
         return dp_pix_reconstruct(rec, record_stride, nf, out, out_frame_stride, out_pitch, out_type, g.M, g.N, g.C, st);
     };
@@ -604,6 +608,33 @@ int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frames, int64_t
     }
     cudaEventDestroy(fork);
     return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
+                               const void *d_region_src, int64_t src_pitch, int64_t src_frame_stride,
+                               uint32_t n_frames, uint32_t stream_id, uint64_t frame_idx0, void *d_records,
+                               int64_t record_stride, void *d_out, int64_t out_frame_stride, int64_t out_pitch,
+                               int out_type, void *d_ws, uint64_t ws_bytes, void *cuda_stream) {
+    t_err[0] = 0;
+    return release_reconstruct_impl(plan, d_frames, frame_stride, d_region_src, src_pitch, src_frame_stride, n_frames,
+                                    stream_id, frame_idx0, nullptr, d_records, record_stride, d_out, out_frame_stride,
+                                    out_pitch, out_type, d_ws, ws_bytes, cuda_stream);
+}
+
+int dp_pix_release_reconstruct_keyed(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
+                                     const void *d_region_src, int64_t src_pitch, int64_t src_frame_stride,
+                                     uint32_t n_frames, const dp_pix_frame_key *d_keys, void *d_records,
+                                     int64_t record_stride, void *d_out, int64_t out_frame_stride, int64_t out_pitch,
+                                     int out_type, void *d_ws, uint64_t ws_bytes, void *cuda_stream) {
+    t_err[0] = 0;
+    if (n_frames > 0 && !d_keys) return fail(DP_PIX_E_INVALID_ARG, "keys are required");
+    return release_reconstruct_impl(plan, d_frames, frame_stride, d_region_src, src_pitch, src_frame_stride, n_frames,
+                                    0, 0, d_keys, d_records, record_stride, d_out, out_frame_stride, out_pitch,
+                                    out_type, d_ws, ws_bytes, cuda_stream);
 }
 
 int dp_pix_store(const void *d_record, void *dst, uint64_t cap, uint64_t *written, int dst_is_host,
