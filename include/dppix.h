@@ -165,11 +165,22 @@ DPPIX_API int dp_pix_plan_destroy(dp_pix_plan_t plan);
  *   DP_PIX_TUNE_SPLIT          dp_pix_release_reconstruct runs its frames in this many chunks on the
  *                              library's side streams, forked from and joined to the caller's stream with
  *                              events, 1..8 (default 1: everything on the caller's stream)
+ *   DP_PIX_TUNE_WAIT_TRIES     tries of the release kernels' bounded waits for their staged rows before a
+ *                              wait gives up with DP_PIX_E_TIMEOUT (through dp_pix_status), 1..2^22
+ *                              (default 2^22, seconds: far beyond any copy's latency)
+ * And one knob for testing the timeout path, which does change results:
+ *   DP_PIX_TUNE_TEST_SHORT_TX  1: every block of the staged release (TILE_LABELS, MASK_U8, MATTE_F32 plans)
+ *                              announces 16 bytes more than its first work item's copies deliver, so that
+ *                              wait runs out: the call reports DP_PIX_E_TIMEOUT and its records are
+ *                              undefined; every copy still lands, and the device stays usable.  0: off
+ *                              (default).
  * dp_pix_plan_tune returns INVALID_ARG for an unknown knob or a value out of range; dp_pix_plan_tuning
  * writes the current value to *value. */
 #define DP_PIX_TUNE_FUSED_PX 1
 #define DP_PIX_TUNE_FUSED_THREADS 2
 #define DP_PIX_TUNE_SPLIT 4
+#define DP_PIX_TUNE_WAIT_TRIES 8
+#define DP_PIX_TUNE_TEST_SHORT_TX 16
 DPPIX_API int dp_pix_plan_tune(dp_pix_plan_t plan, int knob, int value);
 DPPIX_API int dp_pix_plan_tuning(dp_pix_plan_t plan, int knob, int *value);
 

@@ -88,7 +88,7 @@ class Plan:
         return self._h
 
     def tune(self, knob: int, value: int) -> "Plan":
-        """dp_pix_plan_tune: set a launch-shape knob (TUNE_FUSED_PX, TUNE_FUSED_THREADS); results never change."""
+        """dp_pix_plan_tune: set a knob (the TUNE_* constants; the launch-shape knobs never change results)."""
         L.check(L.lib().dp_pix_plan_tune(self._h, int(knob), int(value)), "dp_pix_plan_tune")
         return self
 

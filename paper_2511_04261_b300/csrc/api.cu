@@ -286,6 +286,8 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     g.fused_px = 1024;
     g.fused_threads = 128;
     g.split = 1;
+    g.wait_tries = kWaitTries;
+    g.test_short_tx = 0;
     // staged segment: S tiles of one tile row, S*T*C a multiple of 16 when possible
     int s0 = 16 / (int)gcd64(TC, 16);
     int S = s0 * (int)((384 + (int64_t)s0 * TC - 1) / ((int64_t)s0 * TC));
@@ -405,6 +407,14 @@ int dp_pix_plan_tune(dp_pix_plan_t plan, int knob, int value) {
             if (value < 1 || value > 8) return fail(DP_PIX_E_INVALID_ARG, "split must be 1..8");
             plan->g.split = value;
             return DP_PIX_OK;
+        case DP_PIX_TUNE_WAIT_TRIES:
+            if (value < 1 || value > (int)kWaitTries) return fail(DP_PIX_E_INVALID_ARG, "wait tries must be 1..%u", kWaitTries);
+            plan->g.wait_tries = (uint32_t)value;
+            return DP_PIX_OK;
+        case DP_PIX_TUNE_TEST_SHORT_TX:
+            if (value != 0 && value != 1) return fail(DP_PIX_E_INVALID_ARG, "the short-copy test knob is 0 or 1");
+            plan->g.test_short_tx = value ? 16u : 0u;
+            return DP_PIX_OK;
         default:
             return fail(DP_PIX_E_INVALID_ARG, "unknown knob %d", knob);
     }
@@ -417,6 +427,8 @@ int dp_pix_plan_tuning(dp_pix_plan_t plan, int knob, int *value) {
         case DP_PIX_TUNE_FUSED_PX: *value = plan->g.fused_px; return DP_PIX_OK;
         case DP_PIX_TUNE_FUSED_THREADS: *value = plan->g.fused_threads; return DP_PIX_OK;
         case DP_PIX_TUNE_SPLIT: *value = plan->g.split; return DP_PIX_OK;
+        case DP_PIX_TUNE_WAIT_TRIES: *value = (int)plan->g.wait_tries; return DP_PIX_OK;
+        case DP_PIX_TUNE_TEST_SHORT_TX: *value = plan->g.test_short_tx ? 1 : 0; return DP_PIX_OK;
         default: return fail(DP_PIX_E_INVALID_ARG, "unknown knob %d", knob);
     }
 }

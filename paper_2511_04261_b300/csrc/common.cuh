@@ -15,7 +15,8 @@ constexpr int kMaxK = DP_PIX_MAX_REGIONS;
 constexpr int kMaxT = 128;
 constexpr int kMaxTileBytes = 49152;     // T*T*C limit (one staged tile)
 constexpr int kMaxRankTiles = 16384;     // VARIANCE: tiles of one frame ranked in shared memory
-constexpr int kMaxFrameTiles = 200000;   // tiles of one frame (the map is finalised in shared memory)
+constexpr int kMaxFrameTiles = 200000;
+constexpr uint32_t kWaitTries = 1u << 22;  // default tries of a bounded mbarrier wait   // tiles of one frame (the map is finalised in shared memory)
 constexpr int kHeaderBytes = DP_PIX_RECORD_HEADER_BYTES;
 
 // Geometry and constants of a plan (Alg. 2 steps 1-3, Alg. 3 steps 1-2, Eq. 11).
@@ -53,6 +54,8 @@ struct Geom {
     int32_t vbands;                   // max bands of a staged tile = T / b_min (or T / g for stats)
     int32_t fused_px, fused_threads;  // launch shape of the fused release + reconstruction (tunable)
     int32_t split;                    // frame chunks of a fused call run on side streams (tunable)
+    uint32_t wait_tries;              // tries of a bounded mbarrier wait before it gives up (tunable)
+    uint32_t test_short_tx;           // test knob: bytes announced beyond what a CTA's first item delivers
     // release work units (k_release): a b_r x b_r cell is summed by 2^rel_lp[r] adjacent lanes (row parts);
     // a tile of region r is rel_units[r] units, a multiple of rel_pmax (the largest part count)
     int32_t rel_lp[kMaxK];

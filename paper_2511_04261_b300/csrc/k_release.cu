@@ -186,13 +186,16 @@ __device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void mbar_complete_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
-// Waits for the phase of the given parity to complete; gives up (false) after a bounded number of tries
-// (try_wait itself blocks for a bounded time), so that a copy that never lands cannot hang the GPU.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 22); ++it) {
+// Waits for the phase of the given parity to complete; gives up (false) after `tries` tries (try_wait itself
+// blocks for a bounded time), so that a copy that never lands cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t tries = kWaitTries) {
+    for (uint32_t it = 0; it < tries; ++it) {
         uint32_t done;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done)
@@ -473,10 +476,14 @@ struct RelSeq {
 // The double-buffered item loop of both release kernels: prepare(item, nb) stages an item into buffer nb
 // (rows by bulk copies completing on bars[nb], its tables by cp.async), compute(nb) consumes buffer nb.
 // The mbarrier of a buffer completes one phase per item: thread 0 arrives once every warp has announced
-// the item's bytes.  A wait that gives up raises DP_PIX_E_TIMEOUT and ends the CTA.
+// the item's bytes.  A wait gives up after `tries` tries, raises DP_PIX_E_TIMEOUT and ends the CTA once
+// this item's and the next item's copies have landed (those waits are bounded too).  short_tx > 0 (a test
+// of this path) announces that many bytes more than the CTA's first item delivers, so its phase cannot
+// complete and the wait runs out; the phantom bytes are then retired, so the drain still sees every copy
+// land and none is in flight when the CTA ends.
 template <class Prep, class Comp>
 __device__ __forceinline__ void rel_loop(const RelSeq &seq, uint64_t *bars, int32_t *status, Prep prepare,
-                                         Comp compute) {
+                                         Comp compute, uint32_t tries = kWaitTries, uint32_t short_tx = 0) {
     const uint32_t i0 = seq.first(), items = seq.items;
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
@@ -486,6 +493,7 @@ __device__ __forceinline__ void rel_loop(const RelSeq &seq, uint64_t *bars, int3
     __syncthreads();
     int buf = 0;
     uint32_t ph0 = 0, ph1 = 0;
+    if (threadIdx.x == 0 && i0 < items && short_tx) mbar_expect_tx(&bars[0], short_tx);
     if (i0 < items) prepare(i0, 0);
     cp_async_commit();
     __syncthreads();
@@ -496,11 +504,15 @@ __device__ __forceinline__ void rel_loop(const RelSeq &seq, uint64_t *bars, int3
         if (next) prepare(nitem, buf ^ 1);
         cp_async_commit();
         cp_async_wait_1();
-        const bool ok = mbar_wait(&bars[buf], buf ? ph1 : ph0);
+        const bool ok = mbar_wait(&bars[buf], buf ? ph1 : ph0, tries);
         const int fail = __syncthreads_or(!ok);
         if (threadIdx.x == 0 && next) mbar_arrive(&bars[buf ^ 1]);
         if (fail) {
-            if (threadIdx.x == 0) raise_status(status, DP_PIX_E_TIMEOUT, 0x500u);
+            if (threadIdx.x == 0) {
+                raise_status(status, DP_PIX_E_TIMEOUT, 0x500u);
+                if (short_tx && item == i0) mbar_complete_tx(&bars[buf], short_tx);
+            }
+            (void)mbar_wait(&bars[buf], buf ? ph1 : ph0);                // this item's copies, bounded
             if (next) (void)mbar_wait(&bars[buf ^ 1], buf ? ph0 : ph1);  // the next item's copies, bounded
             cp_async_wait_all();
             return;
@@ -527,7 +539,7 @@ __global__ void __launch_bounds__(kRelThreads) k_release(const Geom g, const Cal
         rel_prepare(g, a, f, item - f * per_frame, it[nb], dyn + nb * buf_bytes, &bars[nb]);
     };
     auto compute = [&](int nb) { rel_compute<C>(g, a, it[nb], dyn + nb * buf_bytes); };
-    rel_loop(seq, bars, a.status, prepare, compute);
+    rel_loop(seq, bars, a.status, prepare, compute, g.wait_tries, g.test_short_tx);
 }
 
 // Batch: items = (tile row, segment) of every image, image i owning [base[2], base[2] + GR * seg_per_row).
