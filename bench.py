@@ -731,7 +731,7 @@ def run_uniform(args):
             try:
                 plan = P.Plan(M=M, N=N, C=1, grids=[b], eps=[UNIFORM["eps"]], m=UNIFORM["m"], seed=UNIFORM["seed"],
                               source=P.SRC_TILE_LABELS, dtype=P.REC_F32)
-            except P.DppixError as e:  # e.g. more tiles per frame than the plan takes (1080p at b = 2, 3)
+            except P.DppixError as e:  # a grid beyond the plan's limits
                 sweep[key][b] = "unsupported: %s" % e
                 continue
             lab = torch.zeros((F, -(-M // b), -(-N // b)), dtype=torch.uint8, device="cuda")
@@ -974,7 +974,7 @@ def run_utility(args):
 # workload "storage": record sizes of the paper's storage study (Sec. VII-A: Alg. 2 over b; Sec. VII-B: Alg. 3
 # over the subgrid factor n) with u8 means, raw and deflated, against a PNG-like deflate of the released frame
 # ------------------------------------------------------------------------------------------------------
-STORAGE = dict(bs=[1, 2, 4, 8, 16, 32, 64], ns=[1, 2, 4, 8, 16, 32, 64], b_adaptive=64, eps=0.5, m_uniform=16.0,
+STORAGE = dict(bs=[1, 2, 4, 8, 16, 32, 64, 128], ns=[1, 2, 4, 8, 16, 32, 64, 128], b_adaptive=128, eps=0.5, m_uniform=16.0,
                m_adaptive=32.0, seed=7, portraits=4, portrait_hw=(1536, 1152))
 STORAGE_METRIC = "deflated u8 record bytes per 1920 x 1080 RGB frame at b = 16 (Alg. 2), against a PNG-like frame"
 
@@ -1020,7 +1020,7 @@ def run_storage(args):
                                "release_reconstruct_ms": e0.elapsed_time(e1) / args.steps, "deflate_ms": 1e3 * t_defl}
             if key == "1920x1080" and b == 16:
                 head = uniform[key][b]
-    # Alg. 3 over the subgrid factor n: portraits with mattes, background b = 64, foreground b / n
+    # Alg. 3 over the subgrid factor n: portraits with mattes, background b = 128, foreground b / n
     adaptive = {}
     Hh, Ww = STORAGE["portrait_hw"]
     ports = [synth.portrait(np.random.default_rng(2000 + i), Hh, Ww) for i in range(STORAGE["portraits"])]
@@ -1040,11 +1040,11 @@ def run_storage(args):
         line = {"metric": STORAGE_METRIC, "value": head["deflated_record_bytes"], "unit": "bytes", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["release_reconstruct_ms"],
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-                "config": {"workload": "storage_u8_records_uniform_b1to64_adaptive_n1to64", "eps": STORAGE["eps"],
+                "config": {"workload": "storage_u8_records_uniform_b1to128_adaptive_n1to128", "eps": STORAGE["eps"],
                            "m": {"uniform": STORAGE["m_uniform"], "adaptive": STORAGE["m_adaptive"]},
                            "record": "u8 means + u8 tile map + header (dp_pix_store), deflated with zlib level 6",
                            "png_like": "PNG up filter + deflate of the released frame (no chunk headers)",
-                           "adaptive": "%d portraits %dx%d, matte >= 0.5, grids [64, 64/n]" % (STORAGE["portraits"], Ww, Hh),
+                           "adaptive": "%d portraits %dx%d, matte >= 0.5, grids [128, 128/n]" % (STORAGE["portraits"], Ww, Hh),
                            "stands_in_for": "PETS09-S2L1 / Venice-2 frames and PPM-100 portraits",
                            "parallelism": "1 GPU" if world == 1 else "replicas"},
                 "uniform": uniform, "adaptive_by_n": adaptive, "png_like_release_bytes_b16": head["png_like_release_bytes"],

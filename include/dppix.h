@@ -149,8 +149,8 @@ typedef struct dp_pix_record_header {
 typedef struct dp_pix_plan_s *dp_pix_plan_t;
 
 /* Validates `d`, derives the geometry and sizes (Alg. 2 steps 1-3, Alg. 3 steps 1-2) and returns an
- * immutable plan.  Host only: no CUDA call.  `sz` may be NULL.  Errors: INVALID_ARG, UNSUPPORTED (b_r > 64,
- * T > 128, T*T*C > 49152, more than 200000 tiles per frame; VARIANCE: more than 16384 tiles or T*C not a
+ * immutable plan.  Host only: no CUDA call.  `sz` may be NULL.  Errors: INVALID_ARG, UNSUPPORTED (b_r > 128,
+ * T > 128, T*T*C > 49152, more than 2^25 tiles per frame; VARIANCE: more than 16384 tiles or T*C not a
  * multiple of 4), PAD_TOO_LARGE (reflect needs P_R <= M-1 and P_C <= N-1; symmetric P_R <= M, P_C <= N). */
 DPPIX_API int dp_pix_plan(const dp_pix_desc *d, dp_pix_plan_t *out, dp_pix_sizes *sz);
 

@@ -203,7 +203,7 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     for (int r = 0; r < d->K; ++r) {
         const int b = d->grid[r];
         if (b < 1) return fail(DP_PIX_E_INVALID_ARG, "grid[%d] must be >= 1", r);
-        if (b > 64) return fail(DP_PIX_E_UNSUPPORTED, "grid[%d] = %d > 64", r, b);
+        if (b > kMaxT) return fail(DP_PIX_E_UNSUPPORTED, "grid[%d] = %d > %d", r, b, kMaxT);
         if (!d->noise_free && !(d->eps[r] > 0)) return fail(DP_PIX_E_INVALID_ARG, "eps[%d] must be > 0", r);
         T = T / gcd64(T, b) * b;
         if (T > kMaxT) return fail(DP_PIX_E_UNSUPPORTED, "T = lcm(grids) > %d", kMaxT);

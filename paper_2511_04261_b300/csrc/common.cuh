@@ -15,8 +15,9 @@ constexpr int kMaxK = DP_PIX_MAX_REGIONS;
 constexpr int kMaxT = 128;
 constexpr int kMaxTileBytes = 49152;     // T*T*C limit (one staged tile)
 constexpr int kMaxRankTiles = 16384;     // VARIANCE: tiles of one frame ranked in shared memory
-constexpr int kMaxFrameTiles = 200000;
-constexpr uint32_t kWaitTries = 1u << 22;  // default tries of a bounded mbarrier wait   // tiles of one frame (the map is finalised in shared memory)
+constexpr int kFinalizeSmemTiles = 200000;  // frames up to this many tiles finalise their map in shared memory
+constexpr int kMaxFrameTiles = 1 << 25;      // tiles of one frame (larger maps are finalised from global memory)
+constexpr uint32_t kWaitTries = 1u << 22;     // default tries of a bounded mbarrier wait
 constexpr int kHeaderBytes = DP_PIX_RECORD_HEADER_BYTES;
 
 // Geometry and constants of a plan (Alg. 2 steps 1-3, Alg. 3 steps 1-2, Eq. 11).

@@ -96,9 +96,10 @@ struct FinalizeSmem {
 };
 static_assert(offsetof(FinalizeSmem, hdr) % 16 == 0, "the header is zeroed in 16-byte words");
 
-// Lays out the record of frame f from the map in shared memory (see file comment); also writes the
-// workspace's per-tile payload offsets and the tile ids in record order (region-major, row-major).
-// FB: bits per packed region counter (the frame has fewer than 2^FB tiles).
+// Lays out the record of frame f from its map (see file comment); also writes the workspace's per-tile
+// payload offsets and the tile ids in record order (region-major, row-major).  map_s: the map in shared
+// memory, or in global memory for frames of more than kFinalizeSmemTiles tiles; a label >= K counts as 0
+// (k_finalize has flagged it).  FB: bits per packed region counter (the frame has fewer than 2^FB tiles).
 template <int FB, int NWORDS>
 __device__ __forceinline__ void finalize_frame_t(const Geom &g, const CallArgs &a, uint32_t f, const uint8_t *map_s, bool write_map,
                                  FinalizeSmem &sm) {
@@ -109,7 +110,10 @@ __device__ __forceinline__ void finalize_frame_t(const Geom &g, const CallArgs &
     if (threadIdx.x < kHeaderBytes / 16) reinterpret_cast<uint4 *>(&sm.hdr)[threadIdx.x] = make_uint4(0, 0, 0, 0);
     PC cnt, excl, total;
     cnt.clear();
-    for (uint32_t i = c0; i < c1; ++i) cnt.inc(map_s[i]);
+    for (uint32_t i = c0; i < c1; ++i) {
+        const uint32_t r = map_s[i];
+        cnt.inc(r < (uint32_t)g.K ? r : 0u);
+    }
     block_excl_scan_packed<PC::NW>(cnt.w, excl.w, total.w, sm.warp_tot);
 
     uint8_t *rec = a.records + (uint64_t)f * (uint64_t)a.record_stride;
@@ -168,7 +172,8 @@ __device__ __forceinline__ void finalize_frame_t(const Geom &g, const CallArgs &
         if (tx == 0) {
             for (int r = 0; r < g.K; ++r) rowidx[ty * g.K + r] = run.get(r);
         }
-        const uint32_t r = map_s[i];
+        uint32_t r = map_s[i];
+        if (r >= (uint32_t)g.K) r = 0;
         const uint32_t ri = run.get(r);
         run.inc(r);
         if (++tx == (uint32_t)g.GC) {
@@ -180,7 +185,10 @@ __device__ __forceinline__ void finalize_frame_t(const Geom &g, const CallArgs &
     }
     if (write_map) {
         uint8_t *map = rec + g.map_offset;
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) map[i] = map_s[i];
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint8_t r = map_s[i];
+            map[i] = r < (uint32_t)g.K ? r : 0;
+        }
     }
     // zero the alignment gaps so that a record is a deterministic byte string
     const uint64_t row_end = g.rowidx_offset + (uint64_t)g.GR * g.K * 4;
@@ -211,16 +219,17 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_finalize(const Geom g, con
     const uint32_t f = blockIdx.x;
     const uint8_t *src = from_labels ? a.src + (uint64_t)f * (uint64_t)a.src_frame_stride
                                      : a.records + (uint64_t)f * (uint64_t)a.record_stride + g.map_offset;
+    const bool smem_map = g.ntiles <= (uint32_t)kFinalizeSmemTiles;
     for (uint32_t i = threadIdx.x; i < g.ntiles; i += blockDim.x) {
         uint8_t r = src[i];
         if (r >= (uint32_t)g.K) {
             raise_status(a.status, DP_PIX_E_DEVICE, 0x100u | r);
             r = 0;
         }
-        map_s[i] = r;
+        if (smem_map) map_s[i] = r;
     }
     __syncthreads();
-    finalize_frame(g, a, f, map_s, from_labels != 0, sm);
+    finalize_frame(g, a, f, smem_map ? map_s : src, from_labels != 0, sm);
 }
 
 // Batch: one CTA per image (map written by k_batch_classify, or caller labels).
@@ -235,16 +244,17 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_batch_finalize(const Batch
         const CallArgs &a = bs.a;
         const bool from_labels = g.source == DP_PIX_SRC_TILE_LABELS;
         const uint8_t *src = from_labels ? a.src : a.records + g.map_offset;
+        const bool smem_map = g.ntiles <= (uint32_t)kFinalizeSmemTiles;
         for (uint32_t t = threadIdx.x; t < g.ntiles; t += blockDim.x) {
             uint8_t r = src[t];
             if (r >= (uint32_t)g.K) {
                 raise_status(a.status, DP_PIX_E_DEVICE, 0x100u | r);
                 r = 0;
             }
-            map_s[t] = r;
+            if (smem_map) map_s[t] = r;
         }
         __syncthreads();
-        finalize_frame(g, a, 0u, map_s, from_labels, sm);
+        finalize_frame(g, a, 0u, smem_map ? map_s : src, from_labels, sm);
         __syncthreads();
     }
 }
@@ -514,7 +524,7 @@ cudaError_t launch_rank_sort(const Geom &g, const CallArgs &a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_finalize_labels(const Geom &g, const CallArgs &a, cudaStream_t s) {
-    const size_t smem = sizeof(FinalizeSmem) + g.ntiles;
+    const size_t smem = sizeof(FinalizeSmem) + (g.ntiles <= (uint32_t)kFinalizeSmemTiles ? g.ntiles : 0u);
     launch_prep(reinterpret_cast<const void *>(k_finalize), kFrameThreads, smem);
     prof_begin("k_finalize", s);
     k_finalize<<<a.n_frames, kFrameThreads, smem, s>>>(g, a, 1);
@@ -523,7 +533,7 @@ cudaError_t launch_finalize_labels(const Geom &g, const CallArgs &a, cudaStream_
 }
 
 cudaError_t launch_finalize_map(const Geom &g, const CallArgs &a, cudaStream_t s) {
-    const size_t smem = sizeof(FinalizeSmem) + g.ntiles;
+    const size_t smem = sizeof(FinalizeSmem) + (g.ntiles <= (uint32_t)kFinalizeSmemTiles ? g.ntiles : 0u);
     launch_prep(reinterpret_cast<const void *>(k_finalize), kFrameThreads, smem);
     prof_begin("k_finalize", s);
     k_finalize<<<a.n_frames, kFrameThreads, smem, s>>>(g, a, 0);
@@ -532,7 +542,7 @@ cudaError_t launch_finalize_map(const Geom &g, const CallArgs &a, cudaStream_t s
 }
 
 cudaError_t launch_batch_finalize(const BatchEntry *tab, uint32_t n_img, uint32_t max_tiles, cudaStream_t s) {
-    const size_t smem = sizeof(FinalizeSmem) + max_tiles;
+    const size_t smem = sizeof(FinalizeSmem) + std::min<uint32_t>(max_tiles, (uint32_t)kFinalizeSmemTiles);
     launch_prep(reinterpret_cast<const void *>(k_batch_finalize), kFrameThreads, smem);
     const int grid = (int)std::min<uint32_t>(n_img, (uint32_t)sm_count());
     prof_begin("k_batch_finalize", s);

@@ -83,7 +83,16 @@ def test_plan_geometry_matches_oracle(seed):
 
 def test_plan_limits():
     with pytest.raises(P.DppixError) as e:
-        P.Plan(M=100, N=100, C=3, grids=[65], eps=[1])
+        P.Plan(M=200, N=200, C=3, grids=[129], eps=[1])
+    assert e.value.code == _lib.E_UNSUPPORTED
+    # the paper's largest grid (b = 128) and its region-adaptive pairs {128, 128 / n} fit
+    assert P.Plan(M=1080, N=1920, C=3, grids=[128], eps=[0.5]).T == 128
+    assert P.Plan(M=1152, N=1536, C=3, grids=[128, 1], eps=[0.5, 0.5], source=_lib.SRC_MATTE_F32).T == 128
+    # one-pixel cells of a 1080p frame: 2,073,600 tiles, finalised from global memory
+    p1 = P.Plan(M=1080, N=1920, C=1, grids=[1], eps=[0.5])
+    assert (p1.GR, p1.GC) == (1080, 1920)
+    with pytest.raises(P.DppixError) as e:
+        P.Plan(M=8192, N=8192, C=1, grids=[1], eps=[0.5])  # 2^26 tiles
     assert e.value.code == _lib.E_UNSUPPORTED
     with pytest.raises(P.DppixError) as e:
         P.Plan(M=100, N=100, C=3, grids=[64, 3], eps=[1, 1])  # T = 192

@@ -359,6 +359,27 @@ def test_uniform_grayscale_768x576(b):
         assert np.array_equal(outs[i], O.reconstruct(np.frombuffer(got, np.uint8), 0))
 
 
+@pytest.mark.parametrize("b", [1, 2, 3])
+def test_uniform_grayscale_1080p_small_grids(b):
+    """The paper's Venice shape (1920 x 1080 grayscale, eps 0.5, m 16) at the smallest grids of its sweep:
+    518,400 tiles at b = 2 and 2,073,600 at b = 1, more than a shared-memory map holds, so the record is
+    laid out from the map in global memory.  Every record element and pixel checked against the oracle."""
+    F, M, N = 2, 1080, 1920
+    clip = synth.moving_rect_clip(seed=800 + b, frames=F, M=M, N=N, C=1)
+    lab = np.zeros((F, -(-M // b), -(-N // b)), dtype=np.uint8)
+    kw = dict(M=M, N=N, C=1, grids=[b], eps=[0.5], m=16, source=O.SRC_TILE_LABELS, dtype=O.DT_F32, seed=13)
+    plan = P.Plan(**kw)
+    recs_d, outs = plan.release_reconstruct(torch.from_numpy(clip).cuda(), torch.from_numpy(lab).cuda())
+    torch.cuda.synchronize()
+    assert P.dp_pix_status() == 0
+    outs = outs.cpu().numpy()
+    for i in range(F):
+        got = P.dp_pix_store(recs_d[i])
+        rec, means, sums, etas = O.release(clip[i], lab[i], frame_idx=i, **kw)
+        compare_records(got, rec, means, sums, etas, O.DT_F32)
+        assert np.array_equal(outs[i], O.reconstruct(np.frombuffer(got, np.uint8), 0))
+
+
 # ------------------------------------------------------------------------------------------------------
 # Full-size workloads at the benchmark's launch configuration, sampled against the oracle
 # ------------------------------------------------------------------------------------------------------
