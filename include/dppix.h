@@ -297,11 +297,29 @@ DPPIX_API int dp_pix_batch_bind(dp_pix_batch_t b, const dp_pix_batch_image *imgs
  * Device-side problems (a bad label) arrive through dp_pix_status().  Errors: INVALID_ARG (not bound), CUDA. */
 DPPIX_API int dp_pix_batch_run(dp_pix_batch_t b, int use_graph, void *cuda_stream);
 
-/* Times the release's segment widths (tiles staged per work item) on the bound batch -- reps runs each,
- * overwriting its records and outputs -- keeps the fastest, rebinds `imgs` (the images bound last) and drops
- * the graph.  Synchronizes cuda_stream.  dp_pix_batch_tuning reports the width in use. */
+/* Release paths of a batch (all give the same bytes):
+ *   DP_PIX_BATCH_PATH_STAGED        each item's rows arrive in shared memory by bulk copies; the images, if any,
+ *                                   are written by a separate reconstruction launch
+ *   DP_PIX_BATCH_PATH_STREAM        each lane streams its 16-byte column chunk of the item's rows straight into
+ *                                   registers (rows realigned by funnel shifts); separate reconstruction
+ *   DP_PIX_BATCH_PATH_STREAM_FUSED  as STREAM, and the same launch writes the u8 images from the cell values
+ * The streaming paths need T * C >= 16 (and their per-item sums within shared memory); the fused one u8
+ * images and f32 or u8 records.  Where a path does not apply the batch takes the next one down. */
+#define DP_PIX_BATCH_PATH_STAGED 0
+#define DP_PIX_BATCH_PATH_STREAM 1
+#define DP_PIX_BATCH_PATH_STREAM_FUSED 2
+
+/* Times the release paths and their segment widths (tiles per work item) on the bound batch -- reps runs
+ * each, overwriting its records and outputs -- keeps the fastest, rebinds `imgs` (the images bound last) and
+ * drops the graph.  Synchronizes cuda_stream.  dp_pix_batch_tuning reports the width and path in use (path
+ * may be NULL). */
 DPPIX_API int dp_pix_batch_autotune(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int reps, void *cuda_stream);
-DPPIX_API int dp_pix_batch_tuning(dp_pix_batch_t b, int *seg_tiles);
+DPPIX_API int dp_pix_batch_tuning(dp_pix_batch_t b, int *seg_tiles, int *path);
+
+/* Chooses a release path (DP_PIX_BATCH_PATH_*, or -1: the default, the staged path)
+ * and segment width (0: the path's default) without timing; takes effect at the next dp_pix_batch_bind.
+ * Errors: INVALID_ARG. */
+DPPIX_API int dp_pix_batch_set_path(dp_pix_batch_t b, int path, int seg_tiles);
 
 /* ---- serving loop (no counterpart in the paper; its deployment motivation is many cameras) --------------- */
 /* A request loop for frames arriving from many cameras.  Requests are queued from host memory by any

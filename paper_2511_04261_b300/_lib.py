@@ -23,6 +23,7 @@ SRC_TILE_LABELS, SRC_MASK_U8, SRC_MATTE_F32, SRC_VARIANCE = 0, 1, 2, 3
 REC_F32, REC_U8, REC_SUM_U32 = 0, 1, 2
 OUT_U8, OUT_F32 = 0, 1
 TUNE_FUSED_PX, TUNE_FUSED_THREADS, TUNE_SPLIT, TUNE_WAIT_TRIES, TUNE_TEST_SHORT_TX = 1, 2, 4, 8, 16
+BATCH_PATH_STAGED, BATCH_PATH_STREAM, BATCH_PATH_STREAM_FUSED = 0, 1, 2
 
 
 class SoftDesc(ct.Structure):
@@ -120,7 +121,8 @@ def lib():
     L.dp_pix_batch_bind.argtypes = [P, ct.POINTER(BatchImage), ct.c_int, P, U64, P]
     L.dp_pix_batch_run.argtypes = [P, ct.c_int, P]
     L.dp_pix_batch_autotune.argtypes = [P, ct.POINTER(BatchImage), ct.c_int, P]
-    L.dp_pix_batch_tuning.argtypes = [P, ct.POINTER(ct.c_int)]
+    L.dp_pix_batch_tuning.argtypes = [P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
+    L.dp_pix_batch_set_path.argtypes = [P, ct.c_int, ct.c_int]
     L.dp_pix_release_keyed.argtypes = [P, P, I64, P, I64, I64, U32, P, P, I64, P, U64, P]
     L.dp_pix_release_reconstruct_keyed.argtypes = [P, P, I64, P, I64, I64, U32, P, P, I64, P, I64, I64, ct.c_int,
                                                    P, U64, P]
@@ -150,6 +152,7 @@ def lib():
                  "dp_pix_release_noalloc", "dp_pix_store", "dp_pix_soft_sizes", "dp_pix_soft_forward",
                  "dp_pix_soft_backward", "dp_pix_batch_plan", "dp_pix_batch_destroy", "dp_pix_batch_sizes",
                  "dp_pix_batch_bind", "dp_pix_batch_run", "dp_pix_batch_autotune", "dp_pix_batch_tuning",
+                 "dp_pix_batch_set_path",
                  "dp_pix_release_keyed", "dp_pix_server_sizes", "dp_pix_server_create", "dp_pix_server_submit",
                  "dp_pix_server_wait", "dp_pix_server_stats_get", "dp_pix_server_counters", "dp_pix_server_destroy",
                  "dp_pix_release_reconstruct_keyed",

@@ -90,6 +90,7 @@ class BatchPlan:
         L.check(L.lib().dp_pix_batch_bind(self._h, arr, int(out_type), ct.c_void_p(ws.data_ptr()),
                                           ws.numel() * ws.element_size(), _stream(stream)), "dp_pix_batch_bind")
         self._imgs = arr
+        self._out_type = int(out_type)
         self._keep = (list(frames), list(region_src) if region_src is not None else None, list(records), ws,
                       list(outs) if outs is not None else None)
         return self
@@ -104,6 +105,20 @@ class BatchPlan:
         return self.seg_tiles()
 
     def seg_tiles(self) -> int:
-        v = ct.c_int(0)
-        L.check(L.lib().dp_pix_batch_tuning(self._h, ct.byref(v)), "dp_pix_batch_tuning")
-        return int(v.value)
+        return self.tuning()[0]
+
+    def tuning(self):
+        """(segment tiles, release path DP_PIX_BATCH_PATH_*) in use."""
+        v, p = ct.c_int(0), ct.c_int(0)
+        L.check(L.lib().dp_pix_batch_tuning(self._h, ct.byref(v), ct.byref(p)), "dp_pix_batch_tuning")
+        return int(v.value), int(p.value)
+
+    def set_path(self, path: int, seg_tiles: int = 0):
+        """dp_pix_batch_set_path: fix the release path (-1: default) and width (0: the path's); rebinds the
+        images bound last."""
+        L.check(L.lib().dp_pix_batch_set_path(self._h, int(path), int(seg_tiles)), "dp_pix_batch_set_path")
+        if self._imgs is not None:
+            frames, srcs, recs, ws, outs = self._keep
+            L.check(L.lib().dp_pix_batch_bind(self._h, self._imgs, self._out_type, ct.c_void_p(ws.data_ptr()),
+                                              ws.numel() * ws.element_size(), _stream(None)), "dp_pix_batch_bind")
+        return self

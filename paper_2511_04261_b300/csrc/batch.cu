@@ -27,6 +27,7 @@ struct dp_pix_batch_s {
     std::vector<uint64_t> ws_off;     // caller order: offset of the image's workspace in d_ws
     uint64_t table_bytes = 0, ws_bytes = 0;
     int seg_tiles = 0;                // release segment width in use (0: the plan's)
+    int path = -1;                    // release path: DP_PIX_BATCH_PATH_* (-1: the default for the geometry)
     // bound state
     bool bound = false;
     std::vector<BatchEntry> tab;      // work order
@@ -34,6 +35,9 @@ struct dp_pix_batch_s {
     int out_type = DP_PIX_OUT_U8, out_align = 16, any_out = 0;
     uint32_t items_cls = 0, items_rel = 0, items_rec = 0, max_gc = 0, max_tiles = 0;
     size_t rel_smem = 0;
+    // streaming kernels (k_batch_stream.cu), where the geometry allows them
+    bool cls_stream = false, rel_stream = false, recon_fused = false;
+    BatchStreamShape rs{};
     // graph (captured on a private stream -- capture is not possible on the legacy default stream -- and
     // launched on the caller's)
     cudaGraphExec_t exec = nullptr;
@@ -83,6 +87,18 @@ int build_table(dp_pix_batch_s *b, const dp_pix_batch_image *imgs, int out_type)
     b->any_out = 0;
     int align = 16;
     const int oes = out_type == DP_PIX_OUT_F32 ? 4 : 1;
+    {
+        const Geom &g0 = b->geo[0];
+        b->cls_stream = (g0.source == DP_PIX_SRC_MASK_U8 || g0.source == DP_PIX_SRC_MATTE_F32) &&
+                        batch_classify_stream_ok(g0.T, g0.source == DP_PIX_SRC_MATTE_F32);
+        b->rs = batch_release_stream_shape(g0.T, g0.C, g0.b_min, b->seg_tiles > 0 ? b->seg_tiles : 1 << 20);
+        // default (path -1): the staged release, measured faster on the portrait batch; the streaming paths
+        // when chosen (dp_pix_batch_set_path, or by the autotuner's timing)
+        b->rel_stream = b->rs.S > 0 && (b->path == DP_PIX_BATCH_PATH_STREAM || b->path == DP_PIX_BATCH_PATH_STREAM_FUSED);
+        // the fused image needs u8 output and stored values it can read back as the reconstruction would
+        b->recon_fused = b->rel_stream && b->path == DP_PIX_BATCH_PATH_STREAM_FUSED && b->rs.recon_ok &&
+                         out_type == DP_PIX_OUT_U8 && g0.dtype != DP_PIX_REC_SUM_U32;
+    }
     for (uint32_t k = 0; k < b->n; ++k) {
         const uint32_t i = b->order[k];
         const dp_pix_batch_image &im = imgs[i];
@@ -103,7 +119,7 @@ int build_table(dp_pix_batch_s *b, const dp_pix_batch_image *imgs, int out_type)
         if (im.out && oes == 4 && ((uintptr_t)im.out % 4 || im.out_pitch % 4))
             return bfail(DP_PIX_E_INVALID_ARG, "image %u: f32 output must be 4-byte aligned", i);
         g.pitch = im.row_pitch;
-        if (b->seg_tiles > 0) apply_seg(g, b->seg_tiles);
+        if (b->seg_tiles > 0 && !b->rel_stream) apply_seg(g, b->seg_tiles);
         BatchEntry &e = b->tab[k];
         e.g = g;
         CallArgs &a = e.a;
@@ -129,11 +145,16 @@ int build_table(dp_pix_batch_s *b, const dp_pix_batch_image *imgs, int out_type)
         e.base[1] = k;
         e.base[2] = rel;
         e.base[3] = rec;
-        {
+        if (b->cls_stream) {
+            cls += (uint32_t)g.GR;
+        } else {
             const int cs = cls_seg_tiles(g.T, g.source == DP_PIX_SRC_MATTE_F32 ? 4 : 1);
             cls += (uint32_t)g.GR * (uint32_t)((g.GC + cs - 1) / cs);
         }
-        rel += (uint32_t)g.GR * (uint32_t)g.seg_per_row;
+        if (b->rel_stream)
+            rel += (uint32_t)g.GR * (uint32_t)((g.GC + b->rs.S - 1) / b->rs.S);
+        else
+            rel += (uint32_t)g.GR * (uint32_t)g.seg_per_row;
         rec += (uint32_t)g.GR;
         b->max_gc = std::max<uint32_t>(b->max_gc, (uint32_t)g.GC);
         b->max_tiles = std::max<uint32_t>(b->max_tiles, g.ntiles);
@@ -159,12 +180,17 @@ int upload(dp_pix_batch_s *b, cudaStream_t s) {
 cudaError_t launch_all(dp_pix_batch_s *b, cudaStream_t s) {
     const BatchEntry *tab = reinterpret_cast<const BatchEntry *>(b->d_ws);
     const Geom &g0 = b->tab[0].g;
+    const int matte = g0.source == DP_PIX_SRC_MATTE_F32;
     cudaError_t e = cudaSuccess;
     if (g0.source == DP_PIX_SRC_MASK_U8 || g0.source == DP_PIX_SRC_MATTE_F32)
-        e = launch_batch_classify(tab, b->n, b->items_cls, g0.T, g0.source == DP_PIX_SRC_MATTE_F32, s);
+        e = b->cls_stream ? launch_batch_classify_stream(tab, b->n, b->items_cls, matte, b->max_gc, s)
+                          : launch_batch_classify(tab, b->n, b->items_cls, g0.T, matte, s);
     if (e == cudaSuccess) e = launch_batch_finalize(tab, b->n, b->max_tiles, s);
-    if (e == cudaSuccess) e = launch_batch_release(tab, b->n, b->items_rel, g0.T, g0.C, g0.seg_tiles, s);
-    if (e == cudaSuccess && b->any_out)
+    const bool fused = b->recon_fused && b->any_out;
+    if (e == cudaSuccess)
+        e = b->rel_stream ? launch_batch_release_stream(tab, b->n, b->items_rel, g0.C, b->rs, fused ? 1 : 0, s)
+                          : launch_batch_release(tab, b->n, b->items_rel, g0.T, g0.C, g0.seg_tiles, s);
+    if (e == cudaSuccess && b->any_out && !fused)
         e = launch_batch_reconstruct(tab, b->n, b->items_rec, b->out_type, g0.C, b->out_align, status_word(), s);
     return e;
 }
@@ -293,15 +319,32 @@ int dp_pix_batch_autotune(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int 
     if (reps < 1) reps = 1;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const Geom &g0 = b->geo[0];
-    const int cands[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
+    // candidates: the staged release (segments of up to 16 tiles, within its shared memory) and the streaming
+    // one (segments up to what its shared memory holds), the latter with the images written by a separate
+    // reconstruction or from the same kernel
+    std::vector<std::pair<int, int>> cands;  // (path, segment tiles)
+    for (int S : {1, 2, 3, 4, 6, 8})
+        if (seg_smem_for(g0, S) <= 200 * 1024) cands.emplace_back(DP_PIX_BATCH_PATH_STAGED, S);
+    const BatchStreamShape full = batch_release_stream_shape(g0.T, g0.C, g0.b_min, 1 << 20);
+    if (full.S > 0) {
+        const bool fusable = full.recon_ok && b->any_out && b->out_type == DP_PIX_OUT_U8 && g0.dtype != DP_PIX_REC_SUM_U32;
+        int last = 0;
+        for (int S : {4, 6, 9, 12, 16, 24, 32}) {
+            const int Ss = std::min(S, full.S);
+            if (Ss == last) continue;
+            last = Ss;
+            cands.emplace_back(DP_PIX_BATCH_PATH_STREAM, Ss);
+            if (fusable) cands.emplace_back(DP_PIX_BATCH_PATH_STREAM_FUSED, Ss);
+        }
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cfail(cudaGetLastError(), "events");
     float best = 1e30f;
-    int best_s = b->seg_tiles;
+    int best_s = b->seg_tiles, best_p = b->path;
     int rc = DP_PIX_OK;
-    for (int S : cands) {
-        if (seg_smem_for(g0, S) > 200 * 1024) continue;
-        b->seg_tiles = S;
+    for (const auto &c : cands) {
+        b->path = c.first;
+        b->seg_tiles = c.second;
         rc = build_table(b, imgs, b->out_type);
         if (!rc) rc = upload(b, s);
         if (rc) break;
@@ -318,12 +361,14 @@ int dp_pix_batch_autotune(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int 
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best) {
             best = ms;
-            best_s = S;
+            best_s = c.second;
+            best_p = c.first;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->seg_tiles = best_s;
+    b->path = best_p;
     drop_graph(b);
     const int rc2 = build_table(b, imgs, b->out_type);
     if (rc2) return rc2;
@@ -331,9 +376,23 @@ int dp_pix_batch_autotune(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int 
     return rc ? rc : rc3;
 }
 
-int dp_pix_batch_tuning(dp_pix_batch_t b, int *seg_tiles) {
+int dp_pix_batch_tuning(dp_pix_batch_t b, int *seg_tiles, int *path) {
     if (!b || !seg_tiles) return bfail(DP_PIX_E_INVALID_ARG, "null argument");
-    *seg_tiles = b->seg_tiles > 0 ? b->seg_tiles : b->geo[0].seg_tiles;
+    *seg_tiles = b->rel_stream ? b->rs.S : (b->seg_tiles > 0 ? b->seg_tiles : b->geo[0].seg_tiles);
+    if (path)
+        *path = !b->rel_stream ? DP_PIX_BATCH_PATH_STAGED
+                               : (b->recon_fused ? DP_PIX_BATCH_PATH_STREAM_FUSED : DP_PIX_BATCH_PATH_STREAM);
+    return DP_PIX_OK;
+}
+
+int dp_pix_batch_set_path(dp_pix_batch_t b, int path, int seg_tiles) {
+    if (!b) return bfail(DP_PIX_E_INVALID_ARG, "batch is NULL");
+    if (path < -1 || path > DP_PIX_BATCH_PATH_STREAM_FUSED) return bfail(DP_PIX_E_INVALID_ARG, "bad path %d", path);
+    if (seg_tiles < 0 || seg_tiles > 64) return bfail(DP_PIX_E_INVALID_ARG, "segment tiles must be 0..64");
+    b->path = path;
+    b->seg_tiles = seg_tiles;
+    b->bound = false;  // takes effect at the next dp_pix_batch_bind
+    drop_graph(b);
     return DP_PIX_OK;
 }
 

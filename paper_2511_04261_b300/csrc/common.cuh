@@ -238,6 +238,32 @@ __device__ __forceinline__ float noisy_mean(uint32_t S, float b2, float inv_b2, 
     return fminf(fmaxf(v, 0.0f), R);
 }
 
+// Noise, clip and store of one cell's C channels (Alg. 3 steps 9-10 and 15-17) from its Philox words;
+// sigma, b^2 and 1/b^2 (0 when not exact) of its region.  ov (optional) receives the value a
+// reconstruction reads back from the stored element (Sec. VI-F).
+__device__ __forceinline__ void emit_values(const Geom &g, int C, uint8_t *dst, const uint32_t *S, uint4 words,
+                                            float sigma, float b2, float inv_b2, float *ov) {
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+        if (ch >= C) break;
+        if (g.dtype == DP_PIX_REC_SUM_U32) {
+            reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
+            if (ov) ov[ch] = __fdiv_rn(__uint2float_rn(S[ch]), b2);
+        } else {
+            const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), sigma);
+            const float v = noisy_mean(S[ch], b2, inv_b2, eta, g.R_f);
+            if (g.dtype == DP_PIX_REC_F32) {
+                reinterpret_cast<float *>(dst)[ch] = v;
+                if (ov) ov[ch] = v;
+            } else {
+                const uint32_t q = __float2uint_rn(v);
+                dst[ch] = (uint8_t)q;
+                if (ov) ov[ch] = (float)q;
+            }
+        }
+    }
+}
+
 // Mirror padding by index: padded index p >= n maps back into [0, n) (Alg. 2 step 4).  Without padding
 // (DP_PIX_PAD_NONE) the sample past the edge is not used, and any index inside the frame is returned.
 __device__ __forceinline__ int reflect_idx(int p, int n, int pad_mode) {
@@ -274,6 +300,17 @@ cudaError_t launch_batch_finalize(const BatchEntry *tab, uint32_t n_img, uint32_
 cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items, int T, int C, int S,
                                  cudaStream_t s);
 size_t release_smem(int T, int C, int S);  // dynamic shared memory of the release kernels for S-tile segments
+// Streaming batch kernels (k_batch_stream.cu): classification of (image, tile row) items, and the release (with
+// the u8 reconstruction when `recon`) of (image, tile row, segment of S tiles) items.
+struct BatchStreamShape {
+    int S, NB, vpitch, csq, cellv_off, edge_off, edge_pitch, smem, recon_ok;  // S = 0: the streaming release does not apply
+};
+bool batch_classify_stream_ok(int T, int matte);
+cudaError_t launch_batch_classify_stream(const BatchEntry *tab, uint32_t n_img, uint32_t items, int matte,
+                                         uint32_t max_gc, cudaStream_t s);
+BatchStreamShape batch_release_stream_shape(int T, int C, int b_min, int max_seg);
+cudaError_t launch_batch_release_stream(const BatchEntry *tab, uint32_t n_img, uint32_t items, int C,
+                                        const BatchStreamShape &bs, int recon, cudaStream_t s);
 cudaError_t launch_batch_reconstruct(const BatchEntry *tab, uint32_t n_img, uint32_t items, int out_type, int max_C,
                                      int out_align, int32_t *status, cudaStream_t s);
 cudaError_t launch_debug_noise(uint64_t seed, const uint32_t *ctr, uint64_t n, uint32_t *words, float *eta,

@@ -113,32 +113,6 @@ __device__ void stage_segment(const Geom &g, const CallArgs &a, uint32_t f, int 
     __syncthreads();
 }
 
-// Noise, clip and store of one cell's C channels (Alg. 3 steps 9-10 and 15-17) from its Philox words;
-// sigma, b^2 and 1/b^2 (0 when not exact) of its region.  ov (optional) receives the value a
-// reconstruction reads back from the stored element (Sec. VI-F).
-__device__ __forceinline__ void emit_values(const Geom &g, int C, uint8_t *dst, const uint32_t *S, uint4 words,
-                                            float sigma, float b2, float inv_b2, float *ov) {
-#pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
-        if (ch >= C) break;
-        if (g.dtype == DP_PIX_REC_SUM_U32) {
-            reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
-            if (ov) ov[ch] = __fdiv_rn(__uint2float_rn(S[ch]), b2);
-        } else {
-            const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), sigma);
-            const float v = noisy_mean(S[ch], b2, inv_b2, eta, g.R_f);
-            if (g.dtype == DP_PIX_REC_F32) {
-                reinterpret_cast<float *>(dst)[ch] = v;
-                if (ov) ov[ch] = v;
-            } else {
-                const uint32_t q = __float2uint_rn(v);
-                dst[ch] = (uint8_t)q;
-                if (ov) ov[ch] = (float)q;
-            }
-        }
-    }
-}
-
 __device__ __forceinline__ void emit_cell(const Geom &g, const CallArgs &a, uint8_t *dst, const uint32_t *S, int r,
                                           uint32_t cell_idx, uint64_t frame, uint32_t sid, float *ov = nullptr) {
     uint4 words = make_uint4(0, 0, 0, 0);

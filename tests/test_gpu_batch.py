@@ -130,3 +130,37 @@ def test_batch_config3_shapes_sampled():
     imgs, mattes = _portraits(sizes, 1003)
     _, got, outs = _run_batch(sizes, imgs, mattes, O.SRC_MATTE)
     _check_against_single_and_oracle(sizes, imgs, mattes, O.SRC_MATTE, got, outs, oracle_every=4)
+
+
+@pytest.mark.parametrize("source", [O.SRC_MATTE, O.SRC_MASK])
+def test_batch_release_paths_give_the_same_bytes(source):
+    """The staged path, the streaming path and the streaming path with the images written in the same launch
+    (DP_PIX_BATCH_PATH_*) at several segment widths write byte-identical records and images."""
+    sizes = [(517, 1003), (64, 75), (300, 241), (1200, 700)]
+    imgs, mattes = _portraits(sizes, 77)
+    srcs = mattes if source == O.SRC_MATTE else [(m < 0.5).astype(np.uint8) for m in mattes]
+    bp = P.BatchPlan(sizes, source=source, dtype=O.DT_F32, **KW)
+    frames = [torch.from_numpy(np.ascontiguousarray(im)).cuda() for im in imgs]
+    src_t = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in srcs]
+    recs = bp.alloc_records()
+    outs = [torch.full((M, N, 3), 7, dtype=torch.uint8, device="cuda") for (M, N) in sizes]
+    bp.bind(frames, src_t, recs, bp.alloc_workspace(), outs=outs, stream_ids=[5 + i for i in range(4)],
+            frame_idx=[100 + i for i in range(4)])
+    ref = None
+    for path, seg in [(P.BATCH_PATH_STAGED, 2), (P.BATCH_PATH_STREAM, 0), (P.BATCH_PATH_STREAM_FUSED, 0),
+                      (P.BATCH_PATH_STREAM, 5), (P.BATCH_PATH_STREAM_FUSED, 3)]:
+        for o in outs:
+            o.fill_(7)
+        bp.set_path(path, seg)
+        assert bp.tuning()[1] == path
+        bp.run(use_graph=False)
+        torch.cuda.synchronize()
+        assert P.dp_pix_status() == 0
+        got = ([P.dp_pix_store(r) for r in recs], [o.cpu().numpy() for o in outs])
+        if ref is None:
+            ref = got
+            _check_against_single_and_oracle(sizes, imgs, srcs, source, got[0], got[1], oracle_every=2)
+        else:
+            assert got[0] == ref[0], (path, seg)
+            for a, b in zip(got[1], ref[1]):
+                assert np.array_equal(a, b), (path, seg)
