@@ -162,9 +162,13 @@ DPPIX_API int dp_pix_plan_destroy(dp_pix_plan_t plan);
  *   DP_PIX_TUNE_FUSED_PX       pixel columns per work item of the fused release + reconstruction,
  *                              64..2048 (default 1024; rounded down to whole, aligned tiles)
  *   DP_PIX_TUNE_FUSED_THREADS  threads per block of that kernel, 96, 128, 192 or 256 (default 128)
- *   DP_PIX_TUNE_SPLIT          dp_pix_release_reconstruct runs its frames in this many chunks on the
- *                              library's side streams, forked from and joined to the caller's stream with
- *                              events, 1..8 (default 1: everything on the caller's stream)
+ *   DP_PIX_TUNE_SPLIT          variance-class dp_pix_release_reconstruct runs its frames as a pipeline of this
+ *                              many chunks: every chunk's statistics and rank on the caller's stream, each
+ *                              chunk's emission (records and images) on a library side stream once its rank is
+ *                              done, forked from and joined to the caller's stream with events, 1..16 (default
+ *                              1: everything on the caller's stream)
+ *   DP_PIX_TUNE_FUSED_CAP      blocks per SM of the fused emission inside that pipeline, so that it leaves room
+ *                              for the next chunk's statistics pass, 0..32 (default 0: its occupancy limit)
  *   DP_PIX_TUNE_WAIT_TRIES     tries of the release kernels' bounded waits for their staged rows before a
  *                              wait gives up with DP_PIX_E_TIMEOUT (through dp_pix_status), 1..2^22
  *                              (default 2^22, seconds: far beyond any copy's latency)
@@ -179,6 +183,7 @@ DPPIX_API int dp_pix_plan_destroy(dp_pix_plan_t plan);
 #define DP_PIX_TUNE_FUSED_PX 1
 #define DP_PIX_TUNE_FUSED_THREADS 2
 #define DP_PIX_TUNE_SPLIT 4
+#define DP_PIX_TUNE_FUSED_CAP 32
 #define DP_PIX_TUNE_WAIT_TRIES 8
 #define DP_PIX_TUNE_TEST_SHORT_TX 16
 DPPIX_API int dp_pix_plan_tune(dp_pix_plan_t plan, int knob, int value);

@@ -22,7 +22,7 @@ PAD_REFLECT, PAD_SYMMETRIC, PAD_NONE = 0, 1, 2
 SRC_TILE_LABELS, SRC_MASK_U8, SRC_MATTE_F32, SRC_VARIANCE = 0, 1, 2, 3
 REC_F32, REC_U8, REC_SUM_U32 = 0, 1, 2
 OUT_U8, OUT_F32 = 0, 1
-TUNE_FUSED_PX, TUNE_FUSED_THREADS, TUNE_SPLIT, TUNE_WAIT_TRIES, TUNE_TEST_SHORT_TX = 1, 2, 4, 8, 16
+TUNE_FUSED_PX, TUNE_FUSED_THREADS, TUNE_SPLIT, TUNE_WAIT_TRIES, TUNE_TEST_SHORT_TX, TUNE_FUSED_CAP = 1, 2, 4, 8, 16, 32
 BATCH_PATH_STAGED, BATCH_PATH_STREAM, BATCH_PATH_STREAM_FUSED = 0, 1, 2
 
 

@@ -286,6 +286,7 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     g.fused_px = 1024;
     g.fused_threads = 128;
     g.split = 1;
+    g.fused_cap = 0;
     g.wait_tries = kWaitTries;
     g.test_short_tx = 0;
     // staged segment: S tiles of one tile row, S*T*C a multiple of 16 when possible
@@ -404,8 +405,12 @@ int dp_pix_plan_tune(dp_pix_plan_t plan, int knob, int value) {
             plan->g.fused_threads = value;
             return DP_PIX_OK;
         case DP_PIX_TUNE_SPLIT:
-            if (value < 1 || value > 8) return fail(DP_PIX_E_INVALID_ARG, "split must be 1..8");
+            if (value < 1 || value > kMaxSplit) return fail(DP_PIX_E_INVALID_ARG, "split must be 1..%d", kMaxSplit);
             plan->g.split = value;
+            return DP_PIX_OK;
+        case DP_PIX_TUNE_FUSED_CAP:
+            if (value < 0 || value > 32) return fail(DP_PIX_E_INVALID_ARG, "fused blocks per SM must be 0..32");
+            plan->g.fused_cap = value;
             return DP_PIX_OK;
         case DP_PIX_TUNE_WAIT_TRIES:
             if (value < 1 || value > (int)kWaitTries) return fail(DP_PIX_E_INVALID_ARG, "wait tries must be 1..%u", kWaitTries);
@@ -427,6 +432,7 @@ int dp_pix_plan_tuning(dp_pix_plan_t plan, int knob, int *value) {
         case DP_PIX_TUNE_FUSED_PX: *value = plan->g.fused_px; return DP_PIX_OK;
         case DP_PIX_TUNE_FUSED_THREADS: *value = plan->g.fused_threads; return DP_PIX_OK;
         case DP_PIX_TUNE_SPLIT: *value = plan->g.split; return DP_PIX_OK;
+        case DP_PIX_TUNE_FUSED_CAP: *value = plan->g.fused_cap; return DP_PIX_OK;
         case DP_PIX_TUNE_WAIT_TRIES: *value = (int)plan->g.wait_tries; return DP_PIX_OK;
         case DP_PIX_TUNE_TEST_SHORT_TX: *value = plan->g.test_short_tx ? 1 : 0; return DP_PIX_OK;
         default: return fail(DP_PIX_E_INVALID_ARG, "unknown knob %d", knob);
@@ -443,6 +449,8 @@ struct FusedOut {
     int64_t frame_stride, pitch;
     int type, align;
     bool fused;
+    int stage;       // variance classes: 0 everything, 1 statistics and rank only, 2 the emission only
+    int max_per_sm;  // blocks per SM of the fused kernel (0: its occupancy limit)
 };
 
 int release_impl(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride, const void *d_region_src,
@@ -512,10 +520,14 @@ int release_impl(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
             if (e == cudaSuccess) e = launch_release(g, a, s);
             break;
         case DP_PIX_SRC_VARIANCE:
-            e = launch_tile_stats(g, a, s);
-            if (e == cudaSuccess) e = launch_rank(g, a, s);
+            if (!fo || fo->stage != 2) {
+                e = launch_tile_stats(g, a, s);
+                if (e == cudaSuccess) e = launch_rank(g, a, s);
+            }
+            if (fo && fo->stage == 1) break;
             if (e == cudaSuccess && g.var_onepass && fo) {
-                e = launch_emit_recon(g, a, fo->out, fo->frame_stride, fo->pitch, fo->type, fo->align, s);
+                e = launch_emit_recon(g, a, fo->out, fo->frame_stride, fo->pitch, fo->type, fo->align, fo->max_per_sm,
+                                      s);
                 fo->fused = e == cudaSuccess;
                 if (e == cudaErrorNotSupported) e = launch_emit(g, a, s);
             } else if (e == cudaSuccess) {
@@ -576,6 +588,7 @@ int release_reconstruct_impl(dp_pix_plan_t plan, const void *d_frames, int64_t f
     while (align > 1 &&
            ((uintptr_t)d_out % align || out_pitch % align || (n_frames > 1 && out_frame_stride % align)))
         align >>= 1;
+    int stage = 0, max_per_sm = 0;
     auto run = [&](uint32_t f0, uint32_t nf, cudaStream_t st) -> int {
         const uint8_t *fr = static_cast<const uint8_t *>(d_frames) + (uint64_t)f0 * (uint64_t)frame_stride;
         const uint8_t *src = d_region_src ? static_cast<const uint8_t *>(d_region_src) + (uint64_t)f0 * src_frame_stride
@@ -584,41 +597,48 @@ int release_reconstruct_impl(dp_pix_plan_t plan, const void *d_frames, int64_t f
         uint8_t *ws = static_cast<uint8_t *>(d_ws) + (uint64_t)f0 * g.ws_per_frame;
         uint8_t *out = static_cast<uint8_t *>(d_out) + (uint64_t)f0 * (uint64_t)out_frame_stride;
         const uint64_t wsb = ws_bytes >= (uint64_t)f0 * g.ws_per_frame ? ws_bytes - (uint64_t)f0 * g.ws_per_frame : 0;
-        FusedOut fo{out, nf > 1 ? out_frame_stride : 0, out_pitch, out_type, align, false};
+        FusedOut fo{out, nf > 1 ? out_frame_stride : 0, out_pitch, out_type, align, false, stage, max_per_sm};
         int rc = release_impl(plan, fr, frame_stride, src, src_pitch, src_frame_stride, nf, stream_id, frame_idx0 + f0,
                               rec, record_stride, ws, wsb, st, &fo, keys ? keys + f0 : nullptr);
-        if (rc || fo.fused) return rc;
+        if (rc || fo.fused || stage == 1) return rc;
         return dp_pix_reconstruct(rec, record_stride, nf, out, out_frame_stride, out_pitch, out_type, g.M, g.N, g.C, st);
     };
     cudaStream_t caller = static_cast<cudaStream_t>(cuda_stream);
     const int split = g.split;
-    if (split <= 1 || n_frames < 2u * (uint32_t)split) return run(0, n_frames, caller);
-    // frames in `split` chunks on the library's side streams, so that one chunk's latency-bound steps (the
-    // frame-wide rank) overlap another chunk's bandwidth-bound ones; forked from and joined to the caller's
-    // stream with events
-    cudaStream_t *side = side_streams(split);
-    if (!side) return fail(DP_PIX_E_CUDA, "side streams unavailable");
-    cudaEvent_t fork = nullptr;
-    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(fork, caller);
-    if (e != cudaSuccess) return cuda_fail(e, "split fork");
-    int rc = DP_PIX_OK;
+    if (split <= 1 || n_frames < 2u * (uint32_t)split || g.source != DP_PIX_SRC_VARIANCE) return run(0, n_frames, caller);
+    // a pipeline over `split` chunks of frames: the statistics and rank of every chunk run in order on the
+    // caller's stream, and each chunk's emission (records and images) on a side stream as soon as its rank is
+    // done, with the fused kernel held to fused_cap blocks per SM -- so that a chunk's issue-bound emission
+    // shares the SMs with the next chunk's bandwidth-bound statistics pass
+    cudaStream_t *side = side_streams(1);
+    if (!side) return fail(DP_PIX_E_CUDA, "side stream unavailable");
+    cudaEvent_t ev[kMaxSplit + 1] = {};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i <= split && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[split], caller);  // the side stream starts after the caller's work
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side[0], ev[split], 0);
+    int rc = e == cudaSuccess ? DP_PIX_OK : cuda_fail(e, "pipeline fork");
     for (int i = 0; i < split && rc == DP_PIX_OK; ++i) {
         const uint32_t f0 = (uint32_t)((uint64_t)n_frames * i / split), f1 = (uint32_t)((uint64_t)n_frames * (i + 1) / split);
-        e = cudaStreamWaitEvent(side[i], fork, 0);
+        stage = 1;
+        rc = run(f0, f1 - f0, caller);
+        if (rc) break;
+        e = cudaEventRecord(ev[i], caller);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side[0], ev[i], 0);
         if (e != cudaSuccess) {
-            rc = cuda_fail(e, "split wait");
+            rc = cuda_fail(e, "pipeline event");
             break;
         }
-        rc = run(f0, f1 - f0, side[i]);
-        cudaEvent_t join = nullptr;
-        e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventRecord(join, side[i]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, join, 0);
-        if (join) cudaEventDestroy(join);
-        if (e != cudaSuccess && rc == DP_PIX_OK) rc = cuda_fail(e, "split join");
+        stage = 2;
+        max_per_sm = g.fused_cap;
+        rc = run(f0, f1 - f0, side[0]);
     }
-    cudaEventDestroy(fork);
+    // join: the caller's stream waits for the last emission
+    e = cudaEventRecord(ev[split], side[0]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, ev[split], 0);
+    if (e != cudaSuccess && rc == DP_PIX_OK) rc = cuda_fail(e, "pipeline join");
+    for (int i = 0; i <= split; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
     return rc;
 }
 

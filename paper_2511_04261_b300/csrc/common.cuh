@@ -18,6 +18,7 @@ constexpr int kMaxRankTiles = 16384;     // VARIANCE: tiles of one frame ranked 
 constexpr int kFinalizeSmemTiles = 200000;  // frames up to this many tiles finalise their map in shared memory
 constexpr int kMaxFrameTiles = 1 << 25;      // tiles of one frame (larger maps are finalised from global memory)
 constexpr uint32_t kWaitTries = 1u << 22;     // default tries of a bounded mbarrier wait
+constexpr int kMaxSplit = 16;                 // frame chunks of a pipelined release + reconstruction
 constexpr int kHeaderBytes = DP_PIX_RECORD_HEADER_BYTES;
 
 // Geometry and constants of a plan (Alg. 2 steps 1-3, Alg. 3 steps 1-2, Eq. 11).
@@ -54,7 +55,8 @@ struct Geom {
     int32_t seg_rowstride;            // bytes per staged row (multiple of 16)
     int32_t vbands;                   // max bands of a staged tile = T / b_min (or T / g for stats)
     int32_t fused_px, fused_threads;  // launch shape of the fused release + reconstruction (tunable)
-    int32_t split;                    // frame chunks of a fused call run on side streams (tunable)
+    int32_t split;                    // frame chunks of a fused call's pipeline (tunable)
+    int32_t fused_cap;                // blocks per SM of the fused kernel inside that pipeline (0: occupancy)
     uint32_t wait_tries;              // tries of a bounded mbarrier wait before it gives up (tunable)
     uint32_t test_short_tx;           // test knob: bytes announced beyond what a CTA's first item delivers
     // release work units (k_release): a b_r x b_r cell is summed by 2^rel_lp[r] adjacent lanes (row parts);
@@ -290,7 +292,8 @@ cudaError_t launch_tile_stats_fast(const Geom &g, const CallArgs &a, cudaStream_
 cudaError_t launch_rank(const Geom &g, const CallArgs &a, cudaStream_t s);
 cudaError_t launch_emit(const Geom &g, const CallArgs &a, cudaStream_t s);
 cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, int64_t out_frame_stride,
-                              int64_t out_pitch, int out_type, int out_align, cudaStream_t s);  // NotSupported: fall back
+                              int64_t out_pitch, int out_type, int out_align, int max_per_sm,
+                              cudaStream_t s);  // NotSupported: fall back; max_per_sm 0: occupancy limit
 cudaError_t launch_reconstruct(const uint8_t *records, int64_t record_stride, uint32_t n, uint8_t *out,
                                int64_t out_frame_stride, int64_t out_pitch, int out_type, int max_M, int max_N,
                                int max_C, int out_align, int32_t *status, cudaStream_t s);

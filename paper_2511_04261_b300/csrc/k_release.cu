@@ -1046,11 +1046,12 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
 
 template <int C, int kOutF32, int kThr>
 cudaError_t launch_er(const Geom &g, const CallArgs &a, uint8_t *out, int64_t ofs, int64_t op, const FusedShape &fs,
-                      cudaStream_t s) {
+                      int max_per_sm, cudaStream_t s) {
     auto kern = k_emit_recon<C, kOutF32, kThr>;
 
     const uint32_t items = a.n_frames * (uint32_t)g.GR * (uint32_t)((g.GC + fs.seg - 1) / fs.seg);
-    const int per_sm = launch_prep(reinterpret_cast<const void *>(kern), kThr, fs.smem);
+    int per_sm = launch_prep(reinterpret_cast<const void *>(kern), kThr, fs.smem);
+    if (max_per_sm > 0 && max_per_sm < per_sm) per_sm = max_per_sm;
     const uint64_t cap = (uint64_t)per_sm * (uint64_t)sm_count();
     const int grid = (int)(items < cap ? items : cap);
     const char *name = kOutF32 ? "k_emit_recon_f32" : "k_emit_recon_u8";
@@ -1152,7 +1153,7 @@ int gcd_int(int a, int b) {
 // the largest whole number of tiles with at most fused_px pixel columns whose output bytes and g-image
 // bytes both start on 16-byte boundaries.
 cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, int64_t out_frame_stride,
-                              int64_t out_pitch, int out_type, int out_align, cudaStream_t s) {
+                              int64_t out_pitch, int out_type, int out_align, int max_per_sm, cudaStream_t s) {
     const int oes = out_type == DP_PIX_OUT_F32 ? 4 : 1;
     const int trb = g.T * g.C * oes;
     if (!g.var_onepass || out_align != 16 || trb < 16 || (reinterpret_cast<uintptr_t>(a.ws) & 15) != 0)
@@ -1184,10 +1185,10 @@ cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, in
     const int thr = g.fused_threads;
 #define DPPIX_ER(CC, F)                                                                        \
     switch (thr) {                                                                             \
-        case 96: return launch_er<CC, F, 96>(g, a, out, out_frame_stride, out_pitch, fs, s);   \
-        case 192: return launch_er<CC, F, 192>(g, a, out, out_frame_stride, out_pitch, fs, s); \
-        case 256: return launch_er<CC, F, 256>(g, a, out, out_frame_stride, out_pitch, fs, s); \
-        default: return launch_er<CC, F, 128>(g, a, out, out_frame_stride, out_pitch, fs, s);  \
+        case 96: return launch_er<CC, F, 96>(g, a, out, out_frame_stride, out_pitch, fs, max_per_sm, s);   \
+        case 192: return launch_er<CC, F, 192>(g, a, out, out_frame_stride, out_pitch, fs, max_per_sm, s); \
+        case 256: return launch_er<CC, F, 256>(g, a, out, out_frame_stride, out_pitch, fs, max_per_sm, s); \
+        default: return launch_er<CC, F, 128>(g, a, out, out_frame_stride, out_pitch, fs, max_per_sm, s);  \
     }
     if (oes == 4) {
         switch (g.C) {

@@ -129,8 +129,11 @@ def test_plan_tuning_knobs():
     assert plan.tuning(P.TUNE_SPLIT) == 1
     plan.tune(P.TUNE_SPLIT, 4)
     assert plan.tuning(P.TUNE_SPLIT) == 4
+    assert plan.tuning(P.TUNE_FUSED_CAP) == 0
+    plan.tune(P.TUNE_FUSED_CAP, 3)
+    assert plan.tuning(P.TUNE_FUSED_CAP) == 3
     for knob, bad in [(P.TUNE_FUSED_PX, 63), (P.TUNE_FUSED_PX, 4096), (P.TUNE_FUSED_THREADS, 160),
-                      (P.TUNE_SPLIT, 0), (P.TUNE_SPLIT, 9), (99, 1)]:
+                      (P.TUNE_SPLIT, 0), (P.TUNE_SPLIT, 17), (P.TUNE_FUSED_CAP, -1), (P.TUNE_FUSED_CAP, 33), (99, 1)]:
         with pytest.raises(P.DppixError) as e:
             plan.tune(knob, bad)
         assert e.value.code == _lib.E_INVALID_ARG

@@ -497,8 +497,8 @@ def test_release_reconstruct_config2_sampled():
 
 @pytest.mark.parametrize("ot", [P.OUT_U8, P.OUT_F32])
 def test_release_reconstruct_launch_shapes_do_not_change_results(ot):
-    """Every fused launch shape (pixel columns per item, threads per block, frame chunks on side streams)
-    gives the same bytes."""
+    """Every fused launch shape (pixel columns per item, threads per block, frame chunks pipelined between the
+    caller's stream and a side stream, blocks per SM of the fused kernel) gives the same bytes."""
     F, M, N = 8, 200, 352
     rng = np.random.default_rng(17)
     imgs = rng.integers(0, 256, size=(F, M, N, 3), dtype=np.uint8)
@@ -507,10 +507,12 @@ def test_release_reconstruct_launch_shapes_do_not_change_results(ot):
               seed=23, m=16)
     t = torch.from_numpy(imgs).cuda()
     base = None
-    for px, thr, split in [(64, 128, 1), (96, 256, 2), (512, 128, 4), (512, 256, 1), (1024, 128, 3),
-                           (2048, 256, 4), (2048, 128, 1), (960, 192, 1), (640, 96, 2)]:
+    for px, thr, split, cap in [(64, 128, 1, 0), (96, 256, 2, 1), (512, 128, 4, 2), (512, 256, 1, 0),
+                                (1024, 128, 3, 0), (2048, 256, 4, 3), (2048, 128, 1, 0), (960, 192, 1, 0),
+                                (640, 96, 2, 4), (1024, 128, 8, 1)]:
         if True:
-            plan = P.Plan(**kw).tune(P.TUNE_FUSED_PX, px).tune(P.TUNE_FUSED_THREADS, thr).tune(P.TUNE_SPLIT, split)
+            plan = (P.Plan(**kw).tune(P.TUNE_FUSED_PX, px).tune(P.TUNE_FUSED_THREADS, thr).tune(P.TUNE_SPLIT, split)
+                    .tune(P.TUNE_FUSED_CAP, cap))
             recs, img = plan.release_reconstruct(t, out_type=ot)
             torch.cuda.synchronize()
             assert P.dp_pix_status() == 0
@@ -521,5 +523,5 @@ def test_release_reconstruct_launch_shapes_do_not_change_results(ot):
                     exp = O.reconstruct(np.frombuffer(got[0][i], np.uint8), 0 if ot == P.OUT_U8 else 1)
                     assert np.array_equal(got[1][i], exp)
             else:
-                assert got[0] == base[0], (px, thr, split)
-                assert np.array_equal(got[1], base[1]), (px, thr, split)
+                assert got[0] == base[0], (px, thr, split, cap)
+                assert np.array_equal(got[1], base[1]), (px, thr, split, cap)
