@@ -178,6 +178,11 @@ DPPIX_API int dp_pix_plan_destroy(dp_pix_plan_t plan);
  *                              wait runs out: the call reports DP_PIX_E_TIMEOUT and its records are
  *                              undefined; every copy still lands, and the device stays usable.  0: off
  *                              (default).
+ *   DP_PIX_TUNE_TEST_SHRINK    bytes (0..2^20) taken off the records' extent that the bounds-checked build
+ *                              (libdppix_checked.so) checks the record writes against, so that a test can make
+ *                              a check fire while every access stays inside the real buffer: the writes past
+ *                              the shrunken extent are skipped and DP_PIX_E_DEVICE (detail 0x601) is raised.
+ *                              No effect in the normal build.  0: off (default).
  * dp_pix_plan_tune returns INVALID_ARG for an unknown knob or a value out of range; dp_pix_plan_tuning
  * writes the current value to *value. */
 #define DP_PIX_TUNE_FUSED_PX 1
@@ -186,6 +191,7 @@ DPPIX_API int dp_pix_plan_destroy(dp_pix_plan_t plan);
 #define DP_PIX_TUNE_FUSED_CAP 32
 #define DP_PIX_TUNE_WAIT_TRIES 8
 #define DP_PIX_TUNE_TEST_SHORT_TX 16
+#define DP_PIX_TUNE_TEST_SHRINK 64
 DPPIX_API int dp_pix_plan_tune(dp_pix_plan_t plan, int knob, int value);
 DPPIX_API int dp_pix_plan_tuning(dp_pix_plan_t plan, int knob, int *value);
 

@@ -8,7 +8,8 @@ import os
 
 MAXK = 8
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdppix.so")
+# DPPIX_CHECKED=1 loads the bounds-checked build (every checked device access tested against its buffer)
+LIB_PATH = os.path.join(HERE, "libdppix_checked.so" if os.environ.get("DPPIX_CHECKED") == "1" else "libdppix.so")
 
 OK = 0
 E_INVALID_ARG, E_UNSUPPORTED, E_PAD_TOO_LARGE, E_BUFFER_TOO_SMALL = -1, -2, -3, -4
@@ -23,6 +24,7 @@ SRC_TILE_LABELS, SRC_MASK_U8, SRC_MATTE_F32, SRC_VARIANCE = 0, 1, 2, 3
 REC_F32, REC_U8, REC_SUM_U32 = 0, 1, 2
 OUT_U8, OUT_F32 = 0, 1
 TUNE_FUSED_PX, TUNE_FUSED_THREADS, TUNE_SPLIT, TUNE_WAIT_TRIES, TUNE_TEST_SHORT_TX, TUNE_FUSED_CAP = 1, 2, 4, 8, 16, 32
+TUNE_TEST_SHRINK = 64
 BATCH_PATH_STAGED, BATCH_PATH_STREAM, BATCH_PATH_STREAM_FUSED = 0, 1, 2
 
 

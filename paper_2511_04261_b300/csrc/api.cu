@@ -289,6 +289,7 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     g.fused_cap = 0;
     g.wait_tries = kWaitTries;
     g.test_short_tx = 0;
+    g.test_shrink = 0;
     // staged segment: S tiles of one tile row, S*T*C a multiple of 16 when possible
     int s0 = 16 / (int)gcd64(TC, 16);
     int S = s0 * (int)((384 + (int64_t)s0 * TC - 1) / ((int64_t)s0 * TC));
@@ -358,6 +359,7 @@ int dp_pix_version(void) { return 10000; }
 const char *dp_pix_last_error(void) { return t_err; }
 
 int dp_pix_plan(const dp_pix_desc *d, dp_pix_plan_t *out, dp_pix_sizes *sz) {
+    DPPIX_RANGE();
     t_err[0] = 0;
     if (!out) return fail(DP_PIX_E_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -420,6 +422,10 @@ int dp_pix_plan_tune(dp_pix_plan_t plan, int knob, int value) {
             if (value != 0 && value != 1) return fail(DP_PIX_E_INVALID_ARG, "the short-copy test knob is 0 or 1");
             plan->g.test_short_tx = value ? 16u : 0u;
             return DP_PIX_OK;
+        case DP_PIX_TUNE_TEST_SHRINK:
+            if (value < 0 || value > (1 << 20)) return fail(DP_PIX_E_INVALID_ARG, "the shrink test knob is 0..2^20");
+            plan->g.test_shrink = (uint32_t)value;
+            return DP_PIX_OK;
         default:
             return fail(DP_PIX_E_INVALID_ARG, "unknown knob %d", knob);
     }
@@ -435,6 +441,7 @@ int dp_pix_plan_tuning(dp_pix_plan_t plan, int knob, int *value) {
         case DP_PIX_TUNE_FUSED_CAP: *value = plan->g.fused_cap; return DP_PIX_OK;
         case DP_PIX_TUNE_WAIT_TRIES: *value = (int)plan->g.wait_tries; return DP_PIX_OK;
         case DP_PIX_TUNE_TEST_SHORT_TX: *value = plan->g.test_short_tx ? 1 : 0; return DP_PIX_OK;
+        case DP_PIX_TUNE_TEST_SHRINK: *value = (int)plan->g.test_shrink; return DP_PIX_OK;
         default: return fail(DP_PIX_E_INVALID_ARG, "unknown knob %d", knob);
     }
 }
@@ -497,6 +504,11 @@ int release_impl(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
     a.ws = static_cast<uint8_t *>(d_ws);
     a.status = status_word();
     a.keys = keys;
+    a.frames_bytes = (uint64_t)(n_frames - 1) * (uint64_t)(n_frames > 1 ? frame_stride : 0) +
+                     (uint64_t)(g.M - 1) * (uint64_t)g.pitch + (uint64_t)g.N * g.C;
+    a.records_bytes = (uint64_t)n_frames * (uint64_t)record_stride;
+    if (g.test_shrink) a.records_bytes = a.records_bytes > g.test_shrink ? a.records_bytes - g.test_shrink : 0;
+    a.ws_bytes = ws_bytes;
     const uintptr_t base = (uintptr_t)d_frames;
     const int64_t fs = n_frames > 1 ? frame_stride : 0;
     const int64_t seg_bytes = (int64_t)g.seg_tiles * g.T * g.C;
@@ -549,6 +561,7 @@ int dp_pix_release(dp_pix_plan_t plan, const void *d_frames, int64_t frame_strid
                    int64_t src_pitch, int64_t src_frame_stride, uint32_t n_frames, uint32_t stream_id,
                    uint64_t frame_idx0, void *d_records, int64_t record_stride, void *d_ws, uint64_t ws_bytes,
                    void *cuda_stream) {
+    DPPIX_RANGE();
     t_err[0] = 0;
     return release_impl(plan, d_frames, frame_stride, d_region_src, src_pitch, src_frame_stride, n_frames, stream_id,
                         frame_idx0, d_records, record_stride, d_ws, ws_bytes, cuda_stream, nullptr);
@@ -557,6 +570,7 @@ int dp_pix_release(dp_pix_plan_t plan, const void *d_frames, int64_t frame_strid
 int dp_pix_release_keyed(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride, const void *d_region_src,
                          int64_t src_pitch, int64_t src_frame_stride, uint32_t n_frames, const dp_pix_frame_key *d_keys,
                          void *d_records, int64_t record_stride, void *d_ws, uint64_t ws_bytes, void *cuda_stream) {
+    DPPIX_RANGE();
     t_err[0] = 0;
     if (n_frames > 0 && !d_keys) return fail(DP_PIX_E_INVALID_ARG, "keys are required");
     return release_impl(plan, d_frames, frame_stride, d_region_src, src_pitch, src_frame_stride, n_frames, 0, 0,
@@ -651,6 +665,7 @@ int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frames, int64_t
                                uint32_t n_frames, uint32_t stream_id, uint64_t frame_idx0, void *d_records,
                                int64_t record_stride, void *d_out, int64_t out_frame_stride, int64_t out_pitch,
                                int out_type, void *d_ws, uint64_t ws_bytes, void *cuda_stream) {
+    DPPIX_RANGE();
     t_err[0] = 0;
     return release_reconstruct_impl(plan, d_frames, frame_stride, d_region_src, src_pitch, src_frame_stride, n_frames,
                                     stream_id, frame_idx0, nullptr, d_records, record_stride, d_out, out_frame_stride,
@@ -662,6 +677,7 @@ int dp_pix_release_reconstruct_keyed(dp_pix_plan_t plan, const void *d_frames, i
                                      uint32_t n_frames, const dp_pix_frame_key *d_keys, void *d_records,
                                      int64_t record_stride, void *d_out, int64_t out_frame_stride, int64_t out_pitch,
                                      int out_type, void *d_ws, uint64_t ws_bytes, void *cuda_stream) {
+    DPPIX_RANGE();
     t_err[0] = 0;
     if (n_frames > 0 && !d_keys) return fail(DP_PIX_E_INVALID_ARG, "keys are required");
     return release_reconstruct_impl(plan, d_frames, frame_stride, d_region_src, src_pitch, src_frame_stride, n_frames,
@@ -671,6 +687,7 @@ int dp_pix_release_reconstruct_keyed(dp_pix_plan_t plan, const void *d_frames, i
 
 int dp_pix_store(const void *d_record, void *dst, uint64_t cap, uint64_t *written, int dst_is_host,
                  void *cuda_stream) {
+    DPPIX_RANGE();
     t_err[0] = 0;
     if (!d_record || !dst) return fail(DP_PIX_E_INVALID_ARG, "record and destination are required");
     int rc = check_cuda_device();
@@ -693,6 +710,7 @@ int dp_pix_store(const void *d_record, void *dst, uint64_t cap, uint64_t *writte
 
 int dp_pix_store_batch(const void *d_records, int64_t record_stride, uint32_t n, void *h_dst, int64_t dst_stride,
                        uint64_t *written, void *cuda_stream) {
+    DPPIX_RANGE();
     t_err[0] = 0;
     if (n == 0) return DP_PIX_OK;
     if (!d_records || !h_dst) return fail(DP_PIX_E_INVALID_ARG, "records and destination are required");
@@ -729,6 +747,7 @@ int dp_pix_store_batch(const void *d_records, int64_t record_stride, uint32_t n,
 int dp_pix_reconstruct(const void *d_records, int64_t record_stride, uint32_t n_records, void *d_out,
                        int64_t out_frame_stride, int64_t out_pitch, int out_type, int32_t max_M, int32_t max_N,
                        int32_t max_C, void *cuda_stream) {
+    DPPIX_RANGE();
     t_err[0] = 0;
     if (n_records == 0) return DP_PIX_OK;
     if (!d_records || !d_out) return fail(DP_PIX_E_INVALID_ARG, "records and output are required");
@@ -757,6 +776,7 @@ int dp_pix_reconstruct(const void *d_records, int64_t record_stride, uint32_t n_
 
 int dp_pix_debug_noise(uint64_t seed, const uint32_t *d_ctr, uint64_t n, uint32_t *d_words, float *d_eta, float sigma,
                        void *cuda_stream) {
+    DPPIX_RANGE();
     t_err[0] = 0;
     if (n == 0) return DP_PIX_OK;
     if (!d_ctr) return fail(DP_PIX_E_INVALID_ARG, "counters are required");
@@ -768,6 +788,7 @@ int dp_pix_debug_noise(uint64_t seed, const uint32_t *d_ctr, uint64_t n, uint32_
 }
 
 int dp_pix_status(void *cuda_stream, uint32_t *detail) {
+    DPPIX_RANGE();
     t_err[0] = 0;
     int rc = check_cuda_device();
     if (rc) return rc;

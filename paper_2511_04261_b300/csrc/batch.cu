@@ -134,6 +134,9 @@ int build_table(dp_pix_batch_s *b, const dp_pix_batch_image *imgs, int out_type)
         a.record_stride = (int64_t)((g.record_cap + 15) / 16 * 16);
         a.ws = b->d_ws + b->ws_off[i];
         a.status = st;
+        a.frames_bytes = (uint64_t)(g.M - 1) * (uint64_t)g.pitch + (uint64_t)g.N * g.C;
+        a.records_bytes = (g.record_cap + 15) / 16 * 16;
+        a.ws_bytes = g.ws_per_frame;
         const uintptr_t base = (uintptr_t)im.frame;
         const int64_t seg_bytes = (int64_t)g.seg_tiles * g.T * g.C;
         a.vec = (base % 16 == 0 && g.pitch % 16 == 0 && seg_bytes % 16 == 0) ? 16
@@ -200,6 +203,7 @@ cudaError_t launch_all(dp_pix_batch_s *b, cudaStream_t s) {
 extern "C" {
 
 int dp_pix_batch_plan(const dp_pix_desc *common, const int32_t *M, const int32_t *N, uint32_t n, dp_pix_batch_t *out) {
+    DPPIX_RANGE();
     if (!common || !M || !N || !out) return bfail(DP_PIX_E_INVALID_ARG, "null argument");
     *out = nullptr;
     if (n < 1 || n > (1u << 20)) return bfail(DP_PIX_E_INVALID_ARG, "batch size must be 1..2^20");
@@ -257,6 +261,7 @@ int dp_pix_batch_sizes(dp_pix_batch_t b, uint64_t *record_bytes, uint64_t *ws_by
 
 int dp_pix_batch_bind(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int out_type, void *d_ws, uint64_t ws_bytes,
                       void *cuda_stream) {
+    DPPIX_RANGE();
     if (!b || !imgs) return bfail(DP_PIX_E_INVALID_ARG, "batch or images NULL");
     if (out_type != DP_PIX_OUT_U8 && out_type != DP_PIX_OUT_F32) return bfail(DP_PIX_E_INVALID_ARG, "bad out_type");
     if (!d_ws || (uintptr_t)d_ws % 256) return bfail(DP_PIX_E_INVALID_ARG, "workspace must be 256-byte aligned");
@@ -277,6 +282,7 @@ int dp_pix_batch_bind(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int out_
 }
 
 int dp_pix_batch_run(dp_pix_batch_t b, int use_graph, void *cuda_stream) {
+    DPPIX_RANGE();
     if (!b || !b->bound) return bfail(DP_PIX_E_INVALID_ARG, "batch not bound");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     if (!use_graph) {
@@ -315,6 +321,7 @@ int dp_pix_batch_run(dp_pix_batch_t b, int use_graph, void *cuda_stream) {
 }
 
 int dp_pix_batch_autotune(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int reps, void *cuda_stream) {
+    DPPIX_RANGE();
     if (!b || !b->bound || !imgs) return bfail(DP_PIX_E_INVALID_ARG, "batch not bound or images NULL");
     if (reps < 1) reps = 1;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "dppix.h"
@@ -59,6 +60,7 @@ struct Geom {
     int32_t fused_cap;                // blocks per SM of the fused kernel inside that pipeline (0: occupancy)
     uint32_t wait_tries;              // tries of a bounded mbarrier wait before it gives up (tunable)
     uint32_t test_short_tx;           // test knob: bytes announced beyond what a CTA's first item delivers
+    uint32_t test_shrink;             // test knob: bytes taken off the records extent the checked build sees
     // release work units (k_release): a b_r x b_r cell is summed by 2^rel_lp[r] adjacent lanes (row parts);
     // a tile of region r is rel_units[r] units, a multiple of rel_pmax (the largest part count)
     int32_t rel_lp[kMaxK];
@@ -98,6 +100,8 @@ struct CallArgs {
     int32_t vec;                      // widest safe global load for frame rows: 16, 4 or 1 bytes
     int32_t *status;                  // device status word
     const dp_pix_frame_key *keys;     // per-frame (stream id, frame index), or NULL: stream_id, frame_idx0 + f
+    // extents of the call's buffers from frames / records / ws (what the bounds-checked build checks against)
+    uint64_t frames_bytes, records_bytes, ws_bytes;
 };
 
 // Noise key of frame f of a call: its stream id and frame index.
@@ -282,6 +286,25 @@ __device__ __forceinline__ void raise_status(int32_t *st, int32_t code, uint32_t
     if (st != nullptr && atomicCAS(reinterpret_cast<int *>(st), 0, code) == 0) st[1] = (int32_t)detail;
 }
 
+// Bounds-checked build (compiled with DPPIX_CHECKED, libdppix_checked.so): the release, fused, statistics,
+// reconstruction and batch kernels check their global accesses of these kinds against the extent of the
+// buffer they belong to; an access outside is skipped and raises DP_PIX_E_DEVICE with detail 0x600 | site.
+// In the normal build chk() is a constant true and costs nothing.
+enum ChkSite : uint32_t { kChkRecord = 1, kChkFrame = 2, kChkWorkspace = 3, kChkOutput = 4 };
+#ifdef DPPIX_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+__device__ __forceinline__ bool chk(const void *p, uint64_t n, const void *base, uint64_t extent, int32_t *status,
+                                    uint32_t site) {
+    if (!kChecked) return true;
+    const uintptr_t x = reinterpret_cast<uintptr_t>(p), b = reinterpret_cast<uintptr_t>(base);
+    if (x >= b && x - b <= extent && n <= extent - (x - b)) return true;
+    raise_status(status, DP_PIX_E_DEVICE, 0x600u | site);
+    return false;
+}
+
 // Launchers (one per kernel file); return cudaError_t of the launch.
 cudaError_t launch_classify(const Geom &g, const CallArgs &a, cudaStream_t s);
 cudaError_t launch_finalize_labels(const Geom &g, const CallArgs &a, cudaStream_t s);
@@ -318,6 +341,16 @@ cudaError_t launch_batch_reconstruct(const BatchEntry *tab, uint32_t n_img, uint
                                      int out_align, int32_t *status, cudaStream_t s);
 cudaError_t launch_debug_noise(uint64_t seed, const uint32_t *ctr, uint64_t n, uint32_t *words, float *eta,
                                float sigma, cudaStream_t s);
+
+// An NVTX range for the duration of a library call (host side; profilers such as Nsight show the calls on
+// the timeline and can filter kernels by them).  Costs a branch when no profiler is attached.
+struct ApiRange {
+    explicit ApiRange(const char *name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+    ApiRange(const ApiRange &) = delete;
+    ApiRange &operator=(const ApiRange &) = delete;
+};
+#define DPPIX_RANGE() ::dppix::ApiRange dppix_api_range_(__func__)
 
 // Host-side launch accounting (api.cu).
 void prof_begin(const char *name, cudaStream_t s);

@@ -390,7 +390,9 @@ __global__ void __launch_bounds__(kBsThreads, 3) k_brel_stream(const BatchEntry 
                 }
                 uint8_t *dst = rec + toff_s[t] + (uint64_t)c * C * g.es;
                 float ov[4] = {0.f, 0.f, 0.f, 0.f};
-                if (n == 0) {  // wholly outside the frame: no sample, stored as 0
+                if (!chk(dst, (uint64_t)C * g.es, a.records, a.records_bytes, a.status, kChkRecord)) {
+                    // bounds-checked build: a write outside the record is skipped
+                } else if (n == 0) {  // wholly outside the frame: no sample, stored as 0
 #pragma unroll
                     for (int chn = 0; chn < C; ++chn) {
                         if (g.es == 4) reinterpret_cast<uint32_t *>(dst)[chn] = 0u;
@@ -467,7 +469,11 @@ __global__ void __launch_bounds__(kBsThreads, 3) k_brel_stream(const BatchEntry 
                     if (f0 + 16 > 0 && f0 < VB) {
                         const uint4 d = o2 ? window16(prev, vec, 16 - o2) : vec;
                         uint8_t *gp = reinterpret_cast<uint8_t *>(orow - (uintptr_t)o2) + ck;
-                        if (f0 >= 0 && f0 + 16 <= VB) {
+                        const uint64_t img_bytes = (uint64_t)(M - 1) * (uint64_t)opitch + (uint64_t)N * C;
+                        if (!chk(gp + max(f0, 0) - f0, (uint64_t)(min(f0 + 16, VB) - max(f0, 0)), tab[i].out,
+                                 img_bytes, a.status, kChkOutput)) {
+                            // bounds-checked build: a store outside the image is skipped
+                        } else if (f0 >= 0 && f0 + 16 <= VB) {
                             __stcs(reinterpret_cast<uint4 *>(gp), d);
                         } else {
 #pragma unroll

@@ -409,7 +409,9 @@ __device__ __forceinline__ void rel_compute(const Geom &g, const CallArgs &a, co
                     sigma = __fdiv_rn(g.sigma_f[r] * g.b2_f[r], (float)n);
                 }
             }
-            if (n == 0) {  // wholly outside the frame: no sample, stored as 0
+            if (!chk(dst, (uint64_t)C * g.es, a.records, a.records_bytes, a.status, kChkRecord)) {
+                // bounds-checked build: a write outside the records is skipped
+            } else if (n == 0) {  // wholly outside the frame: no sample, stored as 0
 #pragma unroll
                 for (int ch = 0; ch < C; ++ch) {
                     if (g.es == 4) reinterpret_cast<uint32_t *>(dst)[ch] = 0u;
@@ -877,7 +879,9 @@ __global__ void __launch_bounds__(kThreads) k_emit(const Geom g, const CallArgs 
             default: gblock_sum_any<4>(p0, rowvals, nb, S); break;
         }
         const uint32_t cell_idx = (ty * cs + cy) * (uint32_t)(g.GC * cs) + tx * cs + cx;
-        emit_cell(g, a, rec + roff[r] + (uint64_t)local * C * g.es, S, r, cell_idx, frame, sid);
+        uint8_t *dst = rec + roff[r] + (uint64_t)local * C * g.es;
+        if (chk(dst, (uint64_t)C * g.es, a.records, a.records_bytes, a.status, kChkRecord))
+            emit_cell(g, a, dst, S, r, cell_idx, frame, sid);
     }
 }
 
@@ -1020,7 +1024,9 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
                 const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * crow + (uint32_t)(tx * cs + cx);
                 float ov[4] = {0.f, 0.f, 0.f, 0.f};
                 const uint4 words = noisy ? philox_finish(pp, cell_idx) : make_uint4(0, 0, 0, 0);
-                emit_values(g, C, rec + st.off[t] + (uint64_t)c * C * g.es, S, words, sigma, b2, inv_b2, ov);
+                uint8_t *dst = rec + st.off[t] + (uint64_t)c * C * g.es;
+                if (chk(dst, (uint64_t)C * g.es, a.records, a.records_bytes, a.status, kChkRecord))
+                    emit_values(g, C, dst, S, words, sigma, b2, inv_b2, ov);
                 const int si = st.base[t] + c;  // the stage keeps segment order for the row writer
                 if (kOutF32) {
                     reinterpret_cast<float4 *>(stage)[si] = make_float4(ov[0], ov[1], ov[2], ov[3]);
@@ -1036,10 +1042,11 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
         if (item + gridDim.x < items) fetch_gseg(item + gridDim.x);  // gseg is free once the cells are done
         // ---- C: output rows ----
         const int x0 = tx0 * T;
+        uint8_t *oframe = out + (uint64_t)f * (uint64_t)out_frame_stride;
         seg_write_rows<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, g.N - x0), min(T, g.M - ty * T),
-                                   out + (uint64_t)f * (uint64_t)out_frame_stride + (int64_t)(ty * T) * out_pitch +
-                                       (int64_t)x0 * C * oes,
-                                   out_pitch, threadIdx.x, kThr);
+                                   oframe + (int64_t)(ty * T) * out_pitch + (int64_t)x0 * C * oes, out_pitch,
+                                   threadIdx.x, kThr, oframe,
+                                   (uint64_t)(g.M - 1) * (uint64_t)out_pitch + (uint64_t)g.N * C * oes, a.status);
         __syncthreads();
     }
 }

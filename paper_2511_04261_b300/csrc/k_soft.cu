@@ -497,6 +497,7 @@ int dp_pix_soft_sizes(const dp_pix_soft_desc *d, uint64_t *pre_bytes) {
 
 int dp_pix_soft_forward(const dp_pix_soft_desc *d, const float *x, const float *w, float *y, float *pre,
                         void *cuda_stream) {
+    DPPIX_RANGE();
     SoftGeom sg;
     int rc = soft_geometry(d, &sg);
     if (rc) return rc;
@@ -527,6 +528,7 @@ int dp_pix_soft_forward(const dp_pix_soft_desc *d, const float *x, const float *
 
 int dp_pix_soft_backward(const dp_pix_soft_desc *d, const float *w, const float *gy, const float *pre, float *dx,
                          float *dw, float *d_ws, void *cuda_stream) {
+    DPPIX_RANGE();
     SoftGeom sg;
     int rc = soft_geometry(d, &sg);
     if (rc) return rc;

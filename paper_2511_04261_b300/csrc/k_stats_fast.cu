@@ -102,9 +102,10 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats_fast(const Geom g, cons
             const int sy = reflect_idx(ty * T + band * G + i, g.M, g.pad_mode);
             const uint8_t *src = fbase + (int64_t)sy * g.pitch;
             uint32_t w[K::NW];
+            const bool in = chk(src, K::BYTES, a.frames, a.frames_bytes, a.status, kChkFrame);
 #pragma unroll
             for (int v = 0; v < K::NV; ++v) {
-                const uint4 x = ld_stream(src + 16 * v);
+                const uint4 x = in ? ld_stream(src + 16 * v) : make_uint4(0u, 0u, 0u, 0u);
                 w[4 * v] = x.x; w[4 * v + 1] = x.y; w[4 * v + 2] = x.z; w[4 * v + 3] = x.w;
             }
 #pragma unroll
@@ -119,8 +120,9 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats_fast(const Geom g, cons
             }
         }
         // g-cell sums of this band -> g-image row ty*T/G + band, cells q*NG .. q*NG+NG-1
-        if (valid) {
-            uint16_t *dst = gimg + (size_t)(ty * bands + band) * GP + (size_t)q * K::NG * C;
+        uint16_t *gdst = gimg + (size_t)(ty * bands + band) * GP + (size_t)q * K::NG * C;
+        if (valid && chk(gdst, K::NG * C * 2, a.ws, a.ws_bytes, a.status, kChkWorkspace)) {
+            uint16_t *dst = gdst;
             constexpr int NVAL = K::NG * C;
             if (NVAL % 2 == 0 && (reinterpret_cast<uintptr_t>(dst) & 3) == 0) {
 #pragma unroll
@@ -148,7 +150,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_stats_fast(const Geom g, cons
         const uint32_t tile = (uint32_t)ty * g.GC + (uint32_t)(q / CPT);
         const unsigned long long n = (unsigned long long)T * T * C;
         uint64_t *keys = reinterpret_cast<uint64_t *>(a.ws + (uint64_t)f * g.ws_per_frame + g.ws_keys);
-        keys[tile] = n * Q64 - (unsigned long long)Ssum * Ssum;
+        if (chk(&keys[tile], 8, a.ws, a.ws_bytes, a.status, kChkWorkspace))
+            keys[tile] = n * Q64 - (unsigned long long)Ssum * Ssum;
     }
 }
 

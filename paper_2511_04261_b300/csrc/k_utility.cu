@@ -239,6 +239,7 @@ extern "C" {
 int dp_pix_sobel_mask(const void *d_frames, int32_t M, int32_t N, int32_t C, int64_t row_pitch, int64_t frame_stride,
                       uint32_t n_frames, int32_t pad_mode, uint32_t tau, void *d_mask, int64_t mask_pitch,
                       int64_t mask_frame_stride, void *cuda_stream) {
+    DPPIX_RANGE();
     if (n_frames == 0) return DP_PIX_OK;  // nothing to do
     if (!d_frames || !d_mask) return set_last_error(DP_PIX_E_INVALID_ARG, "null frame or mask pointer");
     if (M < 2 || N < 2 || C < 1 || C > 4 || n_frames > 65535)
@@ -271,6 +272,7 @@ int dp_pix_sobel_mask(const void *d_frames, int32_t M, int32_t N, int32_t C, int
 int dp_pix_utility(const void *d_x, const void *d_y, int32_t M, int32_t N, int32_t C, int64_t pitch_x, int64_t pitch_y,
                    int64_t frame_stride_x, int64_t frame_stride_y, uint32_t n_frames, dp_pix_utility_t *d_out,
                    void *cuda_stream) {
+    DPPIX_RANGE();
     if (n_frames == 0) return DP_PIX_OK;  // nothing to do
     if (!d_x || !d_y || !d_out) return set_last_error(DP_PIX_E_INVALID_ARG, "null pointer");
     if (M < kWin || N < kWin || C < 1 || C > 4 || n_frames > 65535)

@@ -154,7 +154,10 @@ __device__ __forceinline__ int wrap_count(int &k, int n) {
 // written back during the next, bandwidth-bound pass (64-frame clip step: 205.1 -> 199.4 us).
 template <int C, int kOutF32>
 __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, const uint8_t *stage, int ns, int T, int vpx,
-                               int jmax, uint8_t *orow0, int64_t out_pitch, int tid, int nthr) {
+                               int jmax, uint8_t *orow0, int64_t out_pitch, int tid, int nthr,
+                               const uint8_t *img = nullptr, uint64_t img_bytes = 0, int32_t *status = nullptr) {
+    // bounds-checked build: every store must fall inside the image [img, img + img_bytes) when img is given
+    auto ok = [&](const uint8_t *p, int n) { return img == nullptr || chk(p, n, img, img_bytes, status, kChkOutput); };
     constexpr int oes = kOutF32 ? 4 : 1;
     // write phase: thread = (16-byte column chunk, group of rows); no barrier until the next item
     const int row_bytes = vpx * C * oes;
@@ -228,10 +231,12 @@ __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, cons
                     }
                     vec = build();
                 }
-                __stcs(reinterpret_cast<uint4 *>(dst), vec);
-                __stcs(reinterpret_cast<uint4 *>(dst + out_pitch), vec);
-                __stcs(reinterpret_cast<uint4 *>(dst + 2 * out_pitch), vec);
-                __stcs(reinterpret_cast<uint4 *>(dst + 3 * out_pitch), vec);
+                if (ok(dst, 16) && ok(dst + 3 * out_pitch, 16)) {
+                    __stcs(reinterpret_cast<uint4 *>(dst), vec);
+                    __stcs(reinterpret_cast<uint4 *>(dst + out_pitch), vec);
+                    __stcs(reinterpret_cast<uint4 *>(dst + 2 * out_pitch), vec);
+                    __stcs(reinterpret_cast<uint4 *>(dst + 3 * out_pitch), vec);
+                }
             }
         }
         for (; j < j1; ++j, dst += out_pitch) {
@@ -246,7 +251,9 @@ __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, cons
                 }
                 vec = build();
             }
-            if (full) {
+            if (!ok(dst, full ? 16 : row_bytes - o)) {
+                // bounds-checked build: a store outside the image is skipped
+            } else if (full) {
                 __stcs(reinterpret_cast<uint4 *>(dst), vec);
             } else {
                 for (int i = 0; o + i < row_bytes; ++i) {

@@ -292,6 +292,7 @@ void admit(dp_pix_server_s *s, SrvBatch &b) {
 // Issues the copies, the key kernel, the keyed releases and the callback for batch b.  Called without
 // s->mu; the batch's requests are not touched by other threads until it finishes.
 int launch(dp_pix_server_s *s, SrvBatch &b, const std::vector<SrvReq> &rq) {
+    ApiRange range("dp_pix_server batch");
     cudaStream_t st = b.stream;
     const uint32_t n = (uint32_t)b.tickets.size();
     // key table: rank among the camera's frames in this batch, and a flag on the camera's last one
@@ -454,6 +455,7 @@ int dp_pix_server_sizes(const dp_pix_desc *common, int32_t M, int32_t N, uint64_
 int dp_pix_server_create(const dp_pix_desc *common, const int32_t *M, const int32_t *N, uint32_t n_cameras,
                          const uint64_t *first_frame, uint32_t n_streams, void *d_arena, uint64_t arena_bytes,
                          dp_pix_server_t *out) {
+    DPPIX_RANGE();
     clear_last_error();
     if (!common || !M || !N || !out) return sfail(DP_PIX_E_INVALID_ARG, "null argument");
     *out = nullptr;
@@ -591,6 +593,7 @@ int dp_pix_server_wait(dp_pix_server_t s, uint64_t ticket, int timeout_ms, dp_pi
 }
 
 int dp_pix_server_counters(dp_pix_server_t s, uint64_t *next_frame, uint32_t n) {
+    DPPIX_RANGE();
     clear_last_error();
     if (!s || !next_frame) return sfail(DP_PIX_E_INVALID_ARG, "null argument");
     if (n > s->n_cameras) return sfail(DP_PIX_E_INVALID_ARG, "n %u > cameras %u", n, s->n_cameras);
@@ -622,6 +625,7 @@ int dp_pix_server_stats_get(dp_pix_server_t s, dp_pix_server_stats *st) {
 }
 
 int dp_pix_server_destroy(dp_pix_server_t s) {
+    DPPIX_RANGE();
     if (!s) return DP_PIX_OK;
     {
         std::lock_guard<std::mutex> lk(s->mu);
