@@ -442,6 +442,27 @@ def run_ours(args):
     torch.cuda.synchronize()
     P.dp_pix_status()
 
+    # The step as the library is meant to be driven at this rate: captured once into a CUDA graph and replayed.
+    # The graph holds dp_pix_keys_advance (every frame's key moves on by F, so each replay releases the next F
+    # frames of the stream with fresh noise keys) and the keyed release + reconstruction; the host submits
+    # nothing per step.  The same step issued from Python call by call is timed beside it (direct_call).
+    keys = P.key_table([(rank, args.warmup * F + i) for i in range(F)], device=dev)
+
+    def step_graph():
+        P.dp_pix_keys_advance(keys, F)
+        P.dp_pix_release_reconstruct_keyed(plan, frames, keys, out_type=P.OUT_U8, records=records, out=out, ws=ws)
+
+    if args.path == "fused":
+        step_graph()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step_graph()
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        P.dp_pix_status()
+
     # ---- device-resident timed region ----
     sampler = ClockSampler(torch.cuda.current_device())
     barrier(world)
@@ -450,24 +471,35 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
-        step(frames, (args.warmup + k) * F)
+        if args.path == "fused":
+            graph.replay()
+        else:
+            step(frames, (args.warmup + k) * F)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
     P.dp_pix_status()
     ms = e0.elapsed_time(e1) / args.steps
+    # the same steps issued from Python call by call
+    e0.record(stream)
+    for k in range(args.steps):
+        step(frames, (2 * args.warmup + args.steps + k) * F)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    direct_ms = e0.elapsed_time(e1) / args.steps
     # per-kernel launch durations from a separate pass of the same steps with the library's events around
     # each launch (kept out of the timed region above)
     P.prof_reset()
     P.prof_enable(True)
     for k in range(args.steps):
-        step(frames, (args.warmup + args.steps + k) * F)
+        step(frames, (3 * args.warmup + 2 * args.steps + k) * F)
     torch.cuda.synchronize()
     prof = P.prof_read()
     P.prof_enable(False)
     P.dp_pix_status()
-    launches = sum(v[0] for v in prof.values())  # the profiled pass runs as many steps as the timed region
+    # the profiled pass runs as many steps as the timed region; the graph adds the key-advance launch per step
+    launches = sum(v[0] for v in prof.values()) + (args.steps if args.path == "fused" else 0)
     args.tuning = {"fused_px": plan.tuning(P.TUNE_FUSED_PX), "fused_threads": plan.tuning(P.TUNE_FUSED_THREADS),
                    "split": plan.tuning(P.TUNE_SPLIT)}
     ms_max = max_over_ranks(ms, world)
@@ -495,8 +527,8 @@ def run_ours(args):
                               "moved_bytes adds the g-cell sums and offsets read from the statistics pass; "
                               "step_frac is the step's method bytes (frames read, records and frames written) "
                               "over the step time",
-                "timing": "per-kernel durations from a separate profiled pass of %d steps; the timed region "
-                          "ran without library events" % args.steps,
+                "timing": "per-kernel durations from a separate profiled pass of %d steps issued call by call; "
+                          "the timed region (graph replays) ran without library events" % args.steps,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else
                 "fallback 6.4 TB/s",
                 "kernels": {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / max(1e-9, sum(x[1] for x in prof.values())),
@@ -566,6 +598,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_clip(clip, args.cpu_budget)
+    args.direct_call = {"ms_per_step": direct_ms, "value": world * F * M * N / 1e6 / (direct_ms / 1e3),
+                        "what": "dp_pix_release_reconstruct issued from Python once per step (host submission in "
+                                "the loop; host-bound on slower hosts)"}
     return finish(args, rank, world, value, ms_max, roofline, cpu, e2e, clocks, launches, latency)
 
 
@@ -644,8 +679,11 @@ def finish(args, rank, world, value, ms_max, roofline, cpu, e2e, clocks, launche
                 "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                 "config": config({"parallelism": "replicas: one clip per GPU, no collective" if world > 1 else "1 GPU",
                                   "arith": "u8 samples, exact u32 cell sums, f32 noise/mean",
-                                  "path": "dp_pix_release_reconstruct" if args.path == "fused" else
-                                  "dp_pix_release + dp_pix_reconstruct", "tuning": getattr(args, "tuning", None)}),
+                                  "path": "CUDA graph of dp_pix_keys_advance + dp_pix_release_reconstruct_keyed, "
+                                          "replayed once per step (each replay releases the next 64 frames)"
+                                  if args.path == "fused" else "dp_pix_release + dp_pix_reconstruct",
+                                  "tuning": getattr(args, "tuning", None)}),
+                "direct_call": getattr(args, "direct_call", None),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                 "latency": latency}
         print(json.dumps(line), flush=True)

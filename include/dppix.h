@@ -263,6 +263,13 @@ DPPIX_API int dp_pix_release_reconstruct_keyed(dp_pix_plan_t plan, const void *d
                                                int64_t out_pitch, int out_type, void *d_ws, uint64_t ws_bytes,
                                                void *cuda_stream);
 
+/*
+ * Adds delta to the frame_idx of each of the n keys at d_keys (device, 8-byte aligned), asynchronously on
+ * cuda_stream.  With a keyed release captured in a CUDA graph together with this call, every replay releases
+ * the next frames of each stream (fresh noise keys) while the host submits nothing.  Errors: INVALID_ARG, CUDA.
+ */
+DPPIX_API int dp_pix_keys_advance(dp_pix_frame_key *d_keys, uint32_t n, uint64_t delta, void *cuda_stream);
+
 /* ---- ragged batches (no counterpart in the paper, which releases one frame at a time) ----------------- */
 /* Many images of different sizes released with one set of region parameters.  Each image is released
  * exactly as dp_pix_release would release it alone with a plan for its size (same record bytes, same noise:

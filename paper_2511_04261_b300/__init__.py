@@ -13,7 +13,7 @@ from .api import (Plan, dp_pix_debug_noise, dp_pix_plan, dp_pix_reconstruct, dp_
                   dp_pix_store, dp_pix_store_batch, prof_enable, prof_read, prof_reset, record_header)
 
 from .batch import BatchPlan
-from .serve import Server, dp_pix_release_keyed, dp_pix_release_reconstruct_keyed
+from .serve import Server, dp_pix_keys_advance, dp_pix_release_keyed, dp_pix_release_reconstruct_keyed, key_table
 from .soft import SoftPixelize, SoftSpec, soft_backward, soft_forward, soft_pixelize
 from .utility import dp_pix_sobel_mask, dp_pix_utility, utility_values
 

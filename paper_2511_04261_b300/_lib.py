@@ -126,6 +126,7 @@ def lib():
     L.dp_pix_batch_tuning.argtypes = [P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
     L.dp_pix_batch_set_path.argtypes = [P, ct.c_int, ct.c_int]
     L.dp_pix_release_keyed.argtypes = [P, P, I64, P, I64, I64, U32, P, P, I64, P, U64, P]
+    L.dp_pix_keys_advance.argtypes = [P, U32, U64, P]
     L.dp_pix_release_reconstruct_keyed.argtypes = [P, P, I64, P, I64, I64, U32, P, P, I64, P, I64, I64, ct.c_int,
                                                    P, U64, P]
     L.dp_pix_server_sizes.argtypes = [ct.POINTER(Desc), I32, I32, ct.POINTER(U64), ct.POINTER(U64), ct.POINTER(U64)]
@@ -157,7 +158,7 @@ def lib():
                  "dp_pix_batch_set_path",
                  "dp_pix_release_keyed", "dp_pix_server_sizes", "dp_pix_server_create", "dp_pix_server_submit",
                  "dp_pix_server_wait", "dp_pix_server_stats_get", "dp_pix_server_counters", "dp_pix_server_destroy",
-                 "dp_pix_release_reconstruct_keyed",
+                 "dp_pix_release_reconstruct_keyed", "dp_pix_keys_advance",
                  "dp_pix_store_batch",
                  "dp_pix_reconstruct",
                  "dp_pix_debug_noise", "dp_pix_status", "dp_pix_prof_enable", "dp_pix_prof_read",

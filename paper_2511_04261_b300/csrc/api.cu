@@ -672,6 +672,17 @@ int dp_pix_release_reconstruct(dp_pix_plan_t plan, const void *d_frames, int64_t
                                     out_pitch, out_type, d_ws, ws_bytes, cuda_stream);
 }
 
+int dp_pix_keys_advance(dp_pix_frame_key *d_keys, uint32_t n, uint64_t delta, void *cuda_stream) {
+    t_err[0] = 0;
+    if (n == 0) return DP_PIX_OK;
+    if (!d_keys) return fail(DP_PIX_E_INVALID_ARG, "keys are required");
+    if ((uintptr_t)d_keys % 8) return fail(DP_PIX_E_INVALID_ARG, "keys must be 8-byte aligned");
+    int rc = check_cuda_device();
+    if (rc) return rc;
+    const cudaError_t e = launch_keys_advance(d_keys, n, delta, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? DP_PIX_OK : cuda_fail(e, "keys advance");
+}
+
 int dp_pix_release_reconstruct_keyed(dp_pix_plan_t plan, const void *d_frames, int64_t frame_stride,
                                      const void *d_region_src, int64_t src_pitch, int64_t src_frame_stride,
                                      uint32_t n_frames, const dp_pix_frame_key *d_keys, void *d_records,

@@ -341,6 +341,7 @@ cudaError_t launch_batch_reconstruct(const BatchEntry *tab, uint32_t n_img, uint
                                      int out_align, int32_t *status, cudaStream_t s);
 cudaError_t launch_debug_noise(uint64_t seed, const uint32_t *ctr, uint64_t n, uint32_t *words, float *eta,
                                float sigma, cudaStream_t s);
+cudaError_t launch_keys_advance(dp_pix_frame_key *keys, uint32_t n, uint64_t delta, cudaStream_t s);
 
 // An NVTX range for the duration of a library call (host side; profilers such as Nsight show the calls on
 // the timeline and can filter kernels by them).  Costs a branch when no profiler is attached.

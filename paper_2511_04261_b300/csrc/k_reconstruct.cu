@@ -400,6 +400,11 @@ cudaError_t launch_brc(const BatchEntry *tab, uint32_t n_img, uint32_t items, in
     return cudaGetLastError();
 }
 
+// Adds delta to the frame index of each of n keys (stream ids unchanged).
+__global__ void k_keys_advance(dp_pix_frame_key *keys, uint32_t n, uint64_t delta) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) keys[i].frame_idx += delta;
+}
+
 __global__ void k_debug_noise(uint64_t seed, const uint32_t *ctr, uint64_t n, uint32_t *words, float *eta, float sigma) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
@@ -481,6 +486,14 @@ cudaError_t launch_reconstruct(const uint8_t *records, int64_t record_stride, ui
         default: DPPIX_RC(0, 0);
     }
 #undef DPPIX_RC
+}
+
+cudaError_t launch_keys_advance(dp_pix_frame_key *keys, uint32_t n, uint64_t delta, cudaStream_t s) {
+    const uint32_t blocks = std::min<uint32_t>((n + 255) / 256, 1024);
+    prof_begin("k_keys_advance", s);
+    k_keys_advance<<<blocks, 256, 0, s>>>(keys, n, delta);
+    prof_end("k_keys_advance", s);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_debug_noise(uint64_t seed, const uint32_t *ctr, uint64_t n, uint32_t *words, float *eta,

@@ -10,7 +10,7 @@ import torch
 
 from . import _lib as L
 
-__all__ = ["Server", "dp_pix_release_keyed", "dp_pix_release_reconstruct_keyed"]
+__all__ = ["Server", "dp_pix_release_keyed", "dp_pix_release_reconstruct_keyed", "key_table", "dp_pix_keys_advance"]
 
 
 def _desc(C, grids, eps, R, m, pad_mode, source, dtype, noise_free, seed):
@@ -23,6 +23,19 @@ def _desc(C, grids, eps, R, m, pad_mode, source, dtype, noise_free, seed):
     d.value_range, d.m, d.pad_mode, d.region_source = float(R), float(m), int(pad_mode), int(source)
     d.record_dtype, d.noise_free, d.seed = int(dtype), int(bool(noise_free)), int(seed) & (2**64 - 1)
     return d
+
+
+def dp_pix_keys_advance(keys: torch.Tensor, delta: int, stream=None):
+    """keys: a device key table (key_table); adds delta to every frame index on the device."""
+    n = keys.numel() // ct.sizeof(L.FrameKey)
+    s = ct.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    L.check(L.lib().dp_pix_keys_advance(ct.c_void_p(keys.data_ptr()), n, int(delta) & (2**64 - 1), s),
+            "dp_pix_keys_advance")
+
+
+def key_table(keys, device="cuda") -> torch.Tensor:
+    """Device key table (u8 tensor of dp_pix_frame_key entries) for F pairs (stream_id, frame_idx)."""
+    return _key_table(keys, device)
 
 
 def _key_table(keys, device):
@@ -52,13 +65,16 @@ def dp_pix_release_keyed(plan, frames: torch.Tensor, keys: Sequence[Sequence[int
     return records
 
 
-def dp_pix_release_reconstruct_keyed(plan, frames: torch.Tensor, keys: Sequence[Sequence[int]], out_type=L.OUT_U8,
+def dp_pix_release_reconstruct_keyed(plan, frames: torch.Tensor, keys, out_type=L.OUT_U8,
                                      records=None, out=None, ws=None, stream=None):
     """dp_pix_release_reconstruct with one (stream_id, frame_idx) key per frame.  frames [F, M, N, C] u8 on the
-    GPU; out: [F, M, N, C] u8 / f32 (any row pitch).  Returns (records [F, stride], images)."""
+    GPU; keys: F pairs (stream_id, frame_idx), or a device key table (key_table, used in place, so that a
+    captured graph sees dp_pix_keys_advance's updates); out: [F, M, N, C] u8 / f32 (any row pitch).
+    Returns (records [F, stride], images)."""
     n = frames.shape[0]
     spec = plan.spec
-    kd = _key_table(keys, frames.device)
+    on_device = isinstance(keys, torch.Tensor)
+    kd = keys if on_device else _key_table(keys, frames.device)
     if records is None:
         records = plan.alloc_records(n, device=frames.device)
     if ws is None:
@@ -73,7 +89,8 @@ def dp_pix_release_reconstruct_keyed(plan, frames: torch.Tensor, keys: Sequence[
         ct.c_void_p(kd.data_ptr()), ct.c_void_p(records.data_ptr()), records.stride(0), ct.c_void_p(out.data_ptr()),
         out.stride(0) * es, out.stride(1) * es, int(out_type), ct.c_void_p(ws.data_ptr()), ws.numel(), s),
         "dp_pix_release_reconstruct_keyed")
-    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()  # kd is freed on return
+    if not on_device:  # the temporary key table is freed on return
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
     return records, out
 
 

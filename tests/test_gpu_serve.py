@@ -277,3 +277,35 @@ def test_server_rejects_bad_requests():
         P.Server(SIZES, arena_bytes=1 << 16, **{k: v for k, v in VAR.items() if k != "C"})
     with pytest.raises(ValueError):
         P.Server(SIZES, arena_bytes=64 << 20, first_frame=[0], **{k: v for k, v in VAR.items() if k != "C"})
+
+
+def test_keys_advance_in_a_captured_graph():
+    """dp_pix_keys_advance and the keyed release + reconstruction captured in one CUDA graph: every replay
+    releases the next frames of the stream (fresh keys), byte-identical to direct calls at those indices."""
+    F, M, N = 3, 130, 250
+    clip = torch.from_numpy(synth.moving_rect_clip(seed=5, frames=F, M=M, N=N)).cuda()
+    plan = P.Plan(M=M, N=N, source=P.SRC_VARIANCE, dtype=P.REC_F32, **VAR)
+    keys = P.key_table([(7, 100 + i) for i in range(F)])
+    recs, ws = plan.alloc_records(F), plan.alloc_workspace(F)
+    out = torch.empty((F, M, N, 3), dtype=torch.uint8, device="cuda")
+
+    def step():
+        P.dp_pix_keys_advance(keys, F)
+        P.dp_pix_release_reconstruct_keyed(plan, clip, keys, records=recs, out=out, ws=ws)
+
+    step()  # frames 100 + F ..
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for k in range(2):  # frames 100 + 2F .., then 100 + 3F ..
+        g.replay()
+        torch.cuda.synchronize()
+        assert P.dp_pix_status() == 0
+        ref_r, ref_o = plan.release_reconstruct(clip, None, stream_id=7, frame_idx0=100 + (2 + k) * F)
+        torch.cuda.synchronize()
+        for i in range(F):
+            got = P.dp_pix_store(recs[i])
+            assert got == P.dp_pix_store(ref_r[i]), (k, i)
+            assert P.record_header(got)["frame_idx"] == 100 + (2 + k) * F + i
+        assert torch.equal(out, ref_o)
