@@ -1236,8 +1236,8 @@ def run_batch(args):
     from paper_2511_04261_b300 import build, synth
     build.build()
     world, rank, _ = dist_setup(args.gpus)
-    n = BATCH["n"]
-    sizes = synth.portrait_batch_shapes(seed=1003 + rank, n=n)
+    n = min(BATCH["n"], args.images) if args.images else BATCH["n"]
+    sizes = synth.portrait_batch_shapes(seed=1003 + rank, n=BATCH["n"])[:n]
     frames, mattes = [], []
     for i, (M_, N_) in enumerate(sizes):
         im, al = synth.portrait_device(1003000 + 1000 * rank + i, M_, N_)
@@ -1369,7 +1369,7 @@ def run_batch(args):
         line = {"metric": BATCH_METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-                "config": {"workload": "batch256_portraits_512to4096_matte_b6_b20", "images": n,
+                "config": {"workload": "batch%d_portraits_512to4096_matte_b6_b20" % n, "images": n,
                            "megapixels": px / 1e6, "grids": BATCH["grids"], "eps": BATCH["eps"], "m": BATCH["m"],
                            "T": 60, "region_source": "f32 alpha matte >= 0.5", "record": "f32 means + u8 tile map",
                            "step": "dp_pix_batch_run: classify + finalize + release + reconstruct, CUDA graph",
@@ -1576,6 +1576,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--frames", type=int, default=64, help="frames per step (64 = the benchmark workload)")
+    ap.add_argument("--images", type=int, default=0,
+                    help="batch workload: only the first N of the 256 images (a small case for profiling)")
     ap.add_argument("--fused-px", type=int, default=None, help="DP_PIX_TUNE_FUSED_PX (default: the plan's)")
     ap.add_argument("--fused-threads", type=int, default=None, help="DP_PIX_TUNE_FUSED_THREADS (default: the plan's)")
     ap.add_argument("--split", type=int, default=None, help="DP_PIX_TUNE_SPLIT (default: the plan's)")

@@ -287,6 +287,10 @@ int make_geom(const dp_pix_desc *d, Geom &g) {
     g.fused_threads = 128;
     g.split = 1;
     g.fused_cap = 0;
+    for (int r = 0; r < 10; ++r) {  // the Philox key schedule: each round adds the Weyl constants
+        g.rkey[2 * r] = (uint32_t)d->seed + (uint32_t)r * 0x9E3779B9u;
+        g.rkey[2 * r + 1] = (uint32_t)(d->seed >> 32) + (uint32_t)r * 0xBB67AE85u;
+    }
     g.wait_tries = kWaitTries;
     g.test_short_tx = 0;
     g.test_shrink = 0;

@@ -1023,7 +1023,7 @@ __global__ void __launch_bounds__(kThr, 2048 / kThr / 2)
                 gblock_sum_any<C>(gs16 + (size_t)(cy * nb) * gsv + (size_t)(t * gcs + cx * nb) * C, (size_t)gsv, nb, S);
                 const uint32_t cell_idx = (uint32_t)(ty * cs + cy) * crow + (uint32_t)(tx * cs + cx);
                 float ov[4] = {0.f, 0.f, 0.f, 0.f};
-                const uint4 words = noisy ? philox_finish(pp, cell_idx) : make_uint4(0, 0, 0, 0);
+                const uint4 words = noisy ? philox_finish_rk(pp, cell_idx, g.rkey) : make_uint4(0, 0, 0, 0);
                 uint8_t *dst = rec + st.off[t] + (uint64_t)c * C * g.es;
                 if (chk(dst, (uint64_t)C * g.es, a.records, a.records_bytes, a.status, kChkRecord))
                     emit_values(g, C, dst, S, words, sigma, b2, inv_b2, ov);
