@@ -1286,7 +1286,7 @@ def run_batch(args):
     payload = sum(h["total_bytes"] - h["payload_offset"] for h in hdrs)
     ntiles = sum(h["GR"] * h["GC"] for h in hdrs)
     algo = {"k_batch_classify": 4 * px + ntiles, "k_bcls_stream": 4 * px + ntiles, "k_batch_finalize": ntiles * 9 + n * 512,
-            "k_batch_release": 3 * px + payload, "k_brel_stream": 3 * px + payload,
+            "k_batch_release": 3 * px + payload, "k_batch_tiles": 3 * px + payload, "k_brel_stream": 3 * px + payload,
             "k_brel_stream_recon": 6 * px + payload, "k_batch_reconstruct_u8": 3 * px + payload + ntiles}
     hbm, peak_kind = measured_peaks()
     dom_name, (dom_launches, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
@@ -1374,7 +1374,7 @@ def run_batch(args):
                            "T": 60, "region_source": "f32 alpha matte >= 0.5", "record": "f32 means + u8 tile map",
                            "step": "dp_pix_batch_run: classify + finalize + release + reconstruct, CUDA graph",
                            "seg_tiles_autotuned": seg,
-                           "release_path_autotuned": {0: "staged", 1: "stream", 2: "stream_fused"}.get(path, path),
+                           "release_path_autotuned": {0: "staged", 1: "stream", 2: "stream_fused", 3: "tiles"}.get(path, path),
                            "l2": "inputs larger than L2 (%.0f MB read per step)" % (7 * px / 1e6),
                            "generator": "synth.portrait_device seeds 1003000+i (torch Philox on the GPU)",
                            "parallelism": "1 GPU" if world == 1 else "replicas"},

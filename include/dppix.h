@@ -316,16 +316,21 @@ DPPIX_API int dp_pix_batch_bind(dp_pix_batch_t b, const dp_pix_batch_image *imgs
 DPPIX_API int dp_pix_batch_run(dp_pix_batch_t b, int use_graph, void *cuda_stream);
 
 /* Release paths of a batch (all give the same bytes):
- *   DP_PIX_BATCH_PATH_STAGED        each item's rows arrive in shared memory by bulk copies; the images, if any,
- *                                   are written by a separate reconstruction launch
+ *   DP_PIX_BATCH_PATH_STAGED        each item's rows arrive in shared memory by bulk copies; the CTA's threads
+ *                                   share out the item's (tile, cell, row part) units; the images, if any, are
+ *                                   written by a separate reconstruction launch
  *   DP_PIX_BATCH_PATH_STREAM        each lane streams its 16-byte column chunk of the item's rows straight into
  *                                   registers (rows realigned by funnel shifts); separate reconstruction
  *   DP_PIX_BATCH_PATH_STREAM_FUSED  as STREAM, and the same launch writes the u8 images from the cell values
+ *   DP_PIX_BATCH_PATH_TILES         rows staged as in STAGED, whole warps per tile of the item (segment width
+ *                                   1, 2, 4 or 8 tiles sharing the CTA's 8 warps; default 2); separate
+ *                                   reconstruction.  The default path (-1).
  * The streaming paths need T * C >= 16 (and their per-item sums within shared memory); the fused one u8
- * images and f32 or u8 records.  Where a path does not apply the batch takes the next one down. */
+ * images and f32 or u8 records.  Where a path does not apply the batch takes the staged one. */
 #define DP_PIX_BATCH_PATH_STAGED 0
 #define DP_PIX_BATCH_PATH_STREAM 1
 #define DP_PIX_BATCH_PATH_STREAM_FUSED 2
+#define DP_PIX_BATCH_PATH_TILES 3
 
 /* Times the release paths and their segment widths (tiles per work item) on the bound batch -- reps runs
  * each, overwriting its records and outputs -- keeps the fastest, rebinds `imgs` (the images bound last) and
@@ -334,7 +339,7 @@ DPPIX_API int dp_pix_batch_run(dp_pix_batch_t b, int use_graph, void *cuda_strea
 DPPIX_API int dp_pix_batch_autotune(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int reps, void *cuda_stream);
 DPPIX_API int dp_pix_batch_tuning(dp_pix_batch_t b, int *seg_tiles, int *path);
 
-/* Chooses a release path (DP_PIX_BATCH_PATH_*, or -1: the default, the staged path)
+/* Chooses a release path (DP_PIX_BATCH_PATH_*, or -1: the default, whole warps per tile)
  * and segment width (0: the path's default) without timing; takes effect at the next dp_pix_batch_bind.
  * Errors: INVALID_ARG. */
 DPPIX_API int dp_pix_batch_set_path(dp_pix_batch_t b, int path, int seg_tiles);

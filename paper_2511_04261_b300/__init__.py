@@ -7,7 +7,8 @@ missing or unloadable library raises.
 from . import _lib
 from ._lib import (DppixError, OUT_F32, OUT_U8, PAD_NONE, PAD_REFLECT, PAD_SYMMETRIC, REC_F32, REC_SUM_U32, REC_U8,
                    SRC_MASK_U8, SRC_MATTE_F32, SRC_TILE_LABELS, SRC_VARIANCE, TUNE_FUSED_PX, TUNE_FUSED_THREADS, TUNE_SPLIT,
-                   TUNE_TEST_SHORT_TX, TUNE_WAIT_TRIES, TUNE_FUSED_CAP, TUNE_TEST_SHRINK, BATCH_PATH_STAGED, BATCH_PATH_STREAM, BATCH_PATH_STREAM_FUSED)
+                   TUNE_TEST_SHORT_TX, TUNE_WAIT_TRIES, TUNE_FUSED_CAP, TUNE_TEST_SHRINK, BATCH_PATH_STAGED, BATCH_PATH_STREAM, BATCH_PATH_STREAM_FUSED,
+                   BATCH_PATH_TILES)
 from .api import (Plan, dp_pix_debug_noise, dp_pix_plan, dp_pix_reconstruct, dp_pix_release,
                   dp_pix_release_reconstruct, dp_pix_status,
                   dp_pix_store, dp_pix_store_batch, prof_enable, prof_read, prof_reset, record_header)

@@ -25,7 +25,7 @@ REC_F32, REC_U8, REC_SUM_U32 = 0, 1, 2
 OUT_U8, OUT_F32 = 0, 1
 TUNE_FUSED_PX, TUNE_FUSED_THREADS, TUNE_SPLIT, TUNE_WAIT_TRIES, TUNE_TEST_SHORT_TX, TUNE_FUSED_CAP = 1, 2, 4, 8, 16, 32
 TUNE_TEST_SHRINK = 64
-BATCH_PATH_STAGED, BATCH_PATH_STREAM, BATCH_PATH_STREAM_FUSED = 0, 1, 2
+BATCH_PATH_STAGED, BATCH_PATH_STREAM, BATCH_PATH_STREAM_FUSED, BATCH_PATH_TILES = 0, 1, 2, 3
 
 
 class SoftDesc(ct.Structure):

@@ -37,6 +37,10 @@ struct dp_pix_batch_s {
     size_t rel_smem = 0;
     // streaming kernels (k_batch_stream.cu), where the geometry allows them
     bool cls_stream = false, rel_stream = false, recon_fused = false;
+    // whole warps per tile (k_batch_tiles): segments of tiles_S tiles sharing a CTA's 8 warps
+    bool rel_tiles = false;
+    int tiles_S = 0;
+
     BatchStreamShape rs{};
     // graph (captured on a private stream -- capture is not possible on the legacy default stream -- and
     // launched on the caller's)
@@ -92,12 +96,15 @@ int build_table(dp_pix_batch_s *b, const dp_pix_batch_image *imgs, int out_type)
         b->cls_stream = (g0.source == DP_PIX_SRC_MASK_U8 || g0.source == DP_PIX_SRC_MATTE_F32) &&
                         batch_classify_stream_ok(g0.T, g0.source == DP_PIX_SRC_MATTE_F32);
         b->rs = batch_release_stream_shape(g0.T, g0.C, g0.b_min, b->seg_tiles > 0 ? b->seg_tiles : 1 << 20);
-        // default (path -1): the staged release, measured faster on the portrait batch; the streaming paths
-        // when chosen (dp_pix_batch_set_path, or by the autotuner's timing)
+        // default (path -1): whole warps per tile, 2 tiles per item (256-portrait batch: 2.22 ms against 2.30
+        // ms for the staged unit list); the others when chosen (dp_pix_batch_set_path, or by the autotuner)
         b->rel_stream = b->rs.S > 0 && (b->path == DP_PIX_BATCH_PATH_STREAM || b->path == DP_PIX_BATCH_PATH_STREAM_FUSED);
         // the fused image needs u8 output and stored values it can read back as the reconstruction would
         b->recon_fused = b->rel_stream && b->path == DP_PIX_BATCH_PATH_STREAM_FUSED && b->rs.recon_ok &&
                          out_type == DP_PIX_OUT_U8 && g0.dtype != DP_PIX_REC_SUM_U32;
+        const bool tiles = b->path == DP_PIX_BATCH_PATH_TILES || b->path < 0;
+        b->tiles_S = b->seg_tiles > 0 ? b->seg_tiles : 2;
+        b->rel_tiles = tiles && batch_tiles_smem(g0.T, g0.C, b->tiles_S) > 0;
     }
     for (uint32_t k = 0; k < b->n; ++k) {
         const uint32_t i = b->order[k];
@@ -119,7 +126,8 @@ int build_table(dp_pix_batch_s *b, const dp_pix_batch_image *imgs, int out_type)
         if (im.out && oes == 4 && ((uintptr_t)im.out % 4 || im.out_pitch % 4))
             return bfail(DP_PIX_E_INVALID_ARG, "image %u: f32 output must be 4-byte aligned", i);
         g.pitch = im.row_pitch;
-        if (b->seg_tiles > 0 && !b->rel_stream) apply_seg(g, b->seg_tiles);
+        if (b->rel_tiles) apply_seg(g, b->tiles_S);
+        else if (b->seg_tiles > 0 && !b->rel_stream) apply_seg(g, b->seg_tiles);
         BatchEntry &e = b->tab[k];
         e.g = g;
         CallArgs &a = e.a;
@@ -190,9 +198,14 @@ cudaError_t launch_all(dp_pix_batch_s *b, cudaStream_t s) {
                           : launch_batch_classify(tab, b->n, b->items_cls, g0.T, matte, s);
     if (e == cudaSuccess) e = launch_batch_finalize(tab, b->n, b->max_tiles, s);
     const bool fused = b->recon_fused && b->any_out;
-    if (e == cudaSuccess)
-        e = b->rel_stream ? launch_batch_release_stream(tab, b->n, b->items_rel, g0.C, b->rs, fused ? 1 : 0, s)
-                          : launch_batch_release(tab, b->n, b->items_rel, g0.T, g0.C, g0.seg_tiles, s);
+    if (e == cudaSuccess) {
+        if (b->rel_stream)
+            e = launch_batch_release_stream(tab, b->n, b->items_rel, g0.C, b->rs, fused ? 1 : 0, s);
+        else if (b->rel_tiles)
+            e = launch_batch_tiles(tab, b->n, b->items_rel, g0.T, g0.C, b->tiles_S, s);
+        else
+            e = launch_batch_release(tab, b->n, b->items_rel, g0.T, g0.C, g0.seg_tiles, s);
+    }
     if (e == cudaSuccess && b->any_out && !fused)
         e = launch_batch_reconstruct(tab, b->n, b->items_rec, b->out_type, g0.C, b->out_align, status_word(), s);
     return e;
@@ -344,6 +357,8 @@ int dp_pix_batch_autotune(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int 
             if (fusable) cands.emplace_back(DP_PIX_BATCH_PATH_STREAM_FUSED, Ss);
         }
     }
+    for (int S : {1, 2, 4, 8})
+        if (batch_tiles_smem(g0.T, g0.C, S) > 0) cands.emplace_back(DP_PIX_BATCH_PATH_TILES, S);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cfail(cudaGetLastError(), "events");
     float best = 1e30f;
@@ -385,16 +400,19 @@ int dp_pix_batch_autotune(dp_pix_batch_t b, const dp_pix_batch_image *imgs, int 
 
 int dp_pix_batch_tuning(dp_pix_batch_t b, int *seg_tiles, int *path) {
     if (!b || !seg_tiles) return bfail(DP_PIX_E_INVALID_ARG, "null argument");
-    *seg_tiles = b->rel_stream ? b->rs.S : (b->seg_tiles > 0 ? b->seg_tiles : b->geo[0].seg_tiles);
+    *seg_tiles = b->rel_stream ? b->rs.S
+                 : b->rel_tiles ? b->tiles_S
+                                : (b->seg_tiles > 0 ? b->seg_tiles : b->geo[0].seg_tiles);
     if (path)
-        *path = !b->rel_stream ? DP_PIX_BATCH_PATH_STAGED
-                               : (b->recon_fused ? DP_PIX_BATCH_PATH_STREAM_FUSED : DP_PIX_BATCH_PATH_STREAM);
+        *path = b->rel_tiles    ? DP_PIX_BATCH_PATH_TILES
+                : !b->rel_stream ? DP_PIX_BATCH_PATH_STAGED
+                                 : (b->recon_fused ? DP_PIX_BATCH_PATH_STREAM_FUSED : DP_PIX_BATCH_PATH_STREAM);
     return DP_PIX_OK;
 }
 
 int dp_pix_batch_set_path(dp_pix_batch_t b, int path, int seg_tiles) {
     if (!b) return bfail(DP_PIX_E_INVALID_ARG, "batch is NULL");
-    if (path < -1 || path > DP_PIX_BATCH_PATH_STREAM_FUSED) return bfail(DP_PIX_E_INVALID_ARG, "bad path %d", path);
+    if (path < -1 || path > DP_PIX_BATCH_PATH_TILES) return bfail(DP_PIX_E_INVALID_ARG, "bad path %d", path);
     if (seg_tiles < 0 || seg_tiles > 64) return bfail(DP_PIX_E_INVALID_ARG, "segment tiles must be 0..64");
     b->path = path;
     b->seg_tiles = seg_tiles;

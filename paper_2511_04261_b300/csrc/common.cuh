@@ -340,6 +340,10 @@ cudaError_t launch_batch_finalize(const BatchEntry *tab, uint32_t n_img, uint32_
 cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t items, int T, int C, int S,
                                  cudaStream_t s);
 size_t release_smem(int T, int C, int S);  // dynamic shared memory of the release kernels for S-tile segments
+// Whole-warps-per-tile batch release (S-tile segments sharing 8 warps); 0 smem: S does not apply.
+size_t batch_tiles_smem(int T, int C, int S);
+cudaError_t launch_batch_tiles(const BatchEntry *tab, uint32_t n_img, uint32_t items, int T, int C, int S,
+                               cudaStream_t s);
 // Streaming batch kernels (k_batch_stream.cu): classification of (image, tile row) items, and the release (with
 // the u8 reconstruction when `recon`) of (image, tile row, segment of S tiles) items.
 struct BatchStreamShape {

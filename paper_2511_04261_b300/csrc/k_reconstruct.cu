@@ -196,7 +196,8 @@ __device__ void fast_item(const uint8_t *rec, const RecGeom &rg, uint32_t rec_i,
                                    (uint64_t)(rg.M - 1) * (uint64_t)out_pitch + (uint64_t)rg.N * C * oes, status);
     else if (!kOutF32)
         seg_write_rows_pat<C>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T), orow0,
-                              out_pitch, pat, pat_stride(C), threadIdx.x, blockDim.x);
+                              out_pitch, pat, pat_stride(C), threadIdx.x, blockDim.x, obase,
+                              (uint64_t)(rg.M - 1) * (uint64_t)out_pitch + (uint64_t)rg.N * C, status);
     else
         seg_write_rows_any<C, kOutF32>(st, colinfo, stage, ns, T, min(ns * T, rg.N - x0), min(T, rg.M - ty * T),
                                        orow0, out_pitch, threadIdx.x, blockDim.x);

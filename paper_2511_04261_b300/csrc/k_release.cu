@@ -315,6 +315,52 @@ __device__ __forceinline__ void rows_sum(const uint8_t *raw, const int32_t *rowb
     }
 }
 
+// rows_sum for cells of at most 4 NWO bytes per row, straight-line: each row reads the NWO + 1 words under its
+// bytes, realigns NWO words, masks the bytes past nbytes and adds them with the channel masks of their word
+// position (the cell's first byte is channel 0).
+template <int C, int NWO>
+__device__ __forceinline__ void rows_sum_fixed(const uint8_t *raw, const int32_t *rowbase, int r0, int r1, int L0,
+                                               int nbytes, uint32_t *S) {
+    uint32_t m[NWO];
+#pragma unroll
+    for (int q = 0; q < NWO; ++q) {
+        const int keep = nbytes - 4 * q;
+        m[q] = keep >= 4 ? 0xFFFFFFFFu : (keep <= 0 ? 0u : (1u << (8 * keep)) - 1u);
+    }
+    for (int j = r0; j < r1; ++j) {
+        const int addr = rowbase[j] + L0;
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(raw + (addr & ~3));
+        const uint32_t sh = 8u * (uint32_t)(addr & 3);
+        uint32_t in[NWO + 1];
+#pragma unroll
+        for (int q = 0; q <= NWO; ++q) in[q] = w[q];
+#pragma unroll
+        for (int q = 0; q < NWO; ++q) {
+            const uint32_t x = __funnelshift_r(in[q], in[q + 1], sh) & m[q];
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) S[ch] = __dp4a(x, chan_mask<C>(q % (C == 3 ? 3 : 1), ch), S[ch]);
+        }
+    }
+}
+
+// Sums of a cell's rows, straight-line for cells of up to 32 bytes per row (cell_bytes = b C, the same for all
+// lanes of a warp), the general loop otherwise.
+template <int C>
+__device__ __forceinline__ void cell_rows_sum(const uint8_t *raw, const int32_t *rowbase, int r0, int r1, int L0,
+                                              int nbytes, int cell_bytes, uint32_t *S) {
+    switch ((cell_bytes + 3) >> 2) {
+        case 1:
+        case 2: rows_sum_fixed<C, 2>(raw, rowbase, r0, r1, L0, nbytes, S); break;
+        case 3: rows_sum_fixed<C, 3>(raw, rowbase, r0, r1, L0, nbytes, S); break;
+        case 4: rows_sum_fixed<C, 4>(raw, rowbase, r0, r1, L0, nbytes, S); break;
+        case 5: rows_sum_fixed<C, 5>(raw, rowbase, r0, r1, L0, nbytes, S); break;
+        case 6: rows_sum_fixed<C, 6>(raw, rowbase, r0, r1, L0, nbytes, S); break;
+        case 7:
+        case 8: rows_sum_fixed<C, 8>(raw, rowbase, r0, r1, L0, nbytes, S); break;
+        default: rows_sum<C>(raw, rowbase, r0, r1, L0, nbytes, S); break;
+    }
+}
+
 // Sums, noise and record of the staged item `it` (whole block).
 template <int C>
 __device__ __forceinline__ void rel_compute(const Geom &g, const CallArgs &a, const RelItem &it, uint8_t *raw) {
@@ -480,7 +526,9 @@ __device__ __forceinline__ void rel_loop(const RelSeq &seq, uint64_t *bars, int3
         if (next) prepare(nitem, buf ^ 1);
         cp_async_commit();
         cp_async_wait_1();
-        const bool ok = mbar_wait(&bars[buf], buf ? ph1 : ph0, tries);
+        // warp 0 waits for the copies; the barrier releases the other warps (which do not spin meanwhile) and
+        // orders the landed bytes before their reads
+        const bool ok = threadIdx.x < 32 ? mbar_wait(&bars[buf], buf ? ph1 : ph0, tries) : true;
         const int fail = __syncthreads_or(!ok);
         if (threadIdx.x == 0 && next) mbar_arrive(&bars[buf ^ 1]);
         if (fail) {
@@ -545,6 +593,136 @@ __global__ void __launch_bounds__(kRelThreads) k_batch_release(const BatchEntry 
         rel_prepare(bs[nb].g, bs[nb].a, 0u, item - img_lo, it[nb], dyn + nb * buf_bytes, &bars[nb]);
     };
     auto compute = [&](int nb) { rel_compute<C>(bs[nb].g, bs[nb].a, it[nb], dyn + nb * buf_bytes); };
+    rel_loop(seq, bars, tab[0].a.status, prepare, compute);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// k_batch_tiles: the batch release with whole warps per tile.  Items and their staging are k_batch_release's
+// ((image, tile row, segment of S tiles), rows by bulk copies, double-buffered); the CTA's 8 warps are dealt
+// out W = 8 / S to a tile.  The W warps of a tile take its cells in rounds of 32 W lanes, lane = (cell, row
+// part): a tile of few cells splits each cell into 2^lp row parts on adjacent lanes (added by a butterfly),
+// so that no lane searches a unit list and all lanes of a warp share one region and one cell width (the
+// straight-line row sums of cell_rows_sum apply to the whole warp).
+// ------------------------------------------------------------------------------------------------------
+constexpr int kTilesThreads = 256;  // 8 warps
+
+template <int C>
+__device__ __forceinline__ void tiles_compute(const Geom &g, const CallArgs &a, const RelItem &it, uint8_t *raw) {
+    const int T = g.T, S = g.seg_tiles;
+    const bool strict = g.pad_mode == DP_PIX_PAD_NONE;  // no padding: edge cells keep their samples in the frame
+    const int hv = strict ? min(T, g.M - it.ty * T) : T;  // rows of the item inside the frame
+    if (it.padb > 0 && !strict) {
+        // mirrored columns past the right edge, copied next to the row's last in-image byte
+        const uint8_t *fb0 = a.frames;
+        const int x0 = it.tx0 * T, pb = it.padb;
+        for (int idx = threadIdx.x; idx < T * pb; idx += blockDim.x) {
+            const int j = idx / pb, k = idx - j * pb;
+            const int px = it.xv + k / C, ch = k - (k / C) * C;
+            const int sy = reflect_idx(it.ty * T + j, g.M, g.pad_mode);
+            const int sx = reflect_idx(x0 + px, g.N, g.pad_mode);
+            raw[it.rowbase[j] + it.xv * C + k] = fb0[(int64_t)sy * g.pitch + (int64_t)sx * C + ch];
+        }
+        fence_proxy_async();  // these generic writes precede the bulk copies that later refill the buffer
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ns = it.ns;
+    const uint8_t *mapb = reinterpret_cast<const uint8_t *>(it.mapw) + it.mapoff;
+    const int W = (kTilesThreads / 32) / S;  // warps per tile
+    const int t = warp / W, wl = warp - t * W;
+    if (t >= ns) return;
+    int r = mapb[t];
+    if (r >= g.K) r = 0;
+    const int b = g.grid[r], cs = g.cells_side[r], ncell = cs * cs;
+    int lp = 0;
+    while ((ncell << (lp + 1)) <= 32 * W && (2 << lp) <= b && lp < 5) ++lp;
+    const int units = ncell << lp, rpp = (b + (1 << lp) - 1) >> lp;
+    const float inv_cs = __fdividef(1.0f, (float)cs);
+    const int tx = it.tx0 + t;
+    const int wt = strict ? max(0, min(T, g.N - tx * T)) : T;  // columns of the tile inside the frame
+    uint8_t *rec = a.records + it.tileoff[t];
+    const uint64_t frame = key_frame(a, 0);
+    const uint32_t sid = key_stream(a, 0);
+    const bool noisy = !g.noise_free && g.dtype != DP_PIX_REC_SUM_U32;
+    for (int u0 = 32 * wl; u0 < units; u0 += 32 * W) {  // warp-uniform rounds
+        const int u = u0 + lane;
+        const bool valid = u < units;
+        const int cell = u >> lp, part = u & ((1 << lp) - 1);
+        const int cy = valid ? udiv_small(cell, cs, inv_cs) : 0, cx = cell - cy * cs;
+        uint32_t Sm[4] = {0u, 0u, 0u, 0u};
+        if (valid) {
+            const int r0 = cy * b + part * rpp;
+            int r1 = min(r0 + rpp, (cy + 1) * b);
+            int nbytes = b * C;
+            if (strict) {
+                r1 = min(r1, hv);
+                nbytes = max(0, min(b, wt - cx * b)) * C;
+            }
+            if (r0 < r1 && nbytes > 0)
+                cell_rows_sum<C>(raw, it.rowbase, r0, r1, (t * T + cx * b) * C, nbytes, b * C, Sm);
+        }
+        for (int o = 1; o < (1 << lp); o <<= 1) {  // the 2^lp lanes of a cell are adjacent and aligned
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) Sm[ch] += __shfl_xor_sync(0xffffffffu, Sm[ch], o);
+        }
+        if (!valid || part != 0) continue;
+        const uint32_t cell_idx = (uint32_t)(it.ty * cs + cy) * (uint32_t)(g.GC * cs) + (uint32_t)(tx * cs + cx);
+        uint8_t *dst = rec + (uint64_t)cell * C * g.es;
+        float sigma = g.sigma_f[r], b2 = g.b2_f[r], ib2 = g.inv_b2_f[r];
+        int n = 1;
+        if (strict) {
+            // Alg. 1's partial cell: mean over its h x w samples in the frame, noise scale R m / (h w eps_r)
+            const int h = max(0, min(b, hv - cy * b));
+            const int w = max(0, min(b, wt - cx * b));
+            n = h * w;
+            if (n > 0 && n < b * b) {
+                b2 = (float)n;
+                ib2 = 0.0f;
+                sigma = __fdiv_rn(g.sigma_f[r] * g.b2_f[r], (float)n);
+            }
+        }
+        if (!chk(dst, (uint64_t)C * g.es, a.records, a.records_bytes, a.status, kChkRecord)) {
+            // bounds-checked build: a write outside the record is skipped
+        } else if (n == 0) {  // wholly outside the frame: no sample, stored as 0
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) {
+                if (g.es == 4) reinterpret_cast<uint32_t *>(dst)[ch] = 0u;
+                else dst[ch] = 0;
+            }
+        } else {
+            const uint4 words = noisy ? cell_noise_words(g.seed, cell_idx, (uint32_t)r, sid, frame)
+                                      : make_uint4(0u, 0u, 0u, 0u);
+            emit_values(g, C, dst, Sm, words, sigma, b2, ib2, nullptr);
+        }
+    }
+}
+
+template <int C>
+__global__ void __launch_bounds__(kTilesThreads, 4) k_batch_tiles(const BatchEntry *tab, uint32_t n_img,
+                                                                 uint32_t items, int buf_bytes) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ RelItem it[2];
+    __shared__ BatchShared bs[2];
+    __shared__ uint64_t bars[2];
+    const RelSeq seq(items);
+    int cur0 = -1, cur1 = -1;        // image whose geometry bs[0], bs[1] hold
+    int img = -1;                    // image of the last prepared item, owning items [img_lo, img_hi)
+    uint32_t img_lo = 0, img_hi = 0;
+    auto prepare = [&](uint32_t item, int nb) {
+        if (img < 0 || item >= img_hi) {  // items increase: the image changes at most once per chunk
+            const int i = batch_find(tab, n_img, item, 2);
+            img = i;
+            img_lo = tab[i].base[2];
+            img_hi = i + 1 < (int)n_img ? tab[i + 1].base[2] : items;
+        }
+        int &cur = nb ? cur1 : cur0;
+        if (cur != img) {
+            batch_load(tab, img, bs[nb]);
+            cur = img;
+        }
+        rel_prepare(bs[nb].g, bs[nb].a, 0u, item - img_lo, it[nb], dyn + nb * buf_bytes, &bars[nb]);
+    };
+    auto compute = [&](int nb) { tiles_compute<C>(bs[nb].g, bs[nb].a, it[nb], dyn + nb * buf_bytes); };
     rel_loop(seq, bars, tab[0].a.status, prepare, compute);
 }
 
@@ -1106,6 +1284,43 @@ cudaError_t launch_batch_release(const BatchEntry *tab, uint32_t n_img, uint32_t
         default: k_batch_release<4><<<grid_for(k_batch_release<4>, smem, items, kRelThreads), kRelThreads, smem, s>>>(tab, n_img, items, buf_bytes); break;
     }
     prof_end("k_batch_release", s);
+    return cudaGetLastError();
+}
+
+// Dynamic shared memory of the whole-warps-per-tile batch release for segments of S tiles (S divides the CTA's
+// 8 warps): two buffers of T staged rows.  0: S does not apply (not 1, 2, 4 or 8, or past 200 KB).
+size_t batch_tiles_smem(int T, int C, int S) {
+    if ((S != 1 && S != 2 && S != 4 && S != 8) || T > kTilesThreads || S > kRelSegMax) return 0;
+    const size_t smem = 2 * (size_t)T * (size_t)rel_rowstride(S, T, C);
+    return smem <= 200 * 1024 ? smem : 0;
+}
+
+cudaError_t launch_batch_tiles(const BatchEntry *tab, uint32_t n_img, uint32_t items, int T, int C, int S,
+                               cudaStream_t s) {
+    const size_t smem = batch_tiles_smem(T, C, S);
+    if (smem == 0) return cudaErrorInvalidValue;
+    const int buf_bytes = T * rel_rowstride(S, T, C);
+    const void *kern = nullptr;
+    switch (C) {
+        case 1: kern = reinterpret_cast<const void *>(k_batch_tiles<1>); break;
+        case 2: kern = reinterpret_cast<const void *>(k_batch_tiles<2>); break;
+        case 3: kern = reinterpret_cast<const void *>(k_batch_tiles<3>); break;
+        case 4: kern = reinterpret_cast<const void *>(k_batch_tiles<4>); break;
+        default: return cudaErrorInvalidValue;
+    }
+    const int per_sm = launch_prep(kern, kTilesThreads, smem);
+    const uint64_t cap = (uint64_t)per_sm * (uint64_t)sm_count();
+    const int grid = (int)(items < cap ? items : cap);
+    prof_begin("k_batch_tiles", s);
+    if (grid > 0) {
+        void *args[] = {(void *)&tab, (void *)&n_img, (void *)&items, (void *)&buf_bytes};
+        const cudaError_t e = cudaLaunchKernel(kern, dim3(grid), dim3(kTilesThreads), args, smem, s);
+        if (e != cudaSuccess) {
+            prof_end("k_batch_tiles", s);
+            return e;
+        }
+    }
+    prof_end("k_batch_tiles", s);
     return cudaGetLastError();
 }
 

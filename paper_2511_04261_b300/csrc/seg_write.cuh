@@ -399,11 +399,14 @@ __device__ __forceinline__ uint4 window16(const uint4 &lo, const uint4 &hi, int 
 // Writes the jmax u8 output rows (vpx pixels each, first output byte orow0, any alignment) of a segment whose
 // cell values are staged (packed u8) and whose row groups seg_row_groups marked.  pat: two pattern buffers,
 // pat_stride bytes apart, each of at least 16 * (ceil(vpx C / 16) + 1) bytes (16-byte aligned).  Threads
-// tid = 0..nthr-1 of the group share the work; one barrier per row group.
+// tid = 0..nthr-1 of the group share the work; one barrier per row group.  In the bounds-checked build every
+// store must fall inside the image [img, img + img_bytes) when img is given.
 template <int C>
 __device__ void seg_write_rows_pat(SegTiles &st, const uint32_t *colinfo, const uint8_t *stage, int ns, int T,
                                    int vpx, int jmax, uint8_t *orow0, int64_t out_pitch, uint8_t *pat, int pat_stride,
-                                   int tid, int nthr) {
+                                   int tid, int nthr, const uint8_t *img = nullptr, uint64_t img_bytes = 0,
+                                   int32_t *status = nullptr) {
+    auto ok = [&](const uint8_t *p, int n) { return img == nullptr || chk(p, n, img, img_bytes, status, kChkOutput); };
     constexpr int NPX = FastK<C>::NPX8;
     const int row_bytes = vpx * C;
     const int nch = (row_bytes + 15) >> 4;
@@ -444,10 +447,12 @@ __device__ void seg_write_rows_pat(SegTiles &st, const uint32_t *colinfo, const 
             if (k < nfull) {
                 const uint4 lo = *reinterpret_cast<const uint4 *>(P + 16 * k);
                 const uint4 hi = *reinterpret_cast<const uint4 *>(P + 16 * k + 16);
-                *reinterpret_cast<uint4 *>(row + h + 16 * k) = window16(lo, hi, h);
+                if (ok(row + h + 16 * k, 16)) *reinterpret_cast<uint4 *>(row + h + 16 * k) = window16(lo, hi, h);
             } else if (k == nch) {
-                for (int i = 0; i < h; ++i) row[i] = P[i];
-                for (int i = h + 16 * nfull; i < row_bytes; ++i) row[i] = P[i];
+                for (int i = 0; i < h; ++i)
+                    if (ok(row + i, 1)) row[i] = P[i];
+                for (int i = h + 16 * nfull; i < row_bytes; ++i)
+                    if (ok(row + i, 1)) row[i] = P[i];
             }
         }
         buf ^= 1;  // the next group builds into the other buffer; the barrier above already ordered this one

@@ -134,8 +134,9 @@ def test_batch_config3_shapes_sampled():
 
 @pytest.mark.parametrize("source", [O.SRC_MATTE, O.SRC_MASK])
 def test_batch_release_paths_give_the_same_bytes(source):
-    """The staged path, the streaming path and the streaming path with the images written in the same launch
-    (DP_PIX_BATCH_PATH_*) at several segment widths write byte-identical records and images."""
+    """The staged path, the whole-warps-per-tile path, the streaming path and the streaming path with the images
+    written in the same launch (DP_PIX_BATCH_PATH_*) at several segment widths write byte-identical records and
+    images."""
     sizes = [(517, 1003), (64, 75), (300, 241), (1200, 700)]
     imgs, mattes = _portraits(sizes, 77)
     srcs = mattes if source == O.SRC_MATTE else [(m < 0.5).astype(np.uint8) for m in mattes]
@@ -148,7 +149,8 @@ def test_batch_release_paths_give_the_same_bytes(source):
             frame_idx=[100 + i for i in range(4)])
     ref = None
     for path, seg in [(P.BATCH_PATH_STAGED, 2), (P.BATCH_PATH_STREAM, 0), (P.BATCH_PATH_STREAM_FUSED, 0),
-                      (P.BATCH_PATH_STREAM, 5), (P.BATCH_PATH_STREAM_FUSED, 3)]:
+                      (P.BATCH_PATH_STREAM, 5), (P.BATCH_PATH_STREAM_FUSED, 3), (P.BATCH_PATH_TILES, 0),
+                      (P.BATCH_PATH_TILES, 1), (P.BATCH_PATH_TILES, 4), (P.BATCH_PATH_TILES, 8)]:
         for o in outs:
             o.fill_(7)
         bp.set_path(path, seg)

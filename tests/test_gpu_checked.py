@@ -57,7 +57,7 @@ def _body():
     sizes = [(301, 517), (130, 250)]
     pimgs, mattes = zip(*[synth.portrait(rng, a, b) for a, b in sizes])
     kb = dict(C=3, grids=[6, 20], eps=[0.5, 1.5], R=255.0, m=32.0, seed=3)
-    for path in (P.BATCH_PATH_STAGED, P.BATCH_PATH_STREAM_FUSED):
+    for path in (P.BATCH_PATH_STAGED, P.BATCH_PATH_STREAM_FUSED, P.BATCH_PATH_TILES):
         bp = P.BatchPlan(sizes, source=P.SRC_MATTE_F32, dtype=P.REC_F32, **kb)
         brecs = bp.alloc_records()
         outs = [torch.zeros((a, b, 3), dtype=torch.uint8, device="cuda") for a, b in sizes]

@@ -69,7 +69,10 @@ def test_strict_release_matte():
     compare_records(recs[0], rec, means, sums, etas, O.DT_F32)
 
 
-def test_strict_ragged_batch_matches_oracle():
+@pytest.mark.parametrize("path", [-1, 0, 3])
+def test_strict_ragged_batch_matches_oracle(path):
+    """Alg. 1's partial edge cells in a ragged batch, on the default release path, the staged path and the
+    whole-warps-per-tile path (DP_PIX_BATCH_PATH_STAGED / _TILES = 0 / 3)."""
     sizes = [(181, 251), (64, 60), (7, 130), (300, 119)]
     rng = np.random.default_rng(12)
     imgs, mattes = zip(*[synth.portrait(rng, M, N) for M, N in sizes])
@@ -79,6 +82,7 @@ def test_strict_ragged_batch_matches_oracle():
     srcs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in mattes]
     recs, ws = bp.alloc_records(), bp.alloc_workspace()
     outs = [torch.empty((M, N, 3), dtype=torch.uint8, device="cuda") for M, N in sizes]
+    bp.set_path(path)
     bp.bind(frames, srcs, recs, ws, outs=outs, stream_ids=[2] * len(sizes), frame_idx=list(range(len(sizes))))
     bp.run(use_graph=False)
     torch.cuda.synchronize()
