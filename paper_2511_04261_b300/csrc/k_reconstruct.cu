@@ -28,7 +28,7 @@ __host__ __device__ constexpr int pat_stride(int C) { return 16 * (kMaxSegPx * C
 
 // Dynamic shared memory of the fast path: stage | colinfo | two row patterns (u8 rows of any alignment).
 __host__ __device__ constexpr size_t fast_smem(int out_f32, int fast_c, int out_align) {
-    return (size_t)kStageBytes + kMaxSegPx * 4 +
+    return (size_t)kStageBytes + colinfo_words(kMaxSegPx) * 4 +
            (!out_f32 && fast_c > 0 && out_align != 16 ? 2 * (size_t)pat_stride(fast_c) : 0);
 }
 
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kThreads)
     constexpr int oes = kOutF32 ? 4 : 1;
     uint8_t *stage = dyn;
     uint32_t *colinfo = reinterpret_cast<uint32_t *>(dyn + kStageBytes);
-    uint8_t *pat = dyn + kStageBytes + kMaxSegPx * 4;
+    uint8_t *pat = dyn + kStageBytes + colinfo_words(kMaxSegPx) * 4;
     const uint32_t G = gridDim.x;
     const uint32_t per_rec = n <= G ? G / n : 1u;  // CTAs per record
     const uint32_t slots = n <= G ? n : G;         // records handled concurrently
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(kThreads)
     constexpr int oes = kOutF32 ? 4 : 1;
     uint8_t *stage = dyn;
     uint32_t *colinfo = reinterpret_cast<uint32_t *>(dyn + kStageBytes);
-    uint8_t *pat = dyn + kStageBytes + kMaxSegPx * 4;
+    uint8_t *pat = dyn + kStageBytes + colinfo_words(kMaxSegPx) * 4;
     // chunks of q consecutive tile rows dealt round-robin; a CTA parses a header only when its image changes
     const uint32_t share = (items + gridDim.x - 1) / gridDim.x;
     const uint32_t q = share < kRecChunk ? (share ? share : 1u) : kRecChunk;

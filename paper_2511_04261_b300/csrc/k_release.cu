@@ -1400,7 +1400,7 @@ cudaError_t launch_emit_recon(const Geom &g, const CallArgs &a, uint8_t *out, in
         fs.gseg_bytes = (seg * gtb + 15) / 16 * 16;
         fs.stage_off = gcs * fs.gseg_bytes;
         fs.colinfo_off = fs.stage_off + (seg * csmax * csmax * vb + 15) / 16 * 16;
-        fs.smem = fs.colinfo_off + seg * g.T * 4;
+        fs.smem = fs.colinfo_off + (colinfo_words(seg * g.T) * 4 + 15) / 16 * 16;
         if (fs.smem <= 64 * 1024) break;
     }
     if (seg < sm) return cudaErrorNotSupported;

@@ -14,6 +14,11 @@ namespace dppix {
 constexpr int kSegMaxTiles = 64;    // tiles of one segment
 constexpr int kSegMaxPx = 2048;     // pixel columns of one segment
 
+// The pixel-column map (colinfo) keeps entry i at word i + i / 32: the row writers' lanes read it at strides of
+// 16 / C entries (one 16-byte chunk each), which without the gap every 32 words would pile up in a few banks.
+__host__ __device__ constexpr int colinfo_words(int n) { return n + (n + 31) / 32; }
+__device__ __forceinline__ int cix(int i) { return i + (i >> 5); }
+
 __device__ __forceinline__ uint32_t to_u8(float v) { return __float2uint_rn(fminf(fmaxf(v, 0.0f), 255.0f)); }
 
 struct SegTiles {
@@ -133,7 +138,7 @@ __device__ __forceinline__ void seg_prefix_colinfo(SegTiles &st, int ns, int T, 
     for (int px = tid; px < ns * T; px += nthr) {
         const int t = tp2 ? px >> lt : px / T;
         const int b = st.b[t], pt = px - t * T;
-        colinfo[px] = ((uint32_t)t << 16) | (uint32_t)((b & (b - 1)) == 0 ? pt >> (__ffs(b) - 1) : pt / b);
+        colinfo[cix(px)] = ((uint32_t)t << 16) | (uint32_t)((b & (b - 1)) == 0 ? pt >> (__ffs(b) - 1) : pt / b);
     }
 }
 
@@ -181,14 +186,14 @@ __device__ void seg_write_rows(const SegTiles &st, const uint32_t *colinfo, cons
         // the chunk's real pixels lie in at most two tiles (a tile row has >= 16 bytes); trailing entries past
         // them are never used by the vector builder and are pointed at the last real pixel
         const int lastp = min((e0 + kElems - 1) / C, last_px);
-        const uint32_t cl = colinfo[lastp];
-        const int tA = colinfo[min(l0, last_px)] >> 16;
+        const uint32_t cl = colinfo[cix(lastp)];
+        const int tA = colinfo[cix(min(l0, last_px))] >> 16;
         const int tB = cl >> 16;
         int cc[NPX];
         bool inB[NPX];
 #pragma unroll
         for (int l = 0; l < NPX; ++l) {
-            const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
+            const uint32_t v = l0 + l <= lastp ? colinfo[cix(l0 + l)] : cl;
             cc[l] = (int)(v & 0xFFFFu);
             inB[l] = (int)(v >> 16) != tA;
         }
@@ -288,8 +293,8 @@ __device__ void seg_write_rows_any(const SegTiles &st, const uint32_t *colinfo, 
         const int p = e0 % C;
         const int l0 = e0 / C;
         const int lastp = min((e0 + kElems - 1) / C, last_px);
-        const uint32_t cl = colinfo[lastp];
-        const int tA = colinfo[min(l0, last_px)] >> 16;
+        const uint32_t cl = colinfo[cix(lastp)];
+        const int tA = colinfo[cix(min(l0, last_px))] >> 16;
         const int tB = cl >> 16;
         const int baseA = st.base[tA] + (j / st.b[tA]) * st.cs[tA];
         const int baseB = st.base[tB] + (j / st.b[tB]) * st.cs[tB];
@@ -298,7 +303,7 @@ __device__ void seg_write_rows_any(const SegTiles &st, const uint32_t *colinfo, 
             float4 pv[NPX];
 #pragma unroll
             for (int l = 0; l < NPX; ++l) {
-                const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
+                const uint32_t v = l0 + l <= lastp ? colinfo[cix(l0 + l)] : cl;
                 const int idx = ((int)(v >> 16) != tA ? baseB : baseA) + (int)(v & 0xFFFFu);
                 pv[l] = reinterpret_cast<const float4 *>(stage)[idx];
             }
@@ -307,7 +312,7 @@ __device__ void seg_write_rows_any(const SegTiles &st, const uint32_t *colinfo, 
             uint32_t pv[NPX];
 #pragma unroll
             for (int l = 0; l < NPX; ++l) {
-                const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
+                const uint32_t v = l0 + l <= lastp ? colinfo[cix(l0 + l)] : cl;
                 const int idx = ((int)(v >> 16) != tA ? baseB : baseA) + (int)(v & 0xFFFFu);
                 pv[l] = reinterpret_cast<const uint32_t *>(stage)[idx];
             }
@@ -328,7 +333,7 @@ __device__ void seg_write_rows_any(const SegTiles &st, const uint32_t *colinfo, 
         else if (i - nh < nt) e = tail0 / oes + (i - nh);
         else continue;
         const int px = e / C, ch = e - px * C;
-        const uint32_t v = colinfo[px];
+        const uint32_t v = colinfo[cix(px)];
         const int t = (int)(v >> 16);
         const int idx = st.base[t] + (j / st.b[t]) * st.cs[t] + (int)(v & 0xFFFFu);
         if (kOutF32) {
@@ -425,13 +430,13 @@ __device__ void seg_write_rows_pat(SegTiles &st, const uint32_t *colinfo, const 
             const int e0 = k << 4;
             const int p = e0 % C, l0 = e0 / C;
             const int lastp = min((e0 + 15) / C, last_px);
-            const uint32_t cl = colinfo[lastp];
-            const int tA = colinfo[min(l0, last_px)] >> 16, tB = cl >> 16;
+            const uint32_t cl = colinfo[cix(lastp)];
+            const int tA = colinfo[cix(min(l0, last_px))] >> 16, tB = cl >> 16;
             const int baseA = gb[tA], baseB = gb[tB];
             uint32_t pv[NPX];
 #pragma unroll
             for (int l = 0; l < NPX; ++l) {
-                const uint32_t v = l0 + l <= lastp ? colinfo[l0 + l] : cl;
+                const uint32_t v = l0 + l <= lastp ? colinfo[cix(l0 + l)] : cl;
                 pv[l] = stage32[((int)(v >> 16) != tA ? baseB : baseA) + (int)(v & 0xFFFFu)];
             }
             *reinterpret_cast<uint4 *>(P + 16 * k) = build_u8_phase<C>(p, pv);
