@@ -166,3 +166,42 @@ def test_batch_release_paths_give_the_same_bytes(source):
             assert got[0] == ref[0], (path, seg)
             for a, b in zip(got[1], ref[1]):
                 assert np.array_equal(a, b), (path, seg)
+
+
+@pytest.mark.parametrize("C,grids", [(1, (64, 128)), (2, (2, 3)), (4, (5, 7)), (3, (1, 4)), (1, (3, 8))])
+def test_batch_tiles_path_other_channels_and_tile_sizes(C, grids):
+    """The whole-warps-per-tile release (the default) against the staged one and the oracle, for C = 1, 2, 4
+    and tiles from T = 6 (cells of 2 and 3 px, many per tile) to T = 128 (one cell of 128 px: the cell split
+    into row parts over whole warps) and T = 4 with b = 1 (cells of one pixel): exact u32 sums in the record."""
+    T = math.lcm(*grids)
+    sizes = [(2 * T + 3, 3 * T + 1), (T, T), (T + 1, 5 * T - 2), (T // 2 + 1, 2 * T + 5)]
+    rng = np.random.default_rng(C * 1000 + T)
+    imgs = [rng.integers(0, 256, size=(M, N, C), dtype=np.uint8) for (M, N) in sizes]
+    labels = [rng.integers(0, 2, size=(-(-M // T), -(-N // T)), dtype=np.uint8) for (M, N) in sizes]
+    kw = dict(C=C, grids=list(grids), eps=[0.5, 1.5], R=255.0, m=32.0, seed=3)
+    bp = P.BatchPlan(sizes, source=O.SRC_TILE_LABELS, dtype=O.DT_SUM, **kw)
+    frames = [torch.from_numpy(np.ascontiguousarray(im)).cuda() for im in imgs]
+    src_t = [torch.from_numpy(lab).cuda() for lab in labels]
+    recs = bp.alloc_records()
+    outs = [torch.zeros((M, N, C), dtype=torch.uint8, device="cuda") for (M, N) in sizes]
+    bp.bind(frames, src_t, recs, bp.alloc_workspace(), outs=outs, stream_ids=[9] * len(sizes),
+            frame_idx=list(range(len(sizes))))
+    ref = None
+    # 8 tiles per item stage 2 T rows of 8 T C bytes: past the CTA's shared memory at T = 128
+    for path, seg in [(P.BATCH_PATH_STAGED, 1), (P.BATCH_PATH_TILES, 1), (P.BATCH_PATH_TILES, 2),
+                      (P.BATCH_PATH_TILES, 4 if T > 64 else 8)]:
+        bp.set_path(path, seg)
+        assert bp.tuning()[1] == path
+        bp.run(use_graph=False)
+        torch.cuda.synchronize()
+        assert P.dp_pix_status() == 0
+        got = [P.dp_pix_store(r) for r in recs]
+        if ref is None:
+            ref = got
+            for i, (M, N) in enumerate(sizes):
+                rec, means, sums, etas = O.release(imgs[i], labels[i], M=M, N=N, source=O.SRC_TILE_LABELS,
+                                                   dtype=O.DT_SUM, stream_id=9, frame_idx=i, **kw)
+                compare_records(got[i], rec, means, sums, etas, O.DT_SUM)
+                assert np.array_equal(outs[i].cpu().numpy(), O.reconstruct(np.frombuffer(got[i], np.uint8), 0))
+        else:
+            assert got == ref, (path, seg)

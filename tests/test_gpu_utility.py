@@ -1,6 +1,9 @@
 """Parity of the utility metrics and the Sobel edge mask (dp_pix_utility, dp_pix_sobel_mask) with the
-oracle: masks and squared-error sums bit-exact, SSIM within 1e-5 absolute (each window's value is rounded
-once in fp32 from exact integer sums; the oracle evaluates it in fp64)."""
+oracle: masks and squared-error sums bit-exact; SSIM within 1e-6 of max(|SSIM|, 0.01).  The GPU rounds each
+window's value once in fp32 from exact integer sums (a few units of 2^-24 relative to that window's value)
+and adds the values in fp32 per thread, fp64 across threads; the oracle evaluates everything in fp64.  The
+bound leaves a margin of more than 10 over the largest error measured on these cases (6e-8 at SSIM 0.97,
+5.5e-10 at SSIM 0.0056), and at the near-zero SSIM of a fine pixelization it is relative, not absolute."""
 import numpy as np
 import pytest
 import torch
@@ -12,7 +15,8 @@ from paper_2511_04261_b300 import synth
 
 pytestmark = pytest.mark.gpu
 
-SSIM_TOL = 1e-5
+def ssim_tol(ref):
+    return 1e-6 * max(abs(ref), 0.01)
 
 
 @pytest.mark.parametrize("M,N,C", [(70, 300, 3), (33, 257, 1), (40, 50, 4), (2, 2, 2), (97, 513, 3)])
@@ -49,7 +53,8 @@ def test_utility_matches_oracle(M, N, C):
         assert vals[i]["sse"] == U.sse(x[i], y[i])
         assert vals[i]["mse"] == U.mse(x[i], y[i])
         assert vals[i]["windows"] == (M - 6) * (N - 6)
-        assert abs(vals[i]["ssim"] - U.ssim(x[i], y[i])) <= SSIM_TOL
+        ref = U.ssim(x[i], y[i])
+        assert abs(vals[i]["ssim"] - ref) <= ssim_tol(ref)
 
 
 def test_utility_identical_images_and_strided_inputs():
@@ -81,7 +86,26 @@ def test_sobel_mask_drives_a_mask_release():
     v = P.utility_values(P.dp_pix_utility(ft, out[0]))[0]
     assert v["sse"] == U.sse(f, rec_img)
     sub = P.utility_values(P.dp_pix_utility(ft[:96, :128], out[0][:96, :128]))[0]
-    assert abs(sub["ssim"] - U.ssim(f[:96, :128], rec_img[:96, :128])) <= SSIM_TOL
+    ref = U.ssim(f[:96, :128], rec_img[:96, :128])
+    assert abs(sub["ssim"] - ref) <= ssim_tol(ref)
+
+
+@pytest.mark.parametrize("b", [2, 4, 16])
+def test_ssim_of_fine_pixelizations_near_zero(b):
+    """The paper's utility sweep (Sec. VII-A) reaches SSIM of a few thousandths at b = 2: compare there with a
+    relative bound, on the full 768 x 576 frame of a uniform release."""
+    f, _ = synth.rect_frame(seed=1001)
+    ft = torch.from_numpy(f).cuda()
+    plan = P.Plan(M=576, N=768, C=3, grids=[b], eps=[0.5], m=16.0, source=P.SRC_TILE_LABELS, seed=1)
+    lab = torch.zeros((1, -(-576 // b), -(-768 // b)), dtype=torch.uint8, device="cuda")
+    _, out = plan.release_reconstruct(ft[None], lab)
+    o = out[0].cpu().numpy()
+    v = P.utility_values(P.dp_pix_utility(ft, out[0]))[0]
+    assert v["sse"] == U.sse(f, o)
+    ref = U.ssim(f, o)
+    if b == 2:
+        assert ref < 0.01  # the near-zero regime the relative bound is for
+    assert abs(v["ssim"] - ref) <= ssim_tol(ref)
 
 
 def test_utility_and_sobel_reject_bad_arguments():
