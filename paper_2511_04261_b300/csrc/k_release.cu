@@ -201,9 +201,12 @@ __device__ __forceinline__ int udiv_small(int x, int d, float inv) {
 // Issues one bulk copy per row j < T of image rows ty*T + j (mirrored past M) of `base` (rows `pitch` bytes
 // apart), bytes [0, vb) of each, as the aligned 16-byte granules that hold them, into raw + j * rs;
 // rowbase[j] receives the staged position of byte 0.  Thread j copies row j: the warps with warp*32 < T
-// call this (whole warps).  Each warp announces its rows' bytes to the mbarrier before copying.
+// call this (whole warps).  Each warp announces its rows' bytes to the mbarrier before copying.  In the
+// bounds-checked build a row whose bytes leave [ext, ext + ext_bytes) is not copied (and raises the error).
 __device__ __forceinline__ void stage_rows(const uint8_t *base, int64_t pitch, int M, int pad_mode, int ty, int T, int vb,
-                                           int rs, uint8_t *raw, int32_t *rowbase, uint64_t *bar) {
+                                           int rs, uint8_t *raw, int32_t *rowbase, uint64_t *bar,
+                                           const uint8_t *ext = nullptr, uint64_t ext_bytes = 0,
+                                           int32_t *status = nullptr) {
     const int j = threadIdx.x, lane = threadIdx.x & 31;
     uint32_t bytes = 0;
     const uint8_t *ga = nullptr;
@@ -212,13 +215,15 @@ __device__ __forceinline__ void stage_rows(const uint8_t *base, int64_t pitch, i
         const uintptr_t addr = reinterpret_cast<uintptr_t>(base + (int64_t)sy * pitch);
         const int o = (int)(addr & 15u);
         ga = reinterpret_cast<const uint8_t *>(addr - (uintptr_t)o);
-        bytes = 16u * (uint32_t)((o + vb + 15) >> 4);
+        const bool in = ext == nullptr ||
+                        chk(reinterpret_cast<const uint8_t *>(addr), (uint64_t)vb, ext, ext_bytes, status, kChkFrame);
+        bytes = in ? 16u * (uint32_t)((o + vb + 15) >> 4) : 0u;
         rowbase[j] = j * rs + o;
     }
     const uint32_t wsum = __reduce_add_sync(0xffffffffu, bytes);
     if (lane == 0) mbar_expect_tx(bar, wsum);
     __syncwarp();
-    if (j < T) bulk_g2s(raw + j * rs, ga, bytes, bar);
+    if (j < T && bytes > 0) bulk_g2s(raw + j * rs, ga, bytes, bar);
 }
 
 // Prepares item (f, ty, sg) into `it` and issues the copies of its map bytes, payload offsets and rows
@@ -255,7 +260,7 @@ __device__ __forceinline__ void rel_prepare(const Geom &g, const CallArgs &a, ui
     }
     if (warp * 32 < T)
         stage_rows(a.frames + (uint64_t)f * (uint64_t)a.frame_stride + (int64_t)x0 * C, g.pitch, g.M, g.pad_mode, ty, T,
-                   xv * C, rs, raw, it.rowbase, bar);
+                   xv * C, rs, raw, it.rowbase, bar, a.frames, a.frames_bytes, a.status);
 }
 
 // dp4a mask of channel ch for a word whose first byte is byte 4k of a cell row (C interleaved channels).
@@ -376,7 +381,8 @@ __device__ __forceinline__ void rel_compute(const Geom &g, const CallArgs &a, co
             const int px = it.xv + k / C, ch = k - (k / C) * C;
             const int sy = reflect_idx(it.ty * T + j, g.M, g.pad_mode);
             const int sx = reflect_idx(x0 + px, g.N, g.pad_mode);
-            raw[it.rowbase[j] + it.xv * C + k] = fb0[(int64_t)sy * g.pitch + (int64_t)sx * C + ch];
+            const uint8_t *src = fb0 + (int64_t)sy * g.pitch + (int64_t)sx * C + ch;
+            if (chk(src, 1, a.frames, a.frames_bytes, a.status, kChkFrame)) raw[it.rowbase[j] + it.xv * C + k] = *src;
         }
         fence_proxy_async();  // these generic writes precede the bulk copies that later refill the buffer
         __syncthreads();
@@ -620,7 +626,8 @@ __device__ __forceinline__ void tiles_compute(const Geom &g, const CallArgs &a, 
             const int px = it.xv + k / C, ch = k - (k / C) * C;
             const int sy = reflect_idx(it.ty * T + j, g.M, g.pad_mode);
             const int sx = reflect_idx(x0 + px, g.N, g.pad_mode);
-            raw[it.rowbase[j] + it.xv * C + k] = fb0[(int64_t)sy * g.pitch + (int64_t)sx * C + ch];
+            const uint8_t *src = fb0 + (int64_t)sy * g.pitch + (int64_t)sx * C + ch;
+            if (chk(src, 1, a.frames, a.frames_bytes, a.status, kChkFrame)) raw[it.rowbase[j] + it.xv * C + k] = *src;
         }
         fence_proxy_async();  // these generic writes precede the bulk copies that later refill the buffer
         __syncthreads();
