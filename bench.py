@@ -250,8 +250,9 @@ def moved_bytes(plan, payload_bytes):
 
 
 def traffic_from_profile(kernel, workload=None):
-    """dram bytes per launch from the committed ncu summary of this kernel on this workload, if the kernel
-    source has not changed since the capture (the summary records the source's sha256)."""
+    """dram bytes per launch from the committed ncu summary of this kernel on this workload, if none of the
+    kernel's sources has changed since the capture: the summary lists them (source_files, comma-separated)
+    with the sha256 of their bytes concatenated in that order (sources_sha256)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload or WORKLOAD))
     if not os.path.exists(path):
@@ -262,16 +263,18 @@ def traffic_from_profile(kernel, workload=None):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    src = vals.get("source_file")
-    sha = vals.get("source_sha256")
+    srcs = [x.strip() for x in vals.get("source_files", "").split(",") if x.strip()]
+    sha = vals.get("sources_sha256")
     tr = vals.get("dram_bytes_per_launch_full_workload")
-    if not (src and sha and tr):
+    if not (srcs and sha and tr):
         return None
+    h = hashlib.sha256()
     try:
-        cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+        for src in srcs:
+            h.update(open(os.path.join(ROOT, src), "rb").read())
     except OSError:
         return None
-    return int(float(tr)) if cur == sha else None
+    return int(float(tr)) if h.hexdigest() == sha else None
 
 
 # ------------------------------------------------------------------------------------------------------

@@ -261,18 +261,21 @@ __device__ __forceinline__ float noisy_mean(uint32_t S, float b2, float inv_b2, 
 // Noise, clip and store of one cell's C channels (Alg. 3 steps 9-10 and 15-17) from its Philox words;
 // sigma, b^2 and 1/b^2 (0 when not exact) of its region.  ov (optional) receives the value a
 // reconstruction reads back from the stored element (Sec. VI-F).
-__device__ __forceinline__ void emit_values(const Geom &g, int C, uint8_t *dst, const uint32_t *S, uint4 words,
-                                            float sigma, float b2, float inv_b2, float *ov) {
+// emit_values with the plan's record type, noise switch and clip bound passed as values (callers whose Geom
+// sits in shared memory keep them in registers across the record stores).
+__device__ __forceinline__ void emit_values_s(int dtype, bool noise_free, float R_f, int C, uint8_t *dst,
+                                              const uint32_t *S, uint4 words, float sigma, float b2, float inv_b2,
+                                              float *ov) {
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
         if (ch >= C) break;
-        if (g.dtype == DP_PIX_REC_SUM_U32) {
+        if (dtype == DP_PIX_REC_SUM_U32) {
             reinterpret_cast<uint32_t *>(dst)[ch] = S[ch];
             if (ov) ov[ch] = __fdiv_rn(__uint2float_rn(S[ch]), b2);
         } else {
-            const float eta = g.noise_free ? 0.0f : laplace_from_word(word_of(words, ch), sigma);
-            const float v = noisy_mean(S[ch], b2, inv_b2, eta, g.R_f);
-            if (g.dtype == DP_PIX_REC_F32) {
+            const float eta = noise_free ? 0.0f : laplace_from_word(word_of(words, ch), sigma);
+            const float v = noisy_mean(S[ch], b2, inv_b2, eta, R_f);
+            if (dtype == DP_PIX_REC_F32) {
                 reinterpret_cast<float *>(dst)[ch] = v;
                 if (ov) ov[ch] = v;
             } else {
@@ -282,6 +285,11 @@ __device__ __forceinline__ void emit_values(const Geom &g, int C, uint8_t *dst, 
             }
         }
     }
+}
+
+__device__ __forceinline__ void emit_values(const Geom &g, int C, uint8_t *dst, const uint32_t *S, uint4 words,
+                                            float sigma, float b2, float inv_b2, float *ov) {
+    emit_values_s(g.dtype, g.noise_free != 0, g.R_f, C, dst, S, words, sigma, b2, inv_b2, ov);
 }
 
 // Mirror padding by index: padded index p >= n maps back into [0, n) (Alg. 2 step 4).  Without padding
