@@ -926,13 +926,15 @@ def run_utility(args):
         P.dp_pix_sobel_mask(x, UTILITY["tau"], out=masks)
         P.dp_pix_utility(x, y, out=ubuf)
 
+    step()
+    torch.cuda.synchronize()
+    # the W warm-up steps follow the clock sampler's start-up pause, right before the timed steps
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
     for _ in range(args.warmup):
         step()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(torch.cuda.current_device())
     barrier(world)
     torch.cuda.synchronize()
-    sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
@@ -1129,8 +1131,7 @@ def run_soft(args):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
             step()
-        for _ in range(args.warmup):
-            graph.replay()
+        graph.replay()
         torch.cuda.synchronize()
     except Exception as exc:  # capture refused: time the direct calls
         graph, graph_note = None, "direct calls (graph capture failed: %s)" % type(exc).__name__
@@ -1145,10 +1146,13 @@ def run_soft(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / n
 
+    # the W warm-up steps follow the clock sampler's start-up pause, right before the timed steps
     sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    for _ in range(args.warmup):
+        run()
     barrier(world)
     torch.cuda.synchronize()
-    sampler.start()
     ms_step = timed(run, args.steps)
     barrier(world)
     clocks = sampler.stop()
